@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Benchmark of the per-tile heightmap build on B300.
+
+One step = one pass of the whole hot path over the batched region workload
+(16 x 16 tiles of 640 m, per-tile density lognormal(ln 4, 0.8) pts/m^2, ~578M
+points): exact binning at 640x640 and 64x64 cells, chunk-point extraction,
+Gaussian fill of every tile's 64x64 height + RGB map, and the full-resolution tile
+update.  The step is captured once in a CUDA graph and replayed; the inputs
+(~10 GB of points) are larger than L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs its own replica on its own GPU (tiles are
+independent: weak scaling) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "heightmap tiles/s (plain vs learned fill), full-res points binned/s, % HBM peak"
+WORKLOAD = "batched-region 16x16 tiles x 640 m, lognormal(ln4,0.8) pts/m^2, bin 640^2+64^2, extract, gaussian fill 64^2, tile update"
+SEED = 2
+BIN_SRC = os.path.join(ROOT, "paper_2509_20198_b300", "csrc", "ls_bin.cu")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def bin_traffic_per_point():
+    """DRAM bytes per launch of k_bin_main from the committed ncu summary, scaled per
+    point, or None when the summary is absent or the kernel source changed since."""
+    p = os.path.join(ROOT, "profiles", "k_bin_main_batched_region.txt")
+    if not os.path.exists(p):
+        return None
+    src_hash = hashlib.sha256(open(BIN_SRC, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(p):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("ls_bin.cu sha256[:16]") != src_hash:
+        return None
+    try:
+        return float(vals["dram bytes per point (read+write)"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------------------------
+# the B300 path
+# ------------------------------------------------------------------------------------
+
+class Step:
+    """Pre-allocated buffers and the ordered library calls of one step."""
+
+    def __init__(self, lsb, region, counts, pts, stream):
+        import torch
+        self.lsb, self.region, self.counts, self.pts, self.stream = lsb, region, counts, pts, stream
+        T = region.n_tiles
+        dev = pts["x"].device
+        self.bins = [lsb.empty_bins(T, 640, dev), lsb.empty_bins(T, 64, dev)]
+        self.dropped = torch.zeros(1, dtype=torch.int64, device=dev)
+        cap = pts["x"].numel() // 50000 + T
+        self.samples = {k: torch.empty(cap, dtype=pts[k].dtype, device=dev) for k in "xyzrgb"}
+        self.samples["tile_offsets"] = torch.empty(T + 1, dtype=torch.int64, device=dev)
+        self.cap = cap
+        self.height = torch.empty((T, 64, 64), dtype=torch.float32, device=dev)
+        self.rgb = torch.empty((T, 64, 64, 3), dtype=torch.uint8, device=dev)
+        self.launches = 3 + 2 + 2 + 1
+
+    def run(self):
+        lsb = self.lsb
+        lsb.bin_points(self.pts, self.region, levels=(640, 64), out=self.bins, dropped=self.dropped,
+                       stream=self.stream)
+        lsb.extract_samples_into(self.pts, self.samples, self.cap, stream=self.stream)
+        lsb.fill_sparse(self.samples, self.region, height=self.height, rgb=self.rgb, stream=self.stream)
+        lsb.update_tile(self.bins[1], self.region, None, self.height, self.rgb, stream=self.stream)
+
+
+def run_b300(args, rank, world):
+    import torch
+    import paper_2509_20198_b300 as lsb
+    import synth
+    import synth.gpu as sg
+    from paper_2509_20198_b300 import build
+
+    build.build_library()
+    build.build_synth()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    region, counts = synth.batched_region_workload(seed=SEED)
+    n_points = int(counts.sum())
+    T = region.n_tiles
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        pts = sg.region_points(SEED + 1000 * rank, region, counts, device=dev, stream=stream)
+    stream.synchronize()
+    step = Step(lsb, region, counts, pts, stream)
+    # warm-up outside the graph (allocates the library workspace), then capture
+    with torch.cuda.stream(stream):
+        step.run()
+    stream.synchronize()
+    assert lsb.last_error() == 0
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        step.run()
+    for _ in range(args.warmup):
+        graph.replay()
+    stream.synchronize()
+
+    # ---- device-timed region
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+    bin_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clocks:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(args.steps):
+            graph.replay()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        # binning alone (its own timing pass, same stream, not graph-fused with the rest)
+        for k in range(args.steps):
+            bin_ev[2 * k].record(stream)
+            lsb.bin_points(pts, region, levels=(640, 64), out=step.bins, dropped=step.dropped, stream=stream)
+            bin_ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms_total = t0.elapsed_time(t1)
+    ms_bin = float(np.mean([bin_ev[2 * k].elapsed_time(bin_ev[2 * k + 1]) for k in range(args.steps)]))
+    assert lsb.last_error() == 0
+    ms_step = ms_total / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step, ms_bin], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step, ms_bin = float(t[0]), float(t[1])
+
+    # ---- end-to-end through the public API with host buffers (pinned)
+    e2e = run_e2e(lsb, region, counts, pts, step, stream, min(args.steps, 3), world)
+
+    hbm, peak_kind = peaks()
+    alg_bytes = 18 * n_points + 44 * T * (640 * 640 + 64 * 64)
+    achieved = alg_bytes / (ms_bin * 1e-3) / 1e9
+    tpp = bin_traffic_per_point()
+    out = {
+        "metric": METRIC, "value": round(world * T / (ms_step * 1e-3), 1), "unit": "tiles/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/int64 bins, f32 fill",
+        "data": "synthetic (seeded fBm terrain, LAZ strip order)",
+        "config": {"workload": WORKLOAD, "tiles_per_gpu": T, "points_per_gpu": n_points,
+                   "fill_res": 64, "radius_m": 120, "sigma_m": 40, "parallelism": f"replicas{world}",
+                   "l2": "inputs (~10 GB) larger than L2, no flush", "graph": "one CUDA graph per step"},
+        "points_binned_per_s": round(world * n_points / (ms_step * 1e-3), 1),
+        "bin_only": {"ms": round(ms_bin, 4), "points_per_s": round(n_points / (ms_bin * 1e-3), 1)},
+        "roofline": {"bound": "hbm", "kernel": "ls_bin_points (k_bin_prologue+k_bin_main+k_bin_finalize)",
+                     "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
+                     "algorithmic_bytes": alg_bytes,
+                     "traffic": None if tpp is None else round(tpp * n_points)},
+        "clocks": clocks.summary(),
+        "e2e": e2e,
+        "gpu_launches": step.launches * args.steps,
+    }
+    if rank == 0:
+        out["cpu_baseline"] = cpu_baseline(pts, counts, region, budget_s=args.cpu_seconds)
+    return out
+
+
+def run_e2e(lsb, region, counts, pts, step, stream, steps, world):
+    """Public-API path with host buffers: H2D of the step's points from pinned memory,
+    the step, D2H of its results (64x64 bins and the filled/updated maps)."""
+    import torch
+    host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in pts.items()}
+    for k in host:
+        host[k].copy_(pts[k])
+    res_host = {"height": torch.empty(step.height.shape, pin_memory=True),
+                "rgb": torch.empty(step.rgb.shape, dtype=torch.uint8, pin_memory=True)}
+    res_host.update({k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in step.bins[1].items()})
+    dev_pts = {k: torch.empty_like(v) for k, v in pts.items()}
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = sum(v.numel() * v.element_size() for v in res_host.values())
+    e2e_step = Step(lsb, step.region, step.counts, dev_pts, stream)
+    e2e_step.bins, e2e_step.samples, e2e_step.height, e2e_step.rgb = step.bins, step.samples, step.height, step.rgb
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            for k in host:
+                dev_pts[k].copy_(host[k], non_blocking=True)
+            e2e_step.run()
+            res_host["height"].copy_(step.height, non_blocking=True)
+            res_host["rgb"].copy_(step.rgb, non_blocking=True)
+            for k, v in step.bins[1].items():
+                res_host[k].copy_(v, non_blocking=True)
+        stream.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": round(world * region.n_tiles / dt, 1), "unit": "tiles/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps}
+
+
+# ------------------------------------------------------------------------------------
+# CPU oracle (the baseline and the reference arm)
+# ------------------------------------------------------------------------------------
+
+def oracle_tiles_per_s(tiles_pts, region, budget_s):
+    """Time the oracle's whole path per tile (bin 640 + bin 64, extraction, FP64 fill
+    of the tile with its 3x3 neighbourhood samples, tile update) on host cores."""
+    import oracle
+    import synth
+    done = 0
+    t_used = 0.0
+    for t, p in tiles_pts:
+        one = synth.Region(x0_cm=region.x0_cm + (t % region.tiles_x) * region.tile_cm,
+                           y0_cm=region.y0_cm + (t // region.tiles_x) * region.tile_cm)
+        t0 = time.perf_counter()
+        b640 = oracle.bin_points(p, one, 640)
+        b64 = oracle.bin_points(p, one, 64)
+        idx, soffs = oracle.extract_sample_indices(np.array([0, len(p["x"])], np.int64))
+        s = {k: p[k][idx] for k in "xyzrgb"}
+        f = oracle.fill_sparse(s, one)
+        oracle.update_tile(b64, one, [0], f["height"].astype(np.float32), f["rgb8"])
+        t_used += time.perf_counter() - t0
+        done += 1
+        del b640
+        if t_used >= budget_s:
+            break
+    return done / t_used, done, t_used
+
+
+def _sample_tiles_host(pts, counts, region, k):
+    order = np.argsort(counts)
+    pick = order[np.linspace(0, len(order) - 1, k).astype(int)]
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    out = []
+    for t in pick:
+        a, b = int(offs[t]), int(offs[t + 1])
+        out.append((int(t), {kk: pts[kk][a:b].cpu().numpy() for kk in "xyzrgb"}))
+    return out
+
+
+def cpu_baseline(pts, counts, region, budget_s=12.0):
+    tiles = _sample_tiles_host(pts, counts, region, 12)
+    tps, done, used = oracle_tiles_per_s(tiles, region, budget_s)
+    return {"value": round(tps, 3), "unit": "tiles/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} tiles of the batched region spread over the density range "
+                      f"(serial C oracle: bin 640+64, extract, FP64 fill, update), {used:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle as it stands, on the same workload shape."""
+    import synth
+    region, counts = synth.batched_region_workload(seed=SEED)
+    times, done_all = [], 0
+    order = np.argsort(counts)
+    picks = [int(order[len(order) // 3]), int(order[len(order) // 2])]
+    tiles = [(t, dict(zip("xyzrgb", synth.tile_points(SEED, region, t, int(counts[t]))))) for t in picks]
+    for step in range(args.warmup + args.steps):
+        tps, done, used = oracle_tiles_per_s([tiles[step % len(tiles)]], region, 0.0)
+        if step >= args.warmup:
+            times.append(used / done)
+            done_all += done
+    s_per_tile = float(np.mean(times))
+    value = 1.0 / s_per_tile
+    return {"metric": METRIC, "value": round(value, 3), "unit": "tiles/s", "impl": "reference",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1000 * s_per_tile * region.n_tiles, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64/f64",
+            "data": "synthetic (seeded fBm terrain, LAZ strip order)",
+            "config": {"workload": WORKLOAD, "tiles_per_gpu": region.n_tiles},
+            "cpu_baseline": {"value": round(value, 3), "unit": "tiles/s", "cores": 1, "kind": "oracle",
+                             "sample": f"one of two mid-density tiles per step, {done_all} tiles timed"},
+            "e2e": {"value": round(value, 3), "unit": "tiles/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    out = run_b300(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,81 @@
+"""ctypes view of liblidarscout.so (the C ABI declared in include/lidarscout.h).
+
+Argument marshalling only: every step of the heightmap build runs in the CUDA
+library.  Loading fails loudly when the library is missing; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblidarscout.so")
+
+I32, I64, U64, DBL, FLT = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_float
+VP = ctypes.c_void_p
+
+
+class LsPoints(ctypes.Structure):
+    _fields_ = [("x", VP), ("y", VP), ("z", VP), ("r", VP), ("g", VP), ("b", VP),
+                ("n", I64), ("tile_offsets", VP)]
+
+
+class LsRegion(ctypes.Structure):
+    _fields_ = [("x0_cm", I64), ("y0_cm", I64), ("tile_cm", I32), ("tiles_x", I32),
+                ("tiles_y", I32), ("z_scale", DBL), ("z_offset", DBL)]
+
+
+class LsBins(ctypes.Structure):
+    _fields_ = [("cells", I32), ("count", VP), ("zsum", VP), ("zmin", VP), ("zmax", VP),
+                ("rsum", VP), ("gsum", VP), ("bsum", VP)]
+
+
+class LsFillParams(ctypes.Structure):
+    _fields_ = [("res", I32), ("radius_cm", I32), ("sigma_cm", FLT)]
+
+
+class LsSampleBuffers(ctypes.Structure):
+    _fields_ = [("x", VP), ("y", VP), ("z", VP), ("r", VP), ("g", VP), ("b", VP)]
+
+
+P = ctypes.POINTER
+SIGNATURES = {
+    "ls_bin_points": ([P(LsPoints), P(LsRegion), P(LsBins), I32, VP, VP], I32),
+    "ls_extract_samples": ([P(LsPoints), I64, I32, VP, P(LsSampleBuffers), I64, VP], I32),
+    "ls_fill_sparse": ([P(LsPoints), P(LsRegion), P(LsFillParams), VP, I64, VP, VP, VP], I32),
+    "ls_update_tile": ([P(LsBins), P(LsRegion), VP, I64, VP, VP, VP], I32),
+    "ls_status_string": ([I32], ctypes.c_char_p),
+    "ls_last_error": ([], I32),
+    "ls_release_workspace": ([], I32),
+    "ls_version": ([], I32),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"liblidarscout.so not found at {LIB_PATH}: run "
+                               "`python -m paper_2509_20198_b300.build` (nvcc, sm_103a) first")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+class LsError(RuntimeError):
+    def __init__(self, fn, status):
+        msg = lib().ls_status_string(status).decode()
+        super().__init__(f"{fn} failed: {msg} ({status})")
+        self.status = status
+
+
+def check(fn, status):
+    if status != 0:
+        raise LsError(fn, status)

@@ -1,0 +1,5 @@
+// Single translation unit of liblidarscout.so: device globals (the sticky status
+// word, fixed scratch arrays) exist exactly once without relocatable device code.
+#include "ls_runtime.cu"
+#include "ls_bin.cu"
+#include "ls_fill.cu"

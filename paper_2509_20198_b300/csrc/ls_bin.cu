@@ -1,0 +1,627 @@
+// Exact full-resolution binning of int32-quantised points into per-tile cell grids
+// (count, sum z, min z, max z, sums of R, G, B per cell).  Ground-truth heightmaps
+// are the mean of all points falling onto a texel (Sec. 3.4) and full-resolution
+// points update the heightmap textures (abstract, Sec. 3.5); these exact integer
+// sums are what both need.
+//
+// Design (B300, one CTA per SM, HBM-bound):
+//  * The points arrive in LAZ storage order: tile after tile, and inside a tile in
+//    8 m scan strips.  "Global fine row" G = tile * cells + row is therefore almost
+//    monotone along the stream.  Each CTA streams a contiguous span of points with
+//    128-bit loads and accumulates into a shared-memory ring of W fine rows
+//    (32 bytes per cell: packed R|G, B|count, z-sum, z-min, z-max) with shared
+//    atomics.  When a point lands above the window, the window slides and the rows
+//    that leave are flushed.
+//  * Flush protocol per row (per-row state word in scratch: 0 free, 1 being
+//    written, 2 written): the first CTA to flush a row claims it (0 -> 1), writes
+//    all its cells with plain coalesced stores (empty cells get the sentinels),
+//    fences and publishes 2.  Any later contribution to that row (another CTA's
+//    part of a strip, or a late point) merges with global atomics after seeing 2.
+//    So every output byte is written once by a plain store in the common case and
+//    no memset pass is needed.  Rows that nobody touched get sentinels in a final
+//    pass.  Result is exact for ANY point order; only speed depends on the order.
+//  * Coarse level (e.g. 64x64 from 640x640): reduced exactly from the fine cells
+//    while they are flushed, accumulated in a small shared ring of coarse rows and
+//    merged with global atomics into the (L2-resident) coarse arrays, which a
+//    prologue kernel initialises.
+//  * Packed 32-bit colour sums in shared memory cannot overflow: a row is forced out
+//    of the window before it can have absorbed 65536 points (65536 * 65535 < 2^32).
+#include <climits>
+
+#include "ls_internal.cuh"
+
+namespace ls {
+namespace {
+
+constexpr int kBinThreads = 512;
+constexpr int kPtsPerThread = 4;
+constexpr int kBatch = kBinThreads * kPtsPerThread;  // 2048 points per batch
+constexpr int kResidLimitBatches = 65536 / kBatch;     // residency bound (batches)
+constexpr int kMaxW = 64;
+constexpr int kCW = 4;  // coarse ring rows
+
+struct BinArgs {
+  const int32_t* __restrict__ x;
+  const int32_t* __restrict__ y;
+  const int32_t* __restrict__ z;
+  const uint16_t* __restrict__ r;
+  const uint16_t* __restrict__ g;
+  const uint16_t* __restrict__ b;
+  int64_t n;
+  int64_t x0, y0;
+  uint32_t ext_x, ext_y;
+  FastDiv div_tile, div_cell, div_f;
+  uint32_t tile_cm, cell_cm;
+  int32_t tiles_x, cells, W, f, ccells, has_coarse;
+  int32_t n_rows;  // T * cells
+  // fine level
+  uint32_t* count;
+  int64_t* zsum;
+  int32_t* zmin;
+  int32_t* zmax;
+  uint64_t *rsum, *gsum, *bsum;
+  // coarse level
+  uint32_t* ccount;
+  int64_t* czsum;
+  int32_t* czmin;
+  int32_t* czmax;
+  uint64_t *crsum, *cgsum, *cbsum;
+  uint32_t* row_state;
+  uint64_t* dropped;
+  int64_t span;
+  int64_t n_items;
+  int vec;
+};
+
+// shared-memory layout (dynamic)
+struct Smem {
+  unsigned long long* rg;  // [W*cells] R | G<<32
+  unsigned long long* bc;  // [W*cells] B | count<<32
+  unsigned long long* zs;  // [W*cells] z sum (two's complement)
+  int* mn;                 // [W*cells]
+  int* mx;                 // [W*cells]
+  unsigned long long* crs; // [kCW*ccells] coarse sums
+  unsigned long long* cgs;
+  unsigned long long* cbs;
+  unsigned long long* czs;
+  unsigned* ccnt;
+  int* cmn;
+  int* cmx;
+};
+
+struct Meta {
+  int touched[kMaxW];
+  int enter[kMaxW];  // batch index at which the row entered the window
+  int mode[kMaxW];   // 0 none, 1 store, 2 merge
+  int red[kBinThreads / 32];
+  int bcast;
+  int clo_old, clo_new;  // coarse ring scratch of evict_rows (not shared with block_min)
+  unsigned long long dropped;
+};
+
+__device__ __forceinline__ Smem carve(unsigned char* base, int WC, int CC) {
+  Smem s;
+  s.rg = reinterpret_cast<unsigned long long*>(base);
+  s.bc = s.rg + WC;
+  s.zs = s.bc + WC;
+  s.crs = s.zs + WC;
+  s.cgs = s.crs + CC;
+  s.cbs = s.cgs + CC;
+  s.czs = s.cbs + CC;
+  s.mn = reinterpret_cast<int*>(s.czs + CC);
+  s.mx = s.mn + WC;
+  s.ccnt = reinterpret_cast<unsigned*>(s.mx + WC);
+  s.cmn = reinterpret_cast<int*>(s.ccnt + CC);
+  s.cmx = s.cmn + CC;
+  return s;
+}
+
+__host__ __device__ constexpr size_t smem_bytes(int WC, int CC) {
+  return (size_t)WC * (3 * 8 + 2 * 4) + (size_t)CC * (4 * 8 + 3 * 4);
+}
+
+// Wait (bounded) until a row state is 2.
+__device__ void wait_written(const uint32_t* state) {
+  int it = 0;
+  while (*((volatile const uint32_t*)state) != 2u) {
+    if (++it > kSpinLimit) {
+      set_status(LS_ERR_TIMEOUT);
+      return;
+    }
+    __nanosleep(64);
+  }
+  __threadfence();
+}
+
+__device__ __forceinline__ void store_empty_cell(const BinArgs& a, int64_t o) {
+  a.count[o] = 0u;
+  a.zsum[o] = 0;
+  a.zmin[o] = INT_MAX;
+  a.zmax[o] = INT_MIN;
+  a.rsum[o] = 0ull;
+  a.gsum[o] = 0ull;
+  a.bsum[o] = 0ull;
+}
+
+__device__ __forceinline__ void merge_fine(const BinArgs& a, int64_t o, uint32_t cnt, long long zsum,
+                                           int zmin, int zmax, unsigned long long rs,
+                                           unsigned long long gs, unsigned long long bs) {
+  atomicAdd(&a.count[o], cnt);
+  atomicAdd(reinterpret_cast<unsigned long long*>(&a.zsum[o]), (unsigned long long)zsum);
+  atomicMin(&a.zmin[o], zmin);
+  atomicMax(&a.zmax[o], zmax);
+  atomicAdd(reinterpret_cast<unsigned long long*>(&a.rsum[o]), rs);
+  atomicAdd(reinterpret_cast<unsigned long long*>(&a.gsum[o]), gs);
+  atomicAdd(reinterpret_cast<unsigned long long*>(&a.bsum[o]), bs);
+}
+
+__device__ __forceinline__ void merge_coarse(const BinArgs& a, int64_t o, uint32_t cnt, long long zsum,
+                                             int zmin, int zmax, unsigned long long rs,
+                                             unsigned long long gs, unsigned long long bs) {
+  atomicAdd(&a.ccount[o], cnt);
+  atomicAdd(reinterpret_cast<unsigned long long*>(&a.czsum[o]), (unsigned long long)zsum);
+  atomicMin(&a.czmin[o], zmin);
+  atomicMax(&a.czmax[o], zmax);
+  atomicAdd(reinterpret_cast<unsigned long long*>(&a.crsum[o]), rs);
+  atomicAdd(reinterpret_cast<unsigned long long*>(&a.cgsum[o]), gs);
+  atomicAdd(reinterpret_cast<unsigned long long*>(&a.cbsum[o]), bs);
+}
+
+__device__ __forceinline__ int coarse_row_of(const BinArgs& a, int G) {
+  const int tile = G / a.cells;
+  const int row = G - tile * a.cells;
+  return tile * a.ccells + (int)fdiv((uint32_t)row, a.div_f);
+}
+
+// A point whose row already left this CTA's window: claim the row if nobody has
+// written it yet (single thread writes sentinels), then merge with global atomics.
+__device__ void late_point(const BinArgs& a, int G, int col, int z, uint32_t r, uint32_t g, uint32_t b) {
+  uint32_t* st = &a.row_state[G];
+  if (*((volatile uint32_t*)st) != 2u) {
+    if (atomicCAS(st, 0u, 1u) == 0u) {
+      const int64_t base = (int64_t)G * a.cells;
+      for (int c = 0; c < a.cells; ++c) store_empty_cell(a, base + c);
+      __threadfence();
+      atomicExch(st, 2u);
+    } else {
+      wait_written(st);
+    }
+  }
+  merge_fine(a, (int64_t)G * a.cells + col, 1u, z, z, z, r, g, b);
+  if (a.has_coarse) {
+    const int64_t o = (int64_t)coarse_row_of(a, G) * a.ccells + (int)fdiv((uint32_t)col, a.div_f);
+    merge_coarse(a, o, 1u, z, z, z, r, g, b);
+  }
+}
+
+__device__ __forceinline__ int block_min(int v, Meta& m) {
+  v = __reduce_min_sync(0xffffffffu, v);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();  // m.red may still be read by a previous reduction
+  if (lane == 0) m.red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    int u = lane < (kBinThreads / 32) ? m.red[lane] : INT_MAX;
+    u = __reduce_min_sync(0xffffffffu, u);
+    if (lane == 0) m.bcast = u;
+  }
+  __syncthreads();
+  return m.bcast;
+}
+
+// Flush coarse ring rows [ca, cb) (all inside the ring) to global with atomics.
+__device__ void coarse_evict(const BinArgs& a, Smem& s, int ca, int cb) {
+  const int n = (cb - ca) * a.ccells;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int rr = i / a.ccells, c = i - rr * a.ccells;
+    const int Gc = ca + rr;
+    const int si = (Gc % kCW) * a.ccells + c;
+    const unsigned cnt = s.ccnt[si];
+    if (cnt) {
+      merge_coarse(a, (int64_t)Gc * a.ccells + c, cnt, (long long)s.czs[si], s.cmn[si], s.cmx[si],
+                   s.crs[si], s.cgs[si], s.cbs[si]);
+      s.ccnt[si] = 0u;
+      s.czs[si] = 0ull;
+      s.crs[si] = 0ull;
+      s.cgs[si] = 0ull;
+      s.cbs[si] = 0ull;
+      s.cmn[si] = INT_MAX;
+      s.cmx[si] = INT_MIN;
+    }
+  }
+}
+
+// Evict fine rows [ra, rb) (rb - ra <= W, all inside the ring).  The caller has
+// synchronised the block after the last accumulation.
+__device__ void evict_rows(const BinArgs& a, Smem& s, Meta& m, int ra, int rb, int& clo) {
+  const int nr = rb - ra;
+  if (nr <= 0) return;
+  const int W = a.W;
+  if (threadIdx.x < nr) {
+    const int G = ra + threadIdx.x;
+    const int slot = G & (W - 1);
+    int mode = 0;
+    if (m.touched[slot]) {
+      uint32_t* st = &a.row_state[G];
+      if (atomicCAS(st, 0u, 1u) == 0u) {
+        mode = 1;
+      } else {
+        wait_written(st);
+        mode = 2;
+      }
+    }
+    m.mode[threadIdx.x] = mode;
+  }
+  // coarse ring: make room for the coarse rows of [ra, rb)
+  if (a.has_coarse && threadIdx.x == 0) {
+    const int ca = coarse_row_of(a, ra), cb = coarse_row_of(a, rb - 1);
+    const int c0 = clo < 0 ? ca : clo;
+    m.clo_old = c0;
+    m.clo_new = (cb >= c0 + kCW) ? cb - kCW + 1 : c0;
+  }
+  __syncthreads();
+  if (a.has_coarse) {
+    const int old_clo = m.clo_old, new_clo = m.clo_new;
+    if (new_clo > old_clo) {
+      coarse_evict(a, s, old_clo, new_clo < old_clo + kCW ? new_clo : old_clo + kCW);
+      __syncthreads();
+    }
+    clo = new_clo;
+    // coarse reduction of the fine rows being evicted: one thread per coarse cell
+    // walks the rows in order, so each shared coarse cell has a single writer.
+    for (int c = threadIdx.x; c < a.ccells; c += blockDim.x) {
+      for (int rr = 0; rr < nr; ++rr) {
+        if (m.mode[rr] == 0) continue;
+        const int G = ra + rr;
+        const int slot = G & (W - 1);
+        unsigned cnt = 0;
+        long long zsum = 0;
+        int zmn = INT_MAX, zmx = INT_MIN;
+        unsigned long long rs = 0, gs = 0, bs = 0;
+        for (int k = 0; k < a.f; ++k) {
+          const int si = slot * a.cells + c * a.f + k;
+          const unsigned long long bcv = s.bc[si];
+          const unsigned cn = (unsigned)(bcv >> 32);
+          if (!cn) continue;
+          const unsigned long long rgv = s.rg[si];
+          cnt += cn;
+          zsum += (long long)s.zs[si];
+          zmn = min(zmn, s.mn[si]);
+          zmx = max(zmx, s.mx[si]);
+          rs += rgv & 0xffffffffull;
+          gs += rgv >> 32;
+          bs += bcv & 0xffffffffull;
+        }
+        if (!cnt) continue;
+        const int Gc = coarse_row_of(a, G);
+        if (Gc >= clo && Gc < clo + kCW) {
+          const int ci = (Gc % kCW) * a.ccells + c;
+          s.ccnt[ci] += cnt;
+          s.czs[ci] += (unsigned long long)zsum;
+          s.cmn[ci] = min(s.cmn[ci], zmn);
+          s.cmx[ci] = max(s.cmx[ci], zmx);
+          s.crs[ci] += rs;
+          s.cgs[ci] += gs;
+          s.cbs[ci] += bs;
+        } else {
+          merge_coarse(a, (int64_t)Gc * a.ccells + c, cnt, zsum, zmn, zmx, rs, gs, bs);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // fine rows: store (claimed) or merge, then reset the shared cells
+  for (int rr = 0; rr < nr; ++rr) {
+    const int mode = m.mode[rr];
+    if (mode == 0) continue;
+    const int G = ra + rr;
+    const int slot = G & (W - 1);
+    const int64_t base = (int64_t)G * a.cells;
+    for (int c = threadIdx.x; c < a.cells; c += blockDim.x) {
+      const int si = slot * a.cells + c;
+      const unsigned long long bcv = s.bc[si], rgv = s.rg[si];
+      const unsigned cnt = (unsigned)(bcv >> 32);
+      const long long zsum = (long long)s.zs[si];
+      const int zmn = s.mn[si], zmx = s.mx[si];
+      if (mode == 1) {
+        a.count[base + c] = cnt;
+        a.zsum[base + c] = zsum;
+        a.zmin[base + c] = zmn;
+        a.zmax[base + c] = zmx;
+        a.rsum[base + c] = rgv & 0xffffffffull;
+        a.gsum[base + c] = rgv >> 32;
+        a.bsum[base + c] = bcv & 0xffffffffull;
+      } else if (cnt) {
+        merge_fine(a, base + c, cnt, zsum, zmn, zmx, rgv & 0xffffffffull, rgv >> 32, bcv & 0xffffffffull);
+      }
+      s.rg[si] = 0ull;
+      s.bc[si] = 0ull;
+      s.zs[si] = 0ull;
+      s.mn[si] = INT_MAX;
+      s.mx[si] = INT_MIN;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x < nr) {
+    const int G = ra + threadIdx.x;
+    if (m.mode[threadIdx.x] == 1) atomicExch(&a.row_state[G], 2u);
+    m.touched[G & (W - 1)] = 0;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Meta m;
+  const int WC = a.W * a.cells;
+  const int CC = a.has_coarse ? kCW * a.ccells : 0;
+  Smem s = carve(smem_raw, WC, CC);
+  for (int i = threadIdx.x; i < WC; i += blockDim.x) {
+    s.rg[i] = 0ull; s.bc[i] = 0ull; s.zs[i] = 0ull; s.mn[i] = INT_MAX; s.mx[i] = INT_MIN;
+  }
+  for (int i = threadIdx.x; i < CC; i += blockDim.x) {
+    s.crs[i] = 0ull; s.cgs[i] = 0ull; s.cbs[i] = 0ull; s.czs[i] = 0ull;
+    s.ccnt[i] = 0u; s.cmn[i] = INT_MAX; s.cmx[i] = INT_MIN;
+  }
+  if (threadIdx.x < kMaxW) { m.touched[threadIdx.x] = 0; m.enter[threadIdx.x] = 0; }
+  if (threadIdx.x == 0) m.dropped = 0ull;
+  __syncthreads();
+  unsigned long long my_dropped = 0;
+  const int W = a.W;
+
+  for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+    const int64_t p0 = item * a.span;
+    const int64_t p1 = p0 + a.span < a.n ? p0 + a.span : a.n;
+    int lo = -1;   // lowest fine row of the window (uniform); -1 = empty
+    int clo = -1;  // lowest coarse row of the coarse ring
+    int batch = 0;
+    for (int64_t b0 = p0; b0 < p1; b0 += kBatch, ++batch) {
+      // ---- load 4 consecutive points per thread
+      int G[kPtsPerThread], col[kPtsPerThread], zz[kPtsPerThread];
+      uint32_t rr[kPtsPerThread], gg[kPtsPerThread], bb[kPtsPerThread];
+      const int64_t i0 = b0 + (int64_t)threadIdx.x * kPtsPerThread;
+      int xs[kPtsPerThread], ys[kPtsPerThread];
+      int nvalid = (int)((p1 - i0) < kPtsPerThread ? (p1 - i0) : kPtsPerThread);
+      if (nvalid == kPtsPerThread && a.vec) {
+        const int4 vx = __ldcs(reinterpret_cast<const int4*>(a.x + i0));
+        const int4 vy = __ldcs(reinterpret_cast<const int4*>(a.y + i0));
+        const int4 vz = __ldcs(reinterpret_cast<const int4*>(a.z + i0));
+        const uint2 vr = __ldcs(reinterpret_cast<const uint2*>(a.r + i0));
+        const uint2 vg = __ldcs(reinterpret_cast<const uint2*>(a.g + i0));
+        const uint2 vb = __ldcs(reinterpret_cast<const uint2*>(a.b + i0));
+        xs[0] = vx.x; xs[1] = vx.y; xs[2] = vx.z; xs[3] = vx.w;
+        ys[0] = vy.x; ys[1] = vy.y; ys[2] = vy.z; ys[3] = vy.w;
+        zz[0] = vz.x; zz[1] = vz.y; zz[2] = vz.z; zz[3] = vz.w;
+        rr[0] = vr.x & 0xffffu; rr[1] = vr.x >> 16; rr[2] = vr.y & 0xffffu; rr[3] = vr.y >> 16;
+        gg[0] = vg.x & 0xffffu; gg[1] = vg.x >> 16; gg[2] = vg.y & 0xffffu; gg[3] = vg.y >> 16;
+        bb[0] = vb.x & 0xffffu; bb[1] = vb.x >> 16; bb[2] = vb.y & 0xffffu; bb[3] = vb.y >> 16;
+      } else {
+#pragma unroll
+        for (int k = 0; k < kPtsPerThread; ++k) {
+          if (k < nvalid) {
+            xs[k] = a.x[i0 + k]; ys[k] = a.y[i0 + k]; zz[k] = a.z[i0 + k];
+            rr[k] = a.r[i0 + k]; gg[k] = a.g[i0 + k]; bb[k] = a.b[i0 + k];
+          } else {
+            xs[k] = ys[k] = zz[k] = 0; rr[k] = gg[k] = bb[k] = 0;
+          }
+        }
+      }
+      unsigned pend = 0;
+#pragma unroll
+      for (int k = 0; k < kPtsPerThread; ++k) {
+        G[k] = INT_MAX;
+        col[k] = 0;
+        if (k >= nvalid) continue;
+        const int64_t lx = (int64_t)xs[k] - a.x0, ly = (int64_t)ys[k] - a.y0;
+        if (lx < 0 || ly < 0 || lx >= (int64_t)a.ext_x || ly >= (int64_t)a.ext_y) {
+          ++my_dropped;
+          continue;
+        }
+        const uint32_t ux = (uint32_t)lx, uy = (uint32_t)ly;
+        const uint32_t tx = fdiv(ux, a.div_tile), ty = fdiv(uy, a.div_tile);
+        const uint32_t cx = fdiv(ux - tx * a.tile_cm, a.div_cell);
+        const uint32_t cy = fdiv(uy - ty * a.tile_cm, a.div_cell);
+        G[k] = ((int)ty * a.tiles_x + (int)tx) * a.cells + (int)cy;
+        col[k] = (int)cx;
+        pend |= 1u << k;
+      }
+      // ---- accumulate; slide the window when points land above it
+      while (true) {
+        if (lo >= 0) {
+#pragma unroll
+          for (int k = 0; k < kPtsPerThread; ++k) {
+            if (!(pend & (1u << k))) continue;
+            if (G[k] < lo) {
+              late_point(a, G[k], col[k], zz[k], rr[k], gg[k], bb[k]);
+              pend &= ~(1u << k);
+            } else if (G[k] < lo + W) {
+              const int slot = G[k] & (W - 1);
+              const int si = slot * a.cells + col[k];
+              atomicAdd(&s.rg[si], (unsigned long long)rr[k] | ((unsigned long long)gg[k] << 32));
+              atomicAdd(&s.bc[si], (unsigned long long)bb[k] | (1ull << 32));
+              atomicAdd(&s.zs[si], (unsigned long long)(long long)zz[k]);
+              atomicMin(&s.mn[si], zz[k]);
+              atomicMax(&s.mx[si], zz[k]);
+              m.touched[slot] = 1;
+              pend &= ~(1u << k);
+            }
+          }
+        }
+        int mymin = INT_MAX;
+#pragma unroll
+        for (int k = 0; k < kPtsPerThread; ++k)
+          if (pend & (1u << k)) mymin = min(mymin, G[k]);
+        const int mn = block_min(mymin, m);
+        if (mn == INT_MAX) break;
+        // every pending point lies at or above lo + W: slide so that lo = mn
+        if (lo >= 0) {
+          const int hi = (mn < lo + W) ? mn : lo + W;
+          evict_rows(a, s, m, lo, hi, clo);
+        }
+        lo = mn;
+        if (threadIdx.x < W) m.enter[threadIdx.x] = batch;
+        __syncthreads();
+      }
+      // ---- residency bound: rows that may approach 65536 points leave the window
+      if (lo >= 0 && batch - m.enter[lo & (W - 1)] + 1 >= kResidLimitBatches) {
+        int hi = lo;
+        while (hi < lo + W && batch - m.enter[hi & (W - 1)] + 1 >= kResidLimitBatches) ++hi;
+        __syncthreads();
+        evict_rows(a, s, m, lo, hi, clo);
+        if (threadIdx.x == 0)
+          for (int G2 = lo + W; G2 < hi + W; ++G2) m.enter[G2 & (W - 1)] = batch + 1;
+        lo = hi;
+        __syncthreads();
+      }
+    }
+    // ---- end of the span: flush everything
+    __syncthreads();
+    if (lo >= 0) evict_rows(a, s, m, lo, lo + W, clo);
+    if (a.has_coarse && clo >= 0) {
+      coarse_evict(a, s, clo, clo + kCW);
+      __syncthreads();
+    }
+  }
+  if (a.dropped) {
+    my_dropped = __reduce_add_sync(0xffffffffu, (unsigned)my_dropped);
+    if ((threadIdx.x & 31) == 0 && my_dropped) atomicAdd((unsigned long long*)&m.dropped, my_dropped);
+    __syncthreads();
+    if (threadIdx.x == 0 && m.dropped) atomicAdd((unsigned long long*)a.dropped, m.dropped);
+  }
+}
+
+// Prologue: clear row states and the dropped counter; give the coarse level its
+// empty sentinels (it is only ever merged into with atomics).
+__global__ void k_bin_prologue(BinArgs a, int64_t n_coarse) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n_rows; i += stride)
+    a.row_state[i] = 0u;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_coarse; i += stride) {
+    a.ccount[i] = 0u; a.czsum[i] = 0; a.czmin[i] = INT_MAX; a.czmax[i] = INT_MIN;
+    a.crsum[i] = 0ull; a.cgsum[i] = 0ull; a.cbsum[i] = 0ull;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && a.dropped) *a.dropped = 0ull;
+}
+
+// Epilogue: rows that no point reached get the empty sentinels.
+__global__ void k_bin_finalize(BinArgs a) {
+  for (int64_t G = blockIdx.x; G < a.n_rows; G += gridDim.x) {
+    if (a.row_state[G] != 0u) continue;
+    const int64_t base = G * a.cells;
+    for (int c = threadIdx.x; c < a.cells; c += blockDim.x) store_empty_cell(a, base + c);
+  }
+}
+
+}  // namespace
+
+// Validates and builds the kernel arguments (shared with the fixed-scratch entry).
+ls_status bin_prepare(const ls_points* pts, const ls_region* region, const ls_bins* levels,
+                      int32_t n_levels, uint64_t* dropped, BinArgs* out, size_t* smem, int64_t* n_coarse);
+
+ls_status bin_prepare(const ls_points* pts, const ls_region* region, const ls_bins* levels,
+                      int32_t n_levels, uint64_t* dropped, BinArgs* out, size_t* smem, int64_t* n_coarse) {
+  if (!pts || !region || !levels || n_levels < 1 || n_levels > 2) return LS_ERR_INVALID_ARG;
+  if (pts->n < 0) return LS_ERR_INVALID_ARG;
+  if (pts->n > 0 && (!pts->x || !pts->y || !pts->z || !pts->r || !pts->g || !pts->b))
+    return LS_ERR_INVALID_ARG;
+  if (region->tile_cm <= 0 || region->tiles_x <= 0 || region->tiles_y <= 0) return LS_ERR_INVALID_ARG;
+  const int64_t ext_x = (int64_t)region->tiles_x * region->tile_cm;
+  const int64_t ext_y = (int64_t)region->tiles_y * region->tile_cm;
+  if (ext_x >= (int64_t(1) << 31) || ext_y >= (int64_t(1) << 31)) return LS_ERR_INVALID_ARG;
+  const ls_bins& L0 = levels[0];
+  if (L0.cells <= 0 || L0.cells > 4096 || region->tile_cm % L0.cells) return LS_ERR_INVALID_ARG;
+  if (!L0.count || !L0.zsum || !L0.zmin || !L0.zmax || !L0.rsum || !L0.gsum || !L0.bsum)
+    return LS_ERR_INVALID_ARG;
+  const int64_t T = (int64_t)region->tiles_x * region->tiles_y;
+  const int64_t n_rows = T * L0.cells;
+  if (n_rows >= (int64_t(1) << 31) - 256) return LS_ERR_INVALID_ARG;
+  BinArgs a = {};
+  a.x = pts->x; a.y = pts->y; a.z = pts->z; a.r = pts->r; a.g = pts->g; a.b = pts->b;
+  a.n = pts->n;
+  a.x0 = region->x0_cm; a.y0 = region->y0_cm;
+  a.ext_x = (uint32_t)ext_x; a.ext_y = (uint32_t)ext_y;
+  a.tile_cm = (uint32_t)region->tile_cm;
+  a.cell_cm = (uint32_t)(region->tile_cm / L0.cells);
+  a.div_tile = make_fastdiv(a.tile_cm);
+  a.div_cell = make_fastdiv(a.cell_cm);
+  a.tiles_x = region->tiles_x;
+  a.cells = L0.cells;
+  a.n_rows = (int32_t)n_rows;
+  a.count = L0.count; a.zsum = L0.zsum; a.zmin = L0.zmin; a.zmax = L0.zmax;
+  a.rsum = L0.rsum; a.gsum = L0.gsum; a.bsum = L0.bsum;
+  a.dropped = dropped;
+  a.f = 1;
+  a.ccells = 1;
+  a.div_f = make_fastdiv(1);
+  *n_coarse = 0;
+  if (n_levels == 2) {
+    const ls_bins& L1 = levels[1];
+    if (L1.cells <= 0 || L0.cells % L1.cells) return LS_ERR_INVALID_ARG;
+    if (!L1.count || !L1.zsum || !L1.zmin || !L1.zmax || !L1.rsum || !L1.gsum || !L1.bsum)
+      return LS_ERR_INVALID_ARG;
+    a.has_coarse = 1;
+    a.ccells = L1.cells;
+    a.f = L0.cells / L1.cells;
+    a.div_f = make_fastdiv((uint32_t)a.f);
+    a.ccount = L1.count; a.czsum = L1.zsum; a.czmin = L1.zmin; a.czmax = L1.zmax;
+    a.crsum = L1.rsum; a.cgsum = L1.gsum; a.cbsum = L1.bsum;
+    *n_coarse = T * L1.cells * L1.cells;
+  }
+  // window rows: the largest power of two <= 8 whose ring fits in ~176 KB of shared memory
+  const size_t budget = 176 * 1024;
+  int W = 8;
+  const int CC = a.has_coarse ? kCW * a.ccells : 0;
+  while (W > 1 && smem_bytes(W * a.cells, CC) > budget) W >>= 1;
+  if (W > a.cells) {
+    W = 1;
+    while (W * 2 <= a.cells) W *= 2;
+  }
+  if (smem_bytes(W * a.cells, CC) > budget) return LS_ERR_UNSUPPORTED;
+  a.W = W;
+  *smem = smem_bytes(W * a.cells, CC);
+  // vector loads need 16-byte aligned int32 arrays and 8-byte aligned uint16 arrays
+  a.vec = (((uintptr_t)a.x | (uintptr_t)a.y | (uintptr_t)a.z) % 16 == 0) &&
+          (((uintptr_t)a.r | (uintptr_t)a.g | (uintptr_t)a.b) % 8 == 0);
+  // spans: about 4 per CTA, multiples of the batch size
+  const int64_t grid = kSmCount;
+  int64_t span = (a.n + grid * 4 - 1) / (grid * 4);
+  span = (span + kBatch - 1) / kBatch * kBatch;
+  if (span < kBatch) span = kBatch;
+  a.span = span;
+  a.n_items = (a.n + span - 1) / span;
+  *out = a;
+  return LS_OK;
+}
+
+ls_status bin_launch(BinArgs a, size_t smem, int64_t n_coarse, cudaStream_t stream) {
+  static bool attr_set[64] = {};
+  int dev = 0;
+  LS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    LS_CUDA_TRY(cudaFuncSetAttribute(k_bin_main, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     200 * 1024));
+    attr_set[dev] = true;
+  }
+  const int64_t work = a.n_rows > n_coarse ? a.n_rows : n_coarse;
+  k_bin_prologue<<<grid_cap((work + 255) / 256, kSmCount * 8), 256, 0, stream>>>(a, n_coarse);
+  if (a.n_items > 0) {
+    k_bin_main<<<grid_cap(a.n_items, kSmCount), kBinThreads, smem, stream>>>(a);
+  }
+  k_bin_finalize<<<grid_cap(a.n_rows, kSmCount * 16), 128, 0, stream>>>(a);
+  return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
+}
+
+}  // namespace ls
+
+extern "C" ls_status ls_bin_points(const ls_points* pts, const ls_region* region, const ls_bins* levels,
+                                   int32_t n_levels, uint64_t* dropped, ls_stream_t stream) {
+  ls::BinArgs a;
+  size_t smem = 0;
+  int64_t n_coarse = 0;
+  ls_status st = ls::bin_prepare(pts, region, levels, n_levels, dropped, &a, &smem, &n_coarse);
+  if (st != LS_OK) return st;
+  a.row_state = static_cast<uint32_t*>(ls::workspace(ls::kWsBinRows, (size_t)a.n_rows * 4));
+  if (!a.row_state) return LS_ERR_NO_MEMORY;
+  return ls::bin_launch(a, smem, n_coarse, reinterpret_cast<cudaStream_t>(stream));
+}

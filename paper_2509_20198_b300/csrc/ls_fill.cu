@@ -1,0 +1,487 @@
+// Chunk-point extraction, Gaussian-weighted sparse fill and full-resolution tile
+// update.
+//
+//  * Extraction (Sec. 3.1, 3.2): the first point of every 50,000-point LAZ chunk is
+//    stored uncompressed; sample k of tile t is point tile_offsets[t] + chunk * k.
+//  * Gaussian fill (the High-Quality Splatting baseline of Sec. 4.2): each sample is
+//    a fixed-radius splat, heights and colours are blended with a Gaussian weight;
+//    a texel reached by no splat copies its nearest sample.
+//  * Tile update (abstract, Sec. 3.5): texels with full-resolution points take their
+//    mean height and colour.
+//
+// Fill design (B300): one CTA per output tile.  The samples of the 3x3 tile
+// neighbourhood (three contiguous CSR ranges) are packed 32-byte records that one
+// thread stages into shared memory with three cp.async.bulk copies completing on an
+// mbarrier.  Each warp owns 8x4-texel blocks: lanes test 32 staged samples at a time
+// against the block's box grown by R, a ballot lists the hits, and every lane
+// weighs each hit for its own texel with an exact 64-bit squared distance and
+// __expf.  Results are staged in shared memory and written with 16-byte stores.
+#include <climits>
+#include <cmath>
+
+#include "ls_internal.cuh"
+
+namespace ls {
+namespace {
+
+// Packed sample record (32 bytes): coordinates relative to the region origin.
+struct __align__(16) Rec {
+  int32_t lx, ly, z, idx;
+  uint32_t rg;  // R | G << 16
+  uint32_t b;
+  uint32_t pad0, pad1;
+};
+static_assert(sizeof(Rec) == 32, "record size");
+
+constexpr int kFillThreads = 256;
+constexpr int kStageCap = 2048;  // staged samples per tile (64 KB)
+constexpr int kOutStageRes = 64; // texel maps up to 64x64 are staged in shared memory
+
+// ---------------------------------------------------------------------------------
+// extraction
+// ---------------------------------------------------------------------------------
+__global__ void k_sample_offsets(const int64_t* __restrict__ toff, int64_t n_tiles, int64_t chunk,
+                                 int64_t* __restrict__ soff) {
+  // single CTA exclusive scan of per-tile chunk counts
+  __shared__ int64_t carry;
+  __shared__ int64_t wsum[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < n_tiles; base += blockDim.x) {
+    const int64_t t = base + threadIdx.x;
+    int64_t v = 0;
+    if (t < n_tiles) {
+      const int64_t np = toff[t + 1] - toff[t];
+      v = np > 0 ? (np + chunk - 1) / chunk : 0;
+    }
+    // inclusive warp scan
+    int64_t s = v;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t u = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += u;
+    }
+    if (lane == 31) wsum[warp] = s;
+    __syncthreads();
+    if (warp == 0) {
+      int64_t w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t u = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += u;
+      }
+      wsum[lane] = w;  // inclusive prefix of warp sums
+    }
+    __syncthreads();
+    const int64_t excl = carry + (warp > 0 ? wsum[warp - 1] : 0) + s - v;
+    if (t < n_tiles) soff[t] = excl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) soff[n_tiles] = carry;
+}
+
+__global__ void k_extract(ls_points p, int64_t n_tiles, int64_t chunk, const int64_t* __restrict__ soff,
+                          ls_sample_buffers out, int64_t capacity) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < n_tiles; t += warps) {
+    const int64_t p0 = p.tile_offsets[t], p1 = p.tile_offsets[t + 1];
+    const int64_t s0 = soff[t];
+    for (int64_t k = lane; p0 + k * chunk < p1; k += 32) {
+      const int64_t src = p0 + k * chunk, dst = s0 + k;
+      if (dst >= capacity) {
+        set_status(LS_ERR_OUT_OF_RANGE);
+        break;
+      }
+      out.x[dst] = p.x[src]; out.y[dst] = p.y[src]; out.z[dst] = p.z[src];
+      out.r[dst] = p.r[src]; out.g[dst] = p.g[src]; out.b[dst] = p.b[src];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// fill
+// ---------------------------------------------------------------------------------
+struct FillArgs {
+  const int64_t* __restrict__ toff;  // sample CSR by tile [T+1]
+  const Rec* __restrict__ recs;      // packed samples
+  const int32_t* __restrict__ tile_ids;
+  int64_t n_out;
+  int32_t tiles_x, tiles_y, tile_cm, res, cell_cm;
+  int64_t R2;
+  int32_t R;
+  float k_exp;  // 1 / (2 sigma^2)
+  double z_scale, z_offset;
+  float* height;
+  uint8_t* rgb;
+};
+
+__global__ void k_pack(ls_points s, int64_t n_tiles, int64_t x0, int64_t y0, int32_t tile_cm,
+                       int32_t tiles_x, Rec* __restrict__ recs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < n_tiles; t += warps) {
+    const int64_t q0 = s.tile_offsets[t], q1 = s.tile_offsets[t + 1];
+    const int64_t tx = t % tiles_x, ty = t / tiles_x;
+    for (int64_t q = q0 + lane; q < q1; q += 32) {
+      const int64_t lx = (int64_t)s.x[q] - x0, ly = (int64_t)s.y[q] - y0;
+      if (lx < tx * tile_cm || lx >= (tx + 1) * tile_cm || ly < ty * tile_cm || ly >= (ty + 1) * tile_cm)
+        set_status(LS_ERR_INVALID_ARG);
+      Rec rc;
+      rc.lx = (int32_t)lx; rc.ly = (int32_t)ly; rc.z = s.z[q]; rc.idx = (int32_t)q;
+      rc.rg = (uint32_t)s.r[q] | ((uint32_t)s.g[q] << 16);
+      rc.b = s.b[q];
+      rc.pad0 = rc.pad1 = 0u;
+      recs[q] = rc;
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+struct LaneAcc {
+  float sw, swz, swr, swg, swb;
+  long long bd2;  // nearest squared distance (-1: none yet)
+  int bidx;
+  int bz;
+  uint32_t brg, bb;
+};
+
+__device__ __forceinline__ void consider_nearest(LaneAcc& a, long long d2, const Rec& q) {
+  if (a.bd2 < 0 || d2 < a.bd2 || (d2 == a.bd2 && q.idx < a.bidx)) {
+    a.bd2 = d2; a.bidx = q.idx; a.bz = q.z; a.brg = q.rg; a.bb = q.b;
+  }
+}
+
+// Weigh the samples recs[0..n) that fall in the warp's box for this lane's texel.
+__device__ __forceinline__ void splat_range(const Rec* recs, int n, int bx0, int bx1, int by0, int by1,
+                                            int cx, int cy, const FillArgs& f, int& zref, LaneAcc& a) {
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < n; base += 32) {
+    bool in = false;
+    if (base + lane < n) {
+      const int2 xy = *reinterpret_cast<const int2*>(&recs[base + lane]);
+      in = xy.x >= bx0 && xy.x <= bx1 && xy.y >= by0 && xy.y <= by1;
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, in);
+    while (mask) {
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const Rec q = recs[base + src];
+      if (zref == INT_MIN) zref = q.z;  // warp-uniform provisional height reference
+      const int dx = q.lx - cx, dy = q.ly - cy;
+      const long long d2 = (long long)dx * dx + (long long)dy * dy;
+      consider_nearest(a, d2, q);
+      if (d2 <= f.R2) {
+        const float w = __expf(-(float)d2 * f.k_exp);
+        a.sw += w;
+        a.swz = fmaf(w, (float)(q.z - zref), a.swz);
+        a.swr = fmaf(w, (float)(q.rg & 0xffffu), a.swr);
+        a.swg = fmaf(w, (float)(q.rg >> 16), a.swg);
+        a.swb = fmaf(w, (float)q.b, a.swb);
+      }
+    }
+  }
+}
+
+// Nearest sample among recs[0..n) for lanes that need it (no candidate within R).
+__device__ __forceinline__ void nearest_range(const Rec* recs, int n, bool need, int cx, int cy, LaneAcc& a) {
+  if (!__any_sync(0xffffffffu, need)) return;
+  for (int i = 0; i < n; ++i) {
+    const Rec q = recs[i];
+    if (need) {
+      const int dx = q.lx - cx, dy = q.ly - cy;
+      consider_nearest(a, (long long)dx * dx + (long long)dy * dy, q);
+    }
+  }
+}
+
+// Rings of tiles at Chebyshev distance >= 2 (rare: only when the 3x3 block holds no
+// sample within one tile size of the texel).
+__device__ void nearest_far(const FillArgs& f, int tx, int ty, int cx, int cy, LaneAcc& a) {
+  const int mmax = f.tiles_x > f.tiles_y ? f.tiles_x : f.tiles_y;
+  for (int m = 2; m <= mmax; ++m) {
+    for (int uy = ty - m; uy <= ty + m; ++uy) {
+      if (uy < 0 || uy >= f.tiles_y) continue;
+      const bool edge_row = (uy == ty - m || uy == ty + m);
+      for (int ux = tx - m; ux <= tx + m; ux += (edge_row ? 1 : 2 * m)) {
+        if (ux < 0 || ux >= f.tiles_x) continue;
+        const int64_t u = (int64_t)uy * f.tiles_x + ux;
+        for (int64_t q = f.toff[u]; q < f.toff[u + 1]; ++q) {
+          const Rec rc = f.recs[q];
+          const int dx = rc.lx - cx, dy = rc.ly - cy;
+          consider_nearest(a, (long long)dx * dx + (long long)dy * dy, rc);
+        }
+      }
+    }
+    if (a.bd2 >= 0 && a.bd2 <= (long long)m * f.tile_cm * (long long)m * f.tile_cm) return;
+  }
+}
+
+__global__ void __launch_bounds__(kFillThreads) k_fill(FillArgs f) {
+  extern __shared__ __align__(128) unsigned char fill_dyn[];
+  Rec* stage = reinterpret_cast<Rec*>(fill_dyn);  // kStageCap records (dynamic)
+  __shared__ __align__(16) float out_h[kOutStageRes * kOutStageRes];
+  __shared__ __align__(16) uint8_t out_c[kOutStageRes * kOutStageRes * 3];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int64_t rng_lo[3], rng_n[3];
+  __shared__ int stage_n, staged;
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int res = f.res, cell = f.cell_cm;
+  const bool stage_out = res <= kOutStageRes;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+
+  for (int64_t o = blockIdx.x; o < f.n_out; o += gridDim.x) {
+    const int t = f.tile_ids ? f.tile_ids[o] : (int)o;
+    const int tx = t % f.tiles_x, ty = t / f.tiles_x;
+    // ---- stage the 3x3 neighbourhood (three contiguous CSR ranges)
+    if (threadIdx.x == 0) {
+      int64_t total = 0;
+      const int xa = tx > 0 ? tx - 1 : 0, xb = tx + 1 < f.tiles_x ? tx + 1 : tx;
+      for (int k = 0; k < 3; ++k) {
+        const int uy = ty - 1 + k;
+        rng_lo[k] = 0; rng_n[k] = 0;
+        if (uy < 0 || uy >= f.tiles_y) continue;
+        const int64_t a0 = f.toff[(int64_t)uy * f.tiles_x + xa];
+        const int64_t a1 = f.toff[(int64_t)uy * f.tiles_x + xb + 1];
+        rng_lo[k] = a0; rng_n[k] = a1 - a0;
+        total += a1 - a0;
+      }
+      stage_n = (int)(total < kStageCap ? total : kStageCap);
+      staged = total <= kStageCap;
+      if (staged && total > 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(&bar, (uint32_t)(total * sizeof(Rec)));
+        int64_t d = 0;
+        for (int k = 0; k < 3; ++k) {
+          if (rng_n[k] > 0) bulk_g2s(&stage[d], &f.recs[rng_lo[k]], (uint32_t)(rng_n[k] * sizeof(Rec)), &bar);
+          d += rng_n[k];
+        }
+      }
+    }
+    __syncthreads();
+    const bool use_stage = staged;
+    if (use_stage && stage_n > 0) {
+      int it = 0;
+      while (!mbar_try_wait(&bar, phase)) {
+        if (++it > kSpinLimit) { set_status(LS_ERR_TIMEOUT); break; }
+      }
+      phase ^= 1u;
+    }
+    // ---- texel blocks of 8 x 4 per warp
+    const int bw = res / 8, nblk = bw * (res / 4);
+    for (int blk = warp; blk < nblk; blk += kFillThreads / 32) {
+      const int bj = (blk % bw) * 8, bi = (blk / bw) * 4;
+      const int j = bj + (lane & 7), i = bi + (lane >> 3);
+      const int cx = tx * f.tile_cm + cell * j + cell / 2;
+      const int cy = ty * f.tile_cm + cell * i + cell / 2;
+      const int x0b = tx * f.tile_cm + cell * bj + cell / 2, y0b = ty * f.tile_cm + cell * bi + cell / 2;
+      const int bx0 = x0b - f.R, bx1 = x0b + 7 * cell + f.R;
+      const int by0 = y0b - f.R, by1 = y0b + 3 * cell + f.R;
+      LaneAcc a = {0.f, 0.f, 0.f, 0.f, 0.f, -1ll, INT_MAX, 0, 0u, 0u};
+      int zref = INT_MIN;
+      if (use_stage) {
+        splat_range(stage, stage_n, bx0, bx1, by0, by1, cx, cy, f, zref, a);
+      } else {
+        for (int k = 0; k < 3; ++k)
+          splat_range(f.recs + rng_lo[k], (int)rng_n[k], bx0, bx1, by0, by1, cx, cy, f, zref, a);
+      }
+      const bool need = !(a.sw > 0.f);
+      if (use_stage) {
+        nearest_range(stage, stage_n, need, cx, cy, a);
+      } else {
+        for (int k = 0; k < 3; ++k) nearest_range(f.recs + rng_lo[k], (int)rng_n[k], need, cx, cy, a);
+      }
+      if (need && !(a.bd2 >= 0 && a.bd2 <= (long long)f.tile_cm * f.tile_cm)) nearest_far(f, tx, ty, cx, cy, a);
+      float h;
+      float c3[3];
+      if (!need) {
+        h = (float)(((double)zref + (double)(a.swz / a.sw)) * f.z_scale + f.z_offset);
+        const float inv = 1.0f / a.sw;
+        c3[0] = a.swr * inv * (1.0f / 256.0f);
+        c3[1] = a.swg * inv * (1.0f / 256.0f);
+        c3[2] = a.swb * inv * (1.0f / 256.0f);
+      } else if (a.bd2 >= 0) {
+        h = (float)((double)a.bz * f.z_scale + f.z_offset);
+        c3[0] = (float)(a.brg & 0xffffu) * (1.0f / 256.0f);
+        c3[1] = (float)(a.brg >> 16) * (1.0f / 256.0f);
+        c3[2] = (float)a.bb * (1.0f / 256.0f);
+      } else {
+        h = __int_as_float(0x7fc00000);
+        c3[0] = c3[1] = c3[2] = 0.f;
+      }
+      uint8_t q8[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float v = floorf(c3[c] + 0.5f);
+        q8[c] = (uint8_t)(v > 255.f ? 255.f : v);
+      }
+      const int e = i * res + j;
+      if (stage_out) {
+        out_h[e] = h;
+        out_c[3 * e] = q8[0]; out_c[3 * e + 1] = q8[1]; out_c[3 * e + 2] = q8[2];
+      } else {
+        f.height[o * res * res + e] = h;
+        uint8_t* dst = f.rgb + (o * res * res + e) * 3;
+        dst[0] = q8[0]; dst[1] = q8[1]; dst[2] = q8[2];
+      }
+    }
+    __syncthreads();
+    if (stage_out) {
+      // res^2 * 4 and res^2 * 3 bytes are multiples of 16 for res % 8 == 0
+      const int nh = res * res / 4, nc = res * res * 3 / 16;
+      float4* gh = reinterpret_cast<float4*>(f.height + o * res * res);
+      int4* gc = reinterpret_cast<int4*>(f.rgb + o * res * res * 3);
+      for (int k = threadIdx.x; k < nh; k += blockDim.x) gh[k] = reinterpret_cast<const float4*>(out_h)[k];
+      for (int k = threadIdx.x; k < nc; k += blockDim.x) gc[k] = reinterpret_cast<const int4*>(out_c)[k];
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// tile update
+// ---------------------------------------------------------------------------------
+__global__ void k_update(ls_bins bins, const int32_t* __restrict__ tile_ids, int64_t n, double z_scale,
+                         double z_offset, float* __restrict__ height, uint8_t* __restrict__ rgb) {
+  const int64_t cpt = (int64_t)bins.cells * bins.cells;
+  const int64_t total = n * cpt;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = e / cpt, c = e - o * cpt;
+    const int64_t t = tile_ids ? (int64_t)tile_ids[o] : o;
+    const int64_t src = t * cpt + c;
+    const uint32_t cnt = bins.count[src];
+    if (cnt == 0u) continue;
+    const double nd = (double)cnt;
+    const double mean = __ddiv_rn((double)bins.zsum[src], nd);
+    height[e] = (float)__dadd_rn(__dmul_rn(mean, z_scale), z_offset);
+    const uint64_t sums[3] = {bins.rsum[src], bins.gsum[src], bins.bsum[src]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double v = floor(__dadd_rn(__ddiv_rn(__ddiv_rn((double)sums[k], nd), 256.0), 0.5));
+      rgb[e * 3 + k] = (uint8_t)(v > 255.0 ? 255.0 : v);
+    }
+  }
+}
+
+}  // namespace
+}  // namespace ls
+
+using namespace ls;
+
+extern "C" ls_status ls_extract_samples(const ls_points* pts, int64_t n_tiles, int32_t chunk,
+                                        int64_t* sample_offsets, const ls_sample_buffers* out,
+                                        int64_t capacity, ls_stream_t stream) {
+  if (!pts || !out || !sample_offsets || n_tiles <= 0 || chunk <= 0 || capacity < 0) return LS_ERR_INVALID_ARG;
+  if (!pts->tile_offsets) return LS_ERR_INVALID_ARG;
+  if (pts->n > 0 && (!pts->x || !pts->y || !pts->z || !pts->r || !pts->g || !pts->b)) return LS_ERR_INVALID_ARG;
+  if (capacity > 0 && (!out->x || !out->y || !out->z || !out->r || !out->g || !out->b)) return LS_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  k_sample_offsets<<<1, 1024, 0, s>>>(pts->tile_offsets, n_tiles, chunk, sample_offsets);
+  k_extract<<<grid_cap((n_tiles + 7) / 8, kSmCount * 8), 256, 0, s>>>(*pts, n_tiles, chunk, sample_offsets, *out,
+                                                                     capacity);
+  return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
+}
+
+extern "C" ls_status ls_fill_sparse(const ls_points* samples, const ls_region* region,
+                                    const ls_fill_params* params, const int32_t* tile_ids, int64_t n_out,
+                                    float* height, uint8_t* rgb, ls_stream_t stream) {
+  if (!samples || !region || !params || !height || !rgb || n_out < 0) return LS_ERR_INVALID_ARG;
+  if (!samples->tile_offsets) return LS_ERR_INVALID_ARG;
+  if (samples->n > 0 && (!samples->x || !samples->y || !samples->z || !samples->r || !samples->g || !samples->b))
+    return LS_ERR_INVALID_ARG;
+  if (samples->n >= (int64_t(1) << 31)) return LS_ERR_UNSUPPORTED;
+  if (region->tile_cm <= 0 || region->tiles_x <= 0 || region->tiles_y <= 0) return LS_ERR_INVALID_ARG;
+  if ((int64_t)region->tiles_x * region->tile_cm >= (int64_t(1) << 31) ||
+      (int64_t)region->tiles_y * region->tile_cm >= (int64_t(1) << 31))
+    return LS_ERR_INVALID_ARG;
+  const int64_t T = (int64_t)region->tiles_x * region->tiles_y;
+  if (!tile_ids && n_out != T) return LS_ERR_INVALID_ARG;
+  if (params->res < 8 || params->res > 256 || params->res % 8 || region->tile_cm % params->res)
+    return LS_ERR_INVALID_ARG;
+  if (params->radius_cm < 1 || params->radius_cm > region->tile_cm) return LS_ERR_UNSUPPORTED;
+  if (!(params->sigma_cm > 0.f)) return LS_ERR_INVALID_ARG;
+  if (n_out == 0) return LS_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Rec* recs = static_cast<Rec*>(workspace(kWsFillPacked, (size_t)(samples->n > 0 ? samples->n : 1) * sizeof(Rec)));
+  if (!recs) return LS_ERR_NO_MEMORY;
+  if (samples->n > 0)
+    k_pack<<<grid_cap((T + 7) / 8, kSmCount * 16), 256, 0, s>>>(*samples, T, region->x0_cm, region->y0_cm,
+                                                                 region->tile_cm, region->tiles_x, recs);
+  FillArgs f;
+  f.toff = samples->tile_offsets;
+  f.recs = recs;
+  f.tile_ids = tile_ids;
+  f.n_out = n_out;
+  f.tiles_x = region->tiles_x;
+  f.tiles_y = region->tiles_y;
+  f.tile_cm = region->tile_cm;
+  f.res = params->res;
+  f.cell_cm = region->tile_cm / params->res;
+  f.R = params->radius_cm;
+  f.R2 = (int64_t)params->radius_cm * params->radius_cm;
+  f.k_exp = (float)(1.0 / (2.0 * (double)params->sigma_cm * (double)params->sigma_cm));
+  f.z_scale = region->z_scale;
+  f.z_offset = region->z_offset;
+  f.height = height;
+  f.rgb = rgb;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LS_ERR_CUDA;
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    if (cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kStageCap * sizeof(Rec))) != cudaSuccess)
+      return LS_ERR_CUDA;
+    attr_set[dev] = true;
+  }
+  k_fill<<<grid_cap(n_out, kSmCount * 2), kFillThreads, kStageCap * sizeof(Rec), s>>>(f);
+  return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
+}
+
+extern "C" ls_status ls_update_tile(const ls_bins* bins, const ls_region* region, const int32_t* tile_ids,
+                                    int64_t n, float* height, uint8_t* rgb, ls_stream_t stream) {
+  if (!bins || !region || !height || !rgb || n < 0) return LS_ERR_INVALID_ARG;
+  if (!bins->count || !bins->zsum || !bins->rsum || !bins->gsum || !bins->bsum || bins->cells <= 0)
+    return LS_ERR_INVALID_ARG;
+  if (n == 0) return LS_OK;
+  const int64_t total = n * bins->cells * bins->cells;
+  k_update<<<grid_cap((total + 255) / 256, kSmCount * 16), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      *bins, tile_ids, n, region->z_scale, region->z_offset, height, rgb);
+  return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
+}
