@@ -164,6 +164,109 @@ ls_status ls_update_tile(const ls_bins *bins, const ls_region *region, const int
                          int64_t n, float *height, uint8_t *rgb, ls_stream_t stream);
 
 /* ---------------------------------------------------------------------------------
+ * Tensor-core 3x3 convolution of the learned filler (Sec. 3.4: a U-Net-inspired CNN
+ * refines the heightmaps).  Stride 1, zero padding 1, NHWC BF16 activations, FP32
+ * accumulation (tcgen05 kind::f16, M = 128 pixels, N = c_out, K = 9 * c_in).
+ * Shapes: c_in a multiple of 8; c_out a multiple of 16 in [16, 256]; w a power of
+ * two <= 128; either w*h >= 128 and 128/w divides h, or 128/(w*h) divides n; n*h*w a
+ * multiple of 128.  All device pointers 16-byte aligned.
+ * ------------------------------------------------------------------------------- */
+typedef struct {
+  int32_t n, h, w, cin, cout;
+} ls_conv_shape;
+
+/* bf16 elements of the packed weight operand of a (cin -> cout) 3x3 conv, -1 if the
+ * channel counts are unsupported. */
+int64_t ls_conv3x3_packed_elems(int32_t cin, int32_t cout);
+
+/* Pack fp32 weights w[cout][3][3][cin] (OHWI) into the operand layout of
+ * ls_conv3x3_forward.  transpose_flip = 1 packs the input-gradient convolution of a
+ * layer whose weights are w[cin][3][3][cout] (here cin/cout are the channels of the
+ * gradient conv): W'[o][ky][kx][i] = W[i][2-ky][2-kx][o]. */
+ls_status ls_conv3x3_pack(const float *w, int32_t cin, int32_t cout, int32_t transpose_flip,
+                          uint16_t *packed, ls_stream_t stream);
+
+/* y[p][o] = act(sum_k x_shift[p][k] W[o][k] + bias[o]); act = ReLU if relu != 0; if
+ * mask is non-NULL (bf16, same shape as y) outputs whose mask value is not > 0 are
+ * zeroed (the ReLU derivative of the backward pass).  bias may be NULL. */
+ls_status ls_conv3x3_forward(const uint16_t *x, const uint16_t *packed, const float *bias,
+                             const uint16_t *mask, int32_t relu, const ls_conv_shape *shape,
+                             uint16_t *y, ls_stream_t stream);
+
+/* ---------------------------------------------------------------------------------
+ * Learned filler (Sec. 3.4): a U-Net of `levels` levels with widths[l] channels (two
+ * 3x3 conv + ReLU per level, 2x2 max pooling, 2x nearest upsampling, skip concatenation
+ * [upsampled, skip], 1x1 head with 5 outputs: height, R, G, B residuals added to the
+ * Gaussian fill, and a predicted absolute height error).  Input: 5 channels stored as
+ * bf16 [n][res][res][8] (channels 5..7 zero).  Parameters are a caller-owned flat fp32
+ * device vector: per layer (order e1a, e1b, ..., eLa, eLb, d(L-1)a, d(L-1)b, ..., d1a,
+ * d1b, head) W[c_out][k][k][c_in] then b[c_out]; ls_model_layer_info gives offsets.
+ * The model handle owns packed bf16 weights and activations for max_batch tiles
+ * (allocated by ls_model_create).  Widths: multiples of 16 in [16, 128].
+ * ------------------------------------------------------------------------------- */
+typedef struct ls_model ls_model;
+
+ls_status ls_model_create(int32_t levels, const int32_t *widths, int32_t res, int32_t max_batch,
+                          ls_model **out);
+void ls_model_destroy(ls_model *model);
+int64_t ls_model_param_count(const ls_model *model);
+int32_t ls_model_layer_count(const ls_model *model);
+ls_status ls_model_layer_info(const ls_model *model, int32_t layer, int32_t *cin, int32_t *cout,
+                              int32_t *ksize, int64_t *w_offset, int64_t *b_offset);
+/* Pack the tensor-core operands from params; call after every parameter update. */
+ls_status ls_model_load(ls_model *model, const float *params, ls_stream_t stream);
+/* y: fp32 [n][res][res][5].  Keeps the activations for ls_filler_backward. */
+ls_status ls_filler_forward(ls_model *model, const float *params, const uint16_t *x, int32_t n,
+                            float *y, ls_stream_t stream);
+/* Gradients of all parameters (overwrites grads, flat fp32 like params) given
+ * dL/dy of the last forward call (same n). */
+ls_status ls_filler_backward(ls_model *model, const float *params, const float *dy, int32_t n,
+                             float *grads, ls_stream_t stream);
+/* Loss of Sec. 3.4: masked MSE of height and colour (each squared error clipped to 1),
+ * the two averaged, plus bound_weight * L1(|y4 - |height error||).  base, target:
+ * [n_px][4] (normalised height, R, G, B in 0..1); mask [n_px] (0: texel without truth).
+ * sums: device double[4] scratch; loss: device float[4] (total, height, colour,
+ * bound) or NULL; dy: fp32 [n_px][5]. */
+ls_status ls_filler_loss(const float *y, const float *base, const float *target, const uint8_t *mask,
+                         int64_t n_px, float bound_weight, double *sums, float *loss, float *dy,
+                         ls_stream_t stream);
+/* AdamW with decoupled weight decay (Sec. 3.4 uses lr 1e-4, betas 0.9/0.999, eps 1e-5,
+ * weight decay 1e-2); step counts from 1. */
+ls_status ls_adamw_step(float *p, const float *g, float *m, float *v, int64_t n, float lr, float beta1,
+                        float beta2, float eps, float weight_decay, int32_t step, ls_stream_t stream);
+
+/* Input raster of n tiles (Sec. 3.3/3.4 patch-space normalisation, r = tile_cm/2 in
+ * metres, c_z = mean Gaussian-fill height of the 4 central texels): x bf16
+ * [n][res][res][8]; base fp32 [n][res][res][4] (normalised fill height, fill R, G, B in
+ * 0..1); cz [n]; fill_height/fill_rgb: the Gaussian fill itself; aux: fp32 scratch of
+ * 5 * n * res * res.  res <= 128. */
+ls_status ls_learned_inputs(const ls_points *samples, const ls_region *region,
+                            const ls_fill_params *params, const int32_t *tile_ids, int64_t n,
+                            uint16_t *x, float *base, float *cz, float *fill_height, uint8_t *fill_rgb,
+                            float *aux, ls_stream_t stream);
+/* Training targets from full-resolution bins (cells = res): per texel (mean height in
+ * patch space with the tile's cz, mean R, G, B / 65535), mask = count > 0. */
+ls_status ls_learned_targets(const ls_bins *bins, const ls_region *region, const int32_t *tile_ids,
+                             int64_t n, const float *cz, float *target, uint8_t *mask, ls_stream_t stream);
+/* height = (base + y0) * r + cz, colour = round(clamp(base + y1..3, 0, 1) * 255); tile
+ * bound = RMS(max(y4, 0)) * r metres; tiles whose bound exceeds max_err_m (or is NaN)
+ * take the Gaussian fill instead.  err_bound [n] and used_fallback [n] may be NULL. */
+ls_status ls_learned_finish(const float *y, const float *base, const float *cz, int64_t n, int32_t res,
+                            const ls_region *region, float max_err_m, const float *fill_height,
+                            const uint8_t *fill_rgb, float *height, uint8_t *rgb, float *err_bound,
+                            uint8_t *used_fallback, ls_stream_t stream);
+/* Whole learned fill of n tiles in batches of the model's max_batch: input raster,
+ * network, finish with Gaussian fallback.  scratch: caller-owned device memory of at
+ * least ls_fill_learned_scratch_bytes(model) bytes.  tile_ids may be NULL only when
+ * n = T <= max_batch. */
+size_t ls_fill_learned_scratch_bytes(const ls_model *model);
+ls_status ls_fill_learned(ls_model *model, const float *params, const ls_points *samples,
+                          const ls_region *region, const ls_fill_params *params_fill,
+                          const int32_t *tile_ids, int64_t n, float max_err_m, float *height,
+                          uint8_t *rgb, float *err_bound, uint8_t *used_fallback, void *scratch,
+                          size_t scratch_bytes, ls_stream_t stream);
+
+/* ---------------------------------------------------------------------------------
  * Status helpers.
  * ------------------------------------------------------------------------------- */
 const char *ls_status_string(ls_status s);

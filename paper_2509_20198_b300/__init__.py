@@ -18,7 +18,8 @@ import torch
 from . import _native as N
 
 __all__ = ["bin_points", "extract_samples", "extract_samples_into", "fill_sparse", "update_tile", "last_error",
-           "release_workspace", "empty_bins", "BIN_KEYS"]
+           "release_workspace", "empty_bins", "BIN_KEYS", "Filler", "FillerFn", "filler_loss", "adamw_step",
+           "learned_inputs", "learned_targets", "learned_finish", "fill_learned"]
 
 BIN_KEYS = ("count", "zsum", "zmin", "zmax", "rsum", "gsum", "bsum")
 _BIN_DTYPES = {"count": torch.int32, "zsum": torch.int64, "zmin": torch.int32, "zmax": torch.int32,
@@ -173,3 +174,170 @@ def last_error():
 
 def release_workspace():
     N.check("ls_release_workspace", N.lib().ls_release_workspace())
+
+
+# ------------------------------------------------------------------------------------
+# learned filler
+# ------------------------------------------------------------------------------------
+
+class Filler:
+    """Native U-Net handle (ls_model) plus its flat fp32 parameter tensor.
+
+    Layer order and layout as in include/lidarscout.h; ``params`` is a plain CUDA
+    tensor that the caller may update (then call :meth:`load`)."""
+
+    def __init__(self, widths=(32, 64, 128), res=64, max_batch=256, device="cuda"):
+        self.widths, self.res, self.max_batch = tuple(widths), res, max_batch
+        self.device = torch.device(device)
+        h = ctypes.c_void_p()
+        w = (ctypes.c_int32 * len(widths))(*widths)
+        N.check("ls_model_create", N.lib().ls_model_create(len(widths), w, res, max_batch, ctypes.byref(h)))
+        self._h = h
+        self.n_params = N.lib().ls_model_param_count(h)
+        self.params = torch.zeros(self.n_params, dtype=torch.float32, device=self.device)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            N.lib().ls_model_destroy(h)
+            self._h = None
+
+    def layers(self):
+        """[(cin, cout, k, w_offset, b_offset)] in parameter order."""
+        out = []
+        for i in range(N.lib().ls_model_layer_count(self._h)):
+            a = [ctypes.c_int32() for _ in range(3)] + [ctypes.c_int64() for _ in range(2)]
+            N.check("ls_model_layer_info", N.lib().ls_model_layer_info(self._h, i, *[ctypes.byref(v) for v in a]))
+            out.append(tuple(v.value for v in a))
+        return out
+
+    def load(self, stream=None):
+        N.check("ls_model_load", N.lib().ls_model_load(self._h, _ptr(self.params), _stream(stream)))
+
+    def forward(self, x, stream=None):
+        n = x.shape[0]
+        y = torch.empty((n, self.res, self.res, 5), dtype=torch.float32, device=x.device)
+        N.check("ls_filler_forward", N.lib().ls_filler_forward(self._h, _ptr(self.params), _ptr(_dev(x, "x")), n,
+                                                              _ptr(y), _stream(stream)))
+        return y
+
+    def backward(self, dy, grads=None, stream=None):
+        n = dy.shape[0]
+        if grads is None:
+            grads = torch.empty_like(self.params)
+        N.check("ls_filler_backward", N.lib().ls_filler_backward(self._h, _ptr(self.params),
+                                                                _ptr(_dev(dy.contiguous(), "dy")), n,
+                                                                _ptr(grads), _stream(stream)))
+        return grads
+
+
+class FillerFn(torch.autograd.Function):
+    """torch.autograd.Function whose forward and backward are the library's
+    tensor-core kernels: y = filler(params; x), dL/dparams from dL/dy."""
+
+    @staticmethod
+    def forward(ctx, params, x, filler):
+        ctx.filler = filler
+        filler.load()
+        return filler.forward(x)
+
+    @staticmethod
+    def backward(ctx, dy):
+        return ctx.filler.backward(dy), None, None
+
+
+def filler_loss(y, base, target, mask, bound_weight=0.1, stream=None):
+    """Masked, clipped MSE of Sec. 3.4 (+ bound term).  Returns (loss[4], dL/dy)."""
+    n_px = mask.numel()
+    sums = torch.empty(4, dtype=torch.float64, device=y.device)
+    loss = torch.empty(4, dtype=torch.float32, device=y.device)
+    dy = torch.empty_like(y)
+    N.check("ls_filler_loss", N.lib().ls_filler_loss(_ptr(y), _ptr(base), _ptr(target), _ptr(mask), n_px,
+                                                    float(bound_weight), _ptr(sums), _ptr(loss), _ptr(dy),
+                                                    _stream(stream)))
+    return loss, dy
+
+
+def adamw_step(p, g, m, v, step, lr=1e-4, betas=(0.9, 0.999), eps=1e-5, weight_decay=1e-2, stream=None):
+    N.check("ls_adamw_step", N.lib().ls_adamw_step(_ptr(p), _ptr(g), _ptr(m), _ptr(v), p.numel(), float(lr),
+                                                  float(betas[0]), float(betas[1]), float(eps),
+                                                  float(weight_decay), int(step), _stream(stream)))
+
+
+def learned_inputs(samples, region, tile_ids, res=64, radius_cm=12000, sigma_cm=4000.0, stream=None):
+    """Input raster of the filler for the given tiles.  Returns dict x (bf16 bits as
+    int16 [n,res,res,8]), base [n,res,res,4], cz [n], fill_height, fill_rgb."""
+    dev = samples["x"].device
+    tile_ids = _dev(tile_ids.to(device=dev, dtype=torch.int32).contiguous(), "tile_ids")
+    n = tile_ids.numel()
+    out = {"x": torch.empty((n, res, res, 8), dtype=torch.int16, device=dev),
+           "base": torch.empty((n, res, res, 4), dtype=torch.float32, device=dev),
+           "cz": torch.empty(n, dtype=torch.float32, device=dev),
+           "fill_height": torch.empty((n, res, res), dtype=torch.float32, device=dev),
+           "fill_rgb": torch.empty((n, res, res, 3), dtype=torch.uint8, device=dev)}
+    aux = torch.empty(5 * n * res * res, dtype=torch.float32, device=dev)
+    pts = _points(samples, need_offsets=True)
+    reg = _region(region)
+    prm = N.LsFillParams(res, radius_cm, sigma_cm)
+    N.check("ls_learned_inputs", N.lib().ls_learned_inputs(
+        ctypes.byref(pts), ctypes.byref(reg), ctypes.byref(prm), _ptr(tile_ids), n, _ptr(out["x"]),
+        _ptr(out["base"]), _ptr(out["cz"]), _ptr(out["fill_height"]), _ptr(out["fill_rgb"]), _ptr(aux),
+        _stream(stream)))
+    return out
+
+
+def learned_targets(bins, region, tile_ids, cz, stream=None):
+    """Per-texel mean of the full-resolution points in patch space, and its mask."""
+    cells = bins["count"].shape[-1]
+    dev = cz.device
+    tile_ids = _dev(tile_ids.to(device=dev, dtype=torch.int32).contiguous(), "tile_ids")
+    n = tile_ids.numel()
+    target = torch.empty((n, cells, cells, 4), dtype=torch.float32, device=dev)
+    mask = torch.empty((n, cells, cells), dtype=torch.uint8, device=dev)
+    b = _bins_struct(bins, cells)
+    reg = _region(region)
+    N.check("ls_learned_targets", N.lib().ls_learned_targets(ctypes.byref(b), ctypes.byref(reg), _ptr(tile_ids), n,
+                                                            _ptr(cz), _ptr(target), _ptr(mask), _stream(stream)))
+    return target, mask
+
+
+def learned_finish(y, inputs, region, max_err_m=2.0, stream=None):
+    n, res = y.shape[0], y.shape[1]
+    height = torch.empty((n, res, res), dtype=torch.float32, device=y.device)
+    rgb = torch.empty((n, res, res, 3), dtype=torch.uint8, device=y.device)
+    bound = torch.empty(n, dtype=torch.float32, device=y.device)
+    fb = torch.empty(n, dtype=torch.uint8, device=y.device)
+    reg = _region(region)
+    N.check("ls_learned_finish", N.lib().ls_learned_finish(
+        _ptr(y), _ptr(inputs["base"]), _ptr(inputs["cz"]), n, res, ctypes.byref(reg), float(max_err_m),
+        _ptr(inputs["fill_height"]), _ptr(inputs["fill_rgb"]), _ptr(height), _ptr(rgb), _ptr(bound), _ptr(fb),
+        _stream(stream)))
+    return height, rgb, bound, fb
+
+
+def fill_learned(filler, samples, region, tile_ids, max_err_m=2.0, radius_cm=12000, sigma_cm=4000.0,
+                 height=None, rgb=None, err_bound=None, used_fallback=None, scratch=None, stream=None):
+    """Whole learned fill (input raster, network, finish with Gaussian fallback) of the
+    given tiles in batches of the filler's max_batch."""
+    dev = samples["x"].device
+    tile_ids = _dev(tile_ids.to(device=dev, dtype=torch.int32).contiguous(), "tile_ids")
+    n, res = tile_ids.numel(), filler.res
+    if height is None:
+        height = torch.empty((n, res, res), dtype=torch.float32, device=dev)
+    if rgb is None:
+        rgb = torch.empty((n, res, res, 3), dtype=torch.uint8, device=dev)
+    if err_bound is None:
+        err_bound = torch.empty(n, dtype=torch.float32, device=dev)
+    if used_fallback is None:
+        used_fallback = torch.empty(n, dtype=torch.uint8, device=dev)
+    need = N.lib().ls_fill_learned_scratch_bytes(filler._h)
+    if scratch is None or scratch.numel() < need:
+        scratch = torch.empty(need, dtype=torch.uint8, device=dev)
+    pts = _points(samples, need_offsets=True)
+    reg = _region(region)
+    prm = N.LsFillParams(res, radius_cm, sigma_cm)
+    N.check("ls_fill_learned", N.lib().ls_fill_learned(
+        filler._h, _ptr(filler.params), ctypes.byref(pts), ctypes.byref(reg), ctypes.byref(prm), _ptr(tile_ids),
+        n, float(max_err_m), _ptr(height), _ptr(rgb), _ptr(err_bound), _ptr(used_fallback), _ptr(scratch),
+        scratch.numel(), _stream(stream)))
+    return height, rgb, err_bound, used_fallback

@@ -34,6 +34,10 @@ class LsFillParams(ctypes.Structure):
     _fields_ = [("res", I32), ("radius_cm", I32), ("sigma_cm", FLT)]
 
 
+class LsConvShape(ctypes.Structure):
+    _fields_ = [("n", I32), ("h", I32), ("w", I32), ("cin", I32), ("cout", I32)]
+
+
 class LsSampleBuffers(ctypes.Structure):
     _fields_ = [("x", VP), ("y", VP), ("z", VP), ("r", VP), ("g", VP), ("b", VP)]
 
@@ -44,6 +48,25 @@ SIGNATURES = {
     "ls_extract_samples": ([P(LsPoints), I64, I32, VP, P(LsSampleBuffers), I64, VP], I32),
     "ls_fill_sparse": ([P(LsPoints), P(LsRegion), P(LsFillParams), VP, I64, VP, VP, VP], I32),
     "ls_update_tile": ([P(LsBins), P(LsRegion), VP, I64, VP, VP, VP], I32),
+    "ls_conv3x3_packed_elems": ([I32, I32], I64),
+    "ls_conv3x3_pack": ([VP, I32, I32, I32, VP, VP], I32),
+    "ls_conv3x3_forward": ([VP, VP, VP, VP, I32, P(LsConvShape), VP, VP], I32),
+    "ls_model_create": ([I32, VP, I32, I32, P(VP)], I32),
+    "ls_model_destroy": ([VP], None),
+    "ls_model_param_count": ([VP], I64),
+    "ls_model_layer_count": ([VP], I32),
+    "ls_model_layer_info": ([VP, I32, P(I32), P(I32), P(I32), P(I64), P(I64)], I32),
+    "ls_model_load": ([VP, VP, VP], I32),
+    "ls_filler_forward": ([VP, VP, VP, I32, VP, VP], I32),
+    "ls_filler_backward": ([VP, VP, VP, I32, VP, VP], I32),
+    "ls_filler_loss": ([VP, VP, VP, VP, I64, FLT, VP, VP, VP, VP], I32),
+    "ls_adamw_step": ([VP, VP, VP, VP, I64, FLT, FLT, FLT, FLT, FLT, I32, VP], I32),
+    "ls_learned_inputs": ([P(LsPoints), P(LsRegion), P(LsFillParams), VP, I64, VP, VP, VP, VP, VP, VP, VP], I32),
+    "ls_learned_targets": ([P(LsBins), P(LsRegion), VP, I64, VP, VP, VP, VP], I32),
+    "ls_learned_finish": ([VP, VP, VP, I64, I32, P(LsRegion), FLT, VP, VP, VP, VP, VP, VP, VP], I32),
+    "ls_fill_learned_scratch_bytes": ([VP], ctypes.c_size_t),
+    "ls_fill_learned": ([VP, VP, P(LsPoints), P(LsRegion), P(LsFillParams), VP, I64, FLT, VP, VP, VP, VP, VP,
+                         ctypes.c_size_t, VP], I32),
     "ls_status_string": ([I32], ctypes.c_char_p),
     "ls_last_error": ([], I32),
     "ls_release_workspace": ([], I32),

@@ -1,0 +1,323 @@
+// 3x3 convolution (stride 1, zero padding 1) on the 5th-generation tensor cores as an
+// implicit GEMM: M = 128 output pixels, N = C_out, K = 9 * C_in, BF16 operands, FP32
+// accumulation in TMEM.  This is the convolution of the learned heightmap filler
+// (Sec. 3.4: a U-Net-inspired CNN refines the heightmaps) in its forward pass and,
+// with transposed and flipped weights, in the input-gradient pass of training.
+//
+// Per CTA (persistent over 128-pixel tiles, one CTA per SM, 6 warps):
+//  warp 0  TMA producer: per 8-channel chunk of one tap, one 4-D tiled TMA load of
+//          the shifted 128-pixel slab (out-of-range rows/columns are zero-filled by
+//          the TMA unit: that is the padding) and one 1-D bulk copy of the
+//          pre-packed weight block of the stage;
+//  warp 1  MMA issuer: tcgen05.mma kind::f16 (M=128, N=C_out, K=16) per chunk pair,
+//          tcgen05.commit to free the stage and to publish a finished accumulator;
+//  warps 2-5 epilogue: tcgen05.ld of the accumulator (one pixel per thread), bias,
+//          ReLU or a ReLU-derivative mask, BF16 store (NHWC).
+// Two TMEM accumulators let the epilogue of tile i overlap the MMAs of tile i+1.
+// Operands are K-major without swizzle: an A stage holds up to 8 chunks of
+// 128 rows x 16 bytes (LBO 2048 B between chunks, SBO 128 B between 8-row groups);
+// the packed weights of a stage are C_out rows x 8 chunks (LBO C_out*16 B, SBO 128 B).
+#include <cuda_bf16.h>
+
+#include "ls_tc.cuh"
+
+namespace ls {
+
+bool encode_tmap_bf16_4d(CUtensorMap* map, const void* base, const uint64_t dims[4], const uint64_t strides[3],
+                         const uint32_t box[4]) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      return false;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  cuuint64_t d[4] = {dims[0], dims[1], dims[2], dims[3]};
+  cuuint64_t s[3] = {strides[0], strides[1], strides[2]};
+  cuuint32_t b[4] = {box[0], box[1], box[2], box[3]};
+  cuuint32_t e[4] = {1, 1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), d, s, b, e,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+namespace {
+
+constexpr int kConvThreads = 192;
+constexpr int kConvStages = 4;
+constexpr int kChunksPerStage = 8;
+constexpr int kAStageBytes = kChunksPerStage * 2048;
+
+struct ConvArgs {
+  const uint16_t* __restrict__ wpk;
+  const float* __restrict__ bias;
+  const uint16_t* __restrict__ mask;
+  uint16_t* __restrict__ y;
+  int32_t cin, cout, cpt, kc_real, kc, n_stages, n_mtiles;
+  int32_t tiles_per_img, rows_per_tile, imgs_per_tile;
+  int32_t relu;
+  uint32_t acc_cols, tmem_cols, stage_bytes, idesc;
+};
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__global__ void __launch_bounds__(kConvThreads, 1)
+    k_conv3x3(const __grid_constant__ CUtensorMap xmap, const ConvArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t full[kConvStages], empty[kConvStages], tfull[2], tempty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kConvStages; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&tfull[i], 1);
+      tc::mbar_init(&tempty[i], 128);
+    }
+    abort_flag = 0;
+    tc::mbar_fence_init();
+    tc::prefetch_tmap(&xmap);
+  }
+  if (warp == 1) tc::tmem_alloc(&tmem_base, a.tmem_cols);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t taddr = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int it = 0;
+    for (int m = blockIdx.x; m < a.n_mtiles && !abort_flag; m += gridDim.x) {
+      int n0, y0;
+      if (a.imgs_per_tile == 1) {
+        n0 = m / a.tiles_per_img;
+        y0 = (m - n0 * a.tiles_per_img) * a.rows_per_tile;
+      } else {
+        n0 = m * a.imgs_per_tile;
+        y0 = 0;
+      }
+      for (int s = 0; s < a.n_stages; ++s, ++it) {
+        const int slot = it % kConvStages;
+        const uint32_t ph = (uint32_t)(it / kConvStages) & 1u;
+        if (!tc::mbar_wait(&empty[slot], ph ^ 1u)) { abort_flag = 1; break; }
+        const int c0 = s * kChunksPerStage;
+        const int nc = min(kChunksPerStage, a.kc - c0);
+        uint8_t* A = smem + (size_t)slot * a.stage_bytes;
+        uint8_t* B = A + kAStageBytes;
+        tc::mbar_arrive_expect_tx(&full[slot], (uint32_t)(nc * 2048 + nc * a.cout * 16));
+        for (int k = 0; k < nc; ++k) {
+          int c = c0 + k;
+          if (c >= a.kc_real) c = 0;  // padding chunk: any finite data, its weights are zero
+          const int tap = c / a.cpt, c8 = c - tap * a.cpt;
+          const int ky = tap / 3, kx = tap - ky * 3;
+          tc::tma_load_4d(A + k * 2048, &xmap, c8 * 8, kx - 1, y0 + ky - 1, n0, &full[slot]);
+        }
+        tc::bulk_load(B, a.wpk + (size_t)c0 * a.cout * 8, (uint32_t)(nc * a.cout * 16), &full[slot]);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    int it = 0, ai = 0;
+    for (int m = blockIdx.x; m < a.n_mtiles && !abort_flag; m += gridDim.x, ++ai) {
+      const int acc = ai & 1;
+      const uint32_t aph = (uint32_t)(ai >> 1) & 1u;
+      if (!tc::mbar_wait(&tempty[acc], aph ^ 1u)) { abort_flag = 1; break; }
+      tc::fence_after();
+      const uint32_t d = taddr + (uint32_t)acc * a.acc_cols;
+      for (int s = 0; s < a.n_stages; ++s, ++it) {
+        const int slot = it % kConvStages;
+        const uint32_t ph = (uint32_t)(it / kConvStages) & 1u;
+        if (!tc::mbar_wait(&full[slot], ph)) { abort_flag = 1; break; }
+        tc::fence_after();
+        const uint32_t A = tc::saddr(smem + (size_t)slot * a.stage_bytes);
+        const uint32_t B = A + kAStageBytes;
+        const int nc = min(kChunksPerStage, a.kc - s * kChunksPerStage);
+        for (int j = 0; j < nc / 2; ++j) {
+          const uint64_t ad = tc::sdesc(A + j * 4096, 2048, 128);
+          const uint64_t bd = tc::sdesc(B + j * 2 * a.cout * 16, a.cout * 16, 128);
+          tc::mma_bf16(d, ad, bd, a.idesc, (s > 0 || j > 0) ? 1u : 0u);
+        }
+        tc::mma_commit(&empty[slot]);
+      }
+      tc::mma_commit(&tfull[acc]);
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue: one output pixel per thread
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int ai = 0;
+    for (int m = blockIdx.x; m < a.n_mtiles && !abort_flag; m += gridDim.x, ++ai) {
+      const int acc = ai & 1;
+      const uint32_t aph = (uint32_t)(ai >> 1) & 1u;
+      if (!tc::mbar_wait(&tfull[acc], aph)) { abort_flag = 1; break; }
+      tc::fence_after();
+      const size_t pix = (size_t)m * 128 + row;
+      uint16_t* yp = a.y + pix * a.cout;
+      const uint16_t* mp = a.mask ? a.mask + pix * a.cout : nullptr;
+      for (int c0 = 0; c0 < a.cout; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * a.acc_cols + (uint32_t)c0, v);
+        if (a.bias) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] += __ldg(a.bias + c0 + i);
+        }
+        if (a.relu) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
+        }
+        if (mp) {
+          const uint4 m0 = *reinterpret_cast<const uint4*>(mp + c0);
+          const uint4 m1 = *reinterpret_cast<const uint4*>(mp + c0 + 8);
+          const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            // bf16 > 0: sign bit clear and not +0
+            const uint32_t lo = mw[i] & 0xffffu, hi = mw[i] >> 16;
+            if (!(lo != 0u && !(lo & 0x8000u))) v[2 * i] = 0.f;
+            if (!(hi != 0u && !(hi & 0x8000u))) v[2 * i + 1] = 0.f;
+          }
+        }
+        uint4 o0, o1;
+        o0.x = pack_bf16x2(v[0], v[1]); o0.y = pack_bf16x2(v[2], v[3]);
+        o0.z = pack_bf16x2(v[4], v[5]); o0.w = pack_bf16x2(v[6], v[7]);
+        o1.x = pack_bf16x2(v[8], v[9]); o1.y = pack_bf16x2(v[10], v[11]);
+        o1.z = pack_bf16x2(v[12], v[13]); o1.w = pack_bf16x2(v[14], v[15]);
+        *reinterpret_cast<uint4*>(yp + c0) = o0;
+        *reinterpret_cast<uint4*>(yp + c0 + 8) = o1;
+      }
+      tc::fence_before();
+      tc::mbar_arrive(&tempty[acc]);
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after();
+    tc::tmem_dealloc(taddr, a.tmem_cols);
+  }
+}
+
+// Pack fp32 OHWI weights into the K-major operand layout: chunk c (8 consecutive K
+// elements of one tap) is a block of C_out rows x 16 bytes, 8-row groups of 128 bytes.
+__global__ void k_pack_weights(const float* __restrict__ w, int cin, int cout, int tflip, int kc,
+                               uint16_t* __restrict__ out) {
+  const int64_t total = (int64_t)kc * cout * 8;
+  const int cpt = cin / 8;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / (cout * 8));
+    const int r = (int)(e - (int64_t)c * cout * 8);
+    const int o = (r >> 6) * 8 + ((r & 63) >> 3);
+    const int ee = r & 7;
+    float v = 0.f;
+    if (c < 9 * cpt) {
+      const int tap = c / cpt, ci = (c - tap * cpt) * 8 + ee;
+      const int ky = tap / 3, kx = tap - ky * 3;
+      if (!tflip) {
+        v = w[(((int64_t)o * 3 + ky) * 3 + kx) * cin + ci];
+      } else {
+        // input-gradient conv: W'[o][ky][kx][ci] = W[ci][2-ky][2-kx][o], W is [cin][3][3][cout]
+        v = w[(((int64_t)ci * 3 + (2 - ky)) * 3 + (2 - kx)) * cout + o];
+      }
+    }
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    out[e] = *reinterpret_cast<const uint16_t*>(&h);
+  }
+}
+
+int chunk_count(int cin) {
+  const int kc = 9 * (cin / 8);
+  return kc + (kc & 1);
+}
+
+}  // namespace
+
+// Shared with the model code: validated launch of one convolution.
+ls_status conv3x3_launch(const uint16_t* x, const uint16_t* wpk, const float* bias, const uint16_t* mask, int relu,
+                         int n, int h, int w, int cin, int cout, uint16_t* y, cudaStream_t stream) {
+  if (!x || !wpk || !y || n <= 0 || h <= 0 || w <= 0) return LS_ERR_INVALID_ARG;
+  if (cin < 8 || cin % 8 || cout < 16 || cout > 256 || cout % 16) return LS_ERR_UNSUPPORTED;
+  if (w > 128 || 128 % w) return LS_ERR_UNSUPPORTED;
+  if (((uintptr_t)x | (uintptr_t)wpk | (uintptr_t)y | (uintptr_t)mask) % 16) return LS_ERR_INVALID_ARG;
+  ConvArgs a = {};
+  uint32_t box[4] = {8, (uint32_t)w, 1, 1};
+  if (w * h >= 128) {
+    const int rpt = 128 / w;
+    if (h % rpt) return LS_ERR_UNSUPPORTED;
+    a.rows_per_tile = rpt;
+    a.tiles_per_img = h / rpt;
+    a.imgs_per_tile = 1;
+    box[2] = (uint32_t)rpt;
+  } else {
+    if (128 % (w * h)) return LS_ERR_UNSUPPORTED;
+    const int ipt = 128 / (w * h);
+    if (n % ipt) return LS_ERR_UNSUPPORTED;
+    a.rows_per_tile = h;
+    a.tiles_per_img = 1;
+    a.imgs_per_tile = ipt;
+    box[2] = (uint32_t)h;
+    box[3] = (uint32_t)ipt;
+  }
+  const int64_t P = (int64_t)n * h * w;
+  if (P % 128 || P / 128 > (int64_t)INT32_MAX) return LS_ERR_UNSUPPORTED;
+  a.n_mtiles = (int32_t)(P / 128);
+  a.wpk = wpk; a.bias = bias; a.mask = mask; a.y = y; a.relu = relu;
+  a.cin = cin; a.cout = cout; a.cpt = cin / 8;
+  a.kc_real = 9 * a.cpt;
+  a.kc = chunk_count(cin);
+  a.n_stages = (a.kc + kChunksPerStage - 1) / kChunksPerStage;
+  a.acc_cols = 32;
+  while ((int)a.acc_cols < cout) a.acc_cols <<= 1;
+  a.tmem_cols = 2 * a.acc_cols;
+  a.stage_bytes = (uint32_t)(kAStageBytes + cout * 8 * 16);
+  a.idesc = tc::idesc_bf16(128, cout);
+  CUtensorMap map;
+  const uint64_t dims[4] = {(uint64_t)cin, (uint64_t)w, (uint64_t)h, (uint64_t)n};
+  const uint64_t strides[3] = {(uint64_t)cin * 2, (uint64_t)w * cin * 2, (uint64_t)h * w * cin * 2};
+  if (!encode_tmap_bf16_4d(&map, x, dims, strides, box)) return LS_ERR_CUDA;
+  const size_t smem = (size_t)kConvStages * a.stage_bytes;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  LS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    LS_CUDA_TRY(cudaFuncSetAttribute(k_conv3x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kConvStages * (kAStageBytes + 256 * 128)));
+    attr_set[dev] = true;
+  }
+  k_conv3x3<<<grid_cap(a.n_mtiles, kSmCount), kConvThreads, smem, stream>>>(map, a);
+  return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
+}
+
+}  // namespace ls
+
+extern "C" int64_t ls_conv3x3_packed_elems(int32_t cin, int32_t cout) {
+  if (cin < 8 || cin % 8 || cout < 16 || cout % 16) return -1;
+  return (int64_t)ls::chunk_count(cin) * cout * 8;
+}
+
+extern "C" ls_status ls_conv3x3_pack(const float* w, int32_t cin, int32_t cout, int32_t transpose_flip,
+                                     uint16_t* packed, ls_stream_t stream) {
+  if (!w || !packed || cin < 8 || cin % 8 || cout < 16 || cout % 16) return LS_ERR_INVALID_ARG;
+  const int kc = ls::chunk_count(cin);
+  const int64_t total = (int64_t)kc * cout * 8;
+  ls::k_pack_weights<<<ls::grid_cap((total + 255) / 256, ls::kSmCount * 8), 256, 0,
+                       reinterpret_cast<cudaStream_t>(stream)>>>(w, cin, cout, transpose_flip, kc, packed);
+  return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
+}
+
+extern "C" ls_status ls_conv3x3_forward(const uint16_t* x, const uint16_t* packed, const float* bias,
+                                        const uint16_t* mask, int32_t relu, const ls_conv_shape* shape, uint16_t* y,
+                                        ls_stream_t stream) {
+  if (!shape) return LS_ERR_INVALID_ARG;
+  return ls::conv3x3_launch(x, packed, bias, mask, relu, shape->n, shape->h, shape->w, shape->cin, shape->cout, y,
+                            reinterpret_cast<cudaStream_t>(stream));
+}

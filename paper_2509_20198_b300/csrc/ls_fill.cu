@@ -110,6 +110,7 @@ struct FillArgs {
   const Rec* __restrict__ recs;      // packed samples
   const int32_t* __restrict__ tile_ids;
   int64_t n_out;
+  int64_t n_samples;  // records in recs
   int32_t tiles_x, tiles_y, tile_cm, res, cell_cm;
   int64_t R2;
   int32_t R;
@@ -117,15 +118,22 @@ struct FillArgs {
   double z_scale, z_offset;
   float* height;
   uint8_t* rgb;
+  float4* aux_hc;  // optional per texel: height (m), R, G, B (0..1, unrounded)
+  float* aux_d;    // optional per texel: distance to the nearest sample (cm)
 };
 
 __global__ void k_pack(ls_points s, int64_t n_tiles, int64_t x0, int64_t y0, int32_t tile_cm,
                        int32_t tiles_x, Rec* __restrict__ recs) {
+  // samples outside [0, s.n) (an inconsistent CSR) are reported, never touched
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < n_tiles; t += warps) {
     const int64_t q0 = s.tile_offsets[t], q1 = s.tile_offsets[t + 1];
     const int64_t tx = t % tiles_x, ty = t / tiles_x;
+    if (q0 < 0 || q1 < q0 || q1 > s.n) {
+      if (lane == 0) set_status(LS_ERR_INVALID_ARG);
+      continue;
+    }
     for (int64_t q = q0 + lane; q < q1; q += 32) {
       const int64_t lx = (int64_t)s.x[q] - x0, ly = (int64_t)s.y[q] - y0;
       if (lx < tx * tile_cm || lx >= (tx + 1) * tile_cm || ly < ty * tile_cm || ly >= (ty + 1) * tile_cm)
@@ -236,7 +244,8 @@ __device__ void nearest_far(const FillArgs& f, int tx, int ty, int cx, int cy, L
       for (int ux = tx - m; ux <= tx + m; ux += (edge_row ? 1 : 2 * m)) {
         if (ux < 0 || ux >= f.tiles_x) continue;
         const int64_t u = (int64_t)uy * f.tiles_x + ux;
-        for (int64_t q = f.toff[u]; q < f.toff[u + 1]; ++q) {
+        const int64_t q1 = f.toff[u + 1] < f.n_samples ? f.toff[u + 1] : f.n_samples;
+        for (int64_t q = f.toff[u] < 0 ? 0 : f.toff[u]; q < q1; ++q) {
           const Rec rc = f.recs[q];
           const int dx = rc.lx - cx, dy = rc.ly - cy;
           consider_nearest(a, (long long)dx * dx + (long long)dy * dy, rc);
@@ -268,6 +277,10 @@ __global__ void __launch_bounds__(kFillThreads) k_fill(FillArgs f) {
 
   for (int64_t o = blockIdx.x; o < f.n_out; o += gridDim.x) {
     const int t = f.tile_ids ? f.tile_ids[o] : (int)o;
+    if (t < 0 || t >= f.tiles_x * f.tiles_y) {  // uniform across the CTA
+      if (threadIdx.x == 0) set_status(LS_ERR_INVALID_ARG);
+      continue;
+    }
     const int tx = t % f.tiles_x, ty = t / f.tiles_x;
     // ---- stage the 3x3 neighbourhood (three contiguous CSR ranges)
     if (threadIdx.x == 0) {
@@ -277,8 +290,12 @@ __global__ void __launch_bounds__(kFillThreads) k_fill(FillArgs f) {
         const int uy = ty - 1 + k;
         rng_lo[k] = 0; rng_n[k] = 0;
         if (uy < 0 || uy >= f.tiles_y) continue;
-        const int64_t a0 = f.toff[(int64_t)uy * f.tiles_x + xa];
-        const int64_t a1 = f.toff[(int64_t)uy * f.tiles_x + xb + 1];
+        int64_t a0 = f.toff[(int64_t)uy * f.tiles_x + xa];
+        int64_t a1 = f.toff[(int64_t)uy * f.tiles_x + xb + 1];
+        if (a0 < 0 || a1 < a0 || a1 > f.n_samples) {  // inconsistent CSR: use nothing
+          set_status(LS_ERR_INVALID_ARG);
+          a0 = a1 = 0;
+        }
         rng_lo[k] = a0; rng_n[k] = a1 - a0;
         total += a1 - a0;
       }
@@ -345,6 +362,12 @@ __global__ void __launch_bounds__(kFillThreads) k_fill(FillArgs f) {
         h = __int_as_float(0x7fc00000);
         c3[0] = c3[1] = c3[2] = 0.f;
       }
+      if (f.aux_hc) {
+        const size_t ae = (size_t)o * res * res + (size_t)i * res + j;
+        f.aux_hc[ae] = make_float4(h, c3[0] * (256.0f / 65535.0f), c3[1] * (256.0f / 65535.0f),
+                                   c3[2] * (256.0f / 65535.0f));
+        f.aux_d[ae] = a.bd2 >= 0 ? sqrtf((float)a.bd2) : __int_as_float(0x7f800000);
+      }
       uint8_t q8[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -377,14 +400,18 @@ __global__ void __launch_bounds__(kFillThreads) k_fill(FillArgs f) {
 // ---------------------------------------------------------------------------------
 // tile update
 // ---------------------------------------------------------------------------------
-__global__ void k_update(ls_bins bins, const int32_t* __restrict__ tile_ids, int64_t n, double z_scale,
-                         double z_offset, float* __restrict__ height, uint8_t* __restrict__ rgb) {
+__global__ void k_update(ls_bins bins, const int32_t* __restrict__ tile_ids, int64_t n, int64_t n_tiles,
+                         double z_scale, double z_offset, float* __restrict__ height, uint8_t* __restrict__ rgb) {
   const int64_t cpt = (int64_t)bins.cells * bins.cells;
   const int64_t total = n * cpt;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t o = e / cpt, c = e - o * cpt;
     const int64_t t = tile_ids ? (int64_t)tile_ids[o] : o;
+    if (t < 0 || t >= n_tiles) {
+      set_status(LS_ERR_INVALID_ARG);
+      continue;
+    }
     const int64_t src = t * cpt + c;
     const uint32_t cnt = bins.count[src];
     if (cnt == 0u) continue;
@@ -419,9 +446,12 @@ extern "C" ls_status ls_extract_samples(const ls_points* pts, int64_t n_tiles, i
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 
-extern "C" ls_status ls_fill_sparse(const ls_points* samples, const ls_region* region,
-                                    const ls_fill_params* params, const int32_t* tile_ids, int64_t n_out,
-                                    float* height, uint8_t* rgb, ls_stream_t stream) {
+namespace ls {
+// Validated launch of the Gaussian fill (optionally with the per-texel auxiliary
+// outputs of the learned filler's input raster).  Returns the packed records.
+ls_status fill_launch(const ls_points* samples, const ls_region* region, const ls_fill_params* params,
+                      const int32_t* tile_ids, int64_t n_out, float* height, uint8_t* rgb, float4* aux_hc,
+                      float* aux_d, cudaStream_t s, const void** recs_out) {
   if (!samples || !region || !params || !height || !rgb || n_out < 0) return LS_ERR_INVALID_ARG;
   if (!samples->tile_offsets) return LS_ERR_INVALID_ARG;
   if (samples->n > 0 && (!samples->x || !samples->y || !samples->z || !samples->r || !samples->g || !samples->b))
@@ -438,9 +468,9 @@ extern "C" ls_status ls_fill_sparse(const ls_points* samples, const ls_region* r
   if (params->radius_cm < 1 || params->radius_cm > region->tile_cm) return LS_ERR_UNSUPPORTED;
   if (!(params->sigma_cm > 0.f)) return LS_ERR_INVALID_ARG;
   if (n_out == 0) return LS_OK;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   Rec* recs = static_cast<Rec*>(workspace(kWsFillPacked, (size_t)(samples->n > 0 ? samples->n : 1) * sizeof(Rec)));
   if (!recs) return LS_ERR_NO_MEMORY;
+  if (recs_out) *recs_out = recs;
   if (samples->n > 0)
     k_pack<<<grid_cap((T + 7) / 8, kSmCount * 16), 256, 0, s>>>(*samples, T, region->x0_cm, region->y0_cm,
                                                                  region->tile_cm, region->tiles_x, recs);
@@ -449,6 +479,7 @@ extern "C" ls_status ls_fill_sparse(const ls_points* samples, const ls_region* r
   f.recs = recs;
   f.tile_ids = tile_ids;
   f.n_out = n_out;
+  f.n_samples = samples->n;
   f.tiles_x = region->tiles_x;
   f.tiles_y = region->tiles_y;
   f.tile_cm = region->tile_cm;
@@ -461,6 +492,8 @@ extern "C" ls_status ls_fill_sparse(const ls_points* samples, const ls_region* r
   f.z_offset = region->z_offset;
   f.height = height;
   f.rgb = rgb;
+  f.aux_hc = aux_hc;
+  f.aux_d = aux_d;
   static bool attr_set[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return LS_ERR_CUDA;
@@ -473,6 +506,14 @@ extern "C" ls_status ls_fill_sparse(const ls_points* samples, const ls_region* r
   k_fill<<<grid_cap(n_out, kSmCount * 2), kFillThreads, kStageCap * sizeof(Rec), s>>>(f);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
+}  // namespace ls
+
+extern "C" ls_status ls_fill_sparse(const ls_points* samples, const ls_region* region,
+                                    const ls_fill_params* params, const int32_t* tile_ids, int64_t n_out,
+                                    float* height, uint8_t* rgb, ls_stream_t stream) {
+  return ls::fill_launch(samples, region, params, tile_ids, n_out, height, rgb, nullptr, nullptr,
+                         reinterpret_cast<cudaStream_t>(stream), nullptr);
+}
 
 extern "C" ls_status ls_update_tile(const ls_bins* bins, const ls_region* region, const int32_t* tile_ids,
                                     int64_t n, float* height, uint8_t* rgb, ls_stream_t stream) {
@@ -480,8 +521,10 @@ extern "C" ls_status ls_update_tile(const ls_bins* bins, const ls_region* region
   if (!bins->count || !bins->zsum || !bins->rsum || !bins->gsum || !bins->bsum || bins->cells <= 0)
     return LS_ERR_INVALID_ARG;
   if (n == 0) return LS_OK;
+  if (!tile_ids && n > (int64_t)region->tiles_x * region->tiles_y) return LS_ERR_INVALID_ARG;
   const int64_t total = n * bins->cells * bins->cells;
   k_update<<<grid_cap((total + 255) / 256, kSmCount * 16), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-      *bins, tile_ids, n, region->z_scale, region->z_offset, height, rgb);
+      *bins, tile_ids, n, (int64_t)region->tiles_x * region->tiles_y, region->z_scale, region->z_offset,
+      height, rgb);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }

@@ -187,31 +187,40 @@ def region_samples(seed: int, region: Region, counts, chunk: int = CHUNK):
     ns = (counts + chunk - 1) // chunk
     offs = np.zeros(len(counts) + 1, dtype=np.int64)
     offs[1:] = np.cumsum(ns)
-    cols = {k: [] for k in ("x", "y", "z", "r", "g", "b")}
-    for t, n in enumerate(counts):
-        n = int(n)
-        if n == 0:
-            continue
-        pts = _points_at(seed, region, t, n, np.arange(0, n, chunk, dtype=np.int64))
-        for i, k in enumerate(cols):
-            cols[k].append(pts[i])
+    total = int(offs[-1])
+    tile = np.repeat(np.arange(len(counts), dtype=np.int64), ns)
+    k = np.arange(total, dtype=np.int64) - offs[tile]
     out = {}
-    dt = {"x": np.int32, "y": np.int32, "z": np.int32,
-          "r": np.uint16, "g": np.uint16, "b": np.uint16}
-    for k, v in cols.items():
-        out[k] = np.concatenate(v) if v else np.zeros(0, dtype=dt[k])
+    names = ("x", "y", "z", "r", "g", "b")
+    step = 1 << 20
+    parts = [_points_at(seed, region, tile[a:a + step], counts[tile[a:a + step]], k[a:a + step] * chunk)
+             for a in range(0, total, step)]
+    dt = {"x": np.int32, "y": np.int32, "z": np.int32, "r": np.uint16, "g": np.uint16, "b": np.uint16}
+    for i, name in enumerate(names):
+        out[name] = np.concatenate([p[i] for p in parts]) if parts else np.zeros(0, dtype=dt[name])
     out["tile_offsets"] = offs
     return out
 
 
-def _points_at(seed: int, region: Region, tile: int, n_points: int, idx):
-    """Stream points at arbitrary positions idx of tile `tile` (vectorised)."""
+def _strip_of_multi(idx, n_points):
+    """strip_of for per-point stream positions and per-point tile sizes."""
+    q, rem = np.divmod(n_points, STRIPS)
+    big = rem * (q + 1)
+    qs = np.maximum(q, 1)
+    return np.where(q == 0, idx, np.where(idx < big, idx // (q + 1), rem + (idx - big) // qs))
+
+
+def _points_at(seed: int, region: Region, tile, n_points, idx):
+    """Stream points at positions idx of tiles `tile` holding n_points points each
+    (tile and n_points may be scalars or arrays broadcast against idx)."""
     idx = np.asarray(idx, dtype=np.int64)
+    tile = np.broadcast_to(np.asarray(tile, dtype=np.int64), idx.shape)
+    n_points = np.broadcast_to(np.asarray(n_points, dtype=np.int64), idx.shape)
     tx, ty = tile % region.tiles_x, tile // region.tiles_x
-    key = H(np.uint64(seed) ^ np.uint64(SALT_POINTS), np.uint64(tile))
+    key = H(np.uint64(seed) ^ np.uint64(SALT_POINTS), tile.astype(np.uint64))
     base = H(key, idx.view(np.uint64))
     lane = lambda k: H(base, np.uint64(k))        # noqa: E731
-    s = strip_of(idx, n_points)
+    s = _strip_of_multi(idx, n_points)
     lx = (lane(LANE_X) % np.uint64(region.tile_cm)).astype(np.int64)
     ly = s * STRIP_CM + (lane(LANE_Y) % np.uint64(STRIP_CM)).astype(np.int64)
     gx = region.x0_cm + tx * region.tile_cm + lx

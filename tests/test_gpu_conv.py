@@ -1,0 +1,108 @@
+"""GPU parity of the tcgen05 3x3 convolution against the FP64 oracle conv evaluated on
+the same bf16-rounded operands.  Tolerance: the output is rounded to bf16 (relative
+2^-9) after an FP32 accumulation of up to 1728 products, so
+|gpu - ref| <= 2^-7 |ref| + 2^-9 max|ref| is required elementwise."""
+import numpy as np
+import pytest
+
+from oracle import unet as U
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_bits(a):
+    """Round float32 to bfloat16 (nearest even); returns uint16 bit patterns."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
+    return r
+
+
+def bf16_to_f64(bits):
+    return (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2509_20198_b300 import build, _native
+    build.build_library()
+    return _native
+
+
+def _run_conv(N, x_bits, w, b, mask_bits, relu, shape, flip=False):
+    import ctypes
+    import torch
+    n, h, wd, cin, cout = shape
+    L = N.lib()
+    pk = torch.empty(L.ls_conv3x3_packed_elems(cin, cout), dtype=torch.int16, device="cuda")
+    wt = torch.from_numpy(np.ascontiguousarray(w, np.float32)).cuda()
+    N.check("pack", L.ls_conv3x3_pack(ctypes.c_void_p(wt.data_ptr()), cin, cout, int(flip),
+                                      ctypes.c_void_p(pk.data_ptr()), None))
+    xt = torch.from_numpy(x_bits.view(np.int16)).cuda()
+    bt = None if b is None else torch.from_numpy(np.asarray(b, np.float32)).cuda()
+    mt = None if mask_bits is None else torch.from_numpy(mask_bits.view(np.int16)).cuda()
+    y = torch.empty((n, h, wd, cout), dtype=torch.int16, device="cuda")
+    sh = N.LsConvShape(n, h, wd, cin, cout)
+    N.check("conv", L.ls_conv3x3_forward(ctypes.c_void_p(xt.data_ptr()), ctypes.c_void_p(pk.data_ptr()),
+                                         None if bt is None else ctypes.c_void_p(bt.data_ptr()),
+                                         None if mt is None else ctypes.c_void_p(mt.data_ptr()),
+                                         int(relu), ctypes.byref(sh), ctypes.c_void_p(y.data_ptr()), None))
+    torch.cuda.synchronize()
+    assert L.ls_last_error() == 0
+    return bf16_to_f64(y.cpu().numpy().view(np.uint16))
+
+
+def _close(g, r):
+    tol = 2.0 ** -7 * np.abs(r) + 2.0 ** -9 * np.abs(r).max()
+    bad = np.abs(g - r) > tol
+    assert not bad.any(), f"{bad.sum()} of {bad.size} outside tolerance, max err {np.abs(g - r).max():.3e}"
+
+
+SHAPES = [
+    (2, 64, 64, 8, 32),     # first layer (5 channels padded to 8)
+    (2, 32, 32, 32, 64),
+    (1, 16, 16, 64, 128),
+    (2, 32, 32, 192, 64),   # decoder concat width
+    (1, 64, 64, 96, 32),
+    (16, 4, 4, 8, 16),      # several whole images per 128-pixel tile
+    (2, 16, 16, 128, 256),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_forward_bias_relu(lib, shape):
+    n, h, w, cin, cout = shape
+    rng = np.random.default_rng(cin * 1000 + cout)
+    x = bf16_bits(rng.standard_normal((n, h, w, cin)).astype(np.float32))
+    wt = (rng.standard_normal((cout, 3, 3, cin)) * np.sqrt(2.0 / (9 * cin))).astype(np.float32)
+    b = (rng.standard_normal(cout) * 0.1).astype(np.float32)
+    g = _run_conv(lib, x, wt, b, None, True, shape)
+    wq = bf16_to_f64(bf16_bits(wt))
+    ref = U.relu(U.conv(bf16_to_f64(x), wq, b.astype(np.float64)))
+    _close(g, ref)
+
+
+def test_mask_epilogue_and_no_bias(lib):
+    shape = (2, 32, 32, 64, 32)
+    n, h, w, cin, cout = shape
+    rng = np.random.default_rng(3)
+    x = bf16_bits(rng.standard_normal((n, h, w, cin)).astype(np.float32))
+    wt = (rng.standard_normal((cout, 3, 3, cin)) * 0.05).astype(np.float32)
+    mask_f = rng.standard_normal((n, h, w, cout)).astype(np.float32)
+    mask_f[mask_f < -1.0] = 0.0
+    mask = bf16_bits(mask_f)
+    g = _run_conv(lib, x, wt, None, mask, False, shape)
+    ref = U.conv(bf16_to_f64(x), bf16_to_f64(bf16_bits(wt)), np.zeros(cout)) * (bf16_to_f64(mask) > 0)
+    _close(g, ref)
+
+
+@pytest.mark.parametrize("shape", [(2, 32, 32, 64, 32), (1, 64, 64, 32, 96)])
+def test_input_gradient_via_flipped_weights(lib, shape):
+    """dX of a conv (c_in -> c_out) = conv(dY, W') with the transposed, flipped pack."""
+    n, h, w, ci, co = shape          # original layer: ci -> co
+    rng = np.random.default_rng(ci + co)
+    dy = bf16_bits(rng.standard_normal((n, h, w, co)).astype(np.float32))
+    wt = (rng.standard_normal((co, 3, 3, ci)) * 0.05).astype(np.float32)
+    g = _run_conv(lib, dy, wt, None, None, False, (n, h, w, co, ci), flip=True)
+    x_dummy = np.zeros((n, h, w, ci))
+    dx, _, _ = U.conv_backward(x_dummy, bf16_to_f64(bf16_bits(wt)), bf16_to_f64(dy))
+    _close(g, dx)

@@ -1,0 +1,206 @@
+"""GPU parity of the learned filler: tensor-core forward and backward against the
+FP64 oracle on the same bf16-rounded weights and inputs, against torch autograd as an
+independent reference gradient, plus loss, AdamW, input raster, targets and the
+learned fill with its Gaussian fallback.
+
+Tolerances (derived from the arithmetic): every activation and activation gradient is
+stored in bf16 (relative rounding 2^-9) through up to 11 layers, so network outputs
+and parameter gradients are compared by relative L2 error <= 3e-2 / 6e-2 and cosine
+similarity >= 0.999 / 0.995; the loss and AdamW run in fp32 and match to 1e-5."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import unet as U
+from tests.helpers import to_device
+from tests.test_gpu_conv import bf16_bits, bf16_to_f64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lsb():
+    import paper_2509_20198_b300 as lsb
+    from paper_2509_20198_b300 import build
+    build.build_library()
+    return lsb
+
+
+def _flat(params, layers):
+    return np.concatenate([np.concatenate([params[n + ".w"].ravel(), params[n + ".b"].ravel()])
+                           for n, *_ in layers]).astype(np.float32)
+
+
+def _setup(lsb, widths, n, seed):
+    import torch
+    layers = U.layer_table(widths)
+    rng = np.random.default_rng(seed)
+    params = U.init_params(seed, layers)
+    for k in params:
+        if k.endswith(".b"):
+            params[k] = rng.standard_normal(params[k].shape) * 0.05
+    f = lsb.Filler(widths=widths, res=64, max_batch=max(n, 2))
+    assert f.n_params == U.param_count(layers)
+    flat = _flat(params, layers)
+    f.params.copy_(torch.from_numpy(flat))
+    f.load()
+    x5 = rng.standard_normal((n, 64, 64, 5)).astype(np.float32) * 0.5
+    x5[..., 2] = (rng.random((n, 64, 64)) < 0.02)
+    xb = bf16_bits(np.concatenate([x5, np.zeros((n, 64, 64, 3), np.float32)], axis=3))
+    # oracle operands: bf16-rounded 3x3 weights (the tensor-core operands), fp32 head
+    q = {}
+    for name, ci, co, k in layers:
+        w = params[name + ".w"].astype(np.float32)
+        q[name + ".w"] = bf16_to_f64(bf16_bits(w)) if k == 3 else w.astype(np.float64)
+        q[name + ".b"] = params[name + ".b"].astype(np.float32).astype(np.float64)
+    xo = bf16_to_f64(xb)[..., :5]
+    return f, layers, params, q, xb, xo
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def _cos(a, b):
+    return float((a * b).sum() / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
+
+
+@pytest.mark.parametrize("widths,n", [((32, 64, 128), 2), ((32, 64), 3)])
+def test_forward_matches_oracle(lsb, widths, n):
+    import torch
+    f, layers, params, q, xb, xo = _setup(lsb, widths, n, 1)
+    y = f.forward(torch.from_numpy(xb.view(np.int16)).cuda()).cpu().numpy().astype(np.float64)
+    assert lsb.last_error() == 0
+    yr, _ = U.forward(q, xo, layers)
+    assert _rel(y, yr) < 3e-2 and _cos(y.ravel(), yr.ravel()) > 0.999
+
+
+def test_backward_matches_oracle_and_torch(lsb):
+    import torch
+    widths, n = (32, 64, 128), 2
+    f, layers, params, q, xb, xo = _setup(lsb, widths, n, 2)
+    xt = torch.from_numpy(xb.view(np.int16)).cuda()
+    y = f.forward(xt)
+    rng = np.random.default_rng(5)
+    dy = rng.standard_normal(y.shape).astype(np.float32) * 1e-3
+    g = f.backward(torch.from_numpy(dy).cuda()).cpu().numpy().astype(np.float64)
+    assert lsb.last_error() == 0
+    yr, cache = U.forward(q, xo, layers)
+    gr = U.backward(q, cache, dy.astype(np.float64), layers)
+    # torch autograd (fp64, CPU) on the same operands: an independent reference gradient
+    tp = {k: torch.tensor(v, dtype=torch.float64, requires_grad=True) for k, v in q.items()}
+    h = torch.tensor(xo).permute(0, 3, 1, 2)
+    skips = []
+    L = len(widths)
+    for l in range(1, L + 1):
+        if l > 1:
+            h = torch.nn.functional.max_pool2d(h, 2)
+        for s in "ab":
+            w = tp[f"e{l}{s}.w"].permute(0, 3, 1, 2)
+            h = torch.relu(torch.nn.functional.conv2d(h, w, tp[f"e{l}{s}.b"], padding=1))
+        skips.append(h)
+    for l in range(L - 1, 0, -1):
+        h = torch.cat([torch.nn.functional.interpolate(h, scale_factor=2, mode="nearest"), skips[l - 1]], 1)
+        for s in "ab":
+            w = tp[f"d{l}{s}.w"].permute(0, 3, 1, 2)
+            h = torch.relu(torch.nn.functional.conv2d(h, w, tp[f"d{l}{s}.b"], padding=1))
+    yt = torch.nn.functional.conv2d(h, tp["head.w"].permute(0, 3, 1, 2), tp["head.b"]).permute(0, 2, 3, 1)
+    (yt * torch.tensor(dy, dtype=torch.float64)).sum().backward()
+    off = 0
+    for name, ci, co, k in layers:
+        nw = co * k * k * ci
+        gw, gb = g[off:off + nw].reshape(co, k, k, ci), g[off + nw:off + nw + co]
+        off += nw + co
+        for ref, msg in ((gr, "oracle"), ({kk: tp[kk].grad.numpy() for kk in tp}, "torch")):
+            assert _rel(gw, ref[name + ".w"]) < 6e-2, (name, msg, _rel(gw, ref[name + ".w"]))
+            assert _cos(gw.ravel(), ref[name + ".w"].ravel()) > 0.995, (name, msg)
+            assert _rel(gb, ref[name + ".b"]) < 6e-2, (name, msg, _rel(gb, ref[name + ".b"]))
+
+
+def test_loss_and_adamw_match_oracle(lsb):
+    import torch
+    rng = np.random.default_rng(7)
+    n = 3
+    y = (rng.standard_normal((n, 64, 64, 5)) * 0.3).astype(np.float32)
+    base = rng.standard_normal((n, 64, 64, 4)).astype(np.float32) * 0.2
+    tgt = rng.standard_normal((n, 64, 64, 4)).astype(np.float32) * 0.2
+    tgt[0, :4, :4, 0] += 3.0     # clipped squared errors
+    mask = (rng.random((n, 64, 64)) > 0.2).astype(np.uint8)
+    T = lambda a: torch.from_numpy(a).cuda()  # noqa: E731
+    loss, dy = lsb.filler_loss(T(y), T(base), T(tgt), T(mask))
+    lr_, dyr, parts = U.loss_and_grad(y.astype(np.float64), base[..., 0].astype(np.float64),
+                                      base[..., 1:].astype(np.float64), tgt[..., 0].astype(np.float64),
+                                      tgt[..., 1:].astype(np.float64), mask)
+    l4 = loss.cpu().numpy()
+    assert l4[0] == pytest.approx(lr_, rel=1e-5)
+    assert l4[1] == pytest.approx(parts["height"], rel=1e-5)
+    np.testing.assert_allclose(dy.cpu().numpy(), dyr, rtol=1e-5, atol=1e-12)
+    # AdamW
+    p = rng.standard_normal(1000).astype(np.float32)
+    pg, pm, pv = T(p.copy()), T(np.zeros(1000, np.float32)), T(np.zeros(1000, np.float32))
+    po, mo, vo = p.astype(np.float64), np.zeros(1000), np.zeros(1000)
+    for step in range(1, 4):
+        gr = rng.standard_normal(1000).astype(np.float32)
+        lsb.adamw_step(pg, T(gr), pm, pv, step, lr=1e-3)
+        U.adamw_step(po, gr.astype(np.float64), mo, vo, step, lr=1e-3)
+    np.testing.assert_allclose(pg.cpu().numpy(), po, rtol=1e-5, atol=1e-6)
+
+
+def test_input_raster_and_targets_match_oracle(lsb):
+    import torch
+    region = synth.Region(tiles_x=4, tiles_y=3)
+    counts = synth.uniform_counts(12, 4.0)
+    counts[5] = 2_000_000
+    s = synth.region_samples(21, region, counts)
+    tiles = np.array([5, 0, 11], np.int64)
+    inp = lsb.learned_inputs(to_device(s), region, torch.as_tensor(tiles))
+    torch.cuda.synchronize()
+    assert lsb.last_error() == 0
+    ref = oracle.fill_sparse(s, region, tile_ids=tiles)
+    x = bf16_to_f64(inp["x"].cpu().numpy().view(np.uint16))
+    for o, t in enumerate(tiles):
+        tx, ty = t % region.tiles_x, t // region.tiles_x
+        a, b = s["tile_offsets"][t], s["tile_offsets"][t + 1]
+        xr, bc, cz, r = U.tile_inputs(64, 64000, 1000, region.x0_cm + tx * 64000, region.y0_cm + ty * 64000,
+                                      0.01, 0.0, 12000, s["x"][a:b], s["y"][a:b], s["z"][a:b], s["r"][a:b],
+                                      s["g"][a:b], s["b"][a:b], ref["height"][o], ref["rgbf"][o],
+                                      ref["nearest_d2"][o])
+        assert inp["cz"][o].item() == pytest.approx(cz, abs=1e-3)
+        # bf16 channels: relative 2^-8 plus the fp32 fill error (1e-3 m / 320 m)
+        np.testing.assert_allclose(x[o, ..., :5], xr, rtol=2 ** -8, atol=2e-5)
+        assert (x[o, ..., 5:] == 0).all()
+        np.testing.assert_allclose(inp["base"][o, ..., 1:].cpu().numpy(), bc, atol=1e-4)
+    # targets from the full-resolution bins of tile 5
+    pts = synth.region_points(21, region, np.where(np.arange(12) == 5, counts, 0))
+    (b64,), _ = lsb.bin_points(to_device(pts), region, levels=(64,))
+    tgt, mask = lsb.learned_targets(b64, region, torch.as_tensor(tiles[:1]), inp["cz"][:1])
+    ob = oracle.bin_points(pts, region, 64)
+    cnt = ob["count"][5]
+    m = cnt > 0
+    assert (mask[0].cpu().numpy().astype(bool) == m).all()
+    zm = ob["zsum"][5][m] / cnt[m] * 0.01
+    np.testing.assert_allclose(tgt[0, ..., 0].cpu().numpy()[m], (zm - inp["cz"][0].item()) / 320.0, atol=1e-6)
+    np.testing.assert_allclose(tgt[0, ..., 1].cpu().numpy()[m], ob["rsum"][5][m] / cnt[m] / 65535.0, atol=1e-6)
+
+
+def test_fill_learned_fallback_and_finish(lsb):
+    import torch
+    region = synth.Region(tiles_x=3, tiles_y=3)
+    counts = synth.uniform_counts(9, 4.0)
+    s = to_device(synth.region_samples(22, region, counts))
+    f = lsb.Filler(max_batch=4)
+    f.params.normal_(0, 0.02)
+    f.load()
+    tiles = torch.arange(9, dtype=torch.int32)
+    gh, gc = lsb.fill_sparse(s, region)
+    h0, c0, b0, fb0 = lsb.fill_learned(f, s, region, tiles, max_err_m=-1.0)     # everything falls back
+    assert (fb0 == 1).all() and torch.equal(h0, gh) and torch.equal(c0, gc)
+    h1, c1, b1, fb1 = lsb.fill_learned(f, s, region, tiles, max_err_m=1e30)     # nothing falls back
+    assert (fb1 == 0).all()
+    inp = lsb.learned_inputs(s, region, tiles)
+    y = f.forward(inp["x"])
+    h2, c2, b2, _ = lsb.learned_finish(y, inp, region, max_err_m=1e30)
+    assert torch.allclose(h1, h2) and torch.equal(c1, c2)
+    torch.cuda.synchronize()
+    assert lsb.last_error() == 0
