@@ -237,19 +237,13 @@ __device__ void evict_rows(const BinArgs& a, Smem& s, Meta& m, int ra, int rb, i
   const int nr = rb - ra;
   if (nr <= 0) return;
   const int W = a.W;
+  // claim (0 -> 1) without waiting: a CTA never waits while it holds an unpublished
+  // claim, so two CTAs flushing overlapping rows cannot wait on each other
   if (threadIdx.x < nr) {
     const int G = ra + threadIdx.x;
     const int slot = G & (W - 1);
     int mode = 0;
-    if (m.touched[slot]) {
-      uint32_t* st = &a.row_state[G];
-      if (atomicCAS(st, 0u, 1u) == 0u) {
-        mode = 1;
-      } else {
-        wait_written(st);
-        mode = 2;
-      }
-    }
+    if (m.touched[slot]) mode = (atomicCAS(&a.row_state[G], 0u, 1u) == 0u) ? 1 : 2;
     m.mode[threadIdx.x] = mode;
   }
   // coarse ring: make room for the coarse rows of [ra, rb)
@@ -310,10 +304,37 @@ __device__ void evict_rows(const BinArgs& a, Smem& s, Meta& m, int ra, int rb, i
     }
     __syncthreads();
   }
-  // fine rows: store (claimed) or merge, then reset the shared cells
+  // fine rows claimed here: plain stores of every cell (empty cells get sentinels)
   for (int rr = 0; rr < nr; ++rr) {
-    const int mode = m.mode[rr];
-    if (mode == 0) continue;
+    if (m.mode[rr] != 1) continue;
+    const int G = ra + rr;
+    const int slot = G & (W - 1);
+    const int64_t base = (int64_t)G * a.cells;
+    for (int c = threadIdx.x; c < a.cells; c += blockDim.x) {
+      const int si = slot * a.cells + c;
+      const unsigned long long bcv = s.bc[si], rgv = s.rg[si];
+      a.count[base + c] = (unsigned)(bcv >> 32);
+      a.zsum[base + c] = (long long)s.zs[si];
+      a.zmin[base + c] = s.mn[si];
+      a.zmax[base + c] = s.mx[si];
+      a.rsum[base + c] = rgv & 0xffffffffull;
+      a.gsum[base + c] = rgv >> 32;
+      a.bsum[base + c] = bcv & 0xffffffffull;
+      s.rg[si] = 0ull; s.bc[si] = 0ull; s.zs[si] = 0ull; s.mn[si] = INT_MAX; s.mx[si] = INT_MIN;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  // publish, then (holding no claim any more) wait for rows another CTA is writing
+  if (threadIdx.x < nr) {
+    const int G = ra + threadIdx.x;
+    if (m.mode[threadIdx.x] == 1) atomicExch(&a.row_state[G], 2u);
+    else if (m.mode[threadIdx.x] == 2) wait_written(&a.row_state[G]);
+  }
+  __syncthreads();
+  // rows written first by another CTA: merge with global atomics
+  for (int rr = 0; rr < nr; ++rr) {
+    if (m.mode[rr] != 2) continue;
     const int G = ra + rr;
     const int slot = G & (W - 1);
     const int64_t base = (int64_t)G * a.cells;
@@ -321,33 +342,14 @@ __device__ void evict_rows(const BinArgs& a, Smem& s, Meta& m, int ra, int rb, i
       const int si = slot * a.cells + c;
       const unsigned long long bcv = s.bc[si], rgv = s.rg[si];
       const unsigned cnt = (unsigned)(bcv >> 32);
-      const long long zsum = (long long)s.zs[si];
-      const int zmn = s.mn[si], zmx = s.mx[si];
-      if (mode == 1) {
-        a.count[base + c] = cnt;
-        a.zsum[base + c] = zsum;
-        a.zmin[base + c] = zmn;
-        a.zmax[base + c] = zmx;
-        a.rsum[base + c] = rgv & 0xffffffffull;
-        a.gsum[base + c] = rgv >> 32;
-        a.bsum[base + c] = bcv & 0xffffffffull;
-      } else if (cnt) {
-        merge_fine(a, base + c, cnt, zsum, zmn, zmx, rgv & 0xffffffffull, rgv >> 32, bcv & 0xffffffffull);
-      }
-      s.rg[si] = 0ull;
-      s.bc[si] = 0ull;
-      s.zs[si] = 0ull;
-      s.mn[si] = INT_MAX;
-      s.mx[si] = INT_MIN;
+      if (cnt)
+        merge_fine(a, base + c, cnt, (long long)s.zs[si], s.mn[si], s.mx[si], rgv & 0xffffffffull, rgv >> 32,
+                   bcv & 0xffffffffull);
+      s.rg[si] = 0ull; s.bc[si] = 0ull; s.zs[si] = 0ull; s.mn[si] = INT_MAX; s.mx[si] = INT_MIN;
     }
   }
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x < nr) {
-    const int G = ra + threadIdx.x;
-    if (m.mode[threadIdx.x] == 1) atomicExch(&a.row_state[G], 2u);
-    m.touched[G & (W - 1)] = 0;
-  }
+  if (threadIdx.x < nr) m.touched[(ra + threadIdx.x) & (W - 1)] = 0;
   __syncthreads();
 }
 

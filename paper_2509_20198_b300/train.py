@@ -1,0 +1,163 @@
+"""Training and evaluation of the learned filler on pairs the method generates itself.
+
+Sec. 3.4 trains on ground-truth heightmaps made by taking the mean of all points that
+fall onto a texel, with chunk points simulated as a sparse subsample; the pairs here
+are (input raster of the chunk samples of a tile and its 8 neighbours, per-texel mean
+of the tile's full-resolution points), both computed by this library's kernels.  The
+optimiser is AdamW with a step schedule (Sec. 3.4); every forward and backward pass
+runs in the library's tensor-core kernels through ``FillerFn``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import torch
+
+from . import (Filler, FillerFn, adamw_step, bin_points, filler_loss, learned_inputs, learned_targets,
+               learned_finish)
+
+
+class FillerLossFn(torch.autograd.Function):
+    """Scalar loss of Sec. 3.4 (masked, clipped MSE + bound term); backward returns the
+    kernel-computed dL/dy."""
+
+    @staticmethod
+    def forward(ctx, y, base, target, mask, bound_weight):
+        loss, dy = filler_loss(y, base, target, mask, bound_weight)
+        ctx.save_for_backward(dy)
+        ctx.parts = loss
+        return loss[0].clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        (dy,) = ctx.saved_tensors
+        return dy * g, None, None, None, None
+
+
+@dataclasses.dataclass
+class TileSet:
+    x: torch.Tensor        # bf16 bits int16 [n, res, res, 8]
+    base: torch.Tensor     # [n, res, res, 4]
+    target: torch.Tensor   # [n, res, res, 4]
+    mask: torch.Tensor     # uint8 [n, res, res]
+    cz: torch.Tensor       # [n]
+    fill_height: torch.Tensor
+    fill_rgb: torch.Tensor
+
+    def __len__(self):
+        return self.x.shape[0]
+
+
+def synthetic_tiles(n_tiles, seed0, block=16, density=(3.0, 6.0), device="cuda"):
+    """Pairs on seeded synthetic terrain: regions of (block+2)^2 tiles, one terrain seed
+    each; inputs use the samples of all tiles, targets the full points of the inner
+    block x block tiles only."""
+    import synth
+    import synth.gpu as sg
+    parts = []
+    made, r = 0, 0
+    while made < n_tiles:
+        seed = seed0 + r
+        r += 1
+        side = block + 2
+        region = synth.Region(tiles_x=side, tiles_y=side)
+        rng = np.random.default_rng(seed)
+        dens = rng.uniform(density[0], density[1], side * side)
+        counts = np.rint(dens * 640 * 640).astype(np.int64)
+        inner = np.array([(ty * side + tx) for ty in range(1, side - 1) for tx in range(1, side - 1)], np.int64)
+        samples = sg.region_samples(seed, region, counts, device=device)
+        ids = torch.as_tensor(inner, dtype=torch.int32, device=device)
+        inp = learned_inputs(samples, region, ids)
+        full = np.zeros_like(counts)
+        full[inner] = counts[inner]
+        pts = sg.region_points(seed, region, full, device=device)
+        (b64,), _ = bin_points(pts, region, levels=(64,))
+        target, mask = learned_targets(b64, region, ids, inp["cz"])
+        del pts, b64
+        take = min(len(inner), n_tiles - made)
+        parts.append(TileSet(inp["x"][:take], inp["base"][:take], target[:take], mask[:take], inp["cz"][:take],
+                             inp["fill_height"][:take], inp["fill_rgb"][:take]))
+        made += take
+    cat = lambda k: torch.cat([getattr(p, k) for p in parts])  # noqa: E731
+    return TileSet(*[cat(f.name) for f in dataclasses.fields(TileSet)])
+
+
+def train(filler: Filler, data: TileSet, epochs=20, batch=256, lr=5e-4, weight_decay=1e-2, betas=(0.9, 0.999),
+          eps=1e-5, milestones=(0.6, 0.85), gamma=0.1, bound_weight=0.1, seed=0, log=None):
+    """AdamW training with a step schedule; returns the per-epoch mean losses."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    p = filler.params
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    steps_per_epoch = max(1, len(data) // batch)
+    total = epochs * steps_per_epoch
+    step = 0
+    history = []
+    for ep in range(epochs):
+        order = torch.randperm(len(data), generator=g).to(p.device)
+        acc = torch.zeros((), device=p.device)
+        for k in range(steps_per_epoch):
+            idx = order[k * batch:(k + 1) * batch]
+            x = data.x[idx].contiguous()
+            params = p.detach().requires_grad_(True)
+            y = FillerFn.apply(params, x, filler)
+            loss = FillerLossFn.apply(y, data.base[idx].contiguous(), data.target[idx].contiguous(),
+                                      data.mask[idx].contiguous(), bound_weight)
+            loss.backward()
+            step += 1
+            frac = step / total
+            cur = lr * (gamma ** sum(frac > mm for mm in milestones))
+            adamw_step(p, params.grad, m, v, step, lr=cur, betas=betas, eps=eps, weight_decay=weight_decay)
+            acc += loss.detach()
+        history.append(float(acc.item()) / steps_per_epoch)
+        if log:
+            log(f"epoch {ep + 1}/{epochs} loss {history[-1]:.6f}")
+    filler.load()
+    return history
+
+
+@torch.no_grad()
+def evaluate(filler: Filler, data: TileSet, region_tile_cm=64000, z_scale=0.01, batch=None):
+    """Height RMSE (m) and colour RMSE (8-bit levels) against the full-resolution means
+    for the learned fill and the plain Gaussian fill, on texels with ground truth."""
+    import types
+    batch = batch or filler.max_batch
+    r = 0.5 * region_tile_cm * z_scale
+    reg = types.SimpleNamespace(x0_cm=0, y0_cm=0, tile_cm=region_tile_cm, tiles_x=1, tiles_y=1,
+                                z_scale=z_scale, z_offset=0.0)
+    se_l = se_g = se_lc = se_gc = 0.0
+    cnt = 0.0
+    fallbacks = 0
+    for a in range(0, len(data), batch):
+        sl = slice(a, a + batch)
+        y = filler.forward(data.x[sl].contiguous())
+        inp = {"base": data.base[sl].contiguous(), "cz": data.cz[sl].contiguous(),
+               "fill_height": data.fill_height[sl].contiguous(), "fill_rgb": data.fill_rgb[sl].contiguous()}
+        h, c, bound, fb = learned_finish(y, inp, reg, max_err_m=math.inf)
+        msk = data.mask[sl].bool()
+        th = data.target[sl][..., 0] * r + data.cz[sl][:, None, None]
+        tc = data.target[sl][..., 1:] * 255.0
+        se_l += float(((h - th)[msk] ** 2).sum())
+        se_g += float(((data.fill_height[sl] - th)[msk] ** 2).sum())
+        se_lc += float(((c.float() - tc)[msk] ** 2).sum())
+        se_gc += float(((data.fill_rgb[sl].float() - tc)[msk] ** 2).sum())
+        cnt += float(msk.sum())
+        fallbacks += int((bound > 2.0).sum())
+    return {"height_rmse_learned_m": math.sqrt(se_l / cnt), "height_rmse_gaussian_m": math.sqrt(se_g / cnt),
+            "rgb_rmse_learned": math.sqrt(se_lc / (3 * cnt)), "rgb_rmse_gaussian": math.sqrt(se_gc / (3 * cnt)),
+            "tiles": len(data), "tiles_bound_over_2m": fallbacks}
+
+
+def init_params(filler: Filler, seed=0):
+    """He-normal weights, zero biases; the head starts at zero (identity residual)."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    flat = torch.zeros(filler.n_params)
+    for cin, cout, k, w_off, b_off in filler.layers():
+        n = cout * k * k * cin
+        if k == 1:
+            continue
+        flat[w_off:w_off + n] = torch.randn(n, generator=g) * math.sqrt(2.0 / (cin * k * k))
+    filler.params.copy_(flat.to(filler.params.device))
+    filler.load()
