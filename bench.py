@@ -160,10 +160,14 @@ def run_b300(args, rank, world):
     stream.synchronize()
     step = Step(lsb, region, counts, pts, stream)
     # warm-up outside the graph (allocates the library workspace), then capture
+    lsb.bin_stats(reset=True)
     with torch.cuda.stream(stream):
         step.run()
     stream.synchronize()
-    assert lsb.last_error() == 0
+    status = lsb.last_error()
+    bin_stats = lsb.bin_stats(reset=True)
+    if status != 0:
+        raise RuntimeError(f"library status {status} after the warm-up step; binning stats {bin_stats}")
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
         step.run()
@@ -224,6 +228,7 @@ def run_b300(args, rank, world):
                      "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
                      "algorithmic_bytes": alg_bytes,
                      "traffic": None if tpp is None else round(tpp * n_points)},
+        "bin_stats": bin_stats,
         "clocks": clocks.summary(),
         "e2e": e2e,
         "gpu_launches": step.launches * args.steps,

@@ -110,6 +110,13 @@ typedef struct {
 ls_status ls_bin_points(const ls_points *pts, const ls_region *region, const ls_bins *levels,
                         int32_t n_levels, uint64_t *dropped, ls_stream_t stream);
 
+/* Diagnostics of ls_bin_points, cumulative over calls (synchronous copy):
+ * out[0] points that arrived after their row left the CTA's window (merged with
+ * global atomics), out[1] waits on a row another CTA was writing, out[2] such waits
+ * that ran out, out[3] in-place window flushes forced by the residency bound.
+ * reset != 0 clears the counters after reading. */
+ls_status ls_bin_stats(uint64_t *out, int32_t reset);
+
 /* ---------------------------------------------------------------------------------
  * ls_extract_samples -- the chunk points (Sec. 3.1, 3.2): LAZ stores points in
  * chunks of `chunk` (50,000) consecutive points whose first point is uncompressed;
@@ -192,6 +199,14 @@ ls_status ls_conv3x3_pack(const float *w, int32_t cin, int32_t cout, int32_t tra
 ls_status ls_conv3x3_forward(const uint16_t *x, const uint16_t *packed, const float *bias,
                              const uint16_t *mask, int32_t relu, const ls_conv_shape *shape,
                              uint16_t *y, ls_stream_t stream);
+
+/* Weight and bias gradients of a 3x3 conv (c_in -> c_out <= 128) on the tensor cores:
+ * dw[(tap * c_in + i) * c_out + o] += sum_p x_shift(tap)[p][i] * dz[p][o] with tap =
+ * 3 * ky + kx (zero padding), db[o] += sum_p dz[p][o] (db may be NULL).  x: layer
+ * input bf16 [n][h][w][c_in]; dz: output gradient bf16 [n][h][w][c_out].  dw and db are
+ * fp32 and accumulated into (zero them first). */
+ls_status ls_conv3x3_wgrad(const uint16_t *x, const uint16_t *dz, const ls_conv_shape *shape,
+                           float *dw, float *db, ls_stream_t stream);
 
 /* ---------------------------------------------------------------------------------
  * Learned filler (Sec. 3.4): a U-Net of `levels` levels with widths[l] channels (two

@@ -17,7 +17,7 @@ import torch
 
 from . import _native as N
 
-__all__ = ["bin_points", "extract_samples", "extract_samples_into", "fill_sparse", "update_tile", "last_error",
+__all__ = ["bin_points", "bin_stats", "extract_samples", "extract_samples_into", "fill_sparse", "update_tile", "last_error",
            "release_workspace", "empty_bins", "BIN_KEYS", "Filler", "FillerFn", "filler_loss", "adamw_step",
            "learned_inputs", "learned_targets", "learned_finish", "fill_learned"]
 
@@ -91,6 +91,14 @@ def bin_points(points, region, levels=(640, 64), out=None, dropped=None, stream=
     N.check("ls_bin_points", N.lib().ls_bin_points(ctypes.byref(pts), ctypes.byref(reg), arr,
                                                   len(levels), _ptr(dropped), _stream(stream)))
     return out, dropped
+
+
+def bin_stats(reset=True):
+    """Binning diagnostics: late points, cross-CTA waits, waits that ran out, in-place
+    flushes (cumulative since the last reset)."""
+    out = (ctypes.c_uint64 * 4)()
+    N.check("ls_bin_stats", N.lib().ls_bin_stats(out, int(reset)))
+    return {"late_points": out[0], "waits": out[1], "wait_timeouts": out[2], "inplace_flushes": out[3]}
 
 
 def extract_samples(points, chunk=50000, capacity=None, stream=None):

@@ -45,12 +45,14 @@ class LsSampleBuffers(ctypes.Structure):
 P = ctypes.POINTER
 SIGNATURES = {
     "ls_bin_points": ([P(LsPoints), P(LsRegion), P(LsBins), I32, VP, VP], I32),
+    "ls_bin_stats": ([VP, I32], I32),
     "ls_extract_samples": ([P(LsPoints), I64, I32, VP, P(LsSampleBuffers), I64, VP], I32),
     "ls_fill_sparse": ([P(LsPoints), P(LsRegion), P(LsFillParams), VP, I64, VP, VP, VP], I32),
     "ls_update_tile": ([P(LsBins), P(LsRegion), VP, I64, VP, VP, VP], I32),
     "ls_conv3x3_packed_elems": ([I32, I32], I64),
     "ls_conv3x3_pack": ([VP, I32, I32, I32, VP, VP], I32),
     "ls_conv3x3_forward": ([VP, VP, VP, VP, I32, P(LsConvShape), VP, VP], I32),
+    "ls_conv3x3_wgrad": ([VP, VP, P(LsConvShape), VP, VP, VP], I32),
     "ls_model_create": ([I32, VP, I32, I32, P(VP)], I32),
     "ls_model_destroy": ([VP], None),
     "ls_model_param_count": ([VP], I64),

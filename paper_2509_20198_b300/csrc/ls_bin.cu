@@ -96,7 +96,9 @@ struct Meta {
   int red[kBinThreads / 32];
   int bcast;
   int clo_old, clo_new;  // coarse ring scratch of evict_rows (not shared with block_min)
+  int n_inplace;
   unsigned long long dropped;
+  unsigned long long n_late;
 };
 
 __device__ __forceinline__ Smem carve(unsigned char* base, int WC, int CC) {
@@ -120,17 +122,30 @@ __host__ __device__ constexpr size_t smem_bytes(int WC, int CC) {
   return (size_t)WC * (3 * 8 + 2 * 4) + (size_t)CC * (4 * 8 + 3 * 4);
 }
 
+// Diagnostics of the last calls (cumulative until read): late points, waits on a
+// row another CTA was writing, waits that ran out, rows flushed in place by the
+// residency bound.
+__device__ unsigned long long g_bin_stats[4];
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Wait (bounded) until a row state is 2.
 __device__ void wait_written(const uint32_t* state) {
+  if (ld_acquire(state) == 2u) return;
+  atomicAdd(&g_bin_stats[1], 1ull);
   int it = 0;
-  while (*((volatile const uint32_t*)state) != 2u) {
+  while (ld_acquire(state) != 2u) {
     if (++it > kSpinLimit) {
       set_status(LS_ERR_TIMEOUT);
+      atomicAdd(&g_bin_stats[2], 1ull);
       return;
     }
     __nanosleep(64);
   }
-  __threadfence();
 }
 
 __device__ __forceinline__ void store_empty_cell(const BinArgs& a, int64_t o) {
@@ -177,7 +192,7 @@ __device__ __forceinline__ int coarse_row_of(const BinArgs& a, int G) {
 // written it yet (single thread writes sentinels), then merge with global atomics.
 __device__ void late_point(const BinArgs& a, int G, int col, int z, uint32_t r, uint32_t g, uint32_t b) {
   uint32_t* st = &a.row_state[G];
-  if (*((volatile uint32_t*)st) != 2u) {
+  if (ld_acquire(st) != 2u) {
     if (atomicCAS(st, 0u, 1u) == 0u) {
       const int64_t base = (int64_t)G * a.cells;
       for (int c = 0; c < a.cells; ++c) store_empty_cell(a, base + c);
@@ -367,9 +382,9 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
     s.ccnt[i] = 0u; s.cmn[i] = INT_MAX; s.cmx[i] = INT_MIN;
   }
   if (threadIdx.x < kMaxW) { m.touched[threadIdx.x] = 0; m.enter[threadIdx.x] = 0; }
-  if (threadIdx.x == 0) m.dropped = 0ull;
+  if (threadIdx.x == 0) { m.dropped = 0ull; m.n_late = 0ull; m.n_inplace = 0; }
   __syncthreads();
-  unsigned long long my_dropped = 0;
+  unsigned long long my_dropped = 0, my_late = 0;
   const int W = a.W;
 
   for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
@@ -436,6 +451,7 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
             if (!(pend & (1u << k))) continue;
             if (G[k] < lo) {
               late_point(a, G[k], col[k], zz[k], rr[k], gg[k], bb[k]);
+              ++my_late;
               pend &= ~(1u << k);
             } else if (G[k] < lo + W) {
               const int slot = G[k] & (W - 1);
@@ -465,16 +481,19 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
         if (threadIdx.x < W) m.enter[threadIdx.x] = batch;
         __syncthreads();
       }
-      // ---- residency bound: rows that may approach 65536 points leave the window
-      if (lo >= 0 && batch - m.enter[lo & (W - 1)] + 1 >= kResidLimitBatches) {
-        int hi = lo;
-        while (hi < lo + W && batch - m.enter[hi & (W - 1)] + 1 >= kResidLimitBatches) ++hi;
-        __syncthreads();
-        evict_rows(a, s, m, lo, hi, clo);
-        if (threadIdx.x == 0)
-          for (int G2 = lo + W; G2 < hi + W; ++G2) m.enter[G2 & (W - 1)] = batch + 1;
-        lo = hi;
-        __syncthreads();
+      // ---- residency bound: before any row can have absorbed 65536 points the
+      // window is flushed in place (its rows stay in the window; their next flush
+      // merges), so strip-ordered input never produces late points
+      if (lo >= 0) {
+        bool old_row = false;
+        for (int k = 0; k < W; ++k) old_row |= (batch - m.enter[k] + 1 >= kResidLimitBatches);
+        if (old_row) {
+          __syncthreads();
+          evict_rows(a, s, m, lo, lo + W, clo);
+          if (threadIdx.x < W) m.enter[threadIdx.x] = batch + 1;
+          if (threadIdx.x == 0) ++m.n_inplace;
+          __syncthreads();
+        }
       }
     }
     // ---- end of the span: flush everything
@@ -483,6 +502,15 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
     if (a.has_coarse && clo >= 0) {
       coarse_evict(a, s, clo, clo + kCW);
       __syncthreads();
+    }
+  }
+  {
+    const unsigned lt = __reduce_add_sync(0xffffffffu, (unsigned)my_late);
+    if ((threadIdx.x & 31) == 0 && lt) atomicAdd((unsigned long long*)&m.n_late, (unsigned long long)lt);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (m.n_late) atomicAdd(&g_bin_stats[0], m.n_late);
+      if (m.n_inplace) atomicAdd(&g_bin_stats[3], (unsigned long long)m.n_inplace);
     }
   }
   if (a.dropped) {
@@ -615,6 +643,16 @@ ls_status bin_launch(BinArgs a, size_t smem, int64_t n_coarse, cudaStream_t stre
 }
 
 }  // namespace ls
+
+extern "C" ls_status ls_bin_stats(uint64_t* out, int32_t reset) {
+  if (!out) return LS_ERR_INVALID_ARG;
+  if (cudaMemcpyFromSymbol(out, ls::g_bin_stats, 4 * sizeof(uint64_t)) != cudaSuccess) return LS_ERR_CUDA;
+  if (reset) {
+    const uint64_t z[4] = {0, 0, 0, 0};
+    if (cudaMemcpyToSymbol(ls::g_bin_stats, z, sizeof(z)) != cudaSuccess) return LS_ERR_CUDA;
+  }
+  return LS_OK;
+}
 
 extern "C" ls_status ls_bin_points(const ls_points* pts, const ls_region* region, const ls_bins* levels,
                                    int32_t n_levels, uint64_t* dropped, ls_stream_t stream) {

@@ -202,3 +202,10 @@ ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int 
 }
 
 }  // namespace ls
+
+extern "C" ls_status ls_conv3x3_wgrad(const uint16_t* x, const uint16_t* dz, const ls_conv_shape* shape, float* dw,
+                                      float* db, ls_stream_t stream) {
+  if (!shape) return LS_ERR_INVALID_ARG;
+  return ls::wgrad_launch(x, dz, shape->n, shape->h, shape->w, shape->cin, shape->cout, dw, db,
+                          reinterpret_cast<cudaStream_t>(stream));
+}

@@ -142,9 +142,14 @@ def test_full_size_lognormal_region_sampled_tiles(lsb):
     import synth.gpu as sg
     region, counts = synth.batched_region_workload()
     d = sg.region_points(2, region, counts)
+    lsb.bin_stats(reset=True)
     out, dropped = lsb.bin_points(d, region, levels=(640, 64))
     torch.cuda.synchronize()
+    st = lsb.bin_stats(reset=True)
+    print("bin stats", st)
     assert lsb.last_error() == 0
+    # strip-ordered input: no point arrives after its row left a window
+    assert st["late_points"] == 0 and st["wait_timeouts"] == 0
     n = int(counts.sum())
     assert int(dropped.item()) == 0
     fine, coarse = out
