@@ -235,7 +235,91 @@ def run_b300(args, rank, world):
     }
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline(pts, counts, region, budget_s=args.cpu_seconds)
+    if args.overview:
+        del pts, step, graph
+        torch.cuda.empty_cache()
+        out["overview"] = run_overview(lsb, args, dev, stream)
     return out
+
+
+def run_overview(lsb, args, dev, stream):
+    """Country-scale overview (200 x 200 tiles, 4 pts/m^2, 33 chunk samples per tile):
+    Gaussian fill of all 40,000 tiles in one launch and the learned fill (batches of
+    4096 tiles) on the same samples; height / colour RMSE against the full-resolution
+    means on a seeded 400-tile subset.  The filler is trained first on pairs the method
+    generates (seeds disjoint from the overview)."""
+    import torch
+    import synth
+    import synth.gpu as sg
+    from paper_2509_20198_b300 import train as T
+    region, counts = synth.overview_workload()
+    with torch.cuda.stream(stream):
+        s = sg.region_samples(3, region, counts, device=dev, stream=stream)
+    stream.synchronize()
+    nT = region.n_tiles
+    h = torch.empty((nT, 64, 64), dtype=torch.float32, device=dev)
+    c = torch.empty((nT, 64, 64, 3), dtype=torch.uint8, device=dev)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    with torch.cuda.stream(stream):
+        ms_gauss = timed(lambda: lsb.fill_sparse(s, region, height=h, rgb=c, stream=stream), args.steps)
+    # train the filler (tensor-core forward/backward) on self-generated pairs
+    t0 = time.perf_counter()
+    train_set = T.synthetic_tiles(args.train_tiles, seed0=100, device=dev)
+    filler = lsb.Filler(max_batch=4096, device=dev)
+    T.init_params(filler, seed=0)
+    hist = T.train(filler, train_set, epochs=args.train_epochs, batch=256, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del train_set
+    ids = torch.arange(nT, dtype=torch.int32, device=dev)
+    lh = torch.empty((nT, 64, 64), dtype=torch.float32, device=dev)
+    lc = torch.empty((nT, 64, 64, 3), dtype=torch.uint8, device=dev)
+    eb = torch.empty(nT, dtype=torch.float32, device=dev)
+    fb = torch.empty(nT, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(lsb._native.lib().ls_fill_learned_scratch_bytes(filler._h), dtype=torch.uint8,
+                          device=dev)
+    with torch.cuda.stream(stream):
+        ms_learned = timed(lambda: lsb.fill_learned(filler, s, region, ids, height=lh, rgb=lc, err_bound=eb,
+                                                    used_fallback=fb, scratch=scratch, stream=stream),
+                           max(1, args.steps // 5))
+    assert lsb.last_error() == 0
+    # truth on a seeded 400-tile subset: full points of those tiles only, binned at 64x64
+    sub = np.sort(np.random.default_rng(400).choice(nT, 400, replace=False))
+    full = np.zeros_like(counts)
+    full[sub] = counts[sub]
+    pts = sg.region_points(3, region, full, device=dev)
+    (b64,), _ = lsb.bin_points(pts, region, levels=(64,))
+    del pts
+    sub_t = torch.as_tensor(sub, device=dev)
+    cnt = b64["count"][sub_t].to(torch.float64)
+    m = cnt > 0
+    th = b64["zsum"][sub_t].to(torch.float64) / cnt.clamp(min=1) * region.z_scale + region.z_offset
+    tcol = torch.stack([b64[k][sub_t].to(torch.float64) for k in ("rsum", "gsum", "bsum")], -1) / \
+        cnt.clamp(min=1)[..., None] / 256.0
+    rm = lambda a: float(torch.sqrt(((a.to(torch.float64) - th)[m] ** 2).mean()))  # noqa: E731
+    rc = lambda a: float(torch.sqrt(((a.to(torch.float64) - tcol)[m] ** 2).mean()))  # noqa: E731
+    return {"workload": "overview 200x200 tiles, 4 pts/m^2, 33 samples/tile (1.32M samples)",
+            "gaussian_fill": {"tiles_per_s": round(nT / (ms_gauss * 1e-3), 1), "ms": round(ms_gauss, 3),
+                              "height_rmse_m": round(rm(h[sub_t]), 4), "rgb_rmse_8bit": round(rc(c[sub_t]), 3)},
+            "learned_fill": {"tiles_per_s": round(nT / (ms_learned * 1e-3), 1), "ms": round(ms_learned, 3),
+                             "batch": 4096, "height_rmse_m": round(rm(lh[sub_t]), 4),
+                             "rgb_rmse_8bit": round(rc(lc[sub_t]), 3),
+                             "fallback_tiles": int(fb.sum()), "max_err_m": 2.0},
+            "training": {"tiles": args.train_tiles, "epochs": args.train_epochs, "batch": 256,
+                         "seconds": round(train_s, 1), "loss_first": [round(v, 7) for v in hist[0]],
+                         "loss_last": [round(v, 7) for v in hist[-1]], "loss_parts": "total, height, colour, bound"},
+            "truth": "per-texel mean of the full-resolution points, 400 seeded tiles"}
 
 
 def run_e2e(lsb, region, counts, pts, step, stream, steps, world):
@@ -354,6 +438,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--overview", type=int, default=1, help="also time the 40,000-tile overview fills")
+    ap.add_argument("--train-tiles", type=int, default=4096)
+    ap.add_argument("--train-epochs", type=int, default=20)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

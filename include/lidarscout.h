@@ -238,7 +238,8 @@ ls_status ls_filler_forward(ls_model *model, const float *params, const uint16_t
 ls_status ls_filler_backward(ls_model *model, const float *params, const float *dy, int32_t n,
                              float *grads, ls_stream_t stream);
 /* Loss of Sec. 3.4: masked MSE of height and colour (each squared error clipped to 1),
- * the two averaged, plus bound_weight * L1(|y4 - |height error||).  base, target:
+ * the two averaged, plus bound_weight * mean((y4 - |height error|)^2) (the error
+ * target detached).  base, target:
  * [n_px][4] (normalised height, R, G, B in 0..1); mask [n_px] (0: texel without truth).
  * sums: device double[4] scratch; loss: device float[4] (total, height, colour,
  * bound) or NULL; dy: fp32 [n_px][5]. */

@@ -25,7 +25,7 @@ import numpy as np
 
 N_IN = 5
 N_OUT = 5
-BOUND_WEIGHT = 0.1
+BOUND_WEIGHT = 1.0
 
 
 def layer_table(widths=(32, 64, 128), n_in=N_IN, n_out=N_OUT):
@@ -138,9 +138,15 @@ def _levels(layers):
     return sum(1 for name, *_ in layers if name.endswith("a") and name.startswith("e"))
 
 
-def forward(params, x, layers=LAYERS):
+def _identity(a):
+    return a
+
+
+def forward(params, x, layers=LAYERS, store=None):
     """Forward pass; returns (y, cache).  x: [N,H,W,C_in], H and W divisible by
-    2^(L-1)."""
+    2^(L-1).  store: optional storage rounding applied to every conv output after
+    its ReLU (arithmetic stays FP64; None keeps full precision)."""
+    st = store or _identity
     L = _levels(layers)
     c = {"x": x}
     W = {name: (params[name + ".w"], params[name + ".b"]) for name, *_ in layers}
@@ -148,19 +154,21 @@ def forward(params, x, layers=LAYERS):
     for l in range(1, L + 1):
         if l > 1:
             c[f"p{l - 1}"] = h = maxpool2(h)
-        c[f"e{l}a"] = h = relu(conv(h, *W[f"e{l}a"]))
-        c[f"e{l}b"] = h = relu(conv(h, *W[f"e{l}b"]))
+        c[f"e{l}a"] = h = st(relu(conv(h, *W[f"e{l}a"])))
+        c[f"e{l}b"] = h = st(relu(conv(h, *W[f"e{l}b"])))
     for l in range(L - 1, 0, -1):
         c[f"c{l}"] = h = np.concatenate([upsample2(h), c[f"e{l}b"]], axis=3)
-        c[f"d{l}a"] = h = relu(conv(h, *W[f"d{l}a"]))
-        c[f"d{l}b"] = h = relu(conv(h, *W[f"d{l}b"]))
+        c[f"d{l}a"] = h = st(relu(conv(h, *W[f"d{l}a"])))
+        c[f"d{l}b"] = h = st(relu(conv(h, *W[f"d{l}b"])))
     c["top"] = h
     y = conv(h, *W["head"])
     return y, c
 
 
-def backward(params, cache, dy, layers=LAYERS):
-    """Gradients of all parameters given dL/dy (hand-written chain rule)."""
+def backward(params, cache, dy, layers=LAYERS, store=None):
+    """Gradients of all parameters given dL/dy (hand-written chain rule).  store:
+    optional storage rounding of every activation gradient passed between layers."""
+    st = store or _identity
     L = _levels(layers)
     g = {}
     c = cache
@@ -169,19 +177,20 @@ def backward(params, cache, dy, layers=LAYERS):
         # dout_post is dL/d(relu output); mask by the relu output
         dz = dout_post * (c[name] > 0)
         dx, g[name + ".w"], g[name + ".b"] = conv_backward(xin, params[name + ".w"], dz)
-        return dx
+        return st(dx)
 
     d, g["head.w"], g["head.b"] = conv_backward(c["top"], params["head.w"], dy)
+    d = st(d)
     skip = {}
     for l in range(1, L):
         d = conv_relu_back(f"d{l}b", c[f"d{l}a"], d)
         d = conv_relu_back(f"d{l}a", c[f"c{l}"], d)
         cu = d.shape[3] - c[f"e{l}b"].shape[3]
         skip[l] = d[..., cu:]
-        d = upsample2_backward(d[..., :cu])
+        d = st(upsample2_backward(d[..., :cu]))
     for l in range(L, 0, -1):
         if l < L:
-            d = maxpool2_backward(c[f"e{l}b"], d) + skip[l]
+            d = st((maxpool2_backward(c[f"e{l}b"], d) + skip[l]) * (c[f"e{l}b"] > 0))
         d = conv_relu_back(f"e{l}b", c[f"e{l}a"], d)
         d = conv_relu_back(f"e{l}a", c[f"p{l - 1}"] if l > 1 else c["x"], d)
     return g
@@ -189,7 +198,8 @@ def backward(params, cache, dy, layers=LAYERS):
 
 # ------------------------------------------------------------------------------
 # loss (Sec. 3.4): masked, clipped MSE on height and colour, averaged; plus the
-# L1 regression of the error-bound channel (a reading: the paper has no bound).
+# squared-error regression of the error-bound channel onto the (detached) absolute
+# height error (a reading: the paper has no bound), on the height term's scale.
 # ------------------------------------------------------------------------------
 
 def loss_and_grad(y, base_h, base_c, t_h, t_c, mask, bound_weight=BOUND_WEIGHT):
@@ -205,12 +215,12 @@ def loss_and_grad(y, base_h, base_c, t_h, t_c, mask, bound_weight=BOUND_WEIGHT):
     lc = (np.minimum(sc, 1.0) * m[..., None]).sum() / (3.0 * cnt)
     tb = np.abs(eh)                                  # detached target
     db = y[..., 4] - tb
-    lb = (np.abs(db) * m).sum() / cnt
+    lb = (db * db * m).sum() / cnt
     loss = 0.5 * (lh + lc) + bound_weight * lb
     dy = np.zeros_like(y)
     dy[..., 0] = 0.5 * 2.0 * eh * (sh < 1.0) * m / cnt
     dy[..., 1:4] = 0.5 * 2.0 * ec * (sc < 1.0) * m[..., None] / (3.0 * cnt)
-    dy[..., 4] = bound_weight * np.sign(db) * m / cnt
+    dy[..., 4] = bound_weight * 2.0 * db * m / cnt
     return loss, dy, {"height": lh, "color": lc, "bound": lb}
 
 

@@ -254,7 +254,7 @@ class FillerFn(torch.autograd.Function):
         return ctx.filler.backward(dy), None, None
 
 
-def filler_loss(y, base, target, mask, bound_weight=0.1, stream=None):
+def filler_loss(y, base, target, mask, bound_weight=1.0, stream=None):
     """Masked, clipped MSE of Sec. 3.4 (+ bound term).  Returns (loss[4], dL/dy)."""
     n_px = mask.numel()
     sums = torch.empty(4, dtype=torch.float64, device=y.device)

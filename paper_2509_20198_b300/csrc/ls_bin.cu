@@ -94,7 +94,8 @@ struct Meta {
   int enter[kMaxW];  // batch index at which the row entered the window
   int mode[kMaxW];   // 0 none, 1 store, 2 merge
   int red[kBinThreads / 32];
-  int bcast;
+  int redx[kBinThreads / 32];
+  int bcast, bcastx;
   int clo_old, clo_new;  // coarse ring scratch of evict_rows (not shared with block_min)
   int n_inplace;
   unsigned long long dropped;
@@ -209,19 +210,24 @@ __device__ void late_point(const BinArgs& a, int G, int col, int z, uint32_t r, 
   }
 }
 
-__device__ __forceinline__ int block_min(int v, Meta& m) {
-  v = __reduce_min_sync(0xffffffffu, v);
+// Block-wide min and max (every thread gets both).
+__device__ __forceinline__ void block_minmax(int vmin, int vmax, Meta& m, int& omin, int& omax) {
+  vmin = __reduce_min_sync(0xffffffffu, vmin);
+  vmax = __reduce_max_sync(0xffffffffu, vmax);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();  // m.red may still be read by a previous reduction
-  if (lane == 0) m.red[warp] = v;
+  if (lane == 0) { m.red[warp] = vmin; m.redx[warp] = vmax; }
   __syncthreads();
   if (warp == 0) {
     int u = lane < (kBinThreads / 32) ? m.red[lane] : INT_MAX;
+    int x = lane < (kBinThreads / 32) ? m.redx[lane] : INT_MIN;
     u = __reduce_min_sync(0xffffffffu, u);
-    if (lane == 0) m.bcast = u;
+    x = __reduce_max_sync(0xffffffffu, x);
+    if (lane == 0) { m.bcast = u; m.bcastx = x; }
   }
   __syncthreads();
-  return m.bcast;
+  omin = m.bcast;
+  omax = m.bcastx;
 }
 
 // Flush coarse ring rows [ca, cb) (all inside the ring) to global with atomics.
@@ -466,19 +472,30 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
             }
           }
         }
-        int mymin = INT_MAX;
+        int mymin = INT_MAX, mymax = INT_MIN;
 #pragma unroll
         for (int k = 0; k < kPtsPerThread; ++k)
-          if (pend & (1u << k)) mymin = min(mymin, G[k]);
-        const int mn = block_min(mymin, m);
+          if (pend & (1u << k)) { mymin = min(mymin, G[k]); mymax = max(mymax, G[k]); }
+        int mn, mx;
+        block_minmax(mymin, mymax, m, mn, mx);
         if (mn == INT_MAX) break;
-        // every pending point lies at or above lo + W: slide so that lo = mn
+        // Every pending point lies at or above lo + W.  Slide as little as possible:
+        // keep the window as low as it can be while covering all pending rows (the
+        // lower rows of a strip whose first points are already here come later), or,
+        // when the pending rows span more than W rows, start at the lowest of them.
+        int nlo = (mx - mn < W) ? mx - W + 1 : mn;
+        if (lo >= 0 && nlo < lo + 1) nlo = lo + 1;
+        if (lo < 0) nlo = mn;
         if (lo >= 0) {
-          const int hi = (mn < lo + W) ? mn : lo + W;
+          const int hi = (nlo < lo + W) ? nlo : lo + W;
           evict_rows(a, s, m, lo, hi, clo);
+          // rows [lo + W, nlo + W) enter; rows kept in the window keep their age
+          if (threadIdx.x == 0)
+            for (int G2 = (lo + W > nlo ? lo + W : nlo); G2 < nlo + W; ++G2) m.enter[G2 & (W - 1)] = batch;
+        } else if (threadIdx.x < W) {
+          m.enter[threadIdx.x] = batch;
         }
-        lo = mn;
-        if (threadIdx.x < W) m.enter[threadIdx.x] = batch;
+        lo = nlo;
         __syncthreads();
       }
       // ---- residency bound: before any row can have absorbed 65536 points the

@@ -240,7 +240,8 @@ __global__ void k_pad_in(const float* __restrict__ w, int cout, int cin, int cin
 }
 
 // ---- loss (Sec. 3.4): masked MSE of height and colour, each squared error clipped to
-// 1, height and colour terms averaged; plus the L1 error-bound term -----------------
+// 1, height and colour terms averaged; plus the squared error of the bound channel
+// against the detached absolute height error ---------------------------------------
 // y [P][5]; base [P][4] (normalised fill height, colour 0..1); target [P][4]; mask [P]
 __global__ void k_loss_sums(const float* __restrict__ y, const float* __restrict__ base,
                             const float* __restrict__ target, const uint8_t* __restrict__ mask, int64_t P,
@@ -255,7 +256,8 @@ __global__ void k_loss_sums(const float* __restrict__ y, const float* __restrict
       const float ec = base[p * 4 + k] + y[p * kOut + k] - target[p * 4 + k];
       s[2] += fminf(ec * ec, 1.f);
     }
-    s[3] += fabsf(y[p * kOut + 4] - fabsf(eh));
+    const float db = y[p * kOut + 4] - fabsf(eh);
+    s[3] += db * db;
   }
   for (int k = 0; k < 4; ++k) {
     double v = s[k];
@@ -285,7 +287,7 @@ __global__ void k_loss_grad(const float* __restrict__ y, const float* __restrict
         g[k] = ec * ec < 1.f ? ec * inv3 : 0.f;
       }
       const float db = y[p * kOut + 4] - fabsf(eh);
-      g[4] = bound_weight * (db > 0.f ? inv : (db < 0.f ? -inv : 0.f));
+      g[4] = bound_weight * 2.f * db * inv;
     }
 #pragma unroll
     for (int k = 0; k < kOut; ++k) dy[p * kOut + k] = g[k];

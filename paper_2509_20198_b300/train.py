@@ -20,20 +20,19 @@ from . import (Filler, FillerFn, adamw_step, bin_points, filler_loss, learned_in
 
 
 class FillerLossFn(torch.autograd.Function):
-    """Scalar loss of Sec. 3.4 (masked, clipped MSE + bound term); backward returns the
-    kernel-computed dL/dy."""
+    """Loss of Sec. 3.4 (masked, clipped MSE + bound term) as [total, height, colour,
+    bound]; backward (of the total) returns the kernel-computed dL/dy."""
 
     @staticmethod
     def forward(ctx, y, base, target, mask, bound_weight):
         loss, dy = filler_loss(y, base, target, mask, bound_weight)
         ctx.save_for_backward(dy)
-        ctx.parts = loss
-        return loss[0].clone()
+        return loss
 
     @staticmethod
     def backward(ctx, g):
         (dy,) = ctx.saved_tensors
-        return dy * g, None, None, None, None
+        return dy * g[0], None, None, None, None
 
 
 @dataclasses.dataclass
@@ -85,8 +84,9 @@ def synthetic_tiles(n_tiles, seed0, block=16, density=(3.0, 6.0), device="cuda")
 
 
 def train(filler: Filler, data: TileSet, epochs=20, batch=256, lr=5e-4, weight_decay=1e-2, betas=(0.9, 0.999),
-          eps=1e-5, milestones=(0.6, 0.85), gamma=0.1, bound_weight=0.1, seed=0, log=None):
-    """AdamW training with a step schedule; returns the per-epoch mean losses."""
+          eps=1e-5, milestones=(0.6, 0.85), gamma=0.1, bound_weight=1.0, seed=0, log=None):
+    """AdamW training with a step schedule; returns the per-epoch mean losses
+    [total, height, colour, bound]."""
     g = torch.Generator(device="cpu").manual_seed(seed)
     p = filler.params
     m = torch.zeros_like(p)
@@ -97,7 +97,7 @@ def train(filler: Filler, data: TileSet, epochs=20, batch=256, lr=5e-4, weight_d
     history = []
     for ep in range(epochs):
         order = torch.randperm(len(data), generator=g).to(p.device)
-        acc = torch.zeros((), device=p.device)
+        acc = torch.zeros(4, device=p.device)
         for k in range(steps_per_epoch):
             idx = order[k * batch:(k + 1) * batch]
             x = data.x[idx].contiguous()
@@ -105,15 +105,15 @@ def train(filler: Filler, data: TileSet, epochs=20, batch=256, lr=5e-4, weight_d
             y = FillerFn.apply(params, x, filler)
             loss = FillerLossFn.apply(y, data.base[idx].contiguous(), data.target[idx].contiguous(),
                                       data.mask[idx].contiguous(), bound_weight)
-            loss.backward()
+            loss[0].backward()
             step += 1
             frac = step / total
             cur = lr * (gamma ** sum(frac > mm for mm in milestones))
             adamw_step(p, params.grad, m, v, step, lr=cur, betas=betas, eps=eps, weight_decay=weight_decay)
             acc += loss.detach()
-        history.append(float(acc.item()) / steps_per_epoch)
+        history.append([float(v) / steps_per_epoch for v in acc.tolist()])
         if log:
-            log(f"epoch {ep + 1}/{epochs} loss {history[-1]:.6f}")
+            log(f"epoch {ep + 1}/{epochs} loss {history[-1]}")
     filler.load()
     return history
 

@@ -88,6 +88,11 @@ def test_backward_matches_oracle_and_torch(lsb):
     assert lsb.last_error() == 0
     yr, cache = U.forward(q, xo, layers)
     gr = U.backward(q, cache, dy.astype(np.float64), layers)
+    # the oracle with values rounded to bf16 wherever the kernels store them (its
+    # arithmetic stays FP64): isolates the backward logic from storage precision
+    rnd = lambda a: bf16_to_f64(bf16_bits(a.astype(np.float32)))  # noqa: E731
+    _, cache_b = U.forward(q, xo, layers, store=rnd)
+    gb16 = U.backward(q, cache_b, dy.astype(np.float64), layers, store=rnd)
     # torch autograd (fp64, CPU) on the same operands: an independent reference gradient
     tp = {k: torch.tensor(v, dtype=torch.float64, requires_grad=True) for k, v in q.items()}
     h = torch.tensor(xo).permute(0, 3, 1, 2)
@@ -113,7 +118,8 @@ def test_backward_matches_oracle_and_torch(lsb):
         nw = co * k * k * ci
         gw, gb = g[off:off + nw].reshape(co, k, k, ci), g[off + nw:off + nw + co]
         off += nw + co
-        for ref, msg in ((gr, "oracle"), ({kk: tp[kk].grad.numpy() for kk in tp}, "torch")):
+        for ref, msg in ((gr, "oracle"), ({kk: tp[kk].grad.numpy() for kk in tp}, "torch"),
+                         (gb16, "oracle-bf16-storage")):
             errs[(name, msg)] = (_rel(gw, ref[name + ".w"]), _cos(gw.ravel(), ref[name + ".w"].ravel()),
                                  _rel(gb, ref[name + ".b"]))
     print({k: tuple(round(float(x), 4) for x in v) for k, v in errs.items()})
@@ -121,6 +127,11 @@ def test_backward_matches_oracle_and_torch(lsb):
     # errors compound with depth, so the bar widens with the number of layers between
     # a parameter and the loss (head and the last decoder level: 6e-2)
     for (name, msg), (rw, cw, rb) in errs.items():
+        if msg == "oracle-bf16-storage":
+            # same storage rounding on both sides: only fp32-vs-fp64 arithmetic and
+            # the rare rounding/mask decision it flips remain
+            assert rw < 3e-2 and cw > 0.999 and rb < 3e-2, (name, msg, rw, cw, rb)
+            continue
         deep = name.startswith("e")
         assert rw < (0.25 if deep else 6e-2), (name, msg, rw)
         assert cw > (0.97 if deep else 0.995), (name, msg, cw)

@@ -61,11 +61,11 @@ def test_loss_hand_case():
     loss, dy, parts = U.loss_and_grad(y, base_h, base_c, t_h, t_c, mask)
     assert parts["height"] == 1.0
     assert parts["color"] == pytest.approx((0.01 + 0.04 + 0.09) / 3)
-    assert parts["bound"] == pytest.approx(abs(0.25 - 1.5))
-    assert loss == pytest.approx(0.5 * (1.0 + 0.14 / 3) + 0.1 * 1.25)
+    assert parts["bound"] == pytest.approx((0.25 - 1.5) ** 2)
+    assert loss == pytest.approx(0.5 * (1.0 + 0.14 / 3) + 1.0 * 1.25 ** 2)
     assert dy[0, 0, 0, 0] == 0.0                 # clipped: no gradient
     assert dy[0, 0, 0, 1] == pytest.approx(0.5 * 2 * 0.1 / 3)
-    assert dy[0, 0, 0, 4] == pytest.approx(-0.1)
+    assert dy[0, 0, 0, 4] == pytest.approx(2.0 * (0.25 - 1.5))
     assert (dy[0, 0, 1] == 0).all()
 
 
@@ -120,15 +120,13 @@ def test_loss_gradient_matches_finite_differences():
     h = 1e-7
     for _ in range(40):
         i = tuple(rng.integers(0, s) for s in y.shape)
-        if i[3] == 4:
-            continue   # L1 term: kink-free away from 0 but the target depends on y0
         yp, ym = y.copy(), y.copy()
         yp[i] += h
         ym[i] -= h
         fd = (U.loss_and_grad(yp, bh, bc, th, tc, m)[0] - U.loss_and_grad(ym, bh, bc, th, tc, m)[0]) / (2 * h)
         if i[3] == 0:
             # the bound term's detached target also moves with y0: remove it
-            db = lambda yy: 0.1 * (np.abs(yy[..., 4] - np.abs(bh + yy[..., 0] - th)) * m).sum() / max(m.sum(), 1)  # noqa: E731
+            db = lambda yy: ((yy[..., 4] - np.abs(bh + yy[..., 0] - th)) ** 2 * m).sum() / max(m.sum(), 1)  # noqa: E731
             fd -= (db(yp) - db(ym)) / (2 * h)
         assert fd == pytest.approx(dy[i], abs=1e-7)
 
