@@ -171,12 +171,13 @@ def run_b300(args, rank, world):
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
         step.run()
-    for _ in range(args.warmup):
-        graph.replay()
+    # replay on the timed stream (CUDAGraph.replay launches on the current stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            graph.replay()
     stream.synchronize()
 
     # ---- device-timed region
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
     bin_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
     if world > 1:
         torch.distributed.barrier()
@@ -184,10 +185,11 @@ def run_b300(args, rank, world):
     with ClockSampler(dev.index) as clocks:
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        for k in range(args.steps):
-            graph.replay()
-        t1.record(stream)
+        with torch.cuda.stream(stream):
+            t0.record(stream)
+            for k in range(args.steps):
+                graph.replay()
+            t1.record(stream)
         torch.cuda.synchronize()
         # binning alone (its own timing pass, same stream, not graph-fused with the rest)
         for k in range(args.steps):

@@ -74,6 +74,10 @@ def test_forward_matches_oracle(lsb, widths, n):
     assert lsb.last_error() == 0
     yr, _ = U.forward(q, xo, layers)
     assert _rel(y, yr) < 3e-2 and _cos(y.ravel(), yr.ravel()) > 0.999
+    rnd = lambda a: bf16_to_f64(bf16_bits(a.astype(np.float32)))  # noqa: E731
+    yb, _ = U.forward(q, xo, layers, store=rnd)
+    print("forward rel err vs FP64 oracle", _rel(y, yr), "vs bf16-storage oracle", _rel(y, yb))
+    assert _rel(y, yb) < 2e-2
 
 
 def test_backward_matches_oracle_and_torch(lsb):
@@ -155,7 +159,9 @@ def test_loss_and_adamw_match_oracle(lsb):
     l4 = loss.cpu().numpy()
     assert l4[0] == pytest.approx(lr_, rel=1e-5)
     assert l4[1] == pytest.approx(parts["height"], rel=1e-5)
-    np.testing.assert_allclose(dy.cpu().numpy(), dyr, rtol=1e-5, atol=1e-12)
+    # the bound gradient 2 (y4 - |e_h|)/n cancels in fp32 where y4 ~ |e_h|: absolute
+    # tolerance of a few fp32 ulps of |y4| / n
+    np.testing.assert_allclose(dy.cpu().numpy(), dyr, rtol=1e-5, atol=4e-6 / mask.sum())
     # AdamW
     p = rng.standard_normal(1000).astype(np.float32)
     pg, pm, pv = T(p.copy()), T(np.zeros(1000, np.float32)), T(np.zeros(1000, np.float32))
