@@ -433,6 +433,29 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+def run_profile_case(args):
+    """Small case for profilers: binning only (640^2 + 64^2) of a 3x3-tile region at
+    the batched-region densities (~17M points, ~300 MB, larger than L2)."""
+    import torch
+    import paper_2509_20198_b300 as lsb
+    import synth
+    import synth.gpu as sg
+    from paper_2509_20198_b300 import build
+    build.build_library()
+    build.build_synth()
+    region = synth.Region(tiles_x=3, tiles_y=3)
+    counts = synth.lognormal_counts(SEED, 9)
+    pts = sg.region_points(SEED, region, counts)
+    out, dropped = lsb.bin_points(pts, region, levels=(640, 64))
+    for _ in range(args.steps):
+        lsb.bin_points(pts, region, levels=(640, 64), out=out, dropped=dropped)
+    torch.cuda.synchronize()
+    st = lsb.last_error()
+    print(json.dumps({"case": "bin-small", "points": int(counts.sum()), "status": st,
+                      "bin_stats": lsb.bin_stats()}))
+    return 0 if st == 0 else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -441,11 +464,14 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--overview", type=int, default=1, help="also time the 40,000-tile overview fills")
+    ap.add_argument("--case", default="", choices=["", "bin-small"], help="profiling case instead of the bench")
     ap.add_argument("--train-tiles", type=int, default=4096)
     ap.add_argument("--train-epochs", type=int, default=20)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.case:
+        sys.exit(run_profile_case(args))
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args, rank, world)), flush=True)
