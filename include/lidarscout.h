@@ -110,6 +110,23 @@ typedef struct {
 ls_status ls_bin_points(const ls_points *pts, const ls_region *region, const ls_bins *levels,
                         int32_t n_levels, uint64_t *dropped, ls_stream_t stream);
 
+/* ls_bin_points_fixed_scratch -- the same binning and results as ls_bin_points, for
+ * callers that cannot allocate device memory during the call: an interactive viewer
+ * that bins streamed full-resolution tiles between frames must not pay the device
+ * synchronisation of cudaMalloc/cudaFree, and an application whose device memory is
+ * fully reserved by its own allocator has none to give.  The paper has no
+ * counterpart; this is a service of this library.  The per-row scratch is a fixed
+ * array of 2^20 rows (4 MiB) compiled into the library, held by every GPU that loads
+ * it until the process exits; regions with more than 2^20 fine rows (tiles *
+ * levels[0].cells) are rejected with LS_ERR_UNSUPPORTED.  Nothing is allocated: the
+ * first call on a device looks up the array's device address (make that first call
+ * before any stream capture).  All calls share the array, which keeps the last
+ * call's contents (every call clears the states it uses): calls that overlap on the
+ * GPU, on any streams, race and must be serialised by the caller. */
+ls_status ls_bin_points_fixed_scratch(const ls_points *pts, const ls_region *region,
+                                      const ls_bins *levels, int32_t n_levels, uint64_t *dropped,
+                                      ls_stream_t stream);
+
 /* Diagnostics of ls_bin_points, cumulative over calls (synchronous copy):
  * out[0] points that arrived after their row left the CTA's window (merged with
  * global atomics), out[1] waits on a row another CTA was writing, out[2] such waits

@@ -27,6 +27,7 @@
 //  * Packed 32-bit colour sums in shared memory cannot overflow: a row is forced out
 //    of the window before it can have absorbed 65536 points (65536 * 65535 < 2^32).
 #include <climits>
+#include <mutex>
 
 #include "ls_internal.cuh"
 
@@ -680,5 +681,50 @@ extern "C" ls_status ls_bin_points(const ls_points* pts, const ls_region* region
   if (st != LS_OK) return st;
   a.row_state = static_cast<uint32_t*>(ls::workspace(ls::kWsBinRows, (size_t)a.n_rows * 4));
   if (!a.row_state) return LS_ERR_NO_MEMORY;
+  return ls::bin_launch(a, smem, n_coarse, reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------------------------
+// Variant of ls_bin_points that allocates nothing.  Its per-row claim states live in
+// a fixed array compiled into the library instead of the growable workspace, for
+// callers that must not allocate device memory while binning, e.g. an interactive
+// viewer that streams full-resolution tiles in between frames (cudaMalloc and
+// cudaFree can synchronise the device and stall a frame) or an application whose
+// device memory is fully reserved by its own allocator.
+// ---------------------------------------------------------------------------------
+namespace ls {
+namespace {
+constexpr int64_t kFixedBinRows = int64_t(1) << 20;  // 4 MiB of row states
+static __device__ __align__(256) uint32_t g_bin_rows_fixed[kFixedBinRows];
+std::mutex g_fixed_mu;
+uint32_t* g_fixed_ptr[64] = {};
+}  // namespace
+}  // namespace ls
+
+extern "C" ls_status ls_bin_points_fixed_scratch(const ls_points* pts, const ls_region* region,
+                                                 const ls_bins* levels, int32_t n_levels, uint64_t* dropped,
+                                                 ls_stream_t stream) {
+  ls::BinArgs a;
+  size_t smem = 0;
+  int64_t n_coarse = 0;
+  ls_status st = ls::bin_prepare(pts, region, levels, n_levels, dropped, &a, &smem, &n_coarse);
+  if (st != LS_OK) return st;
+  if ((int64_t)a.n_rows > ls::kFixedBinRows) return LS_ERR_UNSUPPORTED;  // tiles * cells rows over 2^20
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LS_ERR_CUDA;
+  if (dev < 0 || dev >= 64) return LS_ERR_UNSUPPORTED;
+  uint32_t* rows = nullptr;
+  {
+    // once per device, with that device current: the device address of the array
+    // (its name in host code is only a host-side stand-in)
+    std::lock_guard<std::mutex> lock(ls::g_fixed_mu);
+    if (!ls::g_fixed_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, ls::g_bin_rows_fixed) != cudaSuccess || !p) return LS_ERR_CUDA;
+      ls::g_fixed_ptr[dev] = static_cast<uint32_t*>(p);
+    }
+    rows = ls::g_fixed_ptr[dev];
+  }
+  a.row_state = rows;  // cleared by the prologue kernel of every call
   return ls::bin_launch(a, smem, n_coarse, reinterpret_cast<cudaStream_t>(stream));
 }
