@@ -72,16 +72,27 @@ struct BinArgs {
   int64_t span;
   int64_t n_items;
   int vec;
+  int narrow;            // x0 and y0 fit int32: 32-bit region-local coordinates
+  int32_t x0_32, y0_32;
+  // shared-memory row layout: the f fine cells of a coarse cell occupy gs >= f slots
+  // (gs odd), so one thread per coarse cell reads its fine cells without bank conflicts
+  int32_t gs, rstride;
 };
 
-// shared-memory layout (dynamic)
+// shared-memory layout (dynamic).  Every fine accumulator is a 32-bit word (32-bit
+// shared atomics are several times cheaper than 64-bit ones): z is split into its low
+// 16 bits (unsigned) and its high bits (signed), zsum = 65536 * sum(hi) + sum(lo),
+// both sums exact while a cell absorbs at most 65536 points.
 struct Smem {
-  unsigned long long* rg;  // [W*cells] R | G<<32
-  unsigned long long* bc;  // [W*cells] B | count<<32
-  unsigned long long* zs;  // [W*cells] z sum (two's complement)
-  int* mn;                 // [W*cells]
-  int* mx;                 // [W*cells]
-  unsigned long long* crs; // [kCW*ccells] coarse sums
+  unsigned* cnt;  // [W*rstride]
+  unsigned* rs;
+  unsigned* gs;
+  unsigned* bs;
+  unsigned* zlo;
+  int* zhi;
+  int* mn;
+  int* mx;
+  unsigned long long* crs;  // [kCW*ccells] coarse sums
   unsigned long long* cgs;
   unsigned long long* cbs;
   unsigned long long* czs;
@@ -99,20 +110,24 @@ struct Meta {
   int bcast, bcastx;
   int clo_old, clo_new;  // coarse ring scratch of evict_rows (not shared with block_min)
   int n_inplace;
+  int oldest;  // lowest entry batch over the window's slots
   unsigned long long dropped;
   unsigned long long n_late;
 };
 
 __device__ __forceinline__ Smem carve(unsigned char* base, int WC, int CC) {
   Smem s;
-  s.rg = reinterpret_cast<unsigned long long*>(base);
-  s.bc = s.rg + WC;
-  s.zs = s.bc + WC;
-  s.crs = s.zs + WC;
+  s.crs = reinterpret_cast<unsigned long long*>(base);
   s.cgs = s.crs + CC;
   s.cbs = s.cgs + CC;
   s.czs = s.cbs + CC;
-  s.mn = reinterpret_cast<int*>(s.czs + CC);
+  s.cnt = reinterpret_cast<unsigned*>(s.czs + CC);
+  s.rs = s.cnt + WC;
+  s.gs = s.rs + WC;
+  s.bs = s.gs + WC;
+  s.zlo = s.bs + WC;
+  s.zhi = reinterpret_cast<int*>(s.zlo + WC);
+  s.mn = s.zhi + WC;
   s.mx = s.mn + WC;
   s.ccnt = reinterpret_cast<unsigned*>(s.mx + WC);
   s.cmn = reinterpret_cast<int*>(s.ccnt + CC);
@@ -121,7 +136,32 @@ __device__ __forceinline__ Smem carve(unsigned char* base, int WC, int CC) {
 }
 
 __host__ __device__ constexpr size_t smem_bytes(int WC, int CC) {
-  return (size_t)WC * (3 * 8 + 2 * 4) + (size_t)CC * (4 * 8 + 3 * 4);
+  return (size_t)WC * (8 * 4) + (size_t)CC * (4 * 8 + 3 * 4);
+}
+
+// one fine cell, reassembled from its shared words
+struct Cell {
+  unsigned cnt;
+  long long zsum;
+  int zmin, zmax;
+  unsigned r, g, b;
+};
+
+__device__ __forceinline__ Cell read_cell(const Smem& s, int si) {
+  Cell c;
+  c.cnt = s.cnt[si];
+  c.zsum = (long long)s.zhi[si] * 65536 + (long long)s.zlo[si];
+  c.zmin = s.mn[si];
+  c.zmax = s.mx[si];
+  c.r = s.rs[si];
+  c.g = s.gs[si];
+  c.b = s.bs[si];
+  return c;
+}
+
+__device__ __forceinline__ void reset_cell(Smem& s, int si) {
+  s.cnt[si] = 0u; s.rs[si] = 0u; s.gs[si] = 0u; s.bs[si] = 0u;
+  s.zlo[si] = 0u; s.zhi[si] = 0; s.mn[si] = INT_MAX; s.mx[si] = INT_MIN;
 }
 
 // Diagnostics of the last calls (cumulative until read): late points, waits on a
@@ -188,6 +228,27 @@ __device__ __forceinline__ int coarse_row_of(const BinArgs& a, int G) {
   const int tile = G / a.cells;
   const int row = G - tile * a.cells;
   return tile * a.ccells + (int)fdiv((uint32_t)row, a.div_f);
+}
+
+__device__ __forceinline__ uint32_t sh_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// shared-memory reductions without a returned value (no scoreboard wait)
+__device__ __forceinline__ void red_add(unsigned* p, unsigned v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(sh_addr(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(int* p, int v) {
+  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(sh_addr(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_min(int* p, int v) {
+  asm volatile("red.shared.min.s32 [%0], %1;" ::"r"(sh_addr(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_max(int* p, int v) {
+  asm volatile("red.shared.max.s32 [%0], %1;" ::"r"(sh_addr(p)), "r"(v) : "memory");
+}
+
+// shared slot of fine column col in ring slot `slot` (padded layout, see BinArgs)
+__device__ __forceinline__ int sidx(const BinArgs& a, int slot, int col) {
+  const int cg = (int)fdiv((uint32_t)col, a.div_f);
+  return slot * a.rstride + cg * a.gs + (col - cg * a.f);
 }
 
 // A point whose row already left this CTA's window: claim the row if nobody has
@@ -283,45 +344,44 @@ __device__ void evict_rows(const BinArgs& a, Smem& s, Meta& m, int ra, int rb, i
       __syncthreads();
     }
     clo = new_clo;
-    // coarse reduction of the fine rows being evicted: one thread per coarse cell
-    // walks the rows in order, so each shared coarse cell has a single writer.
-    for (int c = threadIdx.x; c < a.ccells; c += blockDim.x) {
-      for (int rr = 0; rr < nr; ++rr) {
-        if (m.mode[rr] == 0) continue;
-        const int G = ra + rr;
-        const int slot = G & (W - 1);
-        unsigned cnt = 0;
-        long long zsum = 0;
-        int zmn = INT_MAX, zmx = INT_MIN;
-        unsigned long long rs = 0, gs = 0, bs = 0;
-        for (int k = 0; k < a.f; ++k) {
-          const int si = slot * a.cells + c * a.f + k;
-          const unsigned long long bcv = s.bc[si];
-          const unsigned cn = (unsigned)(bcv >> 32);
-          if (!cn) continue;
-          const unsigned long long rgv = s.rg[si];
-          cnt += cn;
-          zsum += (long long)s.zs[si];
-          zmn = min(zmn, s.mn[si]);
-          zmx = max(zmx, s.mx[si]);
-          rs += rgv & 0xffffffffull;
-          gs += rgv >> 32;
-          bs += bcv & 0xffffffffull;
-        }
-        if (!cnt) continue;
-        const int Gc = coarse_row_of(a, G);
-        if (Gc >= clo && Gc < clo + kCW) {
-          const int ci = (Gc % kCW) * a.ccells + c;
-          s.ccnt[ci] += cnt;
-          s.czs[ci] += (unsigned long long)zsum;
-          s.cmn[ci] = min(s.cmn[ci], zmn);
-          s.cmx[ci] = max(s.cmx[ci], zmx);
-          s.crs[ci] += rs;
-          s.cgs[ci] += gs;
-          s.cbs[ci] += bs;
-        } else {
-          merge_coarse(a, (int64_t)Gc * a.ccells + c, cnt, zsum, zmn, zmx, rs, gs, bs);
-        }
+    // coarse reduction of the fine rows being evicted: one thread per (fine row,
+    // coarse cell) pair sums its f fine cells, then shared atomics merge pairs that
+    // fall on the same coarse cell
+    for (int e = threadIdx.x; e < nr * a.ccells; e += blockDim.x) {
+      const int rr = e / a.ccells, c = e - rr * a.ccells;
+      if (m.mode[rr] == 0) continue;
+      const int G = ra + rr;
+      const int slot = G & (W - 1);
+      unsigned cnt = 0;
+      long long zsum = 0;
+      int zmn = INT_MAX, zmx = INT_MIN;
+      unsigned long long rs = 0, gs = 0, bs = 0;
+      for (int k = 0; k < a.f; ++k) {
+        const int si = slot * a.rstride + c * a.gs + k;
+        const unsigned cn = s.cnt[si];
+        if (!cn) continue;
+        const Cell fc = read_cell(s, si);
+        cnt += cn;
+        zsum += fc.zsum;
+        zmn = min(zmn, fc.zmin);
+        zmx = max(zmx, fc.zmax);
+        rs += fc.r;
+        gs += fc.g;
+        bs += fc.b;
+      }
+      if (!cnt) continue;
+      const int Gc = coarse_row_of(a, G);
+      if (Gc >= clo && Gc < clo + kCW) {
+        const int ci = (Gc % kCW) * a.ccells + c;
+        atomicAdd(&s.ccnt[ci], cnt);
+        atomicAdd(&s.czs[ci], (unsigned long long)zsum);
+        atomicMin(&s.cmn[ci], zmn);
+        atomicMax(&s.cmx[ci], zmx);
+        atomicAdd(&s.crs[ci], rs);
+        atomicAdd(&s.cgs[ci], gs);
+        atomicAdd(&s.cbs[ci], bs);
+      } else {
+        merge_coarse(a, (int64_t)Gc * a.ccells + c, cnt, zsum, zmn, zmx, rs, gs, bs);
       }
     }
     __syncthreads();
@@ -333,16 +393,16 @@ __device__ void evict_rows(const BinArgs& a, Smem& s, Meta& m, int ra, int rb, i
     const int slot = G & (W - 1);
     const int64_t base = (int64_t)G * a.cells;
     for (int c = threadIdx.x; c < a.cells; c += blockDim.x) {
-      const int si = slot * a.cells + c;
-      const unsigned long long bcv = s.bc[si], rgv = s.rg[si];
-      a.count[base + c] = (unsigned)(bcv >> 32);
-      a.zsum[base + c] = (long long)s.zs[si];
-      a.zmin[base + c] = s.mn[si];
-      a.zmax[base + c] = s.mx[si];
-      a.rsum[base + c] = rgv & 0xffffffffull;
-      a.gsum[base + c] = rgv >> 32;
-      a.bsum[base + c] = bcv & 0xffffffffull;
-      s.rg[si] = 0ull; s.bc[si] = 0ull; s.zs[si] = 0ull; s.mn[si] = INT_MAX; s.mx[si] = INT_MIN;
+      const int si = sidx(a, slot, c);
+      const Cell fc = read_cell(s, si);
+      a.count[base + c] = fc.cnt;
+      a.zsum[base + c] = fc.zsum;
+      a.zmin[base + c] = fc.zmin;
+      a.zmax[base + c] = fc.zmax;
+      a.rsum[base + c] = fc.r;
+      a.gsum[base + c] = fc.g;
+      a.bsum[base + c] = fc.b;
+      reset_cell(s, si);
     }
   }
   __threadfence();
@@ -361,13 +421,10 @@ __device__ void evict_rows(const BinArgs& a, Smem& s, Meta& m, int ra, int rb, i
     const int slot = G & (W - 1);
     const int64_t base = (int64_t)G * a.cells;
     for (int c = threadIdx.x; c < a.cells; c += blockDim.x) {
-      const int si = slot * a.cells + c;
-      const unsigned long long bcv = s.bc[si], rgv = s.rg[si];
-      const unsigned cnt = (unsigned)(bcv >> 32);
-      if (cnt)
-        merge_fine(a, base + c, cnt, (long long)s.zs[si], s.mn[si], s.mx[si], rgv & 0xffffffffull, rgv >> 32,
-                   bcv & 0xffffffffull);
-      s.rg[si] = 0ull; s.bc[si] = 0ull; s.zs[si] = 0ull; s.mn[si] = INT_MAX; s.mx[si] = INT_MIN;
+      const int si = sidx(a, slot, c);
+      const Cell fc = read_cell(s, si);
+      if (fc.cnt) merge_fine(a, base + c, fc.cnt, fc.zsum, fc.zmin, fc.zmax, fc.r, fc.g, fc.b);
+      reset_cell(s, si);
     }
   }
   __syncthreads();
@@ -375,21 +432,69 @@ __device__ void evict_rows(const BinArgs& a, Smem& s, Meta& m, int ra, int rb, i
   __syncthreads();
 }
 
+// Raw points of one thread's slot of a batch (kPtsPerThread consecutive points).
+struct Raw {
+  int x[kPtsPerThread], y[kPtsPerThread], z[kPtsPerThread];
+  uint32_t r[kPtsPerThread], g[kPtsPerThread], b[kPtsPerThread];
+  int n;
+};
+
+__device__ __forceinline__ void load_raw(const BinArgs& a, Raw& v, int64_t i0, int64_t p1) {
+  v.n = (int)((p1 - i0) < kPtsPerThread ? (p1 - i0) : kPtsPerThread);
+  if (v.n == kPtsPerThread && a.vec) {
+    const int4 vx = __ldcs(reinterpret_cast<const int4*>(a.x + i0));
+    const int4 vy = __ldcs(reinterpret_cast<const int4*>(a.y + i0));
+    const int4 vz = __ldcs(reinterpret_cast<const int4*>(a.z + i0));
+    const uint2 vr = __ldcs(reinterpret_cast<const uint2*>(a.r + i0));
+    const uint2 vg = __ldcs(reinterpret_cast<const uint2*>(a.g + i0));
+    const uint2 vb = __ldcs(reinterpret_cast<const uint2*>(a.b + i0));
+    v.x[0] = vx.x; v.x[1] = vx.y; v.x[2] = vx.z; v.x[3] = vx.w;
+    v.y[0] = vy.x; v.y[1] = vy.y; v.y[2] = vy.z; v.y[3] = vy.w;
+    v.z[0] = vz.x; v.z[1] = vz.y; v.z[2] = vz.z; v.z[3] = vz.w;
+    v.r[0] = vr.x & 0xffffu; v.r[1] = vr.x >> 16; v.r[2] = vr.y & 0xffffu; v.r[3] = vr.y >> 16;
+    v.g[0] = vg.x & 0xffffu; v.g[1] = vg.x >> 16; v.g[2] = vg.y & 0xffffu; v.g[3] = vg.y >> 16;
+    v.b[0] = vb.x & 0xffffu; v.b[1] = vb.x >> 16; v.b[2] = vb.y & 0xffffu; v.b[3] = vb.y >> 16;
+  } else {
+#pragma unroll
+    for (int k = 0; k < kPtsPerThread; ++k) {
+      if (k < v.n) {
+        v.x[k] = a.x[i0 + k]; v.y[k] = a.y[i0 + k]; v.z[k] = a.z[i0 + k];
+        v.r[k] = a.r[i0 + k]; v.g[k] = a.g[i0 + k]; v.b[k] = a.b[i0 + k];
+      } else {
+        v.x[k] = v.y[k] = v.z[k] = 0;
+        v.r[k] = v.g[k] = v.b[k] = 0u;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void accumulate(Smem& s, Meta& m, const BinArgs& a, int slot, int col, int z, uint32_t r,
+                                           uint32_t g, uint32_t b) {
+  const int si = sidx(a, slot, col);
+  red_add(&s.cnt[si], 1u);
+  red_add(&s.rs[si], r);
+  red_add(&s.gs[si], g);
+  red_add(&s.bs[si], b);
+  red_add(&s.zlo[si], (unsigned)z & 0xffffu);
+  red_add(&s.zhi[si], z >> 16);
+  red_min(&s.mn[si], z);
+  red_max(&s.mx[si], z);
+  m.touched[slot] = 1;
+}
+
 __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Meta m;
-  const int WC = a.W * a.cells;
+  const int WC = a.W * a.rstride;
   const int CC = a.has_coarse ? kCW * a.ccells : 0;
   Smem s = carve(smem_raw, WC, CC);
-  for (int i = threadIdx.x; i < WC; i += blockDim.x) {
-    s.rg[i] = 0ull; s.bc[i] = 0ull; s.zs[i] = 0ull; s.mn[i] = INT_MAX; s.mx[i] = INT_MIN;
-  }
+  for (int i = threadIdx.x; i < WC; i += blockDim.x) reset_cell(s, i);
   for (int i = threadIdx.x; i < CC; i += blockDim.x) {
     s.crs[i] = 0ull; s.cgs[i] = 0ull; s.cbs[i] = 0ull; s.czs[i] = 0ull;
     s.ccnt[i] = 0u; s.cmn[i] = INT_MAX; s.cmx[i] = INT_MIN;
   }
   if (threadIdx.x < kMaxW) { m.touched[threadIdx.x] = 0; m.enter[threadIdx.x] = 0; }
-  if (threadIdx.x == 0) { m.dropped = 0ull; m.n_late = 0ull; m.n_inplace = 0; }
+  if (threadIdx.x == 0) { m.dropped = 0ull; m.n_late = 0ull; m.n_inplace = 0; m.oldest = 0; }
   __syncthreads();
   unsigned long long my_dropped = 0, my_late = 0;
   const int W = a.W;
@@ -400,49 +505,34 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
     int lo = -1;   // lowest fine row of the window (uniform); -1 = empty
     int clo = -1;  // lowest coarse row of the coarse ring
     int batch = 0;
+    Raw cur, nxt;
+    load_raw(a, cur, p0 + (int64_t)threadIdx.x * kPtsPerThread, p1);
     for (int64_t b0 = p0; b0 < p1; b0 += kBatch, ++batch) {
-      // ---- load 4 consecutive points per thread
-      int G[kPtsPerThread], col[kPtsPerThread], zz[kPtsPerThread];
-      uint32_t rr[kPtsPerThread], gg[kPtsPerThread], bb[kPtsPerThread];
-      const int64_t i0 = b0 + (int64_t)threadIdx.x * kPtsPerThread;
-      int xs[kPtsPerThread], ys[kPtsPerThread];
-      int nvalid = (int)((p1 - i0) < kPtsPerThread ? (p1 - i0) : kPtsPerThread);
-      if (nvalid == kPtsPerThread && a.vec) {
-        const int4 vx = __ldcs(reinterpret_cast<const int4*>(a.x + i0));
-        const int4 vy = __ldcs(reinterpret_cast<const int4*>(a.y + i0));
-        const int4 vz = __ldcs(reinterpret_cast<const int4*>(a.z + i0));
-        const uint2 vr = __ldcs(reinterpret_cast<const uint2*>(a.r + i0));
-        const uint2 vg = __ldcs(reinterpret_cast<const uint2*>(a.g + i0));
-        const uint2 vb = __ldcs(reinterpret_cast<const uint2*>(a.b + i0));
-        xs[0] = vx.x; xs[1] = vx.y; xs[2] = vx.z; xs[3] = vx.w;
-        ys[0] = vy.x; ys[1] = vy.y; ys[2] = vy.z; ys[3] = vy.w;
-        zz[0] = vz.x; zz[1] = vz.y; zz[2] = vz.z; zz[3] = vz.w;
-        rr[0] = vr.x & 0xffffu; rr[1] = vr.x >> 16; rr[2] = vr.y & 0xffffu; rr[3] = vr.y >> 16;
-        gg[0] = vg.x & 0xffffu; gg[1] = vg.x >> 16; gg[2] = vg.y & 0xffffu; gg[3] = vg.y >> 16;
-        bb[0] = vb.x & 0xffffu; bb[1] = vb.x >> 16; bb[2] = vb.y & 0xffffu; bb[3] = vb.y >> 16;
-      } else {
-#pragma unroll
-        for (int k = 0; k < kPtsPerThread; ++k) {
-          if (k < nvalid) {
-            xs[k] = a.x[i0 + k]; ys[k] = a.y[i0 + k]; zz[k] = a.z[i0 + k];
-            rr[k] = a.r[i0 + k]; gg[k] = a.g[i0 + k]; bb[k] = a.b[i0 + k];
-          } else {
-            xs[k] = ys[k] = zz[k] = 0; rr[k] = gg[k] = bb[k] = 0;
-          }
-        }
-      }
+      // prefetch the next batch while this one is processed
+      if (b0 + kBatch < p1) load_raw(a, nxt, b0 + kBatch + (int64_t)threadIdx.x * kPtsPerThread, p1);
+      int G[kPtsPerThread], col[kPtsPerThread];
       unsigned pend = 0;
 #pragma unroll
       for (int k = 0; k < kPtsPerThread; ++k) {
         G[k] = INT_MAX;
         col[k] = 0;
-        if (k >= nvalid) continue;
-        const int64_t lx = (int64_t)xs[k] - a.x0, ly = (int64_t)ys[k] - a.y0;
-        if (lx < 0 || ly < 0 || lx >= (int64_t)a.ext_x || ly >= (int64_t)a.ext_y) {
+        if (k >= cur.n) continue;
+        uint32_t ux, uy;
+        bool in;
+        if (a.narrow) {
+          ux = (uint32_t)cur.x[k] - (uint32_t)a.x0_32;
+          uy = (uint32_t)cur.y[k] - (uint32_t)a.y0_32;
+          in = ux < a.ext_x && uy < a.ext_y;
+        } else {
+          const int64_t lx = (int64_t)cur.x[k] - a.x0, ly = (int64_t)cur.y[k] - a.y0;
+          in = lx >= 0 && ly >= 0 && lx < (int64_t)a.ext_x && ly < (int64_t)a.ext_y;
+          ux = (uint32_t)lx;
+          uy = (uint32_t)ly;
+        }
+        if (!in) {
           ++my_dropped;
           continue;
         }
-        const uint32_t ux = (uint32_t)lx, uy = (uint32_t)ly;
         const uint32_t tx = fdiv(ux, a.div_tile), ty = fdiv(uy, a.div_tile);
         const uint32_t cx = fdiv(ux - tx * a.tile_cm, a.div_cell);
         const uint32_t cy = fdiv(uy - ty * a.tile_cm, a.div_cell);
@@ -450,69 +540,78 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
         col[k] = (int)cx;
         pend |= 1u << k;
       }
-      // ---- accumulate; slide the window when points land above it
-      while (true) {
-        if (lo >= 0) {
+      // ---- common case (one barrier): every point of the block inside the window
+      bool outside = false;
 #pragma unroll
-          for (int k = 0; k < kPtsPerThread; ++k) {
-            if (!(pend & (1u << k))) continue;
-            if (G[k] < lo) {
-              late_point(a, G[k], col[k], zz[k], rr[k], gg[k], bb[k]);
-              ++my_late;
-              pend &= ~(1u << k);
-            } else if (G[k] < lo + W) {
-              const int slot = G[k] & (W - 1);
-              const int si = slot * a.cells + col[k];
-              atomicAdd(&s.rg[si], (unsigned long long)rr[k] | ((unsigned long long)gg[k] << 32));
-              atomicAdd(&s.bc[si], (unsigned long long)bb[k] | (1ull << 32));
-              atomicAdd(&s.zs[si], (unsigned long long)(long long)zz[k]);
-              atomicMin(&s.mn[si], zz[k]);
-              atomicMax(&s.mx[si], zz[k]);
-              m.touched[slot] = 1;
-              pend &= ~(1u << k);
+      for (int k = 0; k < kPtsPerThread; ++k)
+        if (pend & (1u << k)) outside |= (lo < 0) || ((unsigned)(G[k] - lo) >= (unsigned)W);
+      if (!__syncthreads_or(outside)) {
+#pragma unroll
+        for (int k = 0; k < kPtsPerThread; ++k) {
+          if (!(pend & (1u << k))) continue;
+          accumulate(s, m, a, G[k] & (W - 1), col[k], cur.z[k], cur.r[k], cur.g[k], cur.b[k]);
+        }
+      } else {
+        // ---- general case: late points, window slides
+        while (true) {
+          if (lo >= 0) {
+#pragma unroll
+            for (int k = 0; k < kPtsPerThread; ++k) {
+              if (!(pend & (1u << k))) continue;
+              if (G[k] < lo) {
+                late_point(a, G[k], col[k], cur.z[k], cur.r[k], cur.g[k], cur.b[k]);
+                ++my_late;
+                pend &= ~(1u << k);
+              } else if (G[k] < lo + W) {
+                accumulate(s, m, a, G[k] & (W - 1), col[k], cur.z[k], cur.r[k], cur.g[k], cur.b[k]);
+                pend &= ~(1u << k);
+              }
             }
           }
-        }
-        int mymin = INT_MAX, mymax = INT_MIN;
+          int mymin = INT_MAX, mymax = INT_MIN;
 #pragma unroll
-        for (int k = 0; k < kPtsPerThread; ++k)
-          if (pend & (1u << k)) { mymin = min(mymin, G[k]); mymax = max(mymax, G[k]); }
-        int mn, mx;
-        block_minmax(mymin, mymax, m, mn, mx);
-        if (mn == INT_MAX) break;
-        // Every pending point lies at or above lo + W.  Slide as little as possible:
-        // keep the window as low as it can be while covering all pending rows (the
-        // lower rows of a strip whose first points are already here come later), or,
-        // when the pending rows span more than W rows, start at the lowest of them.
-        int nlo = (mx - mn < W) ? mx - W + 1 : mn;
-        if (lo >= 0 && nlo < lo + 1) nlo = lo + 1;
-        if (lo < 0) nlo = mn;
-        if (lo >= 0) {
-          const int hi = (nlo < lo + W) ? nlo : lo + W;
-          evict_rows(a, s, m, lo, hi, clo);
-          // rows [lo + W, nlo + W) enter; rows kept in the window keep their age
-          if (threadIdx.x == 0)
-            for (int G2 = (lo + W > nlo ? lo + W : nlo); G2 < nlo + W; ++G2) m.enter[G2 & (W - 1)] = batch;
-        } else if (threadIdx.x < W) {
-          m.enter[threadIdx.x] = batch;
+          for (int k = 0; k < kPtsPerThread; ++k)
+            if (pend & (1u << k)) { mymin = min(mymin, G[k]); mymax = max(mymax, G[k]); }
+          int mn, mx;
+          block_minmax(mymin, mymax, m, mn, mx);
+          if (mn == INT_MAX) break;
+          // Every pending point lies at or above lo + W.  Slide as little as possible:
+          // keep the window as low as it can be while covering all pending rows (the
+          // lower rows of a strip whose first points are already here come later), or,
+          // when the pending rows span more than W rows, start at the lowest of them.
+          int nlo = (mx - mn < W) ? mx - W + 1 : mn;
+          if (lo >= 0 && nlo < lo + 1) nlo = lo + 1;
+          if (lo < 0) nlo = mn;
+          if (lo >= 0) {
+            const int hi = (nlo < lo + W) ? nlo : lo + W;
+            evict_rows(a, s, m, lo, hi, clo);
+          }
+          if (threadIdx.x == 0) {
+            // rows [max(lo + W, nlo), nlo + W) enter; rows kept in the window keep their age
+            const int first_new = (lo >= 0 && lo + W > nlo) ? lo + W : nlo;
+            for (int G2 = first_new; G2 < nlo + W; ++G2) m.enter[G2 & (W - 1)] = batch;
+            int o = INT_MAX;
+            for (int k = 0; k < W; ++k) o = min(o, m.enter[k]);
+            m.oldest = o;
+          }
+          lo = nlo;
+          __syncthreads();
         }
-        lo = nlo;
-        __syncthreads();
       }
       // ---- residency bound: before any row can have absorbed 65536 points the
       // window is flushed in place (its rows stay in the window; their next flush
       // merges), so strip-ordered input never produces late points
-      if (lo >= 0) {
-        bool old_row = false;
-        for (int k = 0; k < W; ++k) old_row |= (batch - m.enter[k] + 1 >= kResidLimitBatches);
-        if (old_row) {
-          __syncthreads();
-          evict_rows(a, s, m, lo, lo + W, clo);
-          if (threadIdx.x < W) m.enter[threadIdx.x] = batch + 1;
-          if (threadIdx.x == 0) ++m.n_inplace;
-          __syncthreads();
+      if (lo >= 0 && batch - m.oldest + 1 >= kResidLimitBatches) {
+        __syncthreads();
+        evict_rows(a, s, m, lo, lo + W, clo);
+        if (threadIdx.x == 0) {
+          for (int k = 0; k < W; ++k) m.enter[k] = batch + 1;
+          m.oldest = batch + 1;
+          ++m.n_inplace;
         }
+        __syncthreads();
       }
+      cur = nxt;
     }
     // ---- end of the span: flush everything
     __syncthreads();
@@ -616,19 +715,25 @@ ls_status bin_prepare(const ls_points* pts, const ls_region* region, const ls_bi
     a.crsum = L1.rsum; a.cgsum = L1.gsum; a.cbsum = L1.bsum;
     *n_coarse = T * L1.cells * L1.cells;
   }
-  // window rows: the largest power of two <= 8 whose ring fits in ~176 KB of shared memory
-  const size_t budget = 176 * 1024;
+  a.gs = (a.f % 2) ? a.f : a.f + 1;
+  a.rstride = (a.cells / a.f) * a.gs;
+  // window rows: the largest power of two <= 8 whose ring fits in ~196 KB of shared memory
+  const size_t budget = 196 * 1024;
   int W = 8;
   const int CC = a.has_coarse ? kCW * a.ccells : 0;
-  while (W > 1 && smem_bytes(W * a.cells, CC) > budget) W >>= 1;
+  while (W > 1 && smem_bytes(W * a.rstride, CC) > budget) W >>= 1;
   if (W > a.cells) {
     W = 1;
     while (W * 2 <= a.cells) W *= 2;
   }
-  if (smem_bytes(W * a.cells, CC) > budget) return LS_ERR_UNSUPPORTED;
+  if (smem_bytes(W * a.rstride, CC) > budget) return LS_ERR_UNSUPPORTED;
   a.W = W;
-  *smem = smem_bytes(W * a.cells, CC);
+  *smem = smem_bytes(W * a.rstride, CC);
   // vector loads need 16-byte aligned int32 arrays and 8-byte aligned uint16 arrays
+  a.narrow = region->x0_cm >= INT32_MIN && region->x0_cm <= INT32_MAX && region->y0_cm >= INT32_MIN &&
+             region->y0_cm <= INT32_MAX;
+  a.x0_32 = a.narrow ? (int32_t)region->x0_cm : 0;
+  a.y0_32 = a.narrow ? (int32_t)region->y0_cm : 0;
   a.vec = (((uintptr_t)a.x | (uintptr_t)a.y | (uintptr_t)a.z) % 16 == 0) &&
           (((uintptr_t)a.r | (uintptr_t)a.g | (uintptr_t)a.b) % 8 == 0);
   // spans: about 4 per CTA, multiples of the batch size
@@ -648,7 +753,7 @@ ls_status bin_launch(BinArgs a, size_t smem, int64_t n_coarse, cudaStream_t stre
   LS_CUDA_TRY(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
     LS_CUDA_TRY(cudaFuncSetAttribute(k_bin_main, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     200 * 1024));
+                                     210 * 1024));
     attr_set[dev] = true;
   }
   const int64_t work = a.n_rows > n_coarse ? a.n_rows : n_coarse;
