@@ -221,14 +221,27 @@ __device__ __forceinline__ void splat_range(const Rec* recs, int n, int bx0, int
   }
 }
 
-// Nearest sample among recs[0..n) for lanes that need it (no candidate within R).
-__device__ __forceinline__ void nearest_range(const Rec* recs, int n, bool need, int cx, int cy, LaneAcc& a) {
-  if (!__any_sync(0xffffffffu, need)) return;
-  for (int i = 0; i < n; ++i) {
-    const Rec q = recs[i];
-    if (need) {
-      const int dx = q.lx - cx, dy = q.ly - cy;
-      consider_nearest(a, (long long)dx * dx + (long long)dy * dy, q);
+// Nearest sample among recs[0..n) for lanes that need it (no candidate within R),
+// testing only samples inside the warp's block box grown by `grow` (every sample
+// nearer than a lane's current best lies there when grow >= that best distance).
+__device__ __forceinline__ void nearest_range(const Rec* recs, int n, bool need, int cx, int cy, int bx0, int bx1,
+                                              int by0, int by1, LaneAcc& a) {
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < n; base += 32) {
+    bool in = false;
+    if (base + lane < n) {
+      const int2 xy = *reinterpret_cast<const int2*>(&recs[base + lane]);
+      in = xy.x >= bx0 && xy.x <= bx1 && xy.y >= by0 && xy.y <= by1;
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, in);
+    while (mask) {
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const Rec q = recs[base + src];
+      if (need) {
+        const int dx = q.lx - cx, dy = q.ly - cy;
+        consider_nearest(a, (long long)dx * dx + (long long)dy * dy, q);
+      }
     }
   }
 }
@@ -339,10 +352,27 @@ __global__ void __launch_bounds__(kFillThreads) k_fill(FillArgs f) {
           splat_range(f.recs + rng_lo[k], (int)rng_n[k], bx0, bx1, by0, by1, cx, cy, f, zref, a);
       }
       const bool need = !(a.sw > 0.f);
-      if (use_stage) {
-        nearest_range(stage, stage_n, need, cx, cy, a);
-      } else {
-        for (int k = 0; k < 3; ++k) nearest_range(f.recs + rng_lo[k], (int)rng_n[k], need, cx, cy, a);
+      if (__any_sync(0xffffffffu, need)) {
+        // grow the box to the largest current best distance of the lanes in need
+        // (in-box samples were all considered above); a lane without any in-box
+        // sample makes the search unbounded
+        const bool unbounded = need && a.bd2 < 0;
+        const long long bd = need && a.bd2 >= 0 ? a.bd2 : 0;
+        long long wmax = bd;
+        for (int off = 16; off > 0; off >>= 1) {
+          const long long o = __shfl_xor_sync(0xffffffffu, wmax, off);
+          wmax = o > wmax ? o : wmax;
+        }
+        int grow = (int)ceilf(sqrtf((float)wmax)) + 1;
+        if (__any_sync(0xffffffffu, unbounded) || grow > 2 * f.tile_cm) grow = 2 * f.tile_cm;
+        const int gx0 = x0b - grow, gx1 = x0b + 7 * cell + grow;
+        const int gy0 = y0b - grow, gy1 = y0b + 3 * cell + grow;
+        if (use_stage) {
+          nearest_range(stage, stage_n, need, cx, cy, gx0, gx1, gy0, gy1, a);
+        } else {
+          for (int k = 0; k < 3; ++k)
+            nearest_range(f.recs + rng_lo[k], (int)rng_n[k], need, cx, cy, gx0, gx1, gy0, gy1, a);
+        }
       }
       if (need && !(a.bd2 >= 0 && a.bd2 <= (long long)f.tile_cm * f.tile_cm)) nearest_far(f, tx, ty, cx, cy, a);
       float h;
