@@ -26,6 +26,7 @@
 //    prologue kernel initialises.
 //  * Packed 32-bit colour sums in shared memory cannot overflow: a row is forced out
 //    of the window before it can have absorbed 65536 points (65536 * 65535 < 2^32).
+#include <algorithm>
 #include <climits>
 #include <mutex>
 
@@ -34,12 +35,15 @@
 namespace ls {
 namespace {
 
-constexpr int kBinThreads = 512;
+constexpr int kBinThreads = 1024;
 constexpr int kPtsPerThread = 4;
-constexpr int kBatch = kBinThreads * kPtsPerThread;  // 2048 points per batch
+constexpr int kBatch = kBinThreads * kPtsPerThread;  // 4096 points per batch
 constexpr int kResidLimitBatches = 65536 / kBatch;     // residency bound (batches)
 constexpr int kMaxW = 64;
 constexpr int kCW = 4;  // coarse ring rows
+constexpr int kMaxWFlush = 8;  // window rows (W <= 8)
+constexpr int kBinSmemAttr = 224 * 1024;  // dynamic shared memory allowed (budget + margin)
+constexpr int kPfDist = 2;  // batches prefetched into L2 ahead of the loads
 
 struct BinArgs {
   const int32_t* __restrict__ x;
@@ -74,9 +78,10 @@ struct BinArgs {
   int vec;
   int narrow;            // x0 and y0 fit int32: 32-bit region-local coordinates
   int32_t x0_32, y0_32;
-  // shared-memory row layout: the f fine cells of a coarse cell occupy gs >= f slots
-  // (gs odd), so one thread per coarse cell reads its fine cells without bank conflicts
-  int32_t gs, rstride;
+  // shared-memory row layout: the f fine cells of a coarse cell occupy gs >= f slots,
+  // rows are rstride slots apart; the coarse partials split a coarse cell's f columns
+  // at fh (gs and fh chosen against bank conflicts, see bin_coarse_layout)
+  int32_t gs, rstride, fh;
 };
 
 // shared-memory layout (dynamic).  Every fine accumulator is a 32-bit word (32-bit
@@ -99,18 +104,23 @@ struct Smem {
   unsigned* ccnt;
   int* cmn;
   int* cmx;
+  // per-(row, coarse cell) partials of a flush: [8][SC], SC = W * ccells (32-bit)
+  unsigned* sp;
 };
 
 struct Meta {
   int touched[kMaxW];
   int enter[kMaxW];  // batch index at which the row entered the window
   int mode[kMaxW];   // 0 none, 1 store, 2 merge
+  int ckey[kMaxW];   // coarse row of each row being flushed
   int red[kBinThreads / 32];
   int redx[kBinThreads / 32];
   int bcast, bcastx;
   int clo_old, clo_new;  // coarse ring scratch of evict_rows (not shared with block_min)
   int n_inplace;
   int oldest;  // lowest entry batch over the window's slots
+  // rows this CTA claimed and stored in its last flush, published (state 2) later
+  int pend_row[kMaxW];  // -1: none
   unsigned long long dropped;
   unsigned long long n_late;
 };
@@ -132,11 +142,14 @@ __device__ __forceinline__ Smem carve(unsigned char* base, int WC, int CC) {
   s.ccnt = reinterpret_cast<unsigned*>(s.mx + WC);
   s.cmn = reinterpret_cast<int*>(s.ccnt + CC);
   s.cmx = s.cmn + CC;
+  s.sp = reinterpret_cast<unsigned*>(s.cmx + CC);
   return s;
 }
 
-__host__ __device__ constexpr size_t smem_bytes(int WC, int CC) {
-  return (size_t)WC * (8 * 4) + (size_t)CC * (4 * 8 + 3 * 4);
+// fine ring (8 words per cell), coarse ring (4 x 64-bit + 3 x 32-bit per cell) and
+// the flush partials (8 words per (row, coarse cell))
+__host__ __device__ constexpr size_t smem_bytes(int WC, int CC, int SC) {
+  return (size_t)WC * (8 * 4) + (size_t)CC * (4 * 8 + 3 * 4) + (size_t)SC * (8 * 4);
 }
 
 // one fine cell, reassembled from its shared words
@@ -293,9 +306,9 @@ __device__ __forceinline__ void block_minmax(int vmin, int vmax, Meta& m, int& o
 }
 
 // Flush coarse ring rows [ca, cb) (all inside the ring) to global with atomics.
-__device__ void coarse_evict(const BinArgs& a, Smem& s, int ca, int cb) {
+__device__ void coarse_evict(const BinArgs& a, Smem& s, int ca, int cb, int nthreads) {
   const int n = (cb - ca) * a.ccells;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = threadIdx.x; i < n; i += nthreads) {
     const int rr = i / a.ccells, c = i - rr * a.ccells;
     const int Gc = ca + rr;
     const int si = (Gc % kCW) * a.ccells + c;
@@ -314,20 +327,176 @@ __device__ void coarse_evict(const BinArgs& a, Smem& s, int ca, int cb) {
   }
 }
 
+// Publish (state 2) the rows this CTA stored in its previous flush.  Their stores
+// precede at least one block barrier; the fence orders them before the state store.
+// Slot t of the pending list belongs to thread t alone.
+__device__ __forceinline__ void publish_pending(const BinArgs& a, Meta& m) {
+  if (threadIdx.x < kMaxW) {
+    const int G = m.pend_row[threadIdx.x];
+    if (G >= 0) {
+      __threadfence();
+      atomicExch(&a.row_state[G], 2u);
+      m.pend_row[threadIdx.x] = -1;
+    }
+  }
+}
+
+// Partial coarse cell.  32-bit fields suffice for any set of cells in the window:
+// the residency bound keeps the whole window below 65536 points, so count, colour
+// sums and the sum of the low z halves stay below 2^32 and the sum of the high z
+// halves inside int32.
+struct CAcc {
+  unsigned cnt, zlo;
+  int zhi, mn, mx;
+  unsigned r, g, b;
+};
+
+__device__ __forceinline__ void cacc_clear(CAcc& v) {
+  v.cnt = 0u; v.zlo = 0u; v.zhi = 0; v.mn = INT_MAX; v.mx = INT_MIN; v.r = 0u; v.g = 0u; v.b = 0u;
+}
+
+// add fine cell si (an empty cell adds nothing: zero sums, min/max sentinels)
+__device__ __forceinline__ void cacc_cell(CAcc& v, const Smem& s, int si) {
+  v.cnt += s.cnt[si];
+  v.zlo += s.zlo[si];
+  v.zhi += s.zhi[si];
+  v.mn = min(v.mn, s.mn[si]);
+  v.mx = max(v.mx, s.mx[si]);
+  v.r += s.rs[si];
+  v.g += s.gs[si];
+  v.b += s.bs[si];
+}
+
+// v += the partner lane's (lane ^ 1) partial
+__device__ __forceinline__ void cacc_pair(CAcc& v) {
+  v.cnt += __shfl_xor_sync(0xffffffffu, v.cnt, 1);
+  v.zlo += __shfl_xor_sync(0xffffffffu, v.zlo, 1);
+  v.zhi += __shfl_xor_sync(0xffffffffu, v.zhi, 1);
+  v.mn = min(v.mn, __shfl_xor_sync(0xffffffffu, v.mn, 1));
+  v.mx = max(v.mx, __shfl_xor_sync(0xffffffffu, v.mx, 1));
+  v.r += __shfl_xor_sync(0xffffffffu, v.r, 1);
+  v.g += __shfl_xor_sync(0xffffffffu, v.g, 1);
+  v.b += __shfl_xor_sync(0xffffffffu, v.b, 1);
+}
+
+// Partial of coarse cell (key, c) into the coarse ring (plain read-modify-write: the
+// caller is its only writer in this pass) or, for a coarse row outside the ring,
+// into the global coarse arrays with atomics.
+__device__ __forceinline__ void cacc_emit(const BinArgs& a, Smem& s, int key, int c, int clo, const CAcc& v) {
+  if (!v.cnt) return;
+  const long long zs = (long long)v.zhi * 65536 + (long long)v.zlo;
+  if (key >= clo && key < clo + kCW) {
+    const int ci = (key % kCW) * a.ccells + c;
+    s.ccnt[ci] += v.cnt;
+    s.czs[ci] += (unsigned long long)zs;
+    s.cmn[ci] = min(s.cmn[ci], v.mn);
+    s.cmx[ci] = max(s.cmx[ci], v.mx);
+    s.crs[ci] += v.r;
+    s.cgs[ci] += v.g;
+    s.cbs[ci] += v.b;
+  } else {
+    merge_coarse(a, (int64_t)key * a.ccells + c, v.cnt, zs, v.mn, v.mx, v.r, v.g, v.b);
+  }
+}
+
+constexpr int kCoarseThreads = 64;  // warps 0-1 combine the coarse partials of a flush
+
+// Coarse reduction of a flush, step 1 (all threads): lane pair (2c, 2c + 1) of fine
+// row rr sums coarse cell c's f fine columns of that row (split at fh, combined with
+// one shuffle) and the even lane stores the partial in sp[.][rr * ccells + c].
+__device__ void coarse_partials(const BinArgs& a, Smem& s, const Meta& m, int ra, int nr) {
+  const int W = a.W;
+  const int SC = W * a.ccells;
+  const int n = 2 * SC;
+  const int nloop = (n + 31) & ~31;  // whole warps: every lane takes part in the shuffle
+  for (int e = threadIdx.x; e < nloop; e += blockDim.x) {
+    const int h = e & 1, pc = e >> 1;  // pc = rr * ccells + c
+    const int rr = pc / a.ccells, c = pc - rr * a.ccells;
+    const bool live = e < n && rr < nr && m.mode[rr] != 0;
+    CAcc v;
+    cacc_clear(v);
+    if (live) {
+      const int base = ((ra + rr) & (W - 1)) * a.rstride + c * a.gs;
+      const int k1 = h ? a.f : a.fh;
+      for (int k = h ? a.fh : 0; k < k1; ++k) cacc_cell(v, s, base + k);
+    }
+    cacc_pair(v);
+    if (h == 0 && live) {
+      s.sp[0 * SC + pc] = v.cnt;
+      s.sp[1 * SC + pc] = v.zlo;
+      s.sp[2 * SC + pc] = (unsigned)v.zhi;
+      s.sp[3 * SC + pc] = (unsigned)v.mn;
+      s.sp[4 * SC + pc] = (unsigned)v.mx;
+      s.sp[5 * SC + pc] = v.r;
+      s.sp[6 * SC + pc] = v.g;
+      s.sp[7 * SC + pc] = v.b;
+    }
+  }
+}
+
+// Step 2 (threads < kCoarseThreads): one thread per coarse column walks the touched
+// rows' partials in order and emits a coarse cell whenever the coarse row changes.
+__device__ void coarse_combine(const BinArgs& a, Smem& s, const Meta& m, int nr, int clo) {
+  const int SC = a.W * a.ccells;
+  for (int c = threadIdx.x; c < a.ccells; c += kCoarseThreads) {
+    CAcc v;
+    cacc_clear(v);
+    int key = -1;
+#pragma unroll
+    for (int rr = 0; rr < kMaxWFlush; ++rr) {
+      if (rr >= nr || m.mode[rr] == 0) continue;
+      const int kr = m.ckey[rr];
+      if (kr != key) {
+        if (key >= 0) cacc_emit(a, s, key, c, clo, v);
+        cacc_clear(v);
+        key = kr;
+      }
+      const int pc = rr * a.ccells + c;
+      v.cnt += s.sp[0 * SC + pc];
+      v.zlo += s.sp[1 * SC + pc];
+      v.zhi += (int)s.sp[2 * SC + pc];
+      v.mn = min(v.mn, (int)s.sp[3 * SC + pc]);
+      v.mx = max(v.mx, (int)s.sp[4 * SC + pc]);
+      v.r += s.sp[5 * SC + pc];
+      v.g += s.sp[6 * SC + pc];
+      v.b += s.sp[7 * SC + pc];
+    }
+    if (key >= 0) cacc_emit(a, s, key, c, clo, v);
+  }
+}
+
+// Reset the cells of ring slot `slot` to empty, all threads, coalesced.
+__device__ __forceinline__ void reset_row(const BinArgs& a, Smem& s, int slot) {
+  const int o = slot * a.rstride;
+  for (int i = threadIdx.x; i < a.rstride; i += blockDim.x) reset_cell(s, o + i);
+}
+
 // Evict fine rows [ra, rb) (rb - ra <= W, all inside the ring).  The caller has
 // synchronised the block after the last accumulation.
+//
+// Claimed rows are normally published one flush later (publish_pending at the start of
+// the next flush or of the next pass through the general path), so their stores drain
+// while the CTA streams on instead of stalling on a fence.  Deadlock freedom: a CTA
+// only ever waits on another row while it holds no unpublished claim (pending rows are
+// published before any wait; a flush that must merge publishes its own rows first).
 __device__ void evict_rows(const BinArgs& a, Smem& s, Meta& m, int ra, int rb, int& clo) {
   const int nr = rb - ra;
   if (nr <= 0) return;
   const int W = a.W;
-  // claim (0 -> 1) without waiting: a CTA never waits while it holds an unpublished
-  // claim, so two CTAs flushing overlapping rows cannot wait on each other
+  publish_pending(a, m);
+  // claim (0 -> 1) without waiting
+  bool merge_row = false;
   if (threadIdx.x < nr) {
     const int G = ra + threadIdx.x;
     const int slot = G & (W - 1);
     int mode = 0;
-    if (m.touched[slot]) mode = (atomicCAS(&a.row_state[G], 0u, 1u) == 0u) ? 1 : 2;
+    if (m.touched[slot]) {
+      mode = (atomicCAS(&a.row_state[G], 0u, 1u) == 0u) ? 1 : 2;
+      m.touched[slot] = 0;
+    }
     m.mode[threadIdx.x] = mode;
+    m.ckey[threadIdx.x] = a.has_coarse ? coarse_row_of(a, G) : 0;
+    merge_row = mode == 2;
   }
   // coarse ring: make room for the coarse rows of [ra, rb)
   if (a.has_coarse && threadIdx.x == 0) {
@@ -336,108 +505,85 @@ __device__ void evict_rows(const BinArgs& a, Smem& s, Meta& m, int ra, int rb, i
     m.clo_old = c0;
     m.clo_new = (cb >= c0 + kCW) ? cb - kCW + 1 : c0;
   }
-  __syncthreads();
+  const bool any_merge = __syncthreads_or(merge_row);
   if (a.has_coarse) {
+    // coarse ring rows leaving and per-row partials (independent data, all threads)
     const int old_clo = m.clo_old, new_clo = m.clo_new;
-    if (new_clo > old_clo) {
-      coarse_evict(a, s, old_clo, new_clo < old_clo + kCW ? new_clo : old_clo + kCW);
-      __syncthreads();
-    }
     clo = new_clo;
-    // coarse reduction of the fine rows being evicted: one thread per (fine row,
-    // coarse cell) pair sums its f fine cells, then shared atomics merge pairs that
-    // fall on the same coarse cell
-    for (int e = threadIdx.x; e < nr * a.ccells; e += blockDim.x) {
-      const int rr = e / a.ccells, c = e - rr * a.ccells;
-      if (m.mode[rr] == 0) continue;
+    if (new_clo > old_clo)
+      coarse_evict(a, s, old_clo, new_clo < old_clo + kCW ? new_clo : old_clo + kCW, blockDim.x);
+    coarse_partials(a, s, m, ra, nr);
+    __syncthreads();
+  }
+  // warps 0-1 combine the coarse partials while the others store the fine rows claimed
+  // here (every cell, empty ones as sentinels) and reset their cells
+  const int st0 = a.has_coarse ? kCoarseThreads : 0;
+  if (a.has_coarse && threadIdx.x < kCoarseThreads) coarse_combine(a, s, m, nr, clo);
+  if ((int)threadIdx.x >= st0) {
+    const int nst = blockDim.x - st0;
+    for (int rr = 0; rr < nr; ++rr) {
+      if (m.mode[rr] != 1) continue;
       const int G = ra + rr;
       const int slot = G & (W - 1);
-      unsigned cnt = 0;
-      long long zsum = 0;
-      int zmn = INT_MAX, zmx = INT_MIN;
-      unsigned long long rs = 0, gs = 0, bs = 0;
-      for (int k = 0; k < a.f; ++k) {
-        const int si = slot * a.rstride + c * a.gs + k;
-        const unsigned cn = s.cnt[si];
-        if (!cn) continue;
+      const int64_t base = (int64_t)G * a.cells;
+      for (int c = threadIdx.x - st0; c < a.cells; c += nst) {
+        const int si = sidx(a, slot, c);
         const Cell fc = read_cell(s, si);
-        cnt += cn;
-        zsum += fc.zsum;
-        zmn = min(zmn, fc.zmin);
-        zmx = max(zmx, fc.zmax);
-        rs += fc.r;
-        gs += fc.g;
-        bs += fc.b;
+        a.count[base + c] = fc.cnt;
+        a.zsum[base + c] = fc.zsum;
+        a.zmin[base + c] = fc.zmin;
+        a.zmax[base + c] = fc.zmax;
+        a.rsum[base + c] = fc.r;
+        a.gsum[base + c] = fc.g;
+        a.bsum[base + c] = fc.b;
+        reset_cell(s, si);
       }
-      if (!cnt) continue;
-      const int Gc = coarse_row_of(a, G);
-      if (Gc >= clo && Gc < clo + kCW) {
-        const int ci = (Gc % kCW) * a.ccells + c;
-        atomicAdd(&s.ccnt[ci], cnt);
-        atomicAdd(&s.czs[ci], (unsigned long long)zsum);
-        atomicMin(&s.cmn[ci], zmn);
-        atomicMax(&s.cmx[ci], zmx);
-        atomicAdd(&s.crs[ci], rs);
-        atomicAdd(&s.cgs[ci], gs);
-        atomicAdd(&s.cbs[ci], bs);
-      } else {
-        merge_coarse(a, (int64_t)Gc * a.ccells + c, cnt, zsum, zmn, zmx, rs, gs, bs);
+    }
+  }
+  if (!any_merge) {
+    if (threadIdx.x < nr && m.mode[threadIdx.x] == 1) m.pend_row[threadIdx.x] = ra + threadIdx.x;
+  } else {
+    // publish this flush's rows, then wait for rows another claim holds, then merge
+    __syncthreads();
+    if (threadIdx.x < nr) {
+      const int G = ra + threadIdx.x;
+      if (m.mode[threadIdx.x] == 1) {
+        __threadfence();
+        atomicExch(&a.row_state[G], 2u);
+      } else if (m.mode[threadIdx.x] == 2) {
+        wait_written(&a.row_state[G]);
       }
     }
     __syncthreads();
-  }
-  // fine rows claimed here: plain stores of every cell (empty cells get sentinels)
-  for (int rr = 0; rr < nr; ++rr) {
-    if (m.mode[rr] != 1) continue;
-    const int G = ra + rr;
-    const int slot = G & (W - 1);
-    const int64_t base = (int64_t)G * a.cells;
-    for (int c = threadIdx.x; c < a.cells; c += blockDim.x) {
-      const int si = sidx(a, slot, c);
-      const Cell fc = read_cell(s, si);
-      a.count[base + c] = fc.cnt;
-      a.zsum[base + c] = fc.zsum;
-      a.zmin[base + c] = fc.zmin;
-      a.zmax[base + c] = fc.zmax;
-      a.rsum[base + c] = fc.r;
-      a.gsum[base + c] = fc.g;
-      a.bsum[base + c] = fc.b;
-      reset_cell(s, si);
+    for (int rr = 0; rr < nr; ++rr) {
+      if (m.mode[rr] != 2) continue;
+      const int G = ra + rr;
+      const int slot = G & (W - 1);
+      const int64_t base = (int64_t)G * a.cells;
+      for (int c = threadIdx.x; c < a.cells; c += blockDim.x) {
+        const int si = sidx(a, slot, c);
+        const Cell fc = read_cell(s, si);
+        if (fc.cnt) merge_fine(a, base + c, fc.cnt, fc.zsum, fc.zmin, fc.zmax, fc.r, fc.g, fc.b);
+      }
     }
+    __syncthreads();
+    for (int rr = 0; rr < nr; ++rr)
+      if (m.mode[rr] == 2) reset_row(a, s, (ra + rr) & (W - 1));
   }
-  __threadfence();
-  __syncthreads();
-  // publish, then (holding no claim any more) wait for rows another CTA is writing
-  if (threadIdx.x < nr) {
-    const int G = ra + threadIdx.x;
-    if (m.mode[threadIdx.x] == 1) atomicExch(&a.row_state[G], 2u);
-    else if (m.mode[threadIdx.x] == 2) wait_written(&a.row_state[G]);
-  }
-  __syncthreads();
-  // rows written first by another CTA: merge with global atomics
-  for (int rr = 0; rr < nr; ++rr) {
-    if (m.mode[rr] != 2) continue;
-    const int G = ra + rr;
-    const int slot = G & (W - 1);
-    const int64_t base = (int64_t)G * a.cells;
-    for (int c = threadIdx.x; c < a.cells; c += blockDim.x) {
-      const int si = sidx(a, slot, c);
-      const Cell fc = read_cell(s, si);
-      if (fc.cnt) merge_fine(a, base + c, fc.cnt, fc.zsum, fc.zmin, fc.zmax, fc.r, fc.g, fc.b);
-      reset_cell(s, si);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < nr) m.touched[(ra + threadIdx.x) & (W - 1)] = 0;
   __syncthreads();
 }
 
 // Raw points of one thread's slot of a batch (kPtsPerThread consecutive points).
 struct Raw {
   int x[kPtsPerThread], y[kPtsPerThread], z[kPtsPerThread];
-  uint32_t r[kPtsPerThread], g[kPtsPerThread], b[kPtsPerThread];
+  // colours stay packed as loaded, two 16-bit values per word
+  uint32_t r[kPtsPerThread / 2], g[kPtsPerThread / 2], b[kPtsPerThread / 2];
   int n;
 };
+
+__device__ __forceinline__ uint32_t half16(const uint32_t* w, int k) {
+  return (k & 1) ? (w[k >> 1] >> 16) : (w[k >> 1] & 0xffffu);
+}
 
 __device__ __forceinline__ void load_raw(const BinArgs& a, Raw& v, int64_t i0, int64_t p1) {
   v.n = (int)((p1 - i0) < kPtsPerThread ? (p1 - i0) : kPtsPerThread);
@@ -451,21 +597,53 @@ __device__ __forceinline__ void load_raw(const BinArgs& a, Raw& v, int64_t i0, i
     v.x[0] = vx.x; v.x[1] = vx.y; v.x[2] = vx.z; v.x[3] = vx.w;
     v.y[0] = vy.x; v.y[1] = vy.y; v.y[2] = vy.z; v.y[3] = vy.w;
     v.z[0] = vz.x; v.z[1] = vz.y; v.z[2] = vz.z; v.z[3] = vz.w;
-    v.r[0] = vr.x & 0xffffu; v.r[1] = vr.x >> 16; v.r[2] = vr.y & 0xffffu; v.r[3] = vr.y >> 16;
-    v.g[0] = vg.x & 0xffffu; v.g[1] = vg.x >> 16; v.g[2] = vg.y & 0xffffu; v.g[3] = vg.y >> 16;
-    v.b[0] = vb.x & 0xffffu; v.b[1] = vb.x >> 16; v.b[2] = vb.y & 0xffffu; v.b[3] = vb.y >> 16;
+    v.r[0] = vr.x; v.r[1] = vr.y;
+    v.g[0] = vg.x; v.g[1] = vg.y;
+    v.b[0] = vb.x; v.b[1] = vb.y;
   } else {
+#pragma unroll
+    for (int k = 0; k < kPtsPerThread / 2; ++k) v.r[k] = v.g[k] = v.b[k] = 0u;
 #pragma unroll
     for (int k = 0; k < kPtsPerThread; ++k) {
       if (k < v.n) {
         v.x[k] = a.x[i0 + k]; v.y[k] = a.y[i0 + k]; v.z[k] = a.z[i0 + k];
-        v.r[k] = a.r[i0 + k]; v.g[k] = a.g[i0 + k]; v.b[k] = a.b[i0 + k];
+        const int sh = (k & 1) * 16;
+        v.r[k >> 1] |= (uint32_t)a.r[i0 + k] << sh;
+        v.g[k >> 1] |= (uint32_t)a.g[i0 + k] << sh;
+        v.b[k >> 1] |= (uint32_t)a.b[i0 + k] << sh;
       } else {
         v.x[k] = v.y[k] = v.z[k] = 0;
-        v.r[k] = v.g[k] = v.b[k] = 0u;
       }
     }
   }
+}
+
+// Prefetch into L2 of the point records [i0, min(i0 + kBatch, p1)): one 128-byte line
+// per thread (x, y, z: 128 lines each, r, g, b: 64 each for a full batch), issued
+// without waiting.
+constexpr int kPfLines = kBatch * 4 / 128 * 3 + kBatch * 2 / 128 * 3;
+static_assert(kPfLines <= kBinThreads, "one prefetch line per thread");
+__device__ __forceinline__ void prefetch_batch(const BinArgs& a, int64_t i0, int64_t p1) {
+  if (i0 >= p1 || threadIdx.x >= kPfLines) return;
+  const int64_t cnt = (p1 - i0) < kBatch ? (p1 - i0) : kBatch;
+  constexpr int l4 = kBatch * 4 / 128, l2 = kBatch * 2 / 128;
+  const int t = threadIdx.x;
+  const char* p;
+  int64_t off, bytes;
+  if (t < 3 * l4) {
+    const int arr = t / l4;
+    p = reinterpret_cast<const char*>(arr == 0 ? a.x : arr == 1 ? a.y : a.z);
+    off = (int64_t)(t - arr * l4) * 128;
+    bytes = cnt * 4;
+    p += i0 * 4;
+  } else {
+    const int u = t - 3 * l4, arr = u / l2;
+    p = reinterpret_cast<const char*>(arr == 0 ? a.r : arr == 1 ? a.g : a.b);
+    off = (int64_t)(u - arr * l2) * 128;
+    bytes = cnt * 2;
+    p += i0 * 2;
+  }
+  if (off < bytes) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
 }
 
 __device__ __forceinline__ void accumulate(Smem& s, Meta& m, const BinArgs& a, int slot, int col, int z, uint32_t r,
@@ -487,16 +665,16 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
   __shared__ Meta m;
   const int WC = a.W * a.rstride;
   const int CC = a.has_coarse ? kCW * a.ccells : 0;
-  Smem s = carve(smem_raw, WC, CC);
+  Smem s = carve(smem_raw, WC, CC);  // partials after the coarse ring
   for (int i = threadIdx.x; i < WC; i += blockDim.x) reset_cell(s, i);
   for (int i = threadIdx.x; i < CC; i += blockDim.x) {
     s.crs[i] = 0ull; s.cgs[i] = 0ull; s.cbs[i] = 0ull; s.czs[i] = 0ull;
     s.ccnt[i] = 0u; s.cmn[i] = INT_MAX; s.cmx[i] = INT_MIN;
   }
-  if (threadIdx.x < kMaxW) { m.touched[threadIdx.x] = 0; m.enter[threadIdx.x] = 0; }
+  if (threadIdx.x < kMaxW) { m.touched[threadIdx.x] = 0; m.enter[threadIdx.x] = 0; m.pend_row[threadIdx.x] = -1; }
   if (threadIdx.x == 0) { m.dropped = 0ull; m.n_late = 0ull; m.n_inplace = 0; m.oldest = 0; }
   __syncthreads();
-  unsigned long long my_dropped = 0, my_late = 0;
+  unsigned my_dropped = 0, my_late = 0;  // per thread: far below 2^32 points
   const int W = a.W;
 
   for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
@@ -505,11 +683,12 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
     int lo = -1;   // lowest fine row of the window (uniform); -1 = empty
     int clo = -1;  // lowest coarse row of the coarse ring
     int batch = 0;
-    Raw cur, nxt;
-    load_raw(a, cur, p0 + (int64_t)threadIdx.x * kPtsPerThread, p1);
+    Raw cur;
+    for (int d = 1; d < kPfDist; ++d) prefetch_batch(a, p0 + (int64_t)d * kBatch, p1);
     for (int64_t b0 = p0; b0 < p1; b0 += kBatch, ++batch) {
-      // prefetch the next batch while this one is processed
-      if (b0 + kBatch < p1) load_raw(a, nxt, b0 + kBatch + (int64_t)threadIdx.x * kPtsPerThread, p1);
+      // keep the L2 kPfDist batches ahead of the loads
+      prefetch_batch(a, b0 + (int64_t)kPfDist * kBatch, p1);
+      load_raw(a, cur, b0 + (int64_t)threadIdx.x * kPtsPerThread, p1);
       int G[kPtsPerThread], col[kPtsPerThread];
       unsigned pend = 0;
 #pragma unroll
@@ -549,21 +728,25 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
 #pragma unroll
         for (int k = 0; k < kPtsPerThread; ++k) {
           if (!(pend & (1u << k))) continue;
-          accumulate(s, m, a, G[k] & (W - 1), col[k], cur.z[k], cur.r[k], cur.g[k], cur.b[k]);
+          accumulate(s, m, a, G[k] & (W - 1), col[k], cur.z[k], half16(cur.r, k), half16(cur.g, k), half16(cur.b, k));
         }
       } else {
-        // ---- general case: late points, window slides
+        // ---- general case: late points, window slides.  Rows of the last flush are
+        // published first, so a late point never waits on a claim of this CTA.  Only
+        // the first pass can meet late points: every slide keeps the window at or
+        // below the lowest pending row.
+        publish_pending(a, m);
         while (true) {
           if (lo >= 0) {
 #pragma unroll
             for (int k = 0; k < kPtsPerThread; ++k) {
               if (!(pend & (1u << k))) continue;
               if (G[k] < lo) {
-                late_point(a, G[k], col[k], cur.z[k], cur.r[k], cur.g[k], cur.b[k]);
+                late_point(a, G[k], col[k], cur.z[k], half16(cur.r, k), half16(cur.g, k), half16(cur.b, k));
                 ++my_late;
                 pend &= ~(1u << k);
               } else if (G[k] < lo + W) {
-                accumulate(s, m, a, G[k] & (W - 1), col[k], cur.z[k], cur.r[k], cur.g[k], cur.b[k]);
+                accumulate(s, m, a, G[k] & (W - 1), col[k], cur.z[k], half16(cur.r, k), half16(cur.g, k), half16(cur.b, k));
                 pend &= ~(1u << k);
               }
             }
@@ -611,18 +794,18 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
         }
         __syncthreads();
       }
-      cur = nxt;
     }
     // ---- end of the span: flush everything
     __syncthreads();
     if (lo >= 0) evict_rows(a, s, m, lo, lo + W, clo);
     if (a.has_coarse && clo >= 0) {
-      coarse_evict(a, s, clo, clo + kCW);
+      coarse_evict(a, s, clo, clo + kCW, blockDim.x);
       __syncthreads();
     }
   }
+  publish_pending(a, m);
   {
-    const unsigned lt = __reduce_add_sync(0xffffffffu, (unsigned)my_late);
+    const unsigned lt = __reduce_add_sync(0xffffffffu, my_late);
     if ((threadIdx.x & 31) == 0 && lt) atomicAdd((unsigned long long*)&m.n_late, (unsigned long long)lt);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -631,8 +814,9 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
     }
   }
   if (a.dropped) {
-    my_dropped = __reduce_add_sync(0xffffffffu, (unsigned)my_dropped);
-    if ((threadIdx.x & 31) == 0 && my_dropped) atomicAdd((unsigned long long*)&m.dropped, my_dropped);
+    my_dropped = __reduce_add_sync(0xffffffffu, my_dropped);
+    if ((threadIdx.x & 31) == 0 && my_dropped)
+      atomicAdd((unsigned long long*)&m.dropped, (unsigned long long)my_dropped);
     __syncthreads();
     if (threadIdx.x == 0 && m.dropped) atomicAdd((unsigned long long*)a.dropped, m.dropped);
   }
@@ -661,6 +845,33 @@ __global__ void k_bin_finalize(BinArgs a) {
 }
 
 }  // namespace
+
+// Group stride gs (f <= gs < f + 4) and column split fh (1 <= fh <= f) of the coarse
+// partials.  The lanes of a warp (coarse columns c0 + j, j < 16, groups h < 2, one fine
+// row) read words j * gs + h * fh + k at step k; while both groups are active a step
+// costs as many shared-memory wavefronts as the busiest bank has lanes, afterwards as
+// many as the first group alone needs.  Fewest wavefronts win, then fewest steps, then
+// the smallest stride.  E.g. f = 10: gs = 10, fh = 5 puts all 32 lanes on distinct banks.
+static void bin_coarse_layout(int f, int32_t* gs_out, int32_t* fh_out) {
+  int64_t best = INT64_MAX;
+  *gs_out = f;
+  *fh_out = f;
+  for (int gs = f; gs < f + 4; ++gs) {
+    int hits1[32] = {};
+    int worst1 = 0;
+    for (int j = 0; j < 16; ++j) worst1 = std::max(worst1, ++hits1[(j * gs) % 32]);
+    for (int split = 1; split <= f; ++split) {
+      int hits[32] = {};
+      int worst = 0;
+      for (int j = 0; j < 16; ++j)
+        for (int h = 0; h < 2; ++h) worst = std::max(worst, ++hits[(j * gs + h * split) % 32]);
+      const int both = std::min(split, f - split), steps = std::max(split, f - split);
+      const int64_t wavefronts = (int64_t)both * worst + (int64_t)(steps - both) * worst1;
+      const int64_t score = (wavefronts << 24) + ((int64_t)steps << 4) + (gs - f);
+      if (score < best) { best = score; *gs_out = gs; *fh_out = split; }
+    }
+  }
+}
 
 // Validates and builds the kernel arguments (shared with the fixed-scratch entry).
 ls_status bin_prepare(const ls_points* pts, const ls_region* region, const ls_bins* levels,
@@ -715,20 +926,23 @@ ls_status bin_prepare(const ls_points* pts, const ls_region* region, const ls_bi
     a.crsum = L1.rsum; a.cgsum = L1.gsum; a.cbsum = L1.bsum;
     *n_coarse = T * L1.cells * L1.cells;
   }
-  a.gs = (a.f % 2) ? a.f : a.f + 1;
-  a.rstride = (a.cells / a.f) * a.gs;
-  // window rows: the largest power of two <= 8 whose ring fits in ~196 KB of shared memory
-  const size_t budget = 196 * 1024;
+  bin_coarse_layout(a.f, &a.gs, &a.fh);
+  // window rows: the largest power of two <= 8 whose rings fit in ~220 KB of shared memory
+  const size_t budget = 220 * 1024;
   int W = 8;
-  const int CC = a.has_coarse ? kCW * a.ccells : 0;
-  while (W > 1 && smem_bytes(W * a.rstride, CC) > budget) W >>= 1;
   if (W > a.cells) {
     W = 1;
     while (W * 2 <= a.cells) W *= 2;
   }
-  if (smem_bytes(W * a.rstride, CC) > budget) return LS_ERR_UNSUPPORTED;
+  const int CC = a.has_coarse ? kCW * a.ccells : 0;
+  a.rstride = (a.cells / a.f) * a.gs;
+  auto need = [&](int w) { return smem_bytes(w * a.rstride, CC, a.has_coarse ? w * a.ccells : 0); };
+  while (W > 1 && need(W) > budget) W >>= 1;
+  if (need(W) > budget) return LS_ERR_UNSUPPORTED;
+  // every fine column's slot lies inside its row: sidx(col) < (cells / f) * gs <= rstride
+  if (a.rstride < (a.cells / a.f) * a.gs || a.fh < 1 || a.fh > a.f) return LS_ERR_UNSUPPORTED;
   a.W = W;
-  *smem = smem_bytes(W * a.rstride, CC);
+  *smem = need(W);
   // vector loads need 16-byte aligned int32 arrays and 8-byte aligned uint16 arrays
   a.narrow = region->x0_cm >= INT32_MIN && region->x0_cm <= INT32_MAX && region->y0_cm >= INT32_MIN &&
              region->y0_cm <= INT32_MAX;
@@ -753,7 +967,7 @@ ls_status bin_launch(BinArgs a, size_t smem, int64_t n_coarse, cudaStream_t stre
   LS_CUDA_TRY(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
     LS_CUDA_TRY(cudaFuncSetAttribute(k_bin_main, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     210 * 1024));
+                                     kBinSmemAttr));
     attr_set[dev] = true;
   }
   const int64_t work = a.n_rows > n_coarse ? a.n_rows : n_coarse;
