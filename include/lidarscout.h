@@ -102,7 +102,8 @@ typedef struct {
  * level is reduced exactly from the fine one.  All outputs are overwritten.
  * dropped: device uint64[1] or NULL; receives the number of points outside the
  * region.  pts->tile_offsets is not needed and ignored.
- * Uses library scratch (per-row states) of 4 bytes per fine row of the region.
+ * Uses library scratch of 4 bytes per fine row of the region (per-row states) plus a
+ * 4-byte work counter.
  * Errors: LS_ERR_INVALID_ARG (null pointer, cells not dividing tile_cm, > 2 levels,
  * fine level over 4096 cells), LS_ERR_NO_MEMORY, LS_ERR_CUDA.  A bounded device wait
  * that ran out sets LS_ERR_TIMEOUT in the sticky status.

@@ -44,6 +44,7 @@ constexpr int kCW = 4;  // coarse ring rows
 constexpr int kMaxWFlush = 8;  // window rows (W <= 8)
 constexpr int kBinSmemAttr = 224 * 1024;  // dynamic shared memory allowed (budget + margin)
 constexpr int kPfDist = 2;  // batches prefetched into L2 ahead of the loads
+constexpr int kSpansPerCta = 16;  // dynamic load balance vs. rows shared at span ends
 
 struct BinArgs {
   const int32_t* __restrict__ x;
@@ -71,7 +72,7 @@ struct BinArgs {
   int32_t* czmin;
   int32_t* czmax;
   uint64_t *crsum, *cgsum, *cbsum;
-  uint32_t* row_state;
+  uint32_t* row_state;    // [n_rows] claim states, then the span counter
   uint64_t* dropped;
   int64_t span;
   int64_t n_items;
@@ -119,6 +120,7 @@ struct Meta {
   int clo_old, clo_new;  // coarse ring scratch of evict_rows (not shared with block_min)
   int n_inplace;
   int oldest;  // lowest entry batch over the window's slots
+  long long item;  // span taken from the counter
   // rows this CTA claimed and stored in its last flush, published (state 2) later
   int pend_row[kMaxW];  // -1: none
   unsigned long long dropped;
@@ -677,7 +679,14 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
   unsigned my_dropped = 0, my_late = 0;  // per thread: far below 2^32 points
   const int W = a.W;
 
-  for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+  // spans are handed out dynamically: their cost depends on how many strips (window
+  // slides) they hold, not only on their point count
+  uint32_t* span_counter = a.row_state + a.n_rows;
+  while (true) {
+    if (threadIdx.x == 0) m.item = atomicAdd(span_counter, 1u);
+    __syncthreads();
+    const int64_t item = m.item;
+    if (item >= a.n_items) break;
     const int64_t p0 = item * a.span;
     const int64_t p1 = p0 + a.span < a.n ? p0 + a.span : a.n;
     int lo = -1;   // lowest fine row of the window (uniform); -1 = empty
@@ -832,7 +841,10 @@ __global__ void k_bin_prologue(BinArgs a, int64_t n_coarse) {
     a.ccount[i] = 0u; a.czsum[i] = 0; a.czmin[i] = INT_MAX; a.czmax[i] = INT_MIN;
     a.crsum[i] = 0ull; a.cgsum[i] = 0ull; a.cbsum[i] = 0ull;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && a.dropped) *a.dropped = 0ull;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.row_state[a.n_rows] = 0u;  // span counter
+    if (a.dropped) *a.dropped = 0ull;
+  }
 }
 
 // Epilogue: rows that no point reached get the empty sentinels.
@@ -950,9 +962,9 @@ ls_status bin_prepare(const ls_points* pts, const ls_region* region, const ls_bi
   a.y0_32 = a.narrow ? (int32_t)region->y0_cm : 0;
   a.vec = (((uintptr_t)a.x | (uintptr_t)a.y | (uintptr_t)a.z) % 16 == 0) &&
           (((uintptr_t)a.r | (uintptr_t)a.g | (uintptr_t)a.b) % 8 == 0);
-  // spans: about 4 per CTA, multiples of the batch size
+  // spans: about kSpansPerCta per CTA, multiples of the batch size
   const int64_t grid = kSmCount;
-  int64_t span = (a.n + grid * 4 - 1) / (grid * 4);
+  int64_t span = (a.n + grid * kSpansPerCta - 1) / (grid * kSpansPerCta);
   span = (span + kBatch - 1) / kBatch * kBatch;
   if (span < kBatch) span = kBatch;
   a.span = span;
@@ -998,7 +1010,7 @@ extern "C" ls_status ls_bin_points(const ls_points* pts, const ls_region* region
   int64_t n_coarse = 0;
   ls_status st = ls::bin_prepare(pts, region, levels, n_levels, dropped, &a, &smem, &n_coarse);
   if (st != LS_OK) return st;
-  a.row_state = static_cast<uint32_t*>(ls::workspace(ls::kWsBinRows, (size_t)a.n_rows * 4));
+  a.row_state = static_cast<uint32_t*>(ls::workspace(ls::kWsBinRows, ((size_t)a.n_rows + 1) * 4));
   if (!a.row_state) return LS_ERR_NO_MEMORY;
   return ls::bin_launch(a, smem, n_coarse, reinterpret_cast<cudaStream_t>(stream));
 }
@@ -1014,7 +1026,7 @@ extern "C" ls_status ls_bin_points(const ls_points* pts, const ls_region* region
 namespace ls {
 namespace {
 constexpr int64_t kFixedBinRows = int64_t(1) << 20;  // 4 MiB of row states
-static __device__ __align__(256) uint32_t g_bin_rows_fixed[kFixedBinRows];
+static __device__ __align__(256) uint32_t g_bin_rows_fixed[kFixedBinRows + 64];  // + span counter
 std::mutex g_fixed_mu;
 uint32_t* g_fixed_ptr[64] = {};
 }  // namespace
