@@ -63,7 +63,7 @@ def bin_traffic_per_point():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms during the timed region."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -76,7 +76,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -388,18 +388,20 @@ def oracle_tiles_per_s(tiles_pts, region, budget_s):
 
 
 def _sample_tiles_host(pts, counts, region, k):
+    """k tiles spread over the density range, copied to the host one at a time (the
+    copy happens outside the oracle's timed calls)."""
     order = np.argsort(counts)
     pick = order[np.linspace(0, len(order) - 1, k).astype(int)]
+    rng = np.random.default_rng(0)
+    pick = pick[rng.permutation(len(pick))]  # a budget stop still sees the whole density range
     offs = np.concatenate([[0], np.cumsum(counts)])
-    out = []
     for t in pick:
         a, b = int(offs[t]), int(offs[t + 1])
-        out.append((int(t), {kk: pts[kk][a:b].cpu().numpy() for kk in "xyzrgb"}))
-    return out
+        yield int(t), {kk: pts[kk][a:b].cpu().numpy() for kk in "xyzrgb"}
 
 
 def cpu_baseline(pts, counts, region, budget_s=12.0):
-    tiles = _sample_tiles_host(pts, counts, region, 12)
+    tiles = _sample_tiles_host(pts, counts, region, 256)
     tps, done, used = oracle_tiles_per_s(tiles, region, budget_s)
     return {"value": round(tps, 3), "unit": "tiles/s", "cores": 1, "kind": "oracle",
             "sample": f"{done} tiles of the batched region spread over the density range "
@@ -434,8 +436,9 @@ def run_reference(args, rank, world):
 
 
 def run_profile_case(args):
-    """Small case for profilers: binning only (640^2 + 64^2) of a 3x3-tile region at
-    the batched-region densities (~17M points, ~300 MB, larger than L2)."""
+    """Small case for profilers: binning only (640^2 + 64^2) of a k x k-tile region at
+    the batched-region densities (k = 3: ~17M points, ~300 MB; k = 8: ~140M points,
+    ~2.6 GB; both larger than L2)."""
     import torch
     import paper_2509_20198_b300 as lsb
     import synth
@@ -443,8 +446,9 @@ def run_profile_case(args):
     from paper_2509_20198_b300 import build
     build.build_library()
     build.build_synth()
-    region = synth.Region(tiles_x=3, tiles_y=3)
-    counts = synth.lognormal_counts(SEED, 9)
+    k = args.case_tiles
+    region = synth.Region(tiles_x=k, tiles_y=k)
+    counts = synth.lognormal_counts(SEED, k * k)
     pts = sg.region_points(SEED, region, counts)
     out, dropped = lsb.bin_points(pts, region, levels=(640, 64))
     for _ in range(args.steps):
@@ -459,12 +463,13 @@ def run_profile_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--overview", type=int, default=1, help="also time the 40,000-tile overview fills")
     ap.add_argument("--case", default="", choices=["", "bin-small"], help="profiling case instead of the bench")
+    ap.add_argument("--case-tiles", type=int, default=3, help="tiles per side of the profiling case")
     ap.add_argument("--train-tiles", type=int, default=4096)
     ap.add_argument("--train-epochs", type=int, default=20)
     args = ap.parse_args()
