@@ -460,6 +460,38 @@ def run_profile_case(args):
     return 0 if st == 0 else 1
 
 
+def run_learned_case(args):
+    """Profiling case for the learned filler: one forward pass and one training step
+    (forward, loss, backward, AdamW) of the U-Net on a batch of random bf16 inputs, with
+    He-initialised weights; --case-tiles sets the batch."""
+    import torch
+    import paper_2509_20198_b300 as lsb
+    from paper_2509_20198_b300 import build
+    from paper_2509_20198_b300 import train as T
+    build.build_library()
+    n = args.case_tiles
+    f = lsb.Filler(max_batch=n)
+    T.init_params(f, seed=0)
+    g = torch.Generator(device="cpu").manual_seed(SEED)
+    x = torch.zeros((n, 64, 64, 8), dtype=torch.bfloat16)
+    x[..., :5] = torch.randn((n, 64, 64, 5), generator=g).to(torch.bfloat16)
+    x = x.view(torch.int16).cuda()
+    base = torch.zeros((n, 64, 64, 4), device="cuda")
+    target = torch.randn((n, 64, 64, 4), generator=g).mul(0.1).cuda()
+    mask = torch.ones((n, 64, 64), dtype=torch.uint8, device="cuda")
+    m, v = torch.zeros_like(f.params), torch.zeros_like(f.params)
+    for step in range(1, args.steps + 1):
+        y = f.forward(x)
+        loss, dy = lsb.filler_loss(y, base, target, mask, 1.0)
+        grads = f.backward(dy)
+        lsb.adamw_step(f.params, grads, m, v, step, lr=1e-4)
+        f.load()
+    torch.cuda.synchronize()
+    st = lsb.last_error()
+    print(json.dumps({"case": "learned", "tiles": n, "status": st, "loss": [float(t) for t in loss.cpu()]}))
+    return 0 if st == 0 else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -468,13 +500,15 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--overview", type=int, default=1, help="also time the 40,000-tile overview fills")
-    ap.add_argument("--case", default="", choices=["", "bin-small"], help="profiling case instead of the bench")
+    ap.add_argument("--case", default="", choices=["", "bin-small", "learned"], help="profiling case instead of the bench")
     ap.add_argument("--case-tiles", type=int, default=3, help="tiles per side of the profiling case")
     ap.add_argument("--train-tiles", type=int, default=4096)
     ap.add_argument("--train-epochs", type=int, default=20)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.case == "learned":
+        sys.exit(run_learned_case(args))
     if args.case:
         sys.exit(run_profile_case(args))
     if args.impl == "reference":

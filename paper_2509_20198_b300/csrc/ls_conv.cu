@@ -4,7 +4,8 @@
 // (Sec. 3.4: a U-Net-inspired CNN refines the heightmaps) in its forward pass and,
 // with transposed and flipped weights, in the input-gradient pass of training.
 //
-// Per CTA (persistent over 128-pixel tiles, one CTA per SM, 6 warps):
+// Per CTA (persistent over 128-pixel tiles, one CTA per SM, 6 warps, a ring of up to 8
+// operand stages in about 200 KB of shared memory):
 //  warp 0  TMA producer: per 8-channel chunk of one tap, one 4-D tiled TMA load of
 //          the shifted 128-pixel slab (out-of-range rows/columns are zero-filled by
 //          the TMA unit: that is the padding) and one 1-D bulk copy of the
@@ -19,12 +20,14 @@
 // the packed weights of a stage are C_out rows x 8 chunks (LBO C_out*16 B, SBO 128 B).
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "ls_tc.cuh"
 
 namespace ls {
 
 bool encode_tmap_bf16_4d(CUtensorMap* map, const void* base, const uint64_t dims[4], const uint64_t strides[3],
-                         const uint32_t box[4]) {
+                         const uint32_t box[4], int swizzle_bytes) {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
     cudaDriverEntryPointQueryResult q;
@@ -39,17 +42,23 @@ bool encode_tmap_bf16_4d(CUtensorMap* map, const void* base, const uint64_t dims
   cuuint64_t s[3] = {strides[0], strides[1], strides[2]};
   cuuint32_t b[4] = {box[0], box[1], box[2], box[3]};
   cuuint32_t e[4] = {1, 1, 1, 1};
+  const CUtensorMapSwizzle sw = swizzle_bytes == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                : swizzle_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                                      : CU_TENSOR_MAP_SWIZZLE_NONE;
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), d, s, b, e,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 namespace {
 
 constexpr int kConvThreads = 192;
-constexpr int kConvStages = 4;
+constexpr int kConvStages = 8;            // most stages; a launch uses as many as fit
+constexpr size_t kConvSmemBudget = 200 * 1024;
 constexpr int kChunksPerStage = 8;
 constexpr int kAStageBytes = kChunksPerStage * 2048;
+constexpr int kMaxLoads = 9 * 256 / 8;  // TMA loads per 128-pixel tile at most (C_in <= 256)
 
 struct ConvArgs {
   const uint16_t* __restrict__ wpk;
@@ -60,6 +69,11 @@ struct ConvArgs {
   int32_t tiles_per_img, rows_per_tile, imgs_per_tile;
   int32_t relu;
   uint32_t acc_cols, tmem_cols, stage_bytes, idesc;
+  int32_t ring;  // stages in use (<= kConvStages)
+  // A operand: cw-channel blocks of one tap per TMA load (cw = 64 or 32: rows of
+  // 128 / 64 bytes, 128B / 64B swizzle; cw = 8: 8 unswizzled chunks per stage)
+  int32_t cw, cblocks, blocks_per_stage, n_blocks;
+  uint32_t blk_bytes, sbo_a, swz;
 };
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
@@ -73,10 +87,26 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   __shared__ __align__(8) uint64_t full[kConvStages], empty[kConvStages], tfull[2], tempty[2];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
+  // per TMA load of a tile: channel offset | (kx << 16) | (ky << 20), in load order
+  __shared__ uint32_t ktab[kMaxLoads];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_loads = a.cw == 8 ? a.kc : a.n_blocks;
+  for (int i = threadIdx.x; i < n_loads; i += blockDim.x) {
+    int ci, tap;
+    if (a.cw == 8) {
+      const int c = i < a.kc_real ? i : 0;  // padding chunk: any finite data, its weights are zero
+      tap = c / a.cpt;
+      ci = (c - tap * a.cpt) * 8;
+    } else {
+      tap = i / a.cblocks;
+      ci = (i - tap * a.cblocks) * a.cw;
+    }
+    const int ky = tap / 3, kx = tap - ky * 3;
+    ktab[i] = (uint32_t)ci | ((uint32_t)kx << 16) | ((uint32_t)ky << 20);
+  }
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kConvStages; ++i) {
+    for (int i = 0; i < a.ring; ++i) {
       tc::mbar_init(&full[i], 1);
       tc::mbar_init(&empty[i], 1);
     }
@@ -96,7 +126,10 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
-    int it = 0;
+    int slot = 0;
+    uint32_t ph = 0;
+    const int per_stage = a.cw == 8 ? kChunksPerStage : a.blocks_per_stage;
+    const uint32_t load_bytes = a.cw == 8 ? 2048u : a.blk_bytes;
     for (int m = blockIdx.x; m < a.n_mtiles && !abort_flag; m += gridDim.x) {
       int n0, y0;
       if (a.imgs_per_tile == 1) {
@@ -106,48 +139,58 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         n0 = m * a.imgs_per_tile;
         y0 = 0;
       }
-      for (int s = 0; s < a.n_stages; ++s, ++it) {
-        const int slot = it % kConvStages;
-        const uint32_t ph = (uint32_t)(it / kConvStages) & 1u;
+      int li = 0;  // next TMA load of this tile
+      for (int s = 0; s < a.n_stages; ++s) {
         if (!tc::mbar_wait(&empty[slot], ph ^ 1u)) { abort_flag = 1; break; }
         const int c0 = s * kChunksPerStage;
         const int nc = min(kChunksPerStage, a.kc - c0);
+        const int nl = min(per_stage, n_loads - li);
         uint8_t* A = smem + (size_t)slot * a.stage_bytes;
         uint8_t* B = A + kAStageBytes;
-        tc::mbar_arrive_expect_tx(&full[slot], (uint32_t)(nc * 2048 + nc * a.cout * 16));
-        for (int k = 0; k < nc; ++k) {
-          int c = c0 + k;
-          if (c >= a.kc_real) c = 0;  // padding chunk: any finite data, its weights are zero
-          const int tap = c / a.cpt, c8 = c - tap * a.cpt;
-          const int ky = tap / 3, kx = tap - ky * 3;
-          tc::tma_load_4d(A + k * 2048, &xmap, c8 * 8, kx - 1, y0 + ky - 1, n0, &full[slot]);
+        tc::mbar_arrive_expect_tx(&full[slot], (uint32_t)nl * load_bytes + (uint32_t)(nc * a.cout * 16));
+        for (int k = 0; k < nl; ++k, ++li) {
+          const uint32_t e = ktab[li];
+          tc::tma_load_4d(A + k * load_bytes, &xmap, (int)(e & 0xffffu), (int)((e >> 16) & 15u) - 1,
+                          y0 + (int)(e >> 20) - 1, n0, &full[slot]);
         }
         tc::bulk_load(B, a.wpk + (size_t)c0 * a.cout * 8, (uint32_t)(nc * a.cout * 16), &full[slot]);
+        if (++slot == a.ring) { slot = 0; ph ^= 1u; }
       }
     }
   } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    int it = 0, ai = 0;
+    // ---------------- MMA issuer: descriptors are the stage's base plus fixed offsets,
+    // so each MMA costs one add (a single thread feeds the tensor core)
+    uint32_t aoff[4], boff[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      aoff[j] = a.cw == 8 ? (uint32_t)j * 4096u
+                          : (uint32_t)((j * 16) / a.cw) * a.blk_bytes + (uint32_t)(((j * 16) % a.cw) / 16) * 32u;
+      boff[j] = (uint32_t)(j * 2 * a.cout * 16);
+    }
+    const uint32_t s0 = tc::saddr(smem);
+    const uint64_t adesc0 = a.cw == 8 ? tc::sdesc(s0, 2048, 128) : tc::sdesc_sw(s0, a.sbo_a, a.swz);
+    const uint64_t bdesc0 = tc::sdesc(s0 + kAStageBytes, a.cout * 16, 128);
+    const int last_nk = (a.kc - (a.n_stages - 1) * kChunksPerStage) / 2;
+    int slot = 0, ai = 0;
+    uint32_t ph = 0;
     for (int m = blockIdx.x; m < a.n_mtiles && !abort_flag; m += gridDim.x, ++ai) {
       const int acc = ai & 1;
       const uint32_t aph = (uint32_t)(ai >> 1) & 1u;
       if (!tc::mbar_wait(&tempty[acc], aph ^ 1u)) { abort_flag = 1; break; }
       tc::fence_after();
       const uint32_t d = taddr + (uint32_t)acc * a.acc_cols;
-      for (int s = 0; s < a.n_stages; ++s, ++it) {
-        const int slot = it % kConvStages;
-        const uint32_t ph = (uint32_t)(it / kConvStages) & 1u;
+      for (int s = 0; s < a.n_stages; ++s) {
         if (!tc::mbar_wait(&full[slot], ph)) { abort_flag = 1; break; }
         tc::fence_after();
-        const uint32_t A = tc::saddr(smem + (size_t)slot * a.stage_bytes);
-        const uint32_t B = A + kAStageBytes;
-        const int nc = min(kChunksPerStage, a.kc - s * kChunksPerStage);
-        for (int j = 0; j < nc / 2; ++j) {
-          const uint64_t ad = tc::sdesc(A + j * 4096, 2048, 128);
-          const uint64_t bd = tc::sdesc(B + j * 2 * a.cout * 16, a.cout * 16, 128);
-          tc::mma_bf16(d, ad, bd, a.idesc, (s > 0 || j > 0) ? 1u : 0u);
-        }
+        const uint64_t so = (uint64_t)((slot * a.stage_bytes) >> 4);
+        const int nk = s == a.n_stages - 1 ? last_nk : 4;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (j < nk)
+            tc::mma_bf16(d, adesc0 + so + (aoff[j] >> 4), bdesc0 + so + (boff[j] >> 4), a.idesc,
+                         (s > 0 || j > 0) ? 1u : 0u);
         tc::mma_commit(&empty[slot]);
+        if (++slot == a.ring) { slot = 0; ph ^= 1u; }
       }
       tc::mma_commit(&tfull[acc]);
     }
@@ -245,7 +288,7 @@ int chunk_count(int cin) {
 ls_status conv3x3_launch(const uint16_t* x, const uint16_t* wpk, const float* bias, const uint16_t* mask, int relu,
                          int n, int h, int w, int cin, int cout, uint16_t* y, cudaStream_t stream) {
   if (!x || !wpk || !y || n <= 0 || h <= 0 || w <= 0) return LS_ERR_INVALID_ARG;
-  if (cin < 8 || cin % 8 || cout < 16 || cout > 256 || cout % 16) return LS_ERR_UNSUPPORTED;
+  if (cin < 8 || cin % 8 || cin > 256 || cout < 16 || cout > 256 || cout % 16) return LS_ERR_UNSUPPORTED;
   if (w > 128 || 128 % w) return LS_ERR_UNSUPPORTED;
   if (((uintptr_t)x | (uintptr_t)wpk | (uintptr_t)y | (uintptr_t)mask) % 16) return LS_ERR_INVALID_ARG;
   ConvArgs a = {};
@@ -275,6 +318,15 @@ ls_status conv3x3_launch(const uint16_t* x, const uint16_t* wpk, const float* bi
   a.kc_real = 9 * a.cpt;
   a.kc = chunk_count(cin);
   a.n_stages = (a.kc + kChunksPerStage - 1) / kChunksPerStage;
+  // widest channel block per TMA load: fewer, longer rows for the TMA unit
+  a.cw = cin % 64 == 0 ? 64 : cin % 32 == 0 ? 32 : 8;
+  a.cblocks = cin / a.cw;
+  a.blocks_per_stage = 64 / a.cw;
+  a.n_blocks = 9 * a.cblocks;
+  a.blk_bytes = (uint32_t)(128 * a.cw * 2);
+  a.sbo_a = (uint32_t)(8 * a.cw * 2);  // 8 rows of one swizzle atom
+  a.swz = a.cw == 64 ? 2u : a.cw == 32 ? 4u : 0u;
+  box[0] = (uint32_t)a.cw;
   a.acc_cols = 32;
   while ((int)a.acc_cols < cout) a.acc_cols <<= 1;
   a.tmem_cols = 2 * a.acc_cols;
@@ -283,14 +335,16 @@ ls_status conv3x3_launch(const uint16_t* x, const uint16_t* wpk, const float* bi
   CUtensorMap map;
   const uint64_t dims[4] = {(uint64_t)cin, (uint64_t)w, (uint64_t)h, (uint64_t)n};
   const uint64_t strides[3] = {(uint64_t)cin * 2, (uint64_t)w * cin * 2, (uint64_t)h * w * cin * 2};
-  if (!encode_tmap_bf16_4d(&map, x, dims, strides, box)) return LS_ERR_CUDA;
-  const size_t smem = (size_t)kConvStages * a.stage_bytes;
+  if (!encode_tmap_bf16_4d(&map, x, dims, strides, box, a.cw == 8 ? 0 : a.cw * 2)) return LS_ERR_CUDA;
+  a.ring = (int32_t)std::min<size_t>(kConvStages, kConvSmemBudget / a.stage_bytes);
+  if (a.ring < 2) return LS_ERR_UNSUPPORTED;
+  const size_t smem = (size_t)a.ring * a.stage_bytes;
   static bool attr_set[64] = {};
   int dev = 0;
   LS_CUDA_TRY(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
     LS_CUDA_TRY(cudaFuncSetAttribute(k_conv3x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kConvStages * (kAStageBytes + 256 * 128)));
+                                     (int)kConvSmemBudget));
     attr_set[dev] = true;
   }
   k_conv3x3<<<grid_cap(a.n_mtiles, kSmCount), kConvThreads, smem, stream>>>(map, a);

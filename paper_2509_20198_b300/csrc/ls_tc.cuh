@@ -78,6 +78,19 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
   d |= (uint64_t)1 << 46;
   return d;
 }
+// K-major with swizzling (the layout a TMA tile load writes with the same swizzle):
+// rows of 32/64/128 bytes, 8-row atoms SBO bytes apart, the K offset inside a row
+// given by the start address; mode = 6 (32-byte), 4 (64-byte) or 2 (128-byte) in bits
+// 61-63; LBO is not used by these layouts (encoded as 1).
+__device__ __forceinline__ uint64_t sdesc_sw(uint32_t addr, uint32_t sbo, uint32_t mode) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)(mode & 7u) << 61;
+  return d;
+}
 // kind::f16 instruction descriptor: BF16 A and B, FP32 accumulator, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
@@ -121,10 +134,30 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Four 8x8 b16 matrices from shared memory (threads 8i..8i+7 give the 16-byte row
+// addresses of matrix i); thread t receives row t/4, columns 2(t%4), 2(t%4)+1 of each.
+__device__ __forceinline__ void ldmatrix_x4(uint32_t addr, uint32_t (&r)[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr)
+               : "memory");
+}
+// Store four 8x8 b16 matrices transposed: the fragment layout of ldmatrix_x4 in,
+// row j of the transposed matrix i written at the address given by thread 8i + j.
+__device__ __forceinline__ void stmatrix_x4_trans(uint32_t addr, const uint32_t (&r)[4]) {
+  asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3])
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 }  // namespace tc
 
 // Host: encode a tiled tensor map through the driver entry point (no libcuda link).
+// swizzle_bytes: 0 (none), 32, 64 or 128 (the inner box extent in bytes must equal it).
 bool encode_tmap_bf16_4d(CUtensorMap* map, const void* base, const uint64_t dims[4], const uint64_t strides[3],
-                         const uint32_t box[4]);
+                         const uint32_t box[4], int swizzle_bytes = 0);
 
 }  // namespace ls

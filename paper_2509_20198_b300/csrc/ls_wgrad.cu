@@ -1,11 +1,23 @@
 // Weight and bias gradients of a 3x3 convolution on the tensor cores (training of the
 // learned filler, Sec. 3.4).  dW^T[k][o] = sum_p X_shift(k)[p] dZ[p][o] with
 // k = tap * C_in + c_in: a GEMM with M = 9*C_in (tiles of 128 rows), N = C_out and
-// K = pixels.  Both operands are stored pixel-minor (NHWC), so the CUDA-core warps
-// transpose them into K-major shared-memory tiles (one 16-byte global load feeds an
-// 8-row column of a core matrix); one thread issues tcgen05.mma kind::f16 with the
-// FP32 accumulator in TMEM.  Each CTA owns one 128-row tile and one slice of
-// pixels; partial sums are added into the FP32 gradient with atomics.
+// K = pixels (64 per stage).  Each CTA owns one 128-row tile and one slice of pixels;
+// partial sums are added into the FP32 gradient with atomics.
+//
+// Both operands are stored pixel-minor (NHWC), while the MMA reads K-major tiles
+// (pixels contiguous), so every stage is transposed once in shared memory:
+//  warp 0     TMA producer: the M tile's rows are 128 / cw blocks of cw channels of one
+//             tap (cw = 64, 32 or 8 dividing C_in): one 4-D tiled load per block of the
+//             tap-shifted input (cw channels x 64 pixels, zero-filled outside the image:
+//             the padding; rows of 128 / 64 bytes are written with the 128B / 64B
+//             swizzle), and dZ in blocks of cwb output channels, into a raw ring;
+//  warps 1-4  transpose raw -> K-major core matrices with ldmatrix (8x8 b16 blocks:
+//             8 pixel rows of one 16-byte channel chunk, un-swizzled by address) and
+//             stmatrix.trans, 4 blocks per instruction pair, then make the tile visible
+//             to the tensor core (fence.proxy.async);
+//             at the end they read the accumulator from TMEM (one row per thread);
+//  warp 5     issues tcgen05.mma kind::f16 (M=128, N=C_out, K=16) and commits.
+// The bias gradient is a column sum of dZ (k_colsum).
 #include <cuda_bf16.h>
 
 #include "ls_tc.cuh"
@@ -13,157 +25,223 @@
 namespace ls {
 namespace {
 
-constexpr int kWgThreads = 160;        // warps 0-3 stage + epilogue, warp 4 issues MMAs
-constexpr int kWgStages = 3;
-constexpr int kWgPix = 64;             // pixels (K) per stage
+constexpr int kWgThreads = 192;
+constexpr int kWgRaw = 3;   // raw (TMA) stages
+constexpr int kWgOps = 3;   // operand (K-major) stages
+constexpr int kWgPix = 64;  // pixels (K) per stage
 constexpr int kWgABytes = 128 * kWgPix * 2;
 
+// Byte offset in a raw stage of channel ch (multiple of 8) of pixel px, the stage being
+// a sequence of blocks of cw channels x 64 pixels as the TMA wrote them: pixel rows of
+// 2*cw bytes; 16-byte chunk c of row px sits at chunk c ^ (px & 7) (128B swizzle, cw 64)
+// or c ^ ((px >> 1) & 3) (64B swizzle, cw 32); cw 8 rows are plain 16-byte rows.
+__device__ __forceinline__ uint32_t raw_off(int ch, int px, int cw) {
+  const int blk = ch / cw, c = (ch - blk * cw) >> 3;
+  const uint32_t base = (uint32_t)blk * (kWgPix * cw * 2) + (uint32_t)px * (uint32_t)(cw * 2);
+  const int sc = cw == 64 ? (c ^ (px & 7)) : cw == 32 ? (c ^ ((px >> 1) & 3)) : c;
+  return base + (uint32_t)sc * 16u;
+}
+
 struct WgArgs {
-  const uint16_t* __restrict__ x;   // layer input  [P][cin]
-  const uint16_t* __restrict__ dz;  // output grad  [P][cout] (ReLU-masked)
-  float* __restrict__ dwt;          // [9*cin][cout] fp32, accumulated
-  float* __restrict__ db;           // [cout] fp32, accumulated (m-tile 0 only)
-  int32_t n, h, w, cin, cout, rows;  // rows = 9*cin
+  float* __restrict__ dwt;  // [9*cin][cout] fp32, accumulated
+  int32_t cw, cwb;                // channel block widths of the x and dZ loads
+  int32_t h, w, cin, cout, rows;  // rows = 9*cin
+  int32_t rows_per_step;          // image rows per 64-pixel stage (64 / w, or h)
+  int32_t imgs_per_step;          // images per stage (1, or 64 / (h * w))
   int64_t pix_total, pix_per_cta;
   int32_t n_mtiles;
-  uint32_t idesc, tmem_cols;
+  uint32_t idesc, tmem_cols, b_bytes;
 };
 
-__global__ void __launch_bounds__(kWgThreads, 1) k_wgrad(const WgArgs a) {
+__global__ void __launch_bounds__(kWgThreads, 1)
+    k_wgrad(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap dzmap, const WgArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t full[kWgStages], empty[kWgStages], done;
+  __shared__ __align__(8) uint64_t raw_full[kWgRaw], raw_empty[kWgRaw], op_full[kWgOps], op_empty[kWgOps], done;
   __shared__ uint32_t tmem_base;
-  __shared__ float dbs[256];
   __shared__ volatile int abort_flag;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
-  const uint32_t b_bytes = (uint32_t)a.cout * kWgPix * 2;
-  const uint32_t stage_bytes = kWgABytes + b_bytes;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t stage_bytes = kWgABytes + a.b_bytes;
+  uint8_t* raw = smem;
+  uint8_t* ops = smem + (size_t)kWgRaw * stage_bytes;
   const int mt = blockIdx.x % a.n_mtiles;
   const int64_t slice = blockIdx.x / a.n_mtiles;
   const int64_t p_begin = slice * a.pix_per_cta;
   const int64_t p_end = min(p_begin + a.pix_per_cta, a.pix_total);
   const int n_steps = (int)((p_end - p_begin + kWgPix - 1) / kWgPix);
   const int m0 = mt * 128;
+  const int n_og = a.cout / 8;
 
-  if (tid == 0) {
-    for (int i = 0; i < kWgStages; ++i) {
-      tc::mbar_init(&full[i], 128);
-      tc::mbar_init(&empty[i], 1);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kWgRaw; ++i) {
+      tc::mbar_init(&raw_full[i], 1);
+      tc::mbar_init(&raw_empty[i], 4);
+    }
+    for (int i = 0; i < kWgOps; ++i) {
+      tc::mbar_init(&op_full[i], 4);
+      tc::mbar_init(&op_empty[i], 1);
     }
     tc::mbar_init(&done, 1);
     abort_flag = 0;
     tc::mbar_fence_init();
+    tc::prefetch_tmap(&xmap);
+    tc::prefetch_tmap(&dzmap);
   }
-  if (tid < 256) dbs[tid] = 0.f;
-  if (warp == 4) tc::tmem_alloc(&tmem_base, a.tmem_cols);
+  if (warp == 5) tc::tmem_alloc(&tmem_base, a.tmem_cols);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t taddr = tmem_base;
 
-  if (warp < 4) {
-    // ---------------- staging (128 threads)
-    const int og_n = a.cout / 8;
-    const int og = tid % og_n;           // fixed output-channel group: bias partials in registers
-    float dbp[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int s = 0; s < n_steps && !abort_flag; ++s) {
-      const int slot = s % kWgStages;
-      const uint32_t ph = (uint32_t)(s / kWgStages) & 1u;
-      if (!tc::mbar_wait(&empty[slot], ph ^ 1u)) { abort_flag = 1; break; }
-      uint8_t* A = smem + (size_t)slot * stage_bytes;
-      uint8_t* B = A + kWgABytes;
-      const int64_t p0 = p_begin + (int64_t)s * kWgPix;
-      // A: 16 row groups x 64 pixels; element (k_l, p_l) at
-      //    (k_l/8)*128 + (p_l/8)*2048 + (k_l%8)*16 + (p_l%8)*2
-      for (int e = tid; e < 16 * kWgPix; e += 128) {
-        const int g = e / kWgPix, pl = e - g * kWgPix;
-        const int64_t p = p0 + pl;
-        const int k = m0 + g * 8;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (p < p_end && k < a.rows) {
-          const int tap = k / a.cin, ci = k - tap * a.cin;
-          const int ky = tap / 3, kx = tap - ky * 3;
-          const int64_t hw = (int64_t)a.h * a.w;
-          const int64_t nn = p / hw;
-          const int rem = (int)(p - nn * hw);
-          const int yy = rem / a.w + ky - 1, xx = rem % a.w + kx - 1;
-          if (yy >= 0 && yy < a.h && xx >= 0 && xx < a.w)
-            v = *reinterpret_cast<const uint4*>(a.x + ((nn * a.h + yy) * a.w + xx) * a.cin + ci);
-        }
-        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
-        uint16_t* base = reinterpret_cast<uint16_t*>(A + g * 128 + (pl >> 3) * 2048) + (pl & 7);
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer: the tile's block coordinates are fixed, the
+      // pixel position advances by one stage (64 pixels) at a time
+      const int64_t hw = (int64_t)a.h * a.w;
+      const int blk_a = kWgPix * a.cw * 2, blk_b = kWgPix * a.cwb * 2;  // bytes per block load
+      int n_valid = 0;  // blocks of the tile inside the 9*C_in rows
+      int bc[16], bx[16], by[16];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          base[(2 * j) * 8] = (uint16_t)(vv[j] & 0xffffu);
-          base[(2 * j + 1) * 8] = (uint16_t)(vv[j] >> 16);
+      for (int i = 0; i < 16; ++i) {
+        const int k = m0 + i * a.cw;  // a block never straddles two taps: cw divides C_in
+        bc[i] = bx[i] = by[i] = 0;
+        if (i < 128 / a.cw && k < a.rows) {
+          const int tap = k / a.cin;
+          bc[i] = k - tap * a.cin;
+          by[i] = tap / 3 - 1;
+          bx[i] = tap - (tap / 3) * 3 - 1;
+          ++n_valid;
         }
       }
-      // B: C_out/8 row groups x 64 pixels; element (o, p_l) at
-      //    (o/8)*128 + (p_l/8)*(C_out*16) + (o%8)*16 + (p_l%8)*2
-      for (int e = tid; e < og_n * kWgPix; e += 128) {
-        const int pl = e / og_n;  // og == e % og_n == tid % og_n (128 is a multiple of og_n)
-        const int64_t p = p0 + pl;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (p < p_end) v = *reinterpret_cast<const uint4*>(a.dz + p * a.cout + og * 8);
-        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
-        uint16_t* base = reinterpret_cast<uint16_t*>(B + og * 128 + (pl >> 3) * (a.cout * 16)) + (pl & 7);
+      const int n_ob = a.cout / a.cwb;
+      const uint32_t bytes = (uint32_t)(n_valid * blk_a + n_ob * blk_b);
+      int n0 = (int)(p_begin / hw);
+      int y0 = a.imgs_per_step > 1 ? 0 : (int)((p_begin - (int64_t)n0 * hw) / a.w);
+      int slot = 0;
+      uint32_t ph = 0;
+      for (int s = 0; s < n_steps && !abort_flag; ++s) {
+        if (!tc::mbar_wait(&raw_empty[slot], ph ^ 1u)) { abort_flag = 1; break; }
+        uint8_t* RA = raw + (size_t)slot * stage_bytes;
+        uint8_t* RB = RA + kWgABytes;
+        tc::mbar_arrive_expect_tx(&raw_full[slot], bytes);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const uint16_t lo = (uint16_t)(vv[j] & 0xffffu), hi = (uint16_t)(vv[j] >> 16);
-          base[(2 * j) * 8] = lo;
-          base[(2 * j + 1) * 8] = hi;
-          dbp[2 * j] += __uint_as_float((uint32_t)lo << 16);
-          dbp[2 * j + 1] += __uint_as_float((uint32_t)hi << 16);
+        for (int i = 0; i < 16; ++i)
+          if (i < n_valid) tc::tma_load_4d(RA + i * blk_a, &xmap, bc[i], bx[i], y0 + by[i], n0, &raw_full[slot]);
+        for (int ob = 0; ob < n_ob; ++ob)
+          tc::tma_load_4d(RB + ob * blk_b, &dzmap, ob * a.cwb, 0, y0, n0, &raw_full[slot]);
+        // next 64 pixels: more rows of this image, or the next image(s)
+        if (a.imgs_per_step > 1) {
+          n0 += a.imgs_per_step;
+        } else {
+          y0 += a.rows_per_step;
+          if (y0 >= a.h) { y0 = 0; ++n0; }
         }
+        if (++slot == kWgRaw) { slot = 0; ph ^= 1u; }
       }
-      // generic-proxy writes must be visible to the tensor core (async proxy)
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      tc::mbar_arrive(&full[slot]);
     }
-    if (mt == 0) {
+  } else if (warp <= 4) {
+    // ---------------- transposers (warps 1-4), then epilogue
+    const int tw = warp - 1;
+    const int mi = lane >> 3, mj = lane & 7;  // matrix of this lane's row address, row within it
+    const int n_aitems = 32;                  // 16 row groups x 2 quads of pixel groups
+    const int n_items = n_aitems + n_og * 2;
+    // this warp's items (at most 8 of A and 8 of B): lane offsets from the raw stage's
+    // and the operand stage's bases, computed once
+    uint32_t src[16], dst[16];
+    int mine = 0;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) atomicAdd(&dbs[og * 8 + j], dbp[j]);
+    for (int q = 0; q < 16; ++q) {
+      const int it = tw + 4 * q;
+      src[q] = dst[q] = 0u;
+      if (it < n_items) {
+        ++mine;
+        if (it < n_aitems) {
+          // A block (row group g, pixel group pg): raw rows = pixels, K-major core
+          // matrix rows = channels (16 B = 8 pixels)
+          const int g = it >> 1, pg = (it & 1) * 4 + mi;
+          src[q] = raw_off(g * 8, pg * 8 + mj, a.cw);
+          dst[q] = g * 128 + pg * 2048 + mj * 16;
+        } else {
+          const int u = it - n_aitems, og = u >> 1, pg = (u & 1) * 4 + mi;
+          src[q] = kWgABytes + raw_off(og * 8, pg * 8 + mj, a.cwb);
+          dst[q] = kWgABytes + og * 128 + pg * (a.cout * 16) + mj * 16;
+        }
+      }
+    }
+    for (int s = 0; s < n_steps && !abort_flag; ++s) {
+      const int rs = s % kWgRaw, os = s % kWgOps;
+      if (!tc::mbar_wait(&raw_full[rs], (uint32_t)(s / kWgRaw) & 1u)) { abort_flag = 1; break; }
+      if (!tc::mbar_wait(&op_empty[os], ((uint32_t)(s / kWgOps) & 1u) ^ 1u)) { abort_flag = 1; break; }
+      const uint32_t RA = tc::saddr(raw + (size_t)rs * stage_bytes);
+      const uint32_t OA = tc::saddr(ops + (size_t)os * stage_bytes);
+      // four loads in flight before their stores
+#pragma unroll
+      for (int q0 = 0; q0 < 16; q0 += 4) {
+        if (q0 < mine) {
+          uint32_t r[4][4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (q0 + q < mine) tc::ldmatrix_x4(RA + src[q0 + q], r[q]);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (q0 + q < mine) tc::stmatrix_x4_trans(OA + dst[q0 + q], r[q]);
+        }
+      }
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        tc::mbar_arrive(&raw_empty[rs]);
+        tc::mbar_arrive(&op_full[os]);
+      }
     }
     // ---------------- epilogue: TMEM row (k) per thread, atomics into dW^T
     if (n_steps > 0 && !abort_flag && tc::mbar_wait(&done, 0)) {
       tc::fence_after();
-      const int row = (warp & 3) * 32 + lane;
-      const int k = m0 + row;
+      const int q = warp & 3;
+      const int k = m0 + q * 32 + lane;
       for (int c0 = 0; c0 < a.cout; c0 += 16) {
         float v[16];
-        tc::tmem_ld16(taddr + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, v);
+        tc::tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
         if (k < a.rows) {
 #pragma unroll
           for (int i = 0; i < 16; ++i) atomicAdd(&a.dwt[(int64_t)k * a.cout + c0 + i], v[i]);
         }
       }
     }
-  } else if (warp == 4 && lane == 0) {
-    // ---------------- MMA issuer
+  } else if (lane == 0) {
+    // ---------------- MMA issuer (warp 5): descriptors are the stage's base + offsets
+    const uint32_t o0 = tc::saddr(ops);
+    const uint64_t adesc0 = tc::sdesc(o0, 2048, 128);
+    const uint64_t bdesc0 = tc::sdesc(o0 + kWgABytes, a.cout * 16, 128);
     for (int s = 0; s < n_steps && !abort_flag; ++s) {
-      const int slot = s % kWgStages;
-      const uint32_t ph = (uint32_t)(s / kWgStages) & 1u;
-      if (!tc::mbar_wait(&full[slot], ph)) { abort_flag = 1; break; }
+      const int os = s % kWgOps;
+      if (!tc::mbar_wait(&op_full[os], (uint32_t)(s / kWgOps) & 1u)) { abort_flag = 1; break; }
       tc::fence_after();
-      const uint32_t A = tc::saddr(smem + (size_t)slot * stage_bytes);
-      const uint32_t B = A + kWgABytes;
+      const uint64_t so = (uint64_t)((os * stage_bytes) >> 4);
 #pragma unroll
-      for (int j = 0; j < kWgPix / 16; ++j) {
-        const uint64_t ad = tc::sdesc(A + j * 2 * 2048, 2048, 128);
-        const uint64_t bd = tc::sdesc(B + j * 2 * (a.cout * 16), a.cout * 16, 128);
-        tc::mma_bf16(taddr, ad, bd, a.idesc, (s > 0 || j > 0) ? 1u : 0u);
-      }
-      tc::mma_commit(&empty[slot]);
+      for (int j = 0; j < kWgPix / 16; ++j)
+        tc::mma_bf16(taddr, adesc0 + so + (uint64_t)(j * 4096 >> 4), bdesc0 + so + (uint64_t)((j * 2 * a.cout * 16) >> 4),
+                     a.idesc, (s > 0 || j > 0) ? 1u : 0u);
+      tc::mma_commit(&op_empty[os]);
     }
     if (n_steps > 0) tc::mma_commit(&done);
   }
   tc::fence_before();
   __syncthreads();
-  if (mt == 0 && tid < a.cout && a.db) atomicAdd(&a.db[tid], dbs[tid]);
-  if (warp == 4) {
+  if (warp == 5) {
     tc::fence_after();
     tc::tmem_dealloc(taddr, a.tmem_cols);
   }
+}
+
+// db[o] += sum_p dz[p][o]: each thread sums one channel over a strided set of pixels.
+__global__ void k_colsum(const uint16_t* __restrict__ dz, int64_t pix, int cout, float* __restrict__ db) {
+  const int per_block = blockDim.x / cout;  // pixel lanes per block
+  const int c = threadIdx.x % cout, pl = threadIdx.x / cout;
+  if (pl >= per_block) return;
+  float acc = 0.f;
+  for (int64_t p = (int64_t)blockIdx.x * per_block + pl; p < pix; p += (int64_t)gridDim.x * per_block)
+    acc += __uint_as_float((uint32_t)dz[p * cout + c] << 16);
+  atomicAdd(&db[c], acc);
 }
 
 }  // namespace
@@ -171,11 +249,18 @@ __global__ void __launch_bounds__(kWgThreads, 1) k_wgrad(const WgArgs a) {
 // Accumulates into dwt ([9*cin][cout], fp32) and db ([cout], may be NULL).
 ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int w, int cin, int cout, float* dwt,
                        float* db, cudaStream_t stream) {
-  if (!x || !dz || !dwt || n <= 0) return LS_ERR_INVALID_ARG;
+  if (!x || !dz || !dwt || n <= 0 || h <= 0 || w <= 0) return LS_ERR_INVALID_ARG;
   if (cin % 8 || cout < 16 || cout > 128 || cout % 16) return LS_ERR_UNSUPPORTED;
+  // a stage is 64 pixels: whole image rows of one image, or whole images
+  const int64_t hw = (int64_t)h * w;
+  if (w > kWgPix || kWgPix % w || (hw % kWgPix && kWgPix % hw)) return LS_ERR_UNSUPPORTED;
+  if (hw < kWgPix && n % (kWgPix / hw)) return LS_ERR_UNSUPPORTED;
+  if (((uintptr_t)x | (uintptr_t)dz) % 16) return LS_ERR_INVALID_ARG;
   WgArgs a = {};
-  a.x = x; a.dz = dz; a.dwt = dwt; a.db = db;
-  a.n = n; a.h = h; a.w = w; a.cin = cin; a.cout = cout; a.rows = 9 * cin;
+  a.dwt = dwt;
+  a.h = h; a.w = w; a.cin = cin; a.cout = cout; a.rows = 9 * cin;
+  a.rows_per_step = hw >= kWgPix ? kWgPix / w : h;
+  a.imgs_per_step = hw >= kWgPix ? 1 : (int32_t)(kWgPix / hw);
   a.pix_total = (int64_t)n * h * w;
   a.n_mtiles = (a.rows + 127) / 128;
   // about 2 waves of CTAs over the SMs, slices a multiple of the stage
@@ -188,16 +273,34 @@ ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int 
   a.idesc = tc::idesc_bf16(128, cout);
   a.tmem_cols = 32;
   while ((int)a.tmem_cols < cout) a.tmem_cols <<= 1;
-  const size_t smem = (size_t)kWgStages * (kWgABytes + cout * kWgPix * 2);
+  a.b_bytes = (uint32_t)cout * kWgPix * 2;
+  // widest channel blocks per TMA load (fewer, longer rows), dividing the channel counts
+  a.cw = cin % 64 == 0 ? 64 : cin % 32 == 0 ? 32 : 8;
+  a.cwb = cout % 64 == 0 ? 64 : cout % 32 == 0 ? 32 : 8;
+  CUtensorMap xmap, dzmap;
+  const uint32_t box[4] = {(uint32_t)a.cw, (uint32_t)w, (uint32_t)a.rows_per_step, (uint32_t)a.imgs_per_step};
+  const uint32_t boxb[4] = {(uint32_t)a.cwb, (uint32_t)w, (uint32_t)a.rows_per_step, (uint32_t)a.imgs_per_step};
+  const uint64_t xd[4] = {(uint64_t)cin, (uint64_t)w, (uint64_t)h, (uint64_t)n};
+  const uint64_t xs[3] = {(uint64_t)cin * 2, (uint64_t)w * cin * 2, (uint64_t)h * w * cin * 2};
+  const uint64_t zd[4] = {(uint64_t)cout, (uint64_t)w, (uint64_t)h, (uint64_t)n};
+  const uint64_t zs[3] = {(uint64_t)cout * 2, (uint64_t)w * cout * 2, (uint64_t)h * w * cout * 2};
+  if (!encode_tmap_bf16_4d(&xmap, x, xd, xs, box, a.cw == 8 ? 0 : a.cw * 2) ||
+      !encode_tmap_bf16_4d(&dzmap, dz, zd, zs, boxb, a.cwb == 8 ? 0 : a.cwb * 2))
+    return LS_ERR_CUDA;
+  const size_t smem = (size_t)(kWgRaw + kWgOps) * (kWgABytes + a.b_bytes);
   static bool attr_set[64] = {};
   int dev = 0;
   LS_CUDA_TRY(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
     LS_CUDA_TRY(cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kWgStages * (kWgABytes + 128 * kWgPix * 2)));
+                                     (kWgRaw + kWgOps) * (kWgABytes + 128 * kWgPix * 2)));
     attr_set[dev] = true;
   }
-  k_wgrad<<<(unsigned)(slices * a.n_mtiles), kWgThreads, smem, stream>>>(a);
+  k_wgrad<<<(unsigned)(slices * a.n_mtiles), kWgThreads, smem, stream>>>(xmap, dzmap, a);
+  if (db) {
+    const int threads = 256 - 256 % cout;
+    k_colsum<<<kSmCount * 2, threads, 0, stream>>>(dz, a.pix_total, cout, db);
+  }
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 
