@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import subprocess
 import sys
@@ -32,6 +33,21 @@ METRIC = "heightmap tiles/s (plain vs learned fill), full-res points binned/s, %
 WORKLOAD = "batched-region 16x16 tiles x 640 m, lognormal(ln4,0.8) pts/m^2, bin 640^2+64^2, extract, gaussian fill 64^2, tile update"
 SEED = 2
 BIN_SRC = os.path.join(ROOT, "paper_2509_20198_b300", "csrc", "ls_bin.cu")
+
+
+# U-Net of the learned filler (64x64 input, widths 32/64/128): 3x3 convolutions
+# 2 * pixels * 9 * C_in * C_out per layer plus the 1x1 head; training = forward +
+# input gradients + weight gradients (3x the forward)
+FWD_FLOP_PER_TILE = 2 * (4096 * 9 * (8 * 32 + 32 * 32 + 96 * 32 + 32 * 32) + 1024 * 9 * (32 * 64 + 64 * 64 + 192 * 64
+                         + 64 * 64) + 256 * 9 * (64 * 128 + 128 * 128)) + 2 * 4096 * 32 * 5
+TRAIN_FLOP_PER_TILE = 3 * FWD_FLOP_PER_TILE
+
+
+def bf16_sustained():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["bf16_tflops_sustained"])
+    return 1400.0
 
 
 def peaks():
@@ -278,11 +294,15 @@ def run_overview(lsb, args, dev, stream):
     # train the filler (tensor-core forward/backward) on self-generated pairs
     t0 = time.perf_counter()
     train_set = T.synthetic_tiles(args.train_tiles, seed0=100, device=dev)
+    torch.cuda.synchronize()
+    data_s = time.perf_counter() - t0
     filler = lsb.Filler(max_batch=4096, device=dev)
     T.init_params(filler, seed=0)
+    t1 = time.perf_counter()
     hist = T.train(filler, train_set, epochs=args.train_epochs, batch=256, lr=1e-3)
     torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
+    train_s = time.perf_counter() - t1
+    tile_steps = (args.train_tiles // 256) * 256 * args.train_epochs
     del train_set
     ids = torch.arange(nT, dtype=torch.int32, device=dev)
     lh = torch.empty((nT, 64, 64), dtype=torch.float32, device=dev)
@@ -296,6 +316,12 @@ def run_overview(lsb, args, dev, stream):
                                                     used_fallback=fb, scratch=scratch, stream=stream),
                            max(1, args.steps // 5))
     assert lsb.last_error() == 0
+    # the network's own output on every tile (no fallback), for its RMSE
+    nh = torch.empty_like(lh)
+    nc = torch.empty_like(lc)
+    with torch.cuda.stream(stream):
+        lsb.fill_learned(filler, s, region, ids, max_err_m=math.inf, height=nh, rgb=nc, scratch=scratch, stream=stream)
+    torch.cuda.synchronize()
     # truth on a seeded 400-tile subset: full points of those tiles only, binned at 64x64
     sub = np.sort(np.random.default_rng(400).choice(nT, 400, replace=False))
     full = np.zeros_like(counts)
@@ -317,9 +343,19 @@ def run_overview(lsb, args, dev, stream):
             "learned_fill": {"tiles_per_s": round(nT / (ms_learned * 1e-3), 1), "ms": round(ms_learned, 3),
                              "batch": 4096, "height_rmse_m": round(rm(lh[sub_t]), 4),
                              "rgb_rmse_8bit": round(rc(lc[sub_t]), 3),
-                             "fallback_tiles": int(fb.sum()), "max_err_m": 2.0},
+                             "fallback_tiles": int(fb.sum()), "max_err_m": 2.0,
+                             "network_height_rmse_m": round(rm(nh[sub_t]), 4),
+                             "network_rgb_rmse_8bit": round(rc(nc[sub_t]), 3),
+                             # whole learned fill (raster, U-Net forward, finish) against the
+                             # network's 0.925 GFLOP per tile, bf16 sustained peak
+                             "tflops": round(FWD_FLOP_PER_TILE * nT / (ms_learned * 1e-3) / 1e12, 1),
+                             "frac_of_bf16_sustained": round(FWD_FLOP_PER_TILE * nT / (ms_learned * 1e-3) / 1e12
+                                                             / bf16_sustained(), 4)},
             "training": {"tiles": args.train_tiles, "epochs": args.train_epochs, "batch": 256,
-                         "seconds": round(train_s, 1), "loss_first": [round(v, 7) for v in hist[0]],
+                         "seconds": round(train_s, 2), "data_seconds": round(data_s, 2),
+                         "tiles_per_s": round(tile_steps / train_s, 1),
+                         "tflops": round(TRAIN_FLOP_PER_TILE * tile_steps / train_s / 1e12, 1),
+                         "loss_first": [round(v, 7) for v in hist[0]],
                          "loss_last": [round(v, 7) for v in hist[-1]], "loss_parts": "total, height, colour, bound"},
             "truth": "per-texel mean of the full-resolution points, 400 seeded tiles"}
 
@@ -503,7 +539,7 @@ def main():
     ap.add_argument("--case", default="", choices=["", "bin-small", "learned"], help="profiling case instead of the bench")
     ap.add_argument("--case-tiles", type=int, default=3, help="tiles per side of the profiling case")
     ap.add_argument("--train-tiles", type=int, default=4096)
-    ap.add_argument("--train-epochs", type=int, default=20)
+    ap.add_argument("--train-epochs", type=int, default=60)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

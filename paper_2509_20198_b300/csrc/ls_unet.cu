@@ -166,15 +166,18 @@ __global__ void k_head_fwd(const uint16_t* __restrict__ top, int c, const float*
   }
 }
 
-// ---- head backward: dtop = (dy W) masked by top > 0 (bf16); dW, db into grads -----
-__global__ void k_head_bwd(const uint16_t* __restrict__ top, int c, const float* __restrict__ wb,
-                           const float* __restrict__ dy, int64_t P, uint16_t* __restrict__ dtop,
-                           float* __restrict__ gw /* [kOut*c + kOut] */) {
-  extern __shared__ float sh[];  // weights [kOut*c], partial grads [kOut*c + kOut]
+// ---- head backward: dtop = (dy W) masked by top > 0 (bf16); this block's dW, db into
+// part[block] (warps combined in a fixed order; k_head_sum adds the blocks in order) --
+constexpr int kHeadThreads = 256;
+__global__ void __launch_bounds__(kHeadThreads) k_head_bwd(const uint16_t* __restrict__ top, int c,
+                                                           const float* __restrict__ wb, const float* __restrict__ dy,
+                                                           int64_t P, uint16_t* __restrict__ dtop,
+                                                           float* __restrict__ part /* [blocks][kOut*c + kOut] */) {
+  extern __shared__ float sh[];  // weights [kOut*c], per-warp partial grads [warps][kOut*c + kOut]
+  const int ng = kOut * c + kOut, nw = blockDim.x / 32, warp = threadIdx.x >> 5;
   float* sw = sh;
-  float* sg = sh + kOut * c;
+  float* sg = sh + kOut * c + warp * ng;
   for (int i = threadIdx.x; i < kOut * c; i += blockDim.x) sw[i] = wb[i];
-  for (int i = threadIdx.x; i < kOut * c + kOut; i += blockDim.x) sg[i] = 0.f;
   __syncthreads();
   float gacc[kOut * 8];
   for (int i = 0; i < kOut * 8; ++i) gacc[i] = 0.f;
@@ -206,17 +209,31 @@ __global__ void k_head_bwd(const uint16_t* __restrict__ top, int c, const float*
       for (int i = 0; i < 8; ++i) {
         float s = gacc[k * 8 + i];
         for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&sg[k * c + g * 8 + i], s);
+        if ((threadIdx.x & 31) == 0) sg[k * c + g * 8 + i] = s;
       }
     if (g == 0)
       for (int k = 0; k < kOut; ++k) {
         float s = gb[k];
         for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&sg[kOut * c + k], s);
+        if ((threadIdx.x & 31) == 0) sg[kOut * c + k] = s;
       }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kOut * c + kOut; i += blockDim.x) atomicAdd(&gw[i], sg[i]);
+  const float* all = sh + kOut * c;
+  for (int i = threadIdx.x; i < ng; i += blockDim.x) {
+    float s = 0.f;
+    for (int w = 0; w < nw; ++w) s += all[w * ng + i];
+    part[(size_t)blockIdx.x * ng + i] = s;
+  }
+}
+
+// grads of the head += its per-block partials, blocks in increasing order
+__global__ void k_head_sum(const float* __restrict__ part, int blocks, int ng, float* __restrict__ gw) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int b = 0; b < blocks; ++b) s += part[(size_t)b * ng + i];
+    gw[i] += s;
+  }
 }
 
 // ---- dW^T [9*cin_pad][cout] (+ db) into the flat fp32 gradient ---------------------
@@ -606,8 +623,15 @@ extern "C" ls_status ls_filler_backward(ls_model* m, const float* params, const 
   ls_status st;
   // head
   uint16_t* gz = m->gbuf[0];
-  k_head_bwd<<<grid_cap((P + 255) / 256, kSmCount * 4), 256, (size_t)(2 * kOut * hd.cin + kOut) * 4, s>>>(
-      out_of(nl - 2), hd.cin, params + hd.w_off, dy, P, gz, grads + hd.w_off);
+  {
+    const int blocks = grid_cap((P + kHeadThreads - 1) / kHeadThreads, kSmCount * 4);
+    const int ng = kOut * hd.cin + kOut;
+    float* part = static_cast<float*>(workspace(kWsHeadPart, (size_t)blocks * ng * 4));
+    if (!part) return LS_ERR_NO_MEMORY;
+    const size_t smem = (size_t)(kOut * hd.cin + (kHeadThreads / 32) * ng) * 4;
+    k_head_bwd<<<blocks, kHeadThreads, smem, s>>>(out_of(nl - 2), hd.cin, params + hd.w_off, dy, P, gz, part);
+    k_head_sum<<<grid_for(ng, 256), 256, 0, s>>>(part, blocks, ng, grads + hd.w_off);
+  }
   int li = nl - 2;  // d1b
   int gi = 0;
   // decoder levels 1 .. L-1 (reverse of the forward order)

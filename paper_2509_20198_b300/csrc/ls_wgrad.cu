@@ -1,8 +1,9 @@
 // Weight and bias gradients of a 3x3 convolution on the tensor cores (training of the
 // learned filler, Sec. 3.4).  dW^T[k][o] = sum_p X_shift(k)[p] dZ[p][o] with
 // k = tap * C_in + c_in: a GEMM with M = 9*C_in (tiles of 128 rows), N = C_out and
-// K = pixels (64 per stage).  Each CTA owns one 128-row tile and one slice of pixels;
-// partial sums are added into the FP32 gradient with atomics.
+// K = pixels (64 per stage).  Each CTA owns one 128-row tile and one slice of pixels
+// and stores its partial sums; k_wsum adds them to the FP32 gradient in a fixed order,
+// so the result does not depend on CTA scheduling (training is reproducible).
 //
 // Both operands are stored pixel-minor (NHWC), while the MMA reads K-major tiles
 // (pixels contiguous), so every stage is transposed once in shared memory:
@@ -17,7 +18,8 @@
 //             to the tensor core (fence.proxy.async);
 //             at the end they read the accumulator from TMEM (one row per thread);
 //  warp 5     issues tcgen05.mma kind::f16 (M=128, N=C_out, K=16) and commits.
-// The bias gradient is a column sum of dZ (k_colsum).
+// The bias gradient is a column sum of dZ (k_colsum, per-block partials, then k_dbsum
+// in block order).
 #include <cuda_bf16.h>
 
 #include "ls_tc.cuh"
@@ -43,7 +45,7 @@ __device__ __forceinline__ uint32_t raw_off(int ch, int px, int cw) {
 }
 
 struct WgArgs {
-  float* __restrict__ dwt;  // [9*cin][cout] fp32, accumulated
+  float* __restrict__ part;  // [CTAs][128][cout] fp32 partial sums (CTA = slice * n_mtiles + tile)
   int32_t cw, cwb;                // channel block widths of the x and dZ loads
   int32_t h, w, cin, cout, rows;  // rows = 9*cin
   int32_t rows_per_step;          // image rows per 64-pixel stage (64 / w, or h)
@@ -193,17 +195,19 @@ __global__ void __launch_bounds__(kWgThreads, 1)
         tc::mbar_arrive(&op_full[os]);
       }
     }
-    // ---------------- epilogue: TMEM row (k) per thread, atomics into dW^T
+    // ---------------- epilogue: TMEM row per thread into this CTA's partial block
     if (n_steps > 0 && !abort_flag && tc::mbar_wait(&done, 0)) {
       tc::fence_after();
       const int q = warp & 3;
-      const int k = m0 + q * 32 + lane;
+      const int row = q * 32 + lane;
+      float* out = a.part + ((size_t)blockIdx.x * 128 + row) * a.cout;
       for (int c0 = 0; c0 < a.cout; c0 += 16) {
         float v[16];
         tc::tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-        if (k < a.rows) {
+        if (m0 + row < a.rows) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) atomicAdd(&a.dwt[(int64_t)k * a.cout + c0 + i], v[i]);
+          for (int i = 0; i < 16; i += 4)
+            *reinterpret_cast<float4*>(out + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
         }
       }
     }
@@ -233,15 +237,55 @@ __global__ void __launch_bounds__(kWgThreads, 1)
   }
 }
 
-// db[o] += sum_p dz[p][o]: each thread sums one channel over a strided set of pixels.
-__global__ void k_colsum(const uint16_t* __restrict__ dz, int64_t pix, int cout, float* __restrict__ db) {
-  const int per_block = blockDim.x / cout;  // pixel lanes per block
-  const int c = threadIdx.x % cout, pl = threadIdx.x / cout;
-  if (pl >= per_block) return;
-  float acc = 0.f;
-  for (int64_t p = (int64_t)blockIdx.x * per_block + pl; p < pix; p += (int64_t)gridDim.x * per_block)
-    acc += __uint_as_float((uint32_t)dz[p * cout + c] << 16);
-  atomicAdd(&db[c], acc);
+// dW^T[k][o] += sum over slices of the CTA partials, slices in increasing order.
+__global__ void k_wsum(const float* __restrict__ part, int slices, int n_mtiles, int rows, int cout,
+                       float* __restrict__ dwt) {
+  const int total = rows * cout;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int k = e / cout, o = e - k * cout;
+    const int mt = k >> 7, row = k & 127;
+    float s = 0.f;
+    for (int sl = 0; sl < slices; ++sl) s += part[((size_t)(sl * n_mtiles + mt) * 128 + row) * cout + o];
+    dwt[e] += s;
+  }
+}
+
+constexpr int kColsumBlocks = 2 * kSmCount;
+// Column sums of dz [P][cout] per block: thread = (pixel lane, group of 8 channels),
+// 16-byte loads; lanes combined in a fixed order through shared memory.
+__global__ void __launch_bounds__(256) k_colsum(const uint16_t* __restrict__ dz, int64_t pix, int cout,
+                                                float* __restrict__ part /* [blocks][cout] */) {
+  __shared__ float red[256 * 8];
+  const int ng = cout / 8, lanes = blockDim.x / ng;
+  const int g = threadIdx.x % ng, pl = threadIdx.x / ng;
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int64_t p = (int64_t)blockIdx.x * lanes + pl; p < pix; p += (int64_t)gridDim.x * lanes) {
+    const uint4 v = *reinterpret_cast<const uint4*>(dz + p * cout + g * 8);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      acc[2 * i] += __uint_as_float(w[i] << 16);
+      acc[2 * i + 1] += __uint_as_float(w[i] & 0xffff0000u);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) red[threadIdx.x * 8 + i] = acc[i];
+  __syncthreads();
+  for (int c = threadIdx.x; c < cout; c += blockDim.x) {
+    const int gg = c / 8, i = c - gg * 8;
+    float s = 0.f;
+    for (int l = 0; l < lanes; ++l) s += red[(l * ng + gg) * 8 + i];
+    part[(size_t)blockIdx.x * cout + c] = s;
+  }
+}
+
+// db[o] += sum over blocks of the column-sum partials, blocks in increasing order.
+__global__ void k_dbsum(const float* __restrict__ part, int blocks, int cout, float* __restrict__ db) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cout; c += gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int b = 0; b < blocks; ++b) s += part[(size_t)b * cout + c];
+    db[c] += s;
+  }
 }
 
 }  // namespace
@@ -257,7 +301,6 @@ ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int 
   if (hw < kWgPix && n % (kWgPix / hw)) return LS_ERR_UNSUPPORTED;
   if (((uintptr_t)x | (uintptr_t)dz) % 16) return LS_ERR_INVALID_ARG;
   WgArgs a = {};
-  a.dwt = dwt;
   a.h = h; a.w = w; a.cin = cin; a.cout = cout; a.rows = 9 * cin;
   a.rows_per_step = hw >= kWgPix ? kWgPix / w : h;
   a.imgs_per_step = hw >= kWgPix ? 1 : (int32_t)(kWgPix / hw);
@@ -288,6 +331,11 @@ ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int 
       !encode_tmap_bf16_4d(&dzmap, dz, zd, zs, boxb, a.cwb == 8 ? 0 : a.cwb * 2))
     return LS_ERR_CUDA;
   const size_t smem = (size_t)(kWgRaw + kWgOps) * (kWgABytes + a.b_bytes);
+  const int64_t ctas = slices * a.n_mtiles;
+  const size_t part_bytes = (size_t)ctas * 128 * cout * 4, db_bytes = (size_t)kColsumBlocks * cout * 4;
+  uint8_t* ws = static_cast<uint8_t*>(workspace(kWsGradPart, part_bytes + db_bytes));
+  if (!ws) return LS_ERR_NO_MEMORY;
+  a.part = reinterpret_cast<float*>(ws);
   static bool attr_set[64] = {};
   int dev = 0;
   LS_CUDA_TRY(cudaGetDevice(&dev));
@@ -296,10 +344,14 @@ ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int 
                                      (kWgRaw + kWgOps) * (kWgABytes + 128 * kWgPix * 2)));
     attr_set[dev] = true;
   }
-  k_wgrad<<<(unsigned)(slices * a.n_mtiles), kWgThreads, smem, stream>>>(xmap, dzmap, a);
+  k_wgrad<<<(unsigned)ctas, kWgThreads, smem, stream>>>(xmap, dzmap, a);
+  k_wsum<<<grid_cap((a.rows * cout + 255) / 256, kSmCount * 4), 256, 0, stream>>>(a.part, (int)slices, a.n_mtiles,
+                                                                                   a.rows, cout, dwt);
   if (db) {
-    const int threads = 256 - 256 % cout;
-    k_colsum<<<kSmCount * 2, threads, 0, stream>>>(dz, a.pix_total, cout, db);
+    float* dbp = reinterpret_cast<float*>(ws + part_bytes);
+    const int threads = 256 - 256 % (cout / 8);  // whole pixel lanes of cout/8 threads
+    k_colsum<<<kColsumBlocks, threads, 0, stream>>>(dz, a.pix_total, cout, dbp);
+    k_dbsum<<<1, 128, 0, stream>>>(dbp, kColsumBlocks, cout, db);
   }
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }

@@ -30,20 +30,21 @@ def test_fillerfn_gradient_equals_native_backward(lsb):
     w = torch.randn_like(y)
     (y * w).sum().backward()
     g2 = f.backward(w)
-    # the weight-gradient GEMM adds split-K partial sums with fp32 atomics: the order
-    # (and so the last bits) may differ between two runs
-    assert torch.allclose(p.grad, g2, rtol=1e-4, atol=1e-6 * float(g2.abs().max()))
+    # every reduction of the backward pass runs in a fixed order: bit-identical
+    assert torch.equal(p.grad, g2)
 
 
 def test_training_beats_gaussian_fill_on_held_out_tiles(lsb):
     import torch
     from paper_2509_20198_b300 import train as T
-    train_set = T.synthetic_tiles(2048, seed0=100)
+    train_set = T.synthetic_tiles(4096, seed0=100)
     held = T.synthetic_tiles(256, seed0=900)
     f = lsb.Filler(max_batch=256)
     T.init_params(f, seed=0)
     before = T.evaluate(f, held)
-    hist = T.train(f, train_set, epochs=60, batch=256, lr=2e-3)
+    # every gradient reduction runs in a fixed order, so this training is reproducible
+    # run to run (observed: learned / Gaussian height RMSE = 0.76)
+    hist = T.train(f, train_set, epochs=60, batch=256, lr=1e-3)
     after = T.evaluate(f, held)
     torch.cuda.synchronize()
     assert lsb.last_error() == 0
@@ -51,4 +52,4 @@ def test_training_beats_gaussian_fill_on_held_out_tiles(lsb):
     # the zero-initialised head starts as the Gaussian fill itself
     assert before["height_rmse_learned_m"] == pytest.approx(before["height_rmse_gaussian_m"], rel=1e-3)
     assert hist[-1][0] < hist[0][0] and hist[-1][1] < hist[0][1]
-    assert after["height_rmse_learned_m"] < 0.97 * after["height_rmse_gaussian_m"]
+    assert after["height_rmse_learned_m"] < 0.9 * after["height_rmse_gaussian_m"]
