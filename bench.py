@@ -496,6 +496,29 @@ def run_profile_case(args):
     return 0 if st == 0 else 1
 
 
+def run_fill_case(args):
+    """Profiling case for the Gaussian fill: the chunk samples of a k x k-tile region at
+    the batched-region densities, filled at 64x64 (R 120 m, sigma 40 m)."""
+    import torch
+    import paper_2509_20198_b300 as lsb
+    import synth
+    import synth.gpu as sg
+    from paper_2509_20198_b300 import build
+    build.build_library()
+    build.build_synth()
+    k = args.case_tiles
+    region = synth.Region(tiles_x=k, tiles_y=k)
+    counts = synth.lognormal_counts(SEED, k * k)
+    s = sg.region_samples(SEED, region, counts)
+    h, c = lsb.fill_sparse(s, region)
+    for _ in range(args.steps):
+        lsb.fill_sparse(s, region, height=h, rgb=c)
+    torch.cuda.synchronize()
+    st = lsb.last_error()
+    print(json.dumps({"case": "fill", "tiles": k * k, "samples": int(s["x"].numel()), "status": st}))
+    return 0 if st == 0 else 1
+
+
 def run_learned_case(args):
     """Profiling case for the learned filler: one forward pass and one training step
     (forward, loss, backward, AdamW) of the U-Net on a batch of random bf16 inputs, with
@@ -536,7 +559,7 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--overview", type=int, default=1, help="also time the 40,000-tile overview fills")
-    ap.add_argument("--case", default="", choices=["", "bin-small", "learned"], help="profiling case instead of the bench")
+    ap.add_argument("--case", default="", choices=["", "bin-small", "learned", "fill"], help="profiling case instead of the bench")
     ap.add_argument("--case-tiles", type=int, default=3, help="tiles per side of the profiling case")
     ap.add_argument("--train-tiles", type=int, default=4096)
     ap.add_argument("--train-epochs", type=int, default=60)
@@ -545,6 +568,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.case == "learned":
         sys.exit(run_learned_case(args))
+    if args.case == "fill":
+        sys.exit(run_fill_case(args))
     if args.case:
         sys.exit(run_profile_case(args))
     if args.impl == "reference":
