@@ -120,6 +120,7 @@ struct FillArgs {
   uint8_t* rgb;
   float4* aux_hc;  // optional per texel: height (m), R, G, B (0..1, unrounded)
   float* aux_d;    // optional per texel: distance to the nearest sample (cm)
+  int32_t split;   // CTAs per tile, each a band of res / split texel rows (few tiles: more CTAs)
 };
 
 __global__ void k_pack(ls_points s, int64_t n_tiles, int64_t x0, int64_t y0, int32_t tile_cm,
@@ -288,7 +289,9 @@ __global__ void __launch_bounds__(kFillThreads) k_fill(FillArgs f) {
   __syncthreads();
   uint32_t phase = 0;
 
-  for (int64_t o = blockIdx.x; o < f.n_out; o += gridDim.x) {
+  for (int64_t item = blockIdx.x; item < f.n_out * f.split; item += gridDim.x) {
+    const int64_t o = item / f.split;
+    const int part = (int)(item - o * f.split);
     const int t = f.tile_ids ? f.tile_ids[o] : (int)o;
     if (t < 0 || t >= f.tiles_x * f.tiles_y) {  // uniform across the CTA
       if (threadIdx.x == 0) set_status(LS_ERR_INVALID_ARG);
@@ -335,7 +338,8 @@ __global__ void __launch_bounds__(kFillThreads) k_fill(FillArgs f) {
     }
     // ---- texel blocks of 8 x 4 per warp
     const int bw = res / 8, nblk = bw * (res / 4);
-    for (int blk = warp; blk < nblk; blk += kFillThreads / 32) {
+    const int blk0 = part * (nblk / f.split), blk1 = blk0 + nblk / f.split;  // whole block rows
+    for (int blk = blk0 + warp; blk < blk1; blk += kFillThreads / 32) {
       const int bj = (blk % bw) * 8, bi = (blk / bw) * 4;
       const int j = bj + (lane & 7), i = bi + (lane >> 3);
       const int cx = tx * f.tile_cm + cell * j + cell / 2;
@@ -416,12 +420,14 @@ __global__ void __launch_bounds__(kFillThreads) k_fill(FillArgs f) {
     }
     __syncthreads();
     if (stage_out) {
-      // res^2 * 4 and res^2 * 3 bytes are multiples of 16 for res % 8 == 0
-      const int nh = res * res / 4, nc = res * res * 3 / 16;
+      // this part's band of rows; its bytes (rows * res * 4 and * 3) are multiples of 16
+      // for res % 16 == 0
+      const int rows = res / f.split, r0 = part * rows;
+      const int h0 = r0 * res / 4, nh = rows * res / 4, c0 = r0 * res * 3 / 16, nc = rows * res * 3 / 16;
       float4* gh = reinterpret_cast<float4*>(f.height + o * res * res);
       int4* gc = reinterpret_cast<int4*>(f.rgb + o * res * res * 3);
-      for (int k = threadIdx.x; k < nh; k += blockDim.x) gh[k] = reinterpret_cast<const float4*>(out_h)[k];
-      for (int k = threadIdx.x; k < nc; k += blockDim.x) gc[k] = reinterpret_cast<const int4*>(out_c)[k];
+      for (int k = threadIdx.x; k < nh; k += blockDim.x) gh[h0 + k] = reinterpret_cast<const float4*>(out_h)[h0 + k];
+      for (int k = threadIdx.x; k < nc; k += blockDim.x) gc[c0 + k] = reinterpret_cast<const int4*>(out_c)[c0 + k];
       __syncthreads();
     }
   }
@@ -533,7 +539,9 @@ ls_status fill_launch(const ls_points* samples, const ls_region* region, const l
       return LS_ERR_CUDA;
     attr_set[dev] = true;
   }
-  k_fill<<<grid_cap(n_out, kSmCount * 2), kFillThreads, kStageCap * sizeof(Rec), s>>>(f);
+  // few tiles: split each over 4 CTAs (bands of res / 4 texel rows, whole 4-row blocks)
+  f.split = (n_out < 4 * kSmCount && params->res % 64 == 0) ? 4 : 1;
+  k_fill<<<grid_cap(n_out * f.split, kSmCount * 2), kFillThreads, kStageCap * sizeof(Rec), s>>>(f);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 }  // namespace ls

@@ -227,13 +227,21 @@ __global__ void __launch_bounds__(kHeadThreads) k_head_bwd(const uint16_t* __res
   }
 }
 
-// grads of the head += its per-block partials, blocks in increasing order
-__global__ void k_head_sum(const float* __restrict__ part, int blocks, int ng, float* __restrict__ gw) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int b = 0; b < blocks; ++b) s += part[(size_t)b * ng + i];
-    gw[i] += s;
+// grads of the head += its per-block partials: one block per element, thread t sums
+// blocks t, t + 256, ... in order, then a fixed-shape tree over the threads
+__global__ void __launch_bounds__(256) k_head_sum(const float* __restrict__ part, int blocks, int ng,
+                                                  float* __restrict__ gw) {
+  __shared__ float red[256];
+  const int i = blockIdx.x;
+  float s = 0.f;
+  for (int b = threadIdx.x; b < blocks; b += blockDim.x) s += part[(size_t)b * ng + i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) gw[i] += red[0];
 }
 
 // ---- dW^T [9*cin_pad][cout] (+ db) into the flat fp32 gradient ---------------------
@@ -630,7 +638,7 @@ extern "C" ls_status ls_filler_backward(ls_model* m, const float* params, const 
     if (!part) return LS_ERR_NO_MEMORY;
     const size_t smem = (size_t)(kOut * hd.cin + (kHeadThreads / 32) * ng) * 4;
     k_head_bwd<<<blocks, kHeadThreads, smem, s>>>(out_of(nl - 2), hd.cin, params + hd.w_off, dy, P, gz, part);
-    k_head_sum<<<grid_for(ng, 256), 256, 0, s>>>(part, blocks, ng, grads + hd.w_off);
+    k_head_sum<<<ng, 256, 0, s>>>(part, blocks, ng, grads + hd.w_off);
   }
   int li = nl - 2;  // d1b
   int gi = 0;

@@ -237,15 +237,26 @@ __global__ void __launch_bounds__(kWgThreads, 1)
   }
 }
 
-// dW^T[k][o] += sum over slices of the CTA partials, slices in increasing order.
+// dW^T[k][o] += sum over slices of the CTA partials, slices in increasing order (loads
+// issued eight ahead of the in-order additions).
 __global__ void k_wsum(const float* __restrict__ part, int slices, int n_mtiles, int rows, int cout,
                        float* __restrict__ dwt) {
   const int total = rows * cout;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const int k = e / cout, o = e - k * cout;
     const int mt = k >> 7, row = k & 127;
+    const size_t stride = (size_t)n_mtiles * 128 * cout;
+    const float* p = part + ((size_t)mt * 128 + row) * cout + o;
     float s = 0.f;
-    for (int sl = 0; sl < slices; ++sl) s += part[((size_t)(sl * n_mtiles + mt) * 128 + row) * cout + o];
+    int sl = 0;
+    for (; sl + 8 <= slices; sl += 8) {
+      float v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = p[(size_t)(sl + i) * stride];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) s += v[i];
+    }
+    for (; sl < slices; ++sl) s += p[(size_t)sl * stride];
     dwt[e] += s;
   }
 }
@@ -279,13 +290,21 @@ __global__ void __launch_bounds__(256) k_colsum(const uint16_t* __restrict__ dz,
   }
 }
 
-// db[o] += sum over blocks of the column-sum partials, blocks in increasing order.
-__global__ void k_dbsum(const float* __restrict__ part, int blocks, int cout, float* __restrict__ db) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cout; c += gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int b = 0; b < blocks; ++b) s += part[(size_t)b * cout + c];
-    db[c] += s;
+// db[o] += sum over blocks of the column-sum partials: one block per channel, thread t
+// sums blocks t, t + 256, ... in order, then a fixed-shape tree over the threads.
+__global__ void __launch_bounds__(256) k_dbsum(const float* __restrict__ part, int blocks, int cout,
+                                               float* __restrict__ db) {
+  __shared__ float red[256];
+  const int c = blockIdx.x;
+  float s = 0.f;
+  for (int b = threadIdx.x; b < blocks; b += blockDim.x) s += part[(size_t)b * cout + c];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) db[c] += red[0];
 }
 
 }  // namespace
@@ -351,7 +370,7 @@ ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int 
     float* dbp = reinterpret_cast<float*>(ws + part_bytes);
     const int threads = 256 - 256 % (cout / 8);  // whole pixel lanes of cout/8 threads
     k_colsum<<<kColsumBlocks, threads, 0, stream>>>(dz, a.pix_total, cout, dbp);
-    k_dbsum<<<1, 128, 0, stream>>>(dbp, kColsumBlocks, cout, db);
+    k_dbsum<<<cout, 256, 0, stream>>>(dbp, kColsumBlocks, cout, db);
   }
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
