@@ -6,6 +6,8 @@ may import this package.  The product path (paper_2509_20198_b300) never does.
 * oracle.c (built to liboracle.so with gcc, no fused multiply-add): serial integer
   binning, sample extraction, FP64 brute-force Gaussian fill, FP64 tile update.
 * unet.py: FP64 numpy U-Net forward/backward, loss, AdamW, learned-input raster.
+* interp.py: the interpolated heightmaps of Alg. 1 (nearest-neighbour and
+  Delaunay-linear maps of a padded patch), exact integer predicates in Python.
 
 Parity status of each function (what pins it) is listed in the tests under
 tests/test_oracle_*.py.
