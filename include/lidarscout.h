@@ -189,6 +189,65 @@ ls_status ls_update_tile(const ls_bins *bins, const ls_region *region, const int
                          int64_t n, float *height, uint8_t *rgb, ls_stream_t stream);
 
 /* ---------------------------------------------------------------------------------
+ * ls_fill_interp -- the interpolated heightmaps of Alg. 1 (Sec. 3.3): for each
+ * requested tile, the nearest-neighbour (NN) and the Delaunay-linear maps of the
+ * samples in a padded patch, the network inputs of the paper's filler.
+ *
+ * Patch of tile t: the window of side W = tile_cm + 2 * pad_cm centred on the tile
+ * (96 x 96 texels of 10 m around a 640 m tile: pad_cm = 16000, res = 96); texel (i, j)
+ * has the centre (cell * j + cell / 2, cell * i + cell / 2) in window coordinates,
+ * cell = W / res.  Its points are the samples inside the closed window, in sample
+ * order, plus four padding points without data at the window corners.
+ *  - Delaunay triangulation of corners and points, inserted in that order
+ *    (Bowyer-Watson, exact integer predicates, a point equal to an earlier one is
+ *    skipped; with co-circular points the insertion order decides the diagonals).
+ *  - lin: in a triangle of three real points, height and colour are the barycentric
+ *    interpolation of its vertices (height within a few float ulps of the exact
+ *    value, the same value from every triangle containing the texel; colour the exact
+ *    round-half-up of the 8-bit value); every other texel takes its NN value.
+ *  - nn: height (float)(z * z_scale + z_offset) (IEEE double, no contraction) and
+ *    colour round-half-up(c / 256) of the nearest sample (exact squared distance,
+ *    ties to the lowest sample index).  A patch without samples gets NaN and 0.
+ *  - inside: 1 where the linear map interpolates.
+ *
+ * samples: bucketed by tile as for ls_fill_sparse (tile_offsets required, every
+ *   sample inside its bucket's tile, sample order the tie-break order).
+ * tile_ids: int32[n_out] (device), or NULL for all T tiles (n_out = T).
+ * out: every map pointer may be NULL (not written):
+ *   nn_height, lin_height float[n_out][res][res] metres; nn_rgb, lin_rgb
+ *   uint8[n_out][res][res][3]; inside uint8[n_out][res][res];
+ *   triangles int32[n_out][tri_cap][3]: the first tri_cap triangles (counter-
+ *   clockwise global sample indices; -1 - c for window corner c, c = 0..3 at
+ *   (0, 0), (W, 0), (W, W), (0, W)), tri_count int32[n_out]: the number of triangles
+ *   (corner triangles included), -1 for a patch not triangulated.
+ * Limits: res a multiple of 32 in [32, 128]; 0 <= pad_cm <= tile_cm; W divisible by
+ *   res and at most 131072 cm (INVALID_ARG / UNSUPPORTED otherwise); |z| < 2^28 (a
+ *   patch with a larger |z| gets LS_ERR_UNSUPPORTED in the sticky status, tri_count
+ *   -1 and lin = nn); at most 1536 samples per window (more: LS_ERR_OUT_OF_RANGE in
+ *   the sticky status and NaN maps for that patch).
+ * Uses library scratch of 32 bytes per sample and 4 bytes per requested tile.
+ * ------------------------------------------------------------------------------- */
+typedef struct {
+  int32_t res;    /* texels per patch side (96) */
+  int32_t pad_cm; /* padding on every side of the tile (16000) */
+} ls_interp_params;
+
+typedef struct {
+  float *nn_height;
+  uint8_t *nn_rgb;
+  float *lin_height;
+  uint8_t *lin_rgb;
+  uint8_t *inside;
+  int32_t *triangles;
+  int32_t *tri_count;
+  int32_t tri_cap;
+} ls_interp_outputs;
+
+ls_status ls_fill_interp(const ls_points *samples, const ls_region *region,
+                         const ls_interp_params *params, const int32_t *tile_ids, int64_t n_out,
+                         const ls_interp_outputs *out, ls_stream_t stream);
+
+/* ---------------------------------------------------------------------------------
  * Tensor-core 3x3 convolution of the learned filler (Sec. 3.4: a U-Net-inspired CNN
  * refines the heightmaps).  Stride 1, zero padding 1, NHWC BF16 activations, FP32
  * accumulation (tcgen05 kind::f16, M = 128 pixels, N = c_out, K = 9 * c_in).

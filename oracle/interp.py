@@ -85,7 +85,8 @@ def interp_tile(samples, region, t, res=96, pad_cm=16000):
     """Alg. 1 for tile t.  Returns dict: nn_height, lin_height float64 [res, res] (m),
     nn_rgb8, lin_rgb8 float64 [res, res, 3] (8-bit scale, unrounded), inside uint8
     [res, res] (1 where the linear map interpolates), triangles (list of triples of
-    global sample indices, -1 for a corner)."""
+    global sample indices, -1 - c for corner c: 0 = (0, 0), 1 = (W, 0), 2 = (W, W),
+    3 = (0, W) in window coordinates)."""
     X0, Y0, W = window_of(region, t, pad_cm)
     assert W % res == 0
     # the int64 numerators below (weights up to W^2 times heights) stay exact for
@@ -102,7 +103,7 @@ def interp_tile(samples, region, t, res=96, pad_cm=16000):
     out = {"nn_height": np.full((res, res), np.nan), "lin_height": np.full((res, res), np.nan),
            "nn_rgb8": np.zeros((res, res, 3)), "lin_rgb8": np.zeros((res, res, 3)),
            "inside": np.zeros((res, res), np.uint8),
-           "triangles": [tuple(int(sel[v - 4]) if v >= 4 else -1 for v in tr) for tr in tris]}
+           "triangles": [tuple(int(sel[v - 4]) if v >= 4 else -1 - v for v in tr) for tr in tris]}
     gx = cell * np.arange(res, dtype=np.int64) + cell // 2
     GX, GY = np.meshgrid(gx, gx)  # [i][j]: GX column j, GY row i
     # nearest point (exact int64 squared distance; ties to the lowest sample index)

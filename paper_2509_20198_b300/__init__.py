@@ -17,7 +17,8 @@ import torch
 
 from . import _native as N
 
-__all__ = ["bin_points", "bin_stats", "extract_samples", "extract_samples_into", "fill_sparse", "update_tile", "last_error",
+__all__ = ["bin_points", "bin_stats", "extract_samples", "extract_samples_into", "fill_sparse", "fill_interp",
+           "update_tile", "last_error",
            "release_workspace", "empty_bins", "BIN_KEYS", "Filler", "FillerFn", "filler_loss", "adamw_step",
            "learned_inputs", "learned_targets", "learned_finish", "fill_learned"]
 
@@ -159,6 +160,46 @@ def fill_sparse(samples, region, tile_ids=None, res=64, radius_cm=12000, sigma_c
                                                     _ptr(tile_ids), n, _ptr(_dev(height, "height")),
                                                     _ptr(_dev(rgb, "rgb")), _stream(stream)))
     return height, rgb
+
+
+INTERP_MAPS = ("nn_height", "nn_rgb", "lin_height", "lin_rgb", "inside")
+
+
+def fill_interp(samples, region, tile_ids=None, res=96, pad_cm=16000, maps=INTERP_MAPS, tri_cap=0, out=None,
+                stream=None):
+    """Nearest-neighbour and Delaunay-linear maps of Alg. 1 on the padded patch of every
+    requested tile (res x res texels of (tile + 2 pad) / res).
+
+    Returns a dict with the requested maps: nn_height, lin_height float32 [n, res, res]
+    (metres), nn_rgb, lin_rgb uint8 [n, res, res, 3], inside uint8 [n, res, res]; with
+    tri_cap > 0 also triangles int32 [n, tri_cap, 3] (global sample indices, -1 - c for
+    window corner c) and tri_count int32 [n].  `out` may hold pre-allocated tensors of those
+    names (no allocation then, so the call can be captured in a CUDA graph)."""
+    T = int(region.tiles_x) * int(region.tiles_y)
+    dev = samples["x"].device
+    if tile_ids is not None:
+        tile_ids = _dev(tile_ids.to(device=dev, dtype=torch.int32).contiguous(), "tile_ids")
+    n = T if tile_ids is None else tile_ids.numel()
+    shapes = {"nn_height": ((n, res, res), torch.float32), "lin_height": ((n, res, res), torch.float32),
+              "nn_rgb": ((n, res, res, 3), torch.uint8), "lin_rgb": ((n, res, res, 3), torch.uint8),
+              "inside": ((n, res, res), torch.uint8)}
+    if tri_cap > 0:
+        shapes["triangles"] = ((n, tri_cap, 3), torch.int32)
+        shapes["tri_count"] = ((n,), torch.int32)
+    res_maps = dict(out or {})
+    for k, (shape, dt) in shapes.items():
+        if k in res_maps or (k in INTERP_MAPS and k not in maps):
+            continue
+        res_maps[k] = torch.empty(shape, dtype=dt, device=dev)
+    o = N.LsInterpOutputs(*[_ptr(_dev(res_maps[k], k)) if k in res_maps else None
+                            for k in ("nn_height", "nn_rgb", "lin_height", "lin_rgb", "inside", "triangles",
+                                      "tri_count")], int(tri_cap))
+    pts = _points(samples, need_offsets=True)
+    reg = _region(region)
+    prm = N.LsInterpParams(res, pad_cm)
+    N.check("ls_fill_interp", N.lib().ls_fill_interp(ctypes.byref(pts), ctypes.byref(reg), ctypes.byref(prm),
+                                                    _ptr(tile_ids), n, ctypes.byref(o), _stream(stream)))
+    return res_maps
 
 
 def update_tile(bins, region, tile_ids, height, rgb, stream=None):

@@ -34,6 +34,15 @@ class LsFillParams(ctypes.Structure):
     _fields_ = [("res", I32), ("radius_cm", I32), ("sigma_cm", FLT)]
 
 
+class LsInterpParams(ctypes.Structure):
+    _fields_ = [("res", I32), ("pad_cm", I32)]
+
+
+class LsInterpOutputs(ctypes.Structure):
+    _fields_ = [("nn_height", VP), ("nn_rgb", VP), ("lin_height", VP), ("lin_rgb", VP), ("inside", VP),
+                ("triangles", VP), ("tri_count", VP), ("tri_cap", I32)]
+
+
 class LsConvShape(ctypes.Structure):
     _fields_ = [("n", I32), ("h", I32), ("w", I32), ("cin", I32), ("cout", I32)]
 
@@ -50,6 +59,7 @@ SIGNATURES = {
     "ls_extract_samples": ([P(LsPoints), I64, I32, VP, P(LsSampleBuffers), I64, VP], I32),
     "ls_fill_sparse": ([P(LsPoints), P(LsRegion), P(LsFillParams), VP, I64, VP, VP, VP], I32),
     "ls_update_tile": ([P(LsBins), P(LsRegion), VP, I64, VP, VP, VP], I32),
+    "ls_fill_interp": ([P(LsPoints), P(LsRegion), P(LsInterpParams), VP, I64, P(LsInterpOutputs), VP], I32),
     "ls_conv3x3_packed_elems": ([I32, I32], I64),
     "ls_conv3x3_pack": ([VP, I32, I32, I32, VP, VP], I32),
     "ls_conv3x3_forward": ([VP, VP, VP, VP, I32, P(LsConvShape), VP, VP], I32),

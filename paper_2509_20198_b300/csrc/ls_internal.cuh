@@ -51,7 +51,16 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
 // ---------------------------------------------------------------------------------
 // Library scratch workspace (per device, grown on demand).
 // ---------------------------------------------------------------------------------
-enum WorkspaceSlot { kWsBinRows = 0, kWsFillPacked = 1, kWsModel = 2, kWsGradPart = 3, kWsHeadPart = 4, kWsSlots = 5 };
+enum WorkspaceSlot {
+  kWsBinRows = 0,
+  kWsFillPacked = 1,
+  kWsModel = 2,
+  kWsGradPart = 3,
+  kWsHeadPart = 4,
+  kWsInterpRecs = 5,
+  kWsInterpQueue = 6,
+  kWsSlots = 7
+};
 // Returns a device pointer of at least `bytes` for the given slot (nullptr on failure).
 void* workspace(WorkspaceSlot slot, size_t bytes);
 

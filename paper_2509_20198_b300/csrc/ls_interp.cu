@@ -1,0 +1,594 @@
+// Interpolated heightmaps of Alg. 1 (Sec. 3.3): per patch, the nearest-neighbour map
+// and the Delaunay-linear map of the chunk samples that fall in a window made of the
+// tile grown by a padding on every side (96 x 96 texels of 10 m around a 640 m tile),
+// with four padding points (no data) at the window corners.
+//
+// Design (B300): one warp per patch, its whole state in the warp's slice of shared
+// memory, no CTA barrier anywhere.
+//  * gather: the window's samples from the 3x3 tile neighbourhood (three contiguous
+//    CSR ranges of packed records), compacted with ballots in global sample order;
+//  * triangulation: Bowyer-Watson in that order.  For each new point the lanes test
+//    every triangle's circumcircle (a float test with a proven error margin, the
+//    exact int128 determinant inside the margin), list the cavity's boundary edges
+//    with ballots and re-triangulate the cavity in place, keeping neighbour links;
+//  * linear map: the texels of every triangle with three real vertices, flattened
+//    over the lanes by a prefix sum of bounding-box texel counts, tested with exact
+//    int64 orientations.  Heights and colours are functions of the exact barycentric
+//    numerator over the exact area, so every triangle that contains a texel (on a
+//    shared edge or vertex) writes the same value;
+//  * NN map: 8 x 4 texel blocks; per block the candidates are the points whose
+//    distance to the block is at most the smallest farthest-corner distance, then
+//    every lane takes the exact int64 nearest of them (ties to the lowest index).
+// Patches whose window holds more samples than the small tier's capacity are queued
+// on the device for a second launch with one warp per CTA and a larger capacity.
+#include <climits>
+
+#include "ls_internal.cuh"
+
+namespace ls {
+namespace {
+
+constexpr int kInterpMaxRes = 128;
+constexpr int kInterpSmallCap = 96;     // window samples per patch, small tier
+constexpr int kInterpSmallWarps = 4;    // patches (warps) per CTA, small tier
+constexpr int kInterpBigCap = 1536;     // big tier: one warp per CTA
+constexpr int kInterpMaxWindow = 1 << 17;  // window side bound of the exact arithmetic
+constexpr int kInterpZBound = 1 << 28;     // |z| bound of the exact numerators
+
+// Per-warp state of one patch with up to CAP window samples.  A triangulation of
+// CAP + 4 vertices whose hull is the window square has at most 2 * CAP + 2 triangles.
+template <int CAP>
+struct InterpWarp {
+  static constexpr int NV = CAP + 4;
+  static constexpr int NT = 2 * CAP + 2;
+  float4 circ[NT];       // circumcircle: centre x, y, radius^2, error margin
+  int2 P[NV];            // window-local vertex coordinates (0..3: corners)
+  ushort4 tv[NT];        // vertices (counter-clockwise), cavity mark
+  short4 tn[NT];         // neighbour across (v0,v1), (v1,v2), (v2,v0); -1 none
+  ushort4 edge[NT + 2];  // cavity boundary edges: a, b, outside triangle
+  int32_t start[NV];     // new triangle whose boundary edge starts at a vertex (stamped)
+  int32_t z[CAP];
+  float hm[CAP];         // height in metres of each sample
+  uint32_t c8[CAP];      // 8-bit colour of each sample, R | G << 8 | B << 16
+  uint32_t rg[CAP];      // 16-bit R | G << 16
+  uint32_t bl[CAP];      // 16-bit B
+  int32_t gidx[CAP];     // global sample index
+  uint16_t list[NT];     // cavity triangles; later the NN candidates of a block
+  uint32_t inside[kInterpMaxRes * kInterpMaxRes / 32];
+  int32_t rincl[32];
+  int4 rtri[32];
+};
+
+struct InterpArgs {
+  const int64_t* __restrict__ toff;  // sample CSR by tile [T+1]
+  const Rec* __restrict__ recs;      // packed samples (region-relative coordinates)
+  const int32_t* __restrict__ tile_ids;
+  int64_t n_out, n_samples;
+  int32_t tiles_x, tiles_y, tile_cm, res, cell_cm, pad_cm, W;
+  double z_scale, z_offset;
+  float zs_f, zo_f;
+  ls_interp_outputs out;
+  int32_t* queue;  // [0]: patches queued for the big tier, [1..]: their ordinals
+};
+
+__device__ __forceinline__ unsigned lanes_below() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ long long orient2(int2 a, int2 b, int2 c) {
+  return (long long)(b.x - a.x) * (c.y - a.y) - (long long)(b.y - a.y) * (c.x - a.x);
+}
+
+// Sign of the lifted in-circle determinant of (a, b, c, d): > 0 iff d lies strictly
+// inside the circumcircle of the counter-clockwise triangle (a, b, c).  Coordinate
+// differences are below 2^17, so the 2x2 minors fit int64 and the sum int128.
+__device__ __noinline__ bool incircle_exact(int2 a, int2 b, int2 c, int2 d) {
+  const long long adx = a.x - d.x, ady = a.y - d.y;
+  const long long bdx = b.x - d.x, bdy = b.y - d.y;
+  const long long cdx = c.x - d.x, cdy = c.y - d.y;
+  const long long ad = adx * adx + ady * ady, bd = bdx * bdx + bdy * bdy, cd = cdx * cdx + cdy * cdy;
+  const __int128 det = (__int128)adx * (bdy * cd - bd * cdy) - (__int128)ady * (bdx * cd - bd * cdx) +
+                       (__int128)ad * (bdx * cdy - bdy * cdx);
+  return det > 0;
+}
+
+// Circumcircle of the counter-clockwise triangle (a, b, c) in float, with the margin
+// m = S^2 / 2^16, S = |cx| + |cy| + 2 W.  The centre comes from exact int64 numerators
+// over the exact denominator (three float roundings: <= 4 * 2^-24 S with the add), so
+// each of |p - c|^2 and r^2 is within 11 * 2^-24 S^2 of its true value for any p in
+// the window and their difference within 2^-18.5 S^2 < m: outside the band
+// |d^2 - r^2| <= m the float comparison decides the exact predicate.
+__device__ __forceinline__ float4 circumcircle(int2 a, int2 b, int2 c, int W) {
+  const long long bx = b.x - a.x, by = b.y - a.y, cx = c.x - a.x, cy = c.y - a.y;
+  const long long D = 2 * (bx * cy - by * cx);
+  const long long B2 = bx * bx + by * by, C2 = cx * cx + cy * cy;
+  const long long Nx = cy * B2 - by * C2, Ny = bx * C2 - cx * B2;
+  const float Df = (float)D;
+  const float ccx = (float)a.x + __fdiv_rn((float)Nx, Df);
+  const float ccy = (float)a.y + __fdiv_rn((float)Ny, Df);
+  const float rx = (float)a.x - ccx, ry = (float)a.y - ccy;
+  const float S = fabsf(ccx) + fabsf(ccy) + 2.f * (float)W;
+  return make_float4(ccx, ccy, fmaf(rx, rx, ry * ry), S * S * (1.f / 65536.f));
+}
+
+template <int CAP>
+__device__ __forceinline__ bool in_circumcircle(const InterpWarp<CAP>& s, int i, int2 p) {
+  const float4 c = s.circ[i];
+  const float dx = (float)p.x - c.x, dy = (float)p.y - c.y;
+  const float d2 = fmaf(dx, dx, dy * dy);
+  if (d2 < c.z - c.w) return true;
+  if (d2 > c.z + c.w) return false;
+  const ushort4 v = s.tv[i];
+  return incircle_exact(s.P[v.x], s.P[v.y], s.P[v.z], p);
+}
+
+__device__ __forceinline__ short& tn_at(short4& t, int e) { return e == 0 ? t.x : e == 1 ? t.y : t.z; }
+
+// Bowyer-Watson insertion of vertex vi (the whole warp).  Returns false when the
+// cavity is not a simple polygon around the point (impossible with exact predicates;
+// checked all the same).  T is updated.
+template <int CAP>
+__device__ bool insert_point(InterpWarp<CAP>& s, int vi, int W, int& T) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanes_below();
+  const int2 p = s.P[vi];
+  // triangles whose circumcircle holds p strictly inside
+  int nb = 0;
+  for (int base = 0; base < T; base += 32) {
+    const int i = base + lane;
+    const bool bad = i < T && in_circumcircle(s, i, p);
+    const unsigned m = __ballot_sync(0xffffffffu, bad);
+    if (bad) {
+      s.list[nb + __popc(m & lt)] = (uint16_t)i;
+      s.tv[i].w = (uint16_t)vi;
+    }
+    nb += __popc(m);
+  }
+  __syncwarp();
+  if (nb == 0) return true;  // p repeats a vertex
+  // boundary edges of the cavity (the neighbour across is not in it), kept when the
+  // join with p has positive area (a zero-area join lies on the window's edge)
+  int K = 0;
+  bool err = false;
+  for (int base = 0; base < 3 * nb; base += 32) {
+    const int item = base + lane;
+    bool keep = false;
+    ushort4 ed = make_ushort4(0, 0, 0, 0);
+    if (item < 3 * nb) {
+      const int tb = s.list[item / 3], e = item % 3;
+      const ushort4 v = s.tv[tb];
+      const int va = e == 0 ? v.x : e == 1 ? v.y : v.z;
+      const int vb = e == 0 ? v.y : e == 1 ? v.z : v.x;
+      short4 nn = s.tn[tb];
+      const int on = tn_at(nn, e);
+      if (on >= T) {
+        err = true;  // a broken link (never expected): stop before following it
+      } else if (on < 0 || s.tv[on].w != vi) {
+        keep = orient2(s.P[va], s.P[vb], p) > 0;
+        err = !keep && on >= 0;
+      }
+      ed = make_ushort4((uint16_t)va, (uint16_t)vb, (uint16_t)on, 0);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    const int pos = K + __popc(m & lt);
+    if (keep && pos < InterpWarp<CAP>::NT + 2) s.edge[pos] = ed;
+    K += __popc(m);
+  }
+  if (__any_sync(0xffffffffu, err) || K <= nb || T + K - nb > InterpWarp<CAP>::NT) return false;
+  __syncwarp();
+  // new triangles (a, b, p) in the cavity's slots, then in fresh ones
+  for (int j = lane; j < K; j += 32) {
+    const int slot = j < nb ? s.list[j] : T + j - nb;
+    const ushort4 ed = s.edge[j];
+    const int on = (int16_t)ed.z;
+    s.tv[slot] = make_ushort4(ed.x, ed.y, (uint16_t)vi, 0);
+    s.tn[slot] = make_short4((short)on, -1, -1, 0);
+    s.circ[slot] = circumcircle(s.P[ed.x], s.P[ed.y], p, W);
+    if (on >= 0) {
+      const ushort4 ov = s.tv[on];
+      short* tp = &s.tn[on].x;
+      if (ov.x == ed.y && ov.y == ed.x) tp[0] = (short)slot;
+      else if (ov.y == ed.y && ov.z == ed.x) tp[1] = (short)slot;
+      else tp[2] = (short)slot;
+    }
+    s.start[ed.x] = (vi << 16) | slot;
+  }
+  __syncwarp();
+  // link consecutive new triangles: (a, b, p) and (b, c, p) share the edge (b, p)
+  for (int j = lane; j < K; j += 32) {
+    const int slot = j < nb ? s.list[j] : T + j - nb;
+    const int st = s.start[s.edge[j].y];
+    if ((st >> 16) == vi) {
+      const int t2 = st & 0xffff;
+      s.tn[slot].y = (short)t2;
+      s.tn[t2].z = (short)slot;
+    }
+  }
+  __syncwarp();
+  T += K - nb;
+  return true;
+}
+
+// One texel of a triangle with real vertices va, vb, vc (sample slots + 4).
+template <int CAP>
+__device__ __forceinline__ void raster_texel(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o, int va, int vb,
+                                             int vc, int ii, int jj) {
+  const int h = a.cell_cm / 2;
+  const int2 g = make_int2(a.cell_cm * jj + h, a.cell_cm * ii + h);
+  const int2 A = s.P[va], B = s.P[vb], C = s.P[vc];
+  const long long wa = orient2(g, B, C);
+  if (wa < 0) return;
+  const long long wb = orient2(g, C, A);
+  if (wb < 0) return;
+  const long long wc = orient2(g, A, B);
+  if (wc < 0) return;
+  const long long area = wa + wb + wc;
+  const int ka = va - 4, kb = vb - 4, kc = vc - 4;
+  const int e = ii * a.res + jj;
+  const size_t ge = (size_t)o * a.res * a.res + e;
+  if (a.out.lin_height) {
+    // floor(num / area) and 28 fraction bits, exact: a function of the rational value
+    const long long num = wa * s.z[ka] + wb * s.z[kb] + wc * s.z[kc];
+    long long q = num / area, r = num - q * area;
+    if (r < 0) { q -= 1; r += area; }
+    const long long f = (r << 28) / area;
+    const float zc = (float)q + (float)f * (1.f / 268435456.f);
+    a.out.lin_height[ge] = fmaf(zc, a.zs_f, a.zo_f);
+  }
+  if (a.out.lin_rgb) {
+    const uint32_t ca[3] = {s.rg[ka] & 0xffffu, s.rg[ka] >> 16, s.bl[ka]};
+    const uint32_t cb[3] = {s.rg[kb] & 0xffffu, s.rg[kb] >> 16, s.bl[kb]};
+    const uint32_t cc[3] = {s.rg[kc] & 0xffffu, s.rg[kc] >> 16, s.bl[kc]};
+    const float af = (float)area;
+    uint8_t* dst = a.out.lin_rgb + ge * 3;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      // round half up of numc / area / 256; the float estimate is within 6e-5 of the
+      // exact value, so away from a rounding boundary its floor is the exact one
+      const long long numc = wa * ca[ch] + wb * cb[ch] + wc * cc[ch];
+      const float fq = __fdiv_rn((float)numc, af) * (1.f / 256.f) + 0.5f;
+      const float fl = floorf(fq), fr = fq - fl;
+      long long k = (long long)fl;
+      if (!(fr > 1e-3f && fr < 1.f - 1e-3f)) k = (numc + 128 * area) / (256 * area);
+      dst[ch] = (uint8_t)(k > 255 ? 255 : k);
+    }
+  }
+  atomicOr(&s.inside[e >> 5], 1u << (e & 31));
+}
+
+template <int CAP>
+__device__ void raster_linear(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o, int T) {
+  const int lane = threadIdx.x & 31;
+  const int res = a.res, cell = a.cell_cm, h = cell / 2;
+  for (int base = 0; base < T; base += 32) {
+    const int i = base + lane;
+    int cnt = 0, j0 = 0, i0 = 0, bw = 1;
+    ushort4 v = make_ushort4(0, 0, 0, 0);
+    if (i < T) {
+      v = s.tv[i];
+      if (v.x >= 4 && v.y >= 4 && v.z >= 4) {
+        const int2 A = s.P[v.x], B = s.P[v.y], C = s.P[v.z];
+        const int xmin = min(A.x, min(B.x, C.x)), xmax = max(A.x, max(B.x, C.x));
+        const int ymin = min(A.y, min(B.y, C.y)), ymax = max(A.y, max(B.y, C.y));
+        // texel centres cell * j + h inside [min, max]
+        j0 = xmin <= h ? 0 : (xmin - h + cell - 1) / cell;
+        i0 = ymin <= h ? 0 : (ymin - h + cell - 1) / cell;
+        const int j1 = xmax < h ? -1 : min(res - 1, (xmax - h) / cell);
+        const int i1 = ymax < h ? -1 : min(res - 1, (ymax - h) / cell);
+        if (j1 >= j0 && i1 >= i0) {
+          bw = j1 - j0 + 1;
+          cnt = bw * (i1 - i0 + 1);
+        }
+      }
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += u;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) continue;
+    s.rincl[lane] = incl;
+    s.rtri[lane] = make_int4(v.x | (v.y << 16), v.z, j0 | (i0 << 16), bw);
+    __syncwarp();
+    for (int idx = lane; idx < total; idx += 32) {
+      int pos = 0;  // number of triangles of the chunk whose texels all precede idx
+#pragma unroll
+      for (int st = 16; st > 0; st >>= 1)
+        if (s.rincl[pos + st - 1] <= idx) pos += st;
+      const int4 rt = s.rtri[pos];
+      const int local = idx - (pos ? s.rincl[pos - 1] : 0);
+      raster_texel(s, a, o, rt.x & 0xffff, rt.x >> 16, rt.y, (rt.z >> 16) + local / rt.w,
+                   (rt.z & 0xffff) + local % rt.w);
+    }
+    __syncwarp();
+  }
+}
+
+// NN map over 8 x 4 texel blocks; texels outside every real triangle also take it as
+// their linear value.
+template <int CAP>
+__device__ void nearest_maps(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o, int n) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanes_below();
+  const int res = a.res, cell = a.cell_cm, h = cell / 2;
+  const int bxn = res / 8, nblk = bxn * (res / 4);
+  for (int blk = 0; blk < nblk; ++blk) {
+    const int bj = (blk % bxn) * 8, bi = (blk / bxn) * 4;
+    const int jj = bj + (lane & 7), ii = bi + (lane >> 3);
+    const int gxa = cell * bj + h, gxb = gxa + 7 * cell, gya = cell * bi + h, gyb = gya + 3 * cell;
+    // U: the smallest farthest-corner squared distance; every texel's nearest point
+    // (and every point tied with it) lies within sqrt(U) of the block
+    long long U = LLONG_MAX;
+    for (int k = lane; k < n; k += 32) {
+      const int2 q = s.P[4 + k];
+      const int dx = max(abs(q.x - gxa), abs(q.x - gxb)), dy = max(abs(q.y - gya), abs(q.y - gyb));
+      const long long d2 = (long long)dx * dx + (long long)dy * dy;
+      U = d2 < U ? d2 : U;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      const long long u = __shfl_xor_sync(0xffffffffu, U, d);
+      U = u < U ? u : U;
+    }
+    int nc = 0;
+    for (int base = 0; base < n; base += 32) {
+      const int k = base + lane;
+      bool c = false;
+      if (k < n) {
+        const int2 q = s.P[4 + k];
+        const int dx = q.x < gxa ? gxa - q.x : (q.x > gxb ? q.x - gxb : 0);
+        const int dy = q.y < gya ? gya - q.y : (q.y > gyb ? q.y - gyb : 0);
+        c = (long long)dx * dx + (long long)dy * dy <= U;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, c);
+      if (c) s.list[nc + __popc(m & lt)] = (uint16_t)k;
+      nc += __popc(m);
+    }
+    __syncwarp();
+    const int gx = cell * jj + h, gy = cell * ii + h;
+    long long best = LLONG_MAX;
+    int bk = -1;
+    for (int c = 0; c < nc; ++c) {
+      const int k = s.list[c];
+      const int2 q = s.P[4 + k];
+      const long long d2 = (long long)(q.x - gx) * (q.x - gx) + (long long)(q.y - gy) * (q.y - gy);
+      if (d2 < best) { best = d2; bk = k; }
+    }
+    __syncwarp();
+    const int e = ii * res + jj;
+    const size_t ge = (size_t)o * res * res + e;
+    const float hv = bk >= 0 ? s.hm[bk] : __int_as_float(0x7fc00000);
+    const uint32_t c8 = bk >= 0 ? s.c8[bk] : 0u;
+    const bool in = (s.inside[e >> 5] >> (e & 31)) & 1u;
+    if (a.out.nn_height) a.out.nn_height[ge] = hv;
+    if (a.out.nn_rgb) {
+      uint8_t* d = a.out.nn_rgb + ge * 3;
+      d[0] = (uint8_t)c8; d[1] = (uint8_t)(c8 >> 8); d[2] = (uint8_t)(c8 >> 16);
+    }
+    if (!in) {
+      if (a.out.lin_height) a.out.lin_height[ge] = hv;
+      if (a.out.lin_rgb) {
+        uint8_t* d = a.out.lin_rgb + ge * 3;
+        d[0] = (uint8_t)c8; d[1] = (uint8_t)(c8 >> 8); d[2] = (uint8_t)(c8 >> 16);
+      }
+    }
+    if (a.out.inside) a.out.inside[ge] = in ? 1 : 0;
+  }
+}
+
+// Alg. 1 for output ordinal o.  The small tier queues a patch with more than CAP
+// window samples for the big tier; the big tier reports it (LS_ERR_OUT_OF_RANGE) and
+// writes NaN heights.
+template <int CAP, bool BIG>
+__device__ void interp_patch(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanes_below();
+  const int t = a.tile_ids ? a.tile_ids[o] : (int)o;
+  if (t < 0 || t >= a.tiles_x * a.tiles_y) {  // uniform across the warp
+    if (lane == 0) set_status(LS_ERR_INVALID_ARG);
+    return;
+  }
+  const int tx = t % a.tiles_x, ty = t / a.tiles_x;
+  const int64_t X0 = (int64_t)tx * a.tile_cm - a.pad_cm, Y0 = (int64_t)ty * a.tile_cm - a.pad_cm;
+  // ---- gather the window's samples in global order
+  int n = 0;
+  bool zbad = false;
+  for (int k = 0; k < 3; ++k) {
+    const int uy = ty - 1 + k;
+    if (uy < 0 || uy >= a.tiles_y) continue;
+    const int xa = tx > 0 ? tx - 1 : 0, xb = tx + 1 < a.tiles_x ? tx + 1 : tx;
+    const int64_t q0 = a.toff[(int64_t)uy * a.tiles_x + xa], q1 = a.toff[(int64_t)uy * a.tiles_x + xb + 1];
+    if (q0 < 0 || q1 < q0 || q1 > a.n_samples) {  // inconsistent CSR: use nothing
+      if (lane == 0) set_status(LS_ERR_INVALID_ARG);
+      continue;
+    }
+    for (int64_t base = q0; base < q1; base += 32) {
+      const int64_t q = base + lane;
+      bool in = false;
+      int4 r0 = make_int4(0, 0, 0, 0);
+      int2 r1 = make_int2(0, 0);
+      int lx = 0, ly = 0;
+      if (q < q1) {
+        const int4* rp = reinterpret_cast<const int4*>(a.recs + q);
+        r0 = __ldg(rp);
+        r1 = __ldg(reinterpret_cast<const int2*>(rp + 1));
+        const int64_t wx = (int64_t)r0.x - X0, wy = (int64_t)r0.y - Y0;
+        in = wx >= 0 && wx <= a.W && wy >= 0 && wy <= a.W;
+        lx = (int)wx; ly = (int)wy;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, in);
+      const int pos = n + __popc(m & lt);
+      if (in && pos < CAP) {
+        s.P[4 + pos] = make_int2(lx, ly);
+        s.z[pos] = r0.z;
+        s.gidx[pos] = r0.w;
+        s.rg[pos] = (uint32_t)r1.x;
+        s.bl[pos] = (uint32_t)r1.y;
+        zbad |= r0.z >= kInterpZBound || r0.z <= -kInterpZBound;
+      }
+      n += __popc(m);
+    }
+  }
+  bool failed = false;
+  if (n > CAP) {
+    if (!BIG) {
+      if (lane == 0) {
+        const int qpos = atomicAdd(a.queue, 1);
+        a.queue[1 + qpos] = (int)o;
+      }
+      return;
+    }
+    if (lane == 0) set_status(LS_ERR_OUT_OF_RANGE);
+    n = 0;  // NaN maps
+    failed = true;
+  }
+  if (__any_sync(0xffffffffu, zbad)) {
+    if (lane == 0) set_status(LS_ERR_UNSUPPORTED);
+    failed = true;  // nearest-neighbour maps only
+  }
+  // ---- per-sample values, corners, empty inside mask
+  for (int k = lane; k < n; k += 32) {
+    s.hm[k] = (float)__dadd_rn(__dmul_rn((double)s.z[k], a.z_scale), a.z_offset);
+    uint32_t c8 = 0;
+    const uint32_t c16[3] = {s.rg[k] & 0xffffu, s.rg[k] >> 16, s.bl[k]};
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      const uint32_t v = (c16[ch] + 128u) >> 8;  // round half up of c / 256
+      c8 |= (v > 255u ? 255u : v) << (8 * ch);
+    }
+    s.c8[k] = c8;
+  }
+  for (int k = lane; k < n + 4; k += 32) s.start[k] = -1;
+  for (int k = lane; k < a.res * a.res / 32; k += 32) s.inside[k] = 0u;
+  if (lane < 4) s.P[lane] = make_int2(lane == 1 || lane == 2 ? a.W : 0, lane >= 2 ? a.W : 0);
+  __syncwarp();
+  // ---- Delaunay triangulation of corners and samples
+  int T = 0;
+  if (!failed) {
+    if (lane < 2) {
+      const int2 P0 = s.P[0], P1 = s.P[lane + 1], P2 = s.P[lane + 2];
+      s.tv[lane] = make_ushort4(0, (uint16_t)(lane + 1), (uint16_t)(lane + 2), 0);
+      s.tn[lane] = lane == 0 ? make_short4(-1, -1, 1, 0) : make_short4(0, -1, -1, 0);
+      s.circ[lane] = circumcircle(P0, P1, P2, a.W);
+    }
+    __syncwarp();
+    T = 2;
+    for (int k = 0; k < n; ++k) {
+      if (!insert_point(s, 4 + k, a.W, T)) {
+        if (lane == 0) set_status(LS_ERR_UNSUPPORTED);
+        failed = true;
+        T = 0;
+        break;
+      }
+    }
+  }
+  if (a.out.tri_count && lane == 0) a.out.tri_count[o] = failed ? -1 : T;
+  if (a.out.triangles) {
+    const int m = T < a.out.tri_cap ? T : a.out.tri_cap;
+    int32_t* dst = a.out.triangles + (size_t)o * a.out.tri_cap * 3;
+    for (int i = lane; i < m; i += 32) {
+      const ushort4 v = s.tv[i];
+      dst[3 * i] = v.x >= 4 ? s.gidx[v.x - 4] : -1 - v.x;
+      dst[3 * i + 1] = v.y >= 4 ? s.gidx[v.y - 4] : -1 - v.y;
+      dst[3 * i + 2] = v.z >= 4 ? s.gidx[v.z - 4] : -1 - v.z;
+    }
+  }
+  // ---- linear map inside triangles of three real points, then the NN maps
+  if (T > 0) raster_linear(s, a, o, T);
+  __syncwarp();
+  nearest_maps(s, a, o, n);
+  __syncwarp();
+}
+
+template <int CAP, bool BIG>
+__global__ void __launch_bounds__(BIG ? 32 : 32 * kInterpSmallWarps) k_interp(InterpArgs a) {
+  extern __shared__ __align__(16) unsigned char interp_dyn[];
+  InterpWarp<CAP>& s = reinterpret_cast<InterpWarp<CAP>*>(interp_dyn)[threadIdx.x >> 5];
+  const int wpc = blockDim.x >> 5;
+  int64_t items = a.n_out;
+  if (BIG) {
+    const int queued = *reinterpret_cast<volatile int32_t*>(a.queue);
+    items = queued < a.n_out ? queued : a.n_out;
+  }
+  for (int64_t item = (int64_t)blockIdx.x * wpc + (threadIdx.x >> 5); item < items;
+       item += (int64_t)gridDim.x * wpc) {
+    const int64_t o = BIG ? (int64_t)a.queue[1 + item] : item;
+    interp_patch<CAP, BIG>(s, a, o);
+  }
+}
+
+}  // namespace
+}  // namespace ls
+
+extern "C" ls_status ls_fill_interp(const ls_points* samples, const ls_region* region,
+                                    const ls_interp_params* params, const int32_t* tile_ids, int64_t n_out,
+                                    const ls_interp_outputs* out, ls_stream_t stream) {
+  using namespace ls;
+  if (!samples || !region || !params || !out || n_out < 0) return LS_ERR_INVALID_ARG;
+  if (!samples->tile_offsets) return LS_ERR_INVALID_ARG;
+  if (samples->n > 0 && (!samples->x || !samples->y || !samples->z || !samples->r || !samples->g || !samples->b))
+    return LS_ERR_INVALID_ARG;
+  if (samples->n >= (int64_t(1) << 31)) return LS_ERR_UNSUPPORTED;
+  if (region->tile_cm <= 0 || region->tiles_x <= 0 || region->tiles_y <= 0) return LS_ERR_INVALID_ARG;
+  if ((int64_t)region->tiles_x * region->tile_cm >= (int64_t(1) << 31) ||
+      (int64_t)region->tiles_y * region->tile_cm >= (int64_t(1) << 31))
+    return LS_ERR_INVALID_ARG;
+  const int64_t T = (int64_t)region->tiles_x * region->tiles_y;
+  if (!tile_ids && n_out != T) return LS_ERR_INVALID_ARG;
+  const int res = params->res;
+  if (res < 32 || res > kInterpMaxRes || res % 32) return LS_ERR_INVALID_ARG;
+  if (params->pad_cm < 0 || params->pad_cm > region->tile_cm) return LS_ERR_INVALID_ARG;
+  const int64_t W = (int64_t)region->tile_cm + 2 * (int64_t)params->pad_cm;
+  if (W > kInterpMaxWindow) return LS_ERR_UNSUPPORTED;
+  if (W % res) return LS_ERR_INVALID_ARG;
+  if (out->triangles && out->tri_cap <= 0) return LS_ERR_INVALID_ARG;
+  if (n_out == 0) return LS_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Rec* recs = static_cast<Rec*>(workspace(kWsInterpRecs, (size_t)(samples->n > 0 ? samples->n : 1) * sizeof(Rec)));
+  int32_t* queue = static_cast<int32_t*>(workspace(kWsInterpQueue, (size_t)(n_out + 1) * sizeof(int32_t)));
+  if (!recs || !queue) return LS_ERR_NO_MEMORY;
+  if (samples->n > 0)
+    k_pack<<<grid_cap((T + 7) / 8, kSmCount * 16), 256, 0, s>>>(*samples, T, region->x0_cm, region->y0_cm,
+                                                                 region->tile_cm, region->tiles_x, recs);
+  LS_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(int32_t), s));
+  InterpArgs a;
+  a.toff = samples->tile_offsets;
+  a.recs = recs;
+  a.tile_ids = tile_ids;
+  a.n_out = n_out;
+  a.n_samples = samples->n;
+  a.tiles_x = region->tiles_x;
+  a.tiles_y = region->tiles_y;
+  a.tile_cm = region->tile_cm;
+  a.res = res;
+  a.cell_cm = (int32_t)(W / res);
+  a.pad_cm = params->pad_cm;
+  a.W = (int32_t)W;
+  a.z_scale = region->z_scale;
+  a.z_offset = region->z_offset;
+  a.zs_f = (float)region->z_scale;
+  a.zo_f = (float)region->z_offset;
+  a.out = *out;
+  a.queue = queue;
+  const size_t small_smem = sizeof(InterpWarp<kInterpSmallCap>) * kInterpSmallWarps;
+  const size_t big_smem = sizeof(InterpWarp<kInterpBigCap>);
+  static bool attr_set[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LS_ERR_CUDA;
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    LS_CUDA_TRY(cudaFuncSetAttribute(k_interp<kInterpSmallCap, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)small_smem));
+    LS_CUDA_TRY(cudaFuncSetAttribute(k_interp<kInterpBigCap, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)big_smem));
+    attr_set[dev] = true;
+  }
+  k_interp<kInterpSmallCap, false>
+      <<<grid_cap((n_out + kInterpSmallWarps - 1) / kInterpSmallWarps, kSmCount * 3), 32 * kInterpSmallWarps,
+         small_smem, s>>>(a);
+  k_interp<kInterpBigCap, true><<<grid_cap(n_out, kSmCount), 32, big_smem, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
+}
