@@ -11,14 +11,13 @@
 //    every triangle's circumcircle (a float test with a proven error margin, the
 //    exact int128 determinant inside the margin), list the cavity's boundary edges
 //    with ballots and re-triangulate the cavity in place, keeping neighbour links;
-//  * linear map: the texels of every triangle with three real vertices, flattened
-//    over the lanes by a prefix sum of bounding-box texel counts, tested with exact
-//    int64 orientations.  Heights and colours are functions of the exact barycentric
-//    numerator over the exact area, so every triangle that contains a texel (on a
-//    shared edge or vertex) writes the same value;
-//  * NN map: 8 x 4 texel blocks; per block the candidates are the points whose
-//    distance to the block is at most the smallest farthest-corner distance, then
-//    every lane takes the exact int64 nearest of them (ties to the lowest index).
+//  * maps: 8 x 4 texel blocks, one texel per lane.  NN: per block the candidates are
+//    the points whose distance to the block is at most the smallest farthest-corner
+//    distance; every lane takes the exact int64 nearest of them (ties to the lowest
+//    index).  lin: the triangle that holds the texel centre, by a visibility walk
+//    over the neighbour links from the lane's previous texel (exact int64
+//    orientations), then the barycentric interpolation from the exact numerator;
+//    outputs staged per block and stored as whole rows and 4-byte words.
 // Patches whose window holds more samples than the small tier's capacity are queued
 // on the device for a second launch with one warp per CTA and a larger capacity.
 #include <climits>
@@ -28,7 +27,7 @@
 namespace ls {
 namespace {
 
-constexpr int kInterpMaxRes = 128;
+constexpr int kInterpMaxRes = 256;
 constexpr int kInterpSmallCap = 96;     // window samples per patch, small tier
 constexpr int kInterpSmallWarps = 4;    // patches (warps) per CTA, small tier
 constexpr int kInterpBigCap = 1536;     // big tier: one warp per CTA
@@ -54,9 +53,7 @@ struct InterpWarp {
   uint32_t bl[CAP];      // 16-bit B
   int32_t gidx[CAP];     // global sample index
   uint16_t list[NT];     // cavity triangles; later the NN candidates of a block
-  uint32_t inside[kInterpMaxRes * kInterpMaxRes / 32];
-  int32_t rincl[32];
-  int4 rtri[32];
+  __align__(16) uint8_t bytes[224];  // one texel block's colours (NN, lin) and flags
 };
 
 struct InterpArgs {
@@ -81,6 +78,14 @@ __device__ __forceinline__ long long orient2(int2 a, int2 b, int2 c) {
   return (long long)(b.x - a.x) * (c.y - a.y) - (long long)(b.y - a.y) * (c.x - a.x);
 }
 
+// Float of a 64-bit integer with |x| < 2^62 from two 32-bit conversions (relative
+// error below 2^-23).  The 64-bit conversions run on the FP64 pipe, which is narrow.
+__device__ __forceinline__ float ll2f(long long x) {
+  const unsigned long long u = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+  const float f = fmaf((float)(uint32_t)(u >> 32), 4294967296.f, (float)(uint32_t)u);
+  return x < 0 ? -f : f;
+}
+
 // Sign of the lifted in-circle determinant of (a, b, c, d): > 0 iff d lies strictly
 // inside the circumcircle of the counter-clockwise triangle (a, b, c).  Coordinate
 // differences are below 2^17, so the 2x2 minors fit int64 and the sum int128.
@@ -96,18 +101,18 @@ __device__ __noinline__ bool incircle_exact(int2 a, int2 b, int2 c, int2 d) {
 
 // Circumcircle of the counter-clockwise triangle (a, b, c) in float, with the margin
 // m = S^2 / 2^16, S = |cx| + |cy| + 2 W.  The centre comes from exact int64 numerators
-// over the exact denominator (three float roundings: <= 4 * 2^-24 S with the add), so
-// each of |p - c|^2 and r^2 is within 11 * 2^-24 S^2 of its true value for any p in
-// the window and their difference within 2^-18.5 S^2 < m: outside the band
-// |d^2 - r^2| <= m the float comparison decides the exact predicate.
+// over the exact denominator (two conversions within 2^-23, a division and an add:
+// <= 6 * 2^-24 S), so each of |p - c|^2 and r^2 is within 32 * 2^-24 S^2 of its true
+// value for any p in the window and their difference within 2^-18 S^2 < m: outside
+// the band |d^2 - r^2| <= m the float comparison decides the exact predicate.
 __device__ __forceinline__ float4 circumcircle(int2 a, int2 b, int2 c, int W) {
   const long long bx = b.x - a.x, by = b.y - a.y, cx = c.x - a.x, cy = c.y - a.y;
   const long long D = 2 * (bx * cy - by * cx);
   const long long B2 = bx * bx + by * by, C2 = cx * cx + cy * cy;
   const long long Nx = cy * B2 - by * C2, Ny = bx * C2 - cx * B2;
-  const float Df = (float)D;
-  const float ccx = (float)a.x + __fdiv_rn((float)Nx, Df);
-  const float ccy = (float)a.y + __fdiv_rn((float)Ny, Df);
+  const float Df = ll2f(D);
+  const float ccx = (float)a.x + __fdiv_rn(ll2f(Nx), Df);
+  const float ccy = (float)a.y + __fdiv_rn(ll2f(Ny), Df);
   const float rx = (float)a.x - ccx, ry = (float)a.y - ccy;
   const float S = fabsf(ccx) + fabsf(ccy) + 2.f * (float)W;
   return make_float4(ccx, ccy, fmaf(rx, rx, ry * ry), S * S * (1.f / 65536.f));
@@ -211,117 +216,151 @@ __device__ bool insert_point(InterpWarp<CAP>& s, int vi, int W, int& T) {
   return true;
 }
 
-// One texel of a triangle with real vertices va, vb, vc (sample slots + 4).
-template <int CAP>
-__device__ __forceinline__ void raster_texel(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o, int va, int vb,
-                                             int vc, int ii, int jj) {
-  const int h = a.cell_cm / 2;
-  const int2 g = make_int2(a.cell_cm * jj + h, a.cell_cm * ii + h);
-  const int2 A = s.P[va], B = s.P[vb], C = s.P[vc];
-  const long long wa = orient2(g, B, C);
-  if (wa < 0) return;
-  const long long wb = orient2(g, C, A);
-  if (wb < 0) return;
-  const long long wc = orient2(g, A, B);
-  if (wc < 0) return;
-  const long long area = wa + wb + wc;
-  const int ka = va - 4, kb = vb - 4, kc = vc - 4;
-  const int e = ii * a.res + jj;
-  const size_t ge = (size_t)o * a.res * a.res + e;
-  if (a.out.lin_height) {
-    // floor(num / area) and 28 fraction bits, exact: a function of the rational value
-    const long long num = wa * s.z[ka] + wb * s.z[kb] + wc * s.z[kc];
-    long long q = num / area, r = num - q * area;
-    if (r < 0) { q -= 1; r += area; }
-    const long long f = (r << 28) / area;
-    const float zc = (float)q + (float)f * (1.f / 268435456.f);
-    a.out.lin_height[ge] = fmaf(zc, a.zs_f, a.zo_f);
-  }
-  if (a.out.lin_rgb) {
-    const uint32_t ca[3] = {s.rg[ka] & 0xffffu, s.rg[ka] >> 16, s.bl[ka]};
-    const uint32_t cb[3] = {s.rg[kb] & 0xffffu, s.rg[kb] >> 16, s.bl[kb]};
-    const uint32_t cc[3] = {s.rg[kc] & 0xffffu, s.rg[kc] >> 16, s.bl[kc]};
-    const float af = (float)area;
-    uint8_t* dst = a.out.lin_rgb + ge * 3;
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      // round half up of numc / area / 256; the float estimate is within 6e-5 of the
-      // exact value, so away from a rounding boundary its floor is the exact one
-      const long long numc = wa * ca[ch] + wb * cb[ch] + wc * cc[ch];
-      const float fq = __fdiv_rn((float)numc, af) * (1.f / 256.f) + 0.5f;
-      const float fl = floorf(fq), fr = fq - fl;
-      long long k = (long long)fl;
-      if (!(fr > 1e-3f && fr < 1.f - 1e-3f)) k = (numc + 128 * area) / (256 * area);
-      dst[ch] = (uint8_t)(k > 255 ? 255 : k);
-    }
-  }
-  atomicOr(&s.inside[e >> 5], 1u << (e & 31));
-}
+__device__ __forceinline__ bool real_tri(ushort4 v) { return v.x >= 4 && v.y >= 4 && v.z >= 4; }
 
+// Triangle that contains the point g (closed), by a visibility walk from `hint`: cross
+// the first edge that has g strictly on its outer side.  The walk ends on a Delaunay
+// triangulation; a scan of all triangles backs up a walk that runs too long.  w gets
+// the weights of g in the triangle found: w[k] = twice the area of the sub-triangle
+// opposite vertex k.
 template <int CAP>
-__device__ void raster_linear(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o, int T) {
-  const int lane = threadIdx.x & 31;
-  const int res = a.res, cell = a.cell_cm, h = cell / 2;
-  for (int base = 0; base < T; base += 32) {
-    const int i = base + lane;
-    int cnt = 0, j0 = 0, i0 = 0, bw = 1;
-    ushort4 v = make_ushort4(0, 0, 0, 0);
-    if (i < T) {
-      v = s.tv[i];
-      if (v.x >= 4 && v.y >= 4 && v.z >= 4) {
-        const int2 A = s.P[v.x], B = s.P[v.y], C = s.P[v.z];
-        const int xmin = min(A.x, min(B.x, C.x)), xmax = max(A.x, max(B.x, C.x));
-        const int ymin = min(A.y, min(B.y, C.y)), ymax = max(A.y, max(B.y, C.y));
-        // texel centres cell * j + h inside [min, max]
-        j0 = xmin <= h ? 0 : (xmin - h + cell - 1) / cell;
-        i0 = ymin <= h ? 0 : (ymin - h + cell - 1) / cell;
-        const int j1 = xmax < h ? -1 : min(res - 1, (xmax - h) / cell);
-        const int i1 = ymax < h ? -1 : min(res - 1, (ymax - h) / cell);
-        if (j1 >= j0 && i1 >= i0) {
-          bw = j1 - j0 + 1;
-          cnt = bw * (i1 - i0 + 1);
-        }
+__device__ int locate(const InterpWarp<CAP>& s, int2 g, int hint, int T, long long w[3]) {
+  int t = hint;
+  for (int step = 0; step < 2 * T + 8; ++step) {
+    const ushort4 v = s.tv[t];
+    const int2 A = s.P[v.x], B = s.P[v.y], C = s.P[v.z];
+    int e = -1;
+    w[2] = orient2(A, B, g);
+    if (w[2] < 0) {
+      e = 0;
+    } else {
+      w[0] = orient2(B, C, g);
+      if (w[0] < 0) {
+        e = 1;
+      } else {
+        w[1] = orient2(C, A, g);
+        if (w[1] < 0) e = 2;
       }
     }
-    int incl = cnt;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int u = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += u;
+    if (e < 0) return t;
+    short4 nb = s.tn[t];
+    const int nt = tn_at(nb, e);
+    if (nt < 0 || nt >= T) break;
+    t = nt;
+  }
+  for (int i = 0; i < T; ++i) {
+    const ushort4 v = s.tv[i];
+    const int2 A = s.P[v.x], B = s.P[v.y], C = s.P[v.z];
+    w[0] = orient2(B, C, g);
+    w[1] = orient2(C, A, g);
+    w[2] = orient2(A, B, g);
+    if (w[0] >= 0 && w[1] >= 0 && w[2] >= 0) return i;
+  }
+  return -1;
+}
+
+// A triangle of three real points that holds g on its boundary, given the triangle t
+// without data that contains g with the weights w (w[k] = 0: g on the edge opposite
+// vertex k).  -1 if there is none.
+template <int CAP>
+__device__ int real_neighbour(const InterpWarp<CAP>& s, int t, const long long w[3], int T) {
+  const ushort4 v = s.tv[t];
+  const int vid[3] = {v.x, v.y, v.z};
+  const int zeros = (w[0] == 0) + (w[1] == 0) + (w[2] == 0);
+  if (zeros == 1) {  // on the edge opposite vertex k: edge index (k + 1) % 3
+    const int k = w[0] == 0 ? 0 : (w[1] == 0 ? 1 : 2);
+    short4 nb = s.tn[t];
+    const int n = tn_at(nb, (k + 1) % 3);
+    return n >= 0 && n < T && real_tri(s.tv[n]) ? n : -1;
+  }
+  if (zeros != 2) return -1;
+  // g is the vertex with the non-zero weight: turn around it both ways
+  const int c = w[0] != 0 ? vid[0] : (w[1] != 0 ? vid[1] : vid[2]);
+  if (c < 4) return -1;
+  for (int dir = 0; dir < 2; ++dir) {
+    int cur = t;
+    for (int it = 0; it < T; ++it) {
+      const ushort4 u = s.tv[cur];
+      const int k = u.x == c ? 0 : (u.y == c ? 1 : 2);
+      short4 nb = s.tn[cur];
+      const int n = tn_at(nb, dir == 0 ? k : (k + 2) % 3);
+      if (n < 0 || n >= T || n == t) break;
+      if (real_tri(s.tv[n])) return n;
+      cur = n;
     }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    if (total == 0) continue;
-    s.rincl[lane] = incl;
-    s.rtri[lane] = make_int4(v.x | (v.y << 16), v.z, j0 | (i0 << 16), bw);
-    __syncwarp();
-    for (int idx = lane; idx < total; idx += 32) {
-      int pos = 0;  // number of triangles of the chunk whose texels all precede idx
+  }
+  return -1;
+}
+
+// Linear height (metres) and 8-bit colour of g in the real triangle t, from the
+// weights w (twice the areas of the sub-triangles opposite each vertex).
+template <int CAP>
+__device__ __forceinline__ void linear_value(const InterpWarp<CAP>& s, const InterpArgs& a, int t,
+                                             const long long w[3], float& h, uint32_t& c8) {
+  const ushort4 v = s.tv[t];
+  const long long wa = w[0], wb = w[1], wc = w[2];
+  const long long area = wa + wb + wc;
+  const int ka = v.x - 4, kb = v.y - 4, kc = v.z - 4;
+  const float inv = __frcp_rn(ll2f(area));
+  // q = floor(num / area) and r = num - q * area, exact: a float estimate (within 81
+  // of q for |z| < 2^28) corrected in int64.  The product may wrap around in the
+  // unsigned arithmetic; the true remainder fits, so the difference is exact.
+  const long long num = wa * s.z[ka] + wb * s.z[kb] + wc * s.z[kc];
+  int q = (int)floorf(ll2f(num) * inv);
+  long long r = (long long)((unsigned long long)num - (unsigned long long)(long long)q * (unsigned long long)area);
+  const int dq = (int)floorf(ll2f(r) * inv);
+  q += dq;
+  r -= (long long)dq * area;
+  if (r < 0) {
+    q -= 1; r += area;
+  } else if (r >= area) {
+    q += 1; r -= area;
+  }
+  h = fmaf((float)q + ll2f(r) * inv, a.zs_f, a.zo_f);  // the fraction within 2^-21
+  // colours from float barycentric weights (within 2^-21): the 16-bit value within
+  // 0.06, the 8-bit one within 3e-4; near a rounding boundary the exact integers decide
+  const float lb = ll2f(wb) * inv, lc = ll2f(wc) * inv;
+  const uint32_t ca[3] = {s.rg[ka] & 0xffffu, s.rg[ka] >> 16, s.bl[ka]};
+  const uint32_t cb[3] = {s.rg[kb] & 0xffffu, s.rg[kb] >> 16, s.bl[kb]};
+  const uint32_t cc[3] = {s.rg[kc] & 0xffffu, s.rg[kc] >> 16, s.bl[kc]};
+  c8 = 0u;
 #pragma unroll
-      for (int st = 16; st > 0; st >>= 1)
-        if (s.rincl[pos + st - 1] <= idx) pos += st;
-      const int4 rt = s.rtri[pos];
-      const int local = idx - (pos ? s.rincl[pos - 1] : 0);
-      raster_texel(s, a, o, rt.x & 0xffff, rt.x >> 16, rt.y, (rt.z >> 16) + local / rt.w,
-                   (rt.z & 0xffff) + local % rt.w);
+  for (int ch = 0; ch < 3; ++ch) {
+    const float ya = (float)ca[ch];
+    const float y = fmaf(lb, (float)cb[ch] - ya, fmaf(lc, (float)cc[ch] - ya, ya));
+    const float fq = fmaf(y, 1.f / 256.f, 0.5f);
+    const float fl = floorf(fq), fr = fq - fl;
+    int k = (int)fl;
+    if (!(fr > 1e-3f && fr < 1.f - 1e-3f)) {
+      const long long numc = wa * ca[ch] + wb * cb[ch] + wc * cc[ch];
+      k = (int)((numc + 128 * area) / (256 * area));
     }
-    __syncwarp();
+    c8 |= (uint32_t)(k > 255 ? 255 : k) << (8 * ch);
   }
 }
 
-// NN map over 8 x 4 texel blocks; texels outside every real triangle also take it as
-// their linear value.
+// All maps over 8 x 4 texel blocks, one texel per lane.
+//  * NN: the candidates of a block are the points whose distance to the block is at
+//    most U, the smallest farthest-corner distance over all points (every texel's
+//    nearest point, and every point tied with it, is one); each lane takes the exact
+//    nearest candidate, candidates in sample order.
+//  * lin: the triangle that contains the texel centre, found by a walk from the one
+//    the same lane found 8 texels before; a triangle with a padding corner hands the
+//    texel to a real triangle that holds it on its boundary, if any (closed triangles,
+//    as the inside test of Alg. 1), else the texel takes its NN value.
+// Outputs are staged per block and stored as 32-byte rows of heights and 4-byte words
+// of colours and inside flags.
 template <int CAP>
-__device__ void nearest_maps(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o, int n) {
+__device__ void texel_maps(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o, int n, int T) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanes_below();
   const int res = a.res, cell = a.cell_cm, h = cell / 2;
   const int bxn = res / 8, nblk = bxn * (res / 4);
+  int hint = 0;
   for (int blk = 0; blk < nblk; ++blk) {
     const int bj = (blk % bxn) * 8, bi = (blk / bxn) * 4;
     const int jj = bj + (lane & 7), ii = bi + (lane >> 3);
     const int gxa = cell * bj + h, gxb = gxa + 7 * cell, gya = cell * bi + h, gyb = gya + 3 * cell;
-    // U: the smallest farthest-corner squared distance; every texel's nearest point
-    // (and every point tied with it) lies within sqrt(U) of the block
     long long U = LLONG_MAX;
     for (int k = lane; k < n; k += 32) {
       const int2 q = s.P[4 + k];
@@ -349,35 +388,66 @@ __device__ void nearest_maps(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o,
       nc += __popc(m);
     }
     __syncwarp();
-    const int gx = cell * jj + h, gy = cell * ii + h;
+    const int2 g = make_int2(cell * jj + h, cell * ii + h);
     long long best = LLONG_MAX;
     int bk = -1;
     for (int c = 0; c < nc; ++c) {
       const int k = s.list[c];
       const int2 q = s.P[4 + k];
-      const long long d2 = (long long)(q.x - gx) * (q.x - gx) + (long long)(q.y - gy) * (q.y - gy);
+      const long long d2 = (long long)(q.x - g.x) * (q.x - g.x) + (long long)(q.y - g.y) * (q.y - g.y);
       if (d2 < best) { best = d2; bk = k; }
     }
-    __syncwarp();
-    const int e = ii * res + jj;
-    const size_t ge = (size_t)o * res * res + e;
-    const float hv = bk >= 0 ? s.hm[bk] : __int_as_float(0x7fc00000);
-    const uint32_t c8 = bk >= 0 ? s.c8[bk] : 0u;
-    const bool in = (s.inside[e >> 5] >> (e & 31)) & 1u;
-    if (a.out.nn_height) a.out.nn_height[ge] = hv;
-    if (a.out.nn_rgb) {
-      uint8_t* d = a.out.nn_rgb + ge * 3;
-      d[0] = (uint8_t)c8; d[1] = (uint8_t)(c8 >> 8); d[2] = (uint8_t)(c8 >> 16);
-    }
-    if (!in) {
-      if (a.out.lin_height) a.out.lin_height[ge] = hv;
-      if (a.out.lin_rgb) {
-        uint8_t* d = a.out.lin_rgb + ge * 3;
-        d[0] = (uint8_t)c8; d[1] = (uint8_t)(c8 >> 8); d[2] = (uint8_t)(c8 >> 16);
+    const float nn_h = bk >= 0 ? s.hm[bk] : __int_as_float(0x7fc00000);
+    const uint32_t nn_c = bk >= 0 ? s.c8[bk] : 0u;
+    float lin_h = nn_h;
+    uint32_t lin_c = nn_c;
+    bool in = false;
+    if (T > 0) {
+      long long w[3];
+      int t = locate(s, g, hint, T, w);
+      if (t >= 0) {
+        hint = t;
+        if (!real_tri(s.tv[t])) {
+          t = (w[0] == 0 || w[1] == 0 || w[2] == 0) ? real_neighbour(s, t, w, T) : -1;
+          if (t >= 0) {
+            const ushort4 v = s.tv[t];
+            const int2 A = s.P[v.x], B = s.P[v.y], C = s.P[v.z];
+            w[0] = orient2(B, C, g);
+            w[1] = orient2(C, A, g);
+            w[2] = orient2(A, B, g);
+          }
+        }
+        if (t >= 0) {
+          in = true;
+          linear_value(s, a, t, w, lin_h, lin_c);
+        }
       }
     }
-    if (a.out.inside) a.out.inside[ge] = in ? 1 : 0;
+    // ---- stores: heights as rows of 8 floats; colours and flags through the stage
+    const size_t ge = (size_t)o * res * res + (size_t)ii * res + jj;
+    if (a.out.nn_height) a.out.nn_height[ge] = nn_h;
+    if (a.out.lin_height) a.out.lin_height[ge] = lin_h;
+    __syncwarp();  // the previous block's stage has been stored
+    uint8_t* st = s.bytes;
+    st[3 * lane] = (uint8_t)nn_c; st[3 * lane + 1] = (uint8_t)(nn_c >> 8); st[3 * lane + 2] = (uint8_t)(nn_c >> 16);
+    st[96 + 3 * lane] = (uint8_t)lin_c; st[97 + 3 * lane] = (uint8_t)(lin_c >> 8);
+    st[98 + 3 * lane] = (uint8_t)(lin_c >> 16);
+    st[192 + lane] = in ? 1 : 0;
+    __syncwarp();
+    const size_t row0 = (size_t)o * res * res + (size_t)bi * res + bj;  // texel of the block's first row
+    if (lane < 24) {  // 4 rows x 6 words of 8 texels' colours
+      const int r = lane / 6, w = lane % 6;
+      const size_t off = (row0 + (size_t)r * res) * 3 + 4 * w;
+      if (a.out.nn_rgb) *reinterpret_cast<uint32_t*>(a.out.nn_rgb + off) = reinterpret_cast<const uint32_t*>(st)[6 * r + w];
+      if (a.out.lin_rgb)
+        *reinterpret_cast<uint32_t*>(a.out.lin_rgb + off) = reinterpret_cast<const uint32_t*>(st + 96)[6 * r + w];
+    } else if (a.out.inside) {  // 4 rows x 2 words of flags
+      const int r = (lane - 24) >> 1, w = lane & 1;
+      *reinterpret_cast<uint32_t*>(a.out.inside + row0 + (size_t)r * res + 4 * w) =
+          reinterpret_cast<const uint32_t*>(st + 192)[2 * r + w];
+    }
   }
+  __syncwarp();
 }
 
 // Alg. 1 for output ordinal o.  The small tier queues a patch with more than CAP
@@ -463,7 +533,6 @@ __device__ void interp_patch(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o)
     s.c8[k] = c8;
   }
   for (int k = lane; k < n + 4; k += 32) s.start[k] = -1;
-  for (int k = lane; k < a.res * a.res / 32; k += 32) s.inside[k] = 0u;
   if (lane < 4) s.P[lane] = make_int2(lane == 1 || lane == 2 ? a.W : 0, lane >= 2 ? a.W : 0);
   __syncwarp();
   // ---- Delaunay triangulation of corners and samples
@@ -497,11 +566,8 @@ __device__ void interp_patch(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o)
       dst[3 * i + 2] = v.z >= 4 ? s.gidx[v.z - 4] : -1 - v.z;
     }
   }
-  // ---- linear map inside triangles of three real points, then the NN maps
-  if (T > 0) raster_linear(s, a, o, T);
-  __syncwarp();
-  nearest_maps(s, a, o, n);
-  __syncwarp();
+  // ---- NN map and linear map inside triangles of three real points
+  texel_maps(s, a, o, n, T);
 }
 
 template <int CAP, bool BIG>
@@ -540,7 +606,11 @@ extern "C" ls_status ls_fill_interp(const ls_points* samples, const ls_region* r
   const int64_t T = (int64_t)region->tiles_x * region->tiles_y;
   if (!tile_ids && n_out != T) return LS_ERR_INVALID_ARG;
   const int res = params->res;
-  if (res < 32 || res > kInterpMaxRes || res % 32) return LS_ERR_INVALID_ARG;
+  if (res < 8 || res > kInterpMaxRes || res % 8) return LS_ERR_INVALID_ARG;
+  // colours and flags are stored as 4-byte words
+  if ((reinterpret_cast<uintptr_t>(out->nn_rgb) | reinterpret_cast<uintptr_t>(out->lin_rgb) |
+       reinterpret_cast<uintptr_t>(out->inside)) & 3u)
+    return LS_ERR_INVALID_ARG;
   if (params->pad_cm < 0 || params->pad_cm > region->tile_cm) return LS_ERR_INVALID_ARG;
   const int64_t W = (int64_t)region->tile_cm + 2 * (int64_t)params->pad_cm;
   if (W > kInterpMaxWindow) return LS_ERR_UNSUPPORTED;
@@ -586,9 +656,17 @@ extern "C" ls_status ls_fill_interp(const ls_points* samples, const ls_region* r
                                      (int)big_smem));
     attr_set[dev] = true;
   }
+  static int small_per_sm[64] = {};
+  if (dev >= 0 && dev < 64 && small_per_sm[dev] == 0) {
+    int b = 0;
+    LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_interp<kInterpSmallCap, false>,
+                                                              32 * kInterpSmallWarps, small_smem));
+    small_per_sm[dev] = b > 0 ? b : 1;
+  }
+  const int per_sm = dev >= 0 && dev < 64 ? small_per_sm[dev] : 1;
   k_interp<kInterpSmallCap, false>
-      <<<grid_cap((n_out + kInterpSmallWarps - 1) / kInterpSmallWarps, kSmCount * 3), 32 * kInterpSmallWarps,
-         small_smem, s>>>(a);
+      <<<grid_cap((n_out + kInterpSmallWarps - 1) / kInterpSmallWarps, (int64_t)kSmCount * per_sm),
+         32 * kInterpSmallWarps, small_smem, s>>>(a);
   k_interp<kInterpBigCap, true><<<grid_cap(n_out, kSmCount), 32, big_smem, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }

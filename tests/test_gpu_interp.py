@@ -233,3 +233,22 @@ def test_overview_full_size_sampled(lsb):
     tiles = list(rng.choice(region.n_tiles, size=6, replace=False)) + [0, region.n_tiles - 1]
     for t in tiles:
         check_patch(got, int(t), host, region, int(t), msg=f"overview tile {t}")
+
+
+def test_slivers_and_extreme_heights(lsb):
+    """Nearly collinear clusters (sliver triangles whose height and colour steps per
+    texel are huge) with heights near +-2^27 cm and extreme colours."""
+    region = synth.Region(tiles_x=1, tiles_y=1, z_offset=7.0)
+    rng = np.random.default_rng(17)
+    n = 60
+    t = rng.integers(0, region.tile_cm, n)
+    lx = t
+    # around the texel-centre row at y = 31500 (window y 47500)
+    ly = 31500 + (t // 7) % 3 - 1 + rng.integers(-2, 3, n) * (rng.random(n) < 0.2)
+    z = rng.choice([-(2 ** 27) + 5, 2 ** 27 - 5, 0, 12345], size=n)
+    rgb = rng.choice([0, 65535, 32768, 127], size=(n, 3))
+    samples = bucket(region, region.x0_cm + lx, region.y0_cm + ly, z, rgb=rgb)
+    got, st = run_gpu(lsb, samples, region)
+    assert st == 0
+    ref = check_patch(got, 0, samples, region, 0, msg="slivers")
+    assert ref["inside"].sum() > 0
