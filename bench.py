@@ -262,9 +262,10 @@ def run_b300(args, rank, world):
 
 def run_overview(lsb, args, dev, stream):
     """Country-scale overview (200 x 200 tiles, 4 pts/m^2, 33 chunk samples per tile):
-    Gaussian fill of all 40,000 tiles in one launch and the learned fill (batches of
-    4096 tiles) on the same samples; height / colour RMSE against the full-resolution
-    means on a seeded 400-tile subset.  The filler is trained first on pairs the method
+    Gaussian fill of all 40,000 tiles in one launch, the nearest-neighbour and
+    Delaunay-linear maps of Alg. 1 on the 96 x 96 padded patches of all tiles, and the
+    learned fill (batches of 4096 tiles) on the same samples; height / colour RMSE
+    against the full-resolution means on a seeded 400-tile subset.  The filler is trained first on pairs the method
     generates (seeds disjoint from the overview)."""
     import torch
     import synth
@@ -291,6 +292,11 @@ def run_overview(lsb, args, dev, stream):
 
     with torch.cuda.stream(stream):
         ms_gauss = timed(lambda: lsb.fill_sparse(s, region, height=h, rgb=c, stream=stream), args.steps)
+    # Alg. 1 maps (nearest-neighbour and Delaunay-linear) on the 96 x 96 padded patches
+    with torch.cuda.stream(stream):
+        im = lsb.fill_interp(s, region, res=96, pad_cm=16000, stream=stream)
+        ms_interp = timed(lambda: lsb.fill_interp(s, region, res=96, pad_cm=16000, out=im, stream=stream), args.steps)
+    assert lsb.last_error() == 0
     # train the filler (tensor-core forward/backward) on self-generated pairs
     t0 = time.perf_counter()
     train_set = T.synthetic_tiles(args.train_tiles, seed0=100, device=dev)
@@ -337,9 +343,21 @@ def run_overview(lsb, args, dev, stream):
         cnt.clamp(min=1)[..., None] / 256.0
     rm = lambda a: float(torch.sqrt(((a.to(torch.float64) - th)[m] ** 2).mean()))  # noqa: E731
     rc = lambda a: float(torch.sqrt(((a.to(torch.float64) - tcol)[m] ** 2).mean()))  # noqa: E731
+    crop = lambda a: a[sub_t][:, 16:80, 16:80]  # the tile's 64 x 64 texels inside the patch  # noqa: E731
+    inside = float(im["inside"][:, 16:80, 16:80].to(torch.float32).mean())
+    interp_bytes = nT * 96 * 96 * (4 + 4 + 3 + 3 + 1)
     return {"workload": "overview 200x200 tiles, 4 pts/m^2, 33 samples/tile (1.32M samples)",
             "gaussian_fill": {"tiles_per_s": round(nT / (ms_gauss * 1e-3), 1), "ms": round(ms_gauss, 3),
                               "height_rmse_m": round(rm(h[sub_t]), 4), "rgb_rmse_8bit": round(rc(c[sub_t]), 3)},
+            "interp_fill": {"tiles_per_s": round(nT / (ms_interp * 1e-3), 1), "ms": round(ms_interp, 3),
+                            "patch": "96x96 texels of 10 m (tile + 160 m padding), Alg. 1",
+                            "nn_height_rmse_m": round(rm(crop(im["nn_height"])), 4),
+                            "lin_height_rmse_m": round(rm(crop(im["lin_height"])), 4),
+                            "nn_rgb_rmse_8bit": round(rc(crop(im["nn_rgb"])), 3),
+                            "lin_rgb_rmse_8bit": round(rc(crop(im["lin_rgb"])), 3),
+                            "inside_fraction_of_tile": round(inside, 4),
+                            # integer/latency-bound kernel: output bytes per second for scale
+                            "output_gbs": round(interp_bytes / (ms_interp * 1e-3) / 1e9, 1)},
             "learned_fill": {"tiles_per_s": round(nT / (ms_learned * 1e-3), 1), "ms": round(ms_learned, 3),
                              "batch": 4096, "height_rmse_m": round(rm(lh[sub_t]), 4),
                              "rgb_rmse_8bit": round(rc(lc[sub_t]), 3),

@@ -15,8 +15,9 @@
 //    the points whose distance to the block is at most the smallest farthest-corner
 //    distance; every lane takes the exact int64 nearest of them (ties to the lowest
 //    index).  lin: the triangle that holds the texel centre, by a visibility walk
-//    over the neighbour links from the lane's previous texel (exact int64
-//    orientations), then the barycentric interpolation from the exact numerator;
+//    over the neighbour links from the lane's texel of the previous block (blocks in
+//    serpentine column order; exact int64 orientations), then the barycentric
+//    interpolation from the exact numerator;
 //    outputs staged per block and stored as whole rows and 4-byte words.
 // Patches whose window holds more samples than the small tier's capacity are queued
 // on the device for a second launch with one warp per CTA and a larger capacity.
@@ -228,22 +229,13 @@ __device__ int locate(const InterpWarp<CAP>& s, int2 g, int hint, int T, long lo
   int t = hint;
   for (int step = 0; step < 2 * T + 8; ++step) {
     const ushort4 v = s.tv[t];
-    const int2 A = s.P[v.x], B = s.P[v.y], C = s.P[v.z];
-    int e = -1;
-    w[2] = orient2(A, B, g);
-    if (w[2] < 0) {
-      e = 0;
-    } else {
-      w[0] = orient2(B, C, g);
-      if (w[0] < 0) {
-        e = 1;
-      } else {
-        w[1] = orient2(C, A, g);
-        if (w[1] < 0) e = 2;
-      }
-    }
-    if (e < 0) return t;
     short4 nb = s.tn[t];
+    const int2 A = s.P[v.x], B = s.P[v.y], C = s.P[v.z];
+    w[2] = orient2(A, B, g);
+    w[0] = orient2(B, C, g);
+    w[1] = orient2(C, A, g);
+    const int e = w[2] < 0 ? 0 : (w[0] < 0 ? 1 : (w[1] < 0 ? 2 : -1));
+    if (e < 0) return t;
     const int nt = tn_at(nb, e);
     if (nt < 0 || nt >= T) break;
     t = nt;
@@ -345,7 +337,8 @@ __device__ __forceinline__ void linear_value(const InterpWarp<CAP>& s, const Int
 //    nearest point, and every point tied with it, is one); each lane takes the exact
 //    nearest candidate, candidates in sample order.
 //  * lin: the triangle that contains the texel centre, found by a walk from the one
-//    the same lane found 8 texels before; a triangle with a padding corner hands the
+//    the same lane found in the previous block (4 texels above or below, or 8 to the
+//    left); a triangle with a padding corner hands the
 //    texel to a real triangle that holds it on its boundary, if any (closed triangles,
 //    as the inside test of Alg. 1), else the texel takes its NN value.
 // Outputs are staged per block and stored as 32-byte rows of heights and 4-byte words
@@ -355,10 +348,13 @@ __device__ void texel_maps(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o, i
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanes_below();
   const int res = a.res, cell = a.cell_cm, h = cell / 2;
-  const int bxn = res / 8, nblk = bxn * (res / 4);
+  const int byn = res / 4, nblk = (res / 8) * byn;
   int hint = 0;
+  // blocks column by column, down one column and up the next, so that a lane's
+  // previous texel (its walk's start) is 4 texels above or below, or 8 to the left
   for (int blk = 0; blk < nblk; ++blk) {
-    const int bj = (blk % bxn) * 8, bi = (blk / bxn) * 4;
+    const int col = blk / byn, rr = blk % byn;
+    const int bj = col * 8, bi = ((col & 1) ? byn - 1 - rr : rr) * 4;
     const int jj = bj + (lane & 7), ii = bi + (lane >> 3);
     const int gxa = cell * bj + h, gxb = gxa + 7 * cell, gya = cell * bi + h, gyb = gya + 3 * cell;
     long long U = LLONG_MAX;
