@@ -537,6 +537,29 @@ def run_fill_case(args):
     return 0 if st == 0 else 1
 
 
+def run_interp_case(args):
+    """Profiling case for the Alg. 1 maps: the chunk samples of a k x k-tile overview
+    region (4 pts/m^2, 33 samples per tile), NN and linear maps of the 96 x 96 padded
+    patches."""
+    import torch
+    import paper_2509_20198_b300 as lsb
+    import synth
+    import synth.gpu as sg
+    from paper_2509_20198_b300 import build
+    build.build_library()
+    build.build_synth()
+    k = args.case_tiles
+    region, counts = synth.overview_workload(tiles=k)
+    s = sg.region_samples(3, region, counts)
+    out = lsb.fill_interp(s, region, res=96, pad_cm=16000)
+    for _ in range(args.steps):
+        lsb.fill_interp(s, region, res=96, pad_cm=16000, out=out)
+    torch.cuda.synchronize()
+    st = lsb.last_error()
+    print(json.dumps({"case": "interp", "tiles": k * k, "samples": int(s["x"].numel()), "status": st}))
+    return 0 if st == 0 else 1
+
+
 def run_learned_case(args):
     """Profiling case for the learned filler: one forward pass and one training step
     (forward, loss, backward, AdamW) of the U-Net on a batch of random bf16 inputs, with
@@ -577,7 +600,8 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--overview", type=int, default=1, help="also time the 40,000-tile overview fills")
-    ap.add_argument("--case", default="", choices=["", "bin-small", "learned", "fill"], help="profiling case instead of the bench")
+    ap.add_argument("--case", default="", choices=["", "bin-small", "learned", "fill", "interp"],
+                    help="profiling case instead of the bench")
     ap.add_argument("--case-tiles", type=int, default=3, help="tiles per side of the profiling case")
     ap.add_argument("--train-tiles", type=int, default=4096)
     ap.add_argument("--train-epochs", type=int, default=60)
@@ -588,6 +612,8 @@ def main():
         sys.exit(run_learned_case(args))
     if args.case == "fill":
         sys.exit(run_fill_case(args))
+    if args.case == "interp":
+        sys.exit(run_interp_case(args))
     if args.case:
         sys.exit(run_profile_case(args))
     if args.impl == "reference":

@@ -15,9 +15,8 @@
 //    the points whose distance to the block is at most the smallest farthest-corner
 //    distance; every lane takes the exact int64 nearest of them (ties to the lowest
 //    index).  lin: the triangle that holds the texel centre, by a visibility walk
-//    over the neighbour links from the lane's texel of the previous block (blocks in
-//    serpentine column order; exact int64 orientations), then the barycentric
-//    interpolation from the exact numerator;
+//    over the neighbour links from the lane's texel of the block above (exact int64
+//    orientations), then the barycentric interpolation from the exact numerator;
 //    outputs staged per block and stored as whole rows and 4-byte words.
 // Patches whose window holds more samples than the small tier's capacity are queued
 // on the device for a second launch with one warp per CTA and a larger capacity.
@@ -28,7 +27,7 @@
 namespace ls {
 namespace {
 
-constexpr int kInterpMaxRes = 256;
+constexpr int kInterpMaxRes = 128;
 constexpr int kInterpSmallCap = 96;     // window samples per patch, small tier
 constexpr int kInterpSmallWarps = 4;    // patches (warps) per CTA, small tier
 constexpr int kInterpBigCap = 1536;     // big tier: one warp per CTA
@@ -55,6 +54,7 @@ struct InterpWarp {
   int32_t gidx[CAP];     // global sample index
   uint16_t list[NT];     // cavity triangles; later the NN candidates of a block
   __align__(16) uint8_t bytes[224];  // one texel block's colours (NN, lin) and flags
+  uint16_t hints[kInterpMaxRes / 8][32];  // per block column and lane: the last triangle
 };
 
 struct InterpArgs {
@@ -226,7 +226,7 @@ __device__ __forceinline__ bool real_tri(ushort4 v) { return v.x >= 4 && v.y >= 
 // opposite vertex k.
 template <int CAP>
 __device__ int locate(const InterpWarp<CAP>& s, int2 g, int hint, int T, long long w[3]) {
-  int t = hint;
+  int t = hint >= 0 && hint < T ? hint : 0;
   for (int step = 0; step < 2 * T + 8; ++step) {
     const ushort4 v = s.tv[t];
     short4 nb = s.tn[t];
@@ -337,8 +337,7 @@ __device__ __forceinline__ void linear_value(const InterpWarp<CAP>& s, const Int
 //    nearest point, and every point tied with it, is one); each lane takes the exact
 //    nearest candidate, candidates in sample order.
 //  * lin: the triangle that contains the texel centre, found by a walk from the one
-//    the same lane found in the previous block (4 texels above or below, or 8 to the
-//    left); a triangle with a padding corner hands the
+//    the same lane found in the block above (4 texels up); a triangle with a padding corner hands the
 //    texel to a real triangle that holds it on its boundary, if any (closed triangles,
 //    as the inside test of Alg. 1), else the texel takes its NN value.
 // Outputs are staged per block and stored as 32-byte rows of heights and 4-byte words
@@ -348,13 +347,14 @@ __device__ void texel_maps(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o, i
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanes_below();
   const int res = a.res, cell = a.cell_cm, h = cell / 2;
-  const int byn = res / 4, nblk = (res / 8) * byn;
+  const int bxn = res / 8, nblk = bxn * (res / 4);
   int hint = 0;
-  // blocks column by column, down one column and up the next, so that a lane's
-  // previous texel (its walk's start) is 4 texels above or below, or 8 to the left
+  // blocks row by row (whole 32-byte sectors of every output row are written by
+  // consecutive blocks); a lane's walk starts from the triangle it found in the block
+  // above (4 texels up), in the first block row from the block to the left
   for (int blk = 0; blk < nblk; ++blk) {
-    const int col = blk / byn, rr = blk % byn;
-    const int bj = col * 8, bi = ((col & 1) ? byn - 1 - rr : rr) * 4;
+    const int bj = (blk % bxn) * 8, bi = (blk / bxn) * 4;
+    if (bi > 0) hint = s.hints[bj >> 3][lane];
     const int jj = bj + (lane & 7), ii = bi + (lane >> 3);
     const int gxa = cell * bj + h, gxb = gxa + 7 * cell, gya = cell * bi + h, gyb = gya + 3 * cell;
     long long U = LLONG_MAX;
@@ -403,6 +403,7 @@ __device__ void texel_maps(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o, i
       int t = locate(s, g, hint, T, w);
       if (t >= 0) {
         hint = t;
+        s.hints[bj >> 3][lane] = (uint16_t)t;
         if (!real_tri(s.tv[t])) {
           t = (w[0] == 0 || w[1] == 0 || w[2] == 0) ? real_neighbour(s, t, w, T) : -1;
           if (t >= 0) {
