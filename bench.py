@@ -257,6 +257,8 @@ def run_b300(args, rank, world):
         del pts, step, graph
         torch.cuda.empty_cache()
         out["overview"] = run_overview(lsb, args, dev, stream)
+        torch.cuda.empty_cache()
+        out["resolutions"] = run_resolutions(lsb, args, dev, stream)
     return out
 
 
@@ -376,6 +378,70 @@ def run_overview(lsb, args, dev, stream):
                          "loss_first": [round(v, 7) for v in hist[0]],
                          "loss_last": [round(v, 7) for v in hist[-1]], "loss_parts": "total, height, colour, bound"},
             "truth": "per-texel mean of the full-resolution points, 400 seeded tiles"}
+
+
+def run_resolutions(lsb, args, dev, stream):
+    """Texel-size study (1, 2.5, 5, 10, 20, 40 m texels) through the same kernels on a
+    20 x 20-tile region at 4 pts/m^2: the truth (exact binning of all points at that
+    cell size), the Gaussian fill of every tile and the Alg. 1 maps of every padded patch
+    (tile + 160 m), timed, with their height RMSE against the truth."""
+    import torch
+    import synth
+    import synth.gpu as sg
+    region, counts = synth.overview_workload(tiles=20)
+    nT = region.n_tiles
+    with torch.cuda.stream(stream):
+        s = sg.region_samples(5, region, counts, device=dev, stream=stream)
+        pts = sg.region_points(5, region, counts, device=dev, stream=stream)
+    stream.synchronize()
+    n_points = int(counts.sum())
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    rows = []
+    reps = max(1, args.steps // 4)
+    for texel_cm in (100, 250, 500, 1000, 2000, 4000):
+        cells = region.tile_cm // texel_cm
+        pres = (region.tile_cm + 2 * 16000) // texel_cm
+        a = 16000 // texel_cm  # the tile's texels start here inside the patch
+        with torch.cuda.stream(stream):
+            bins = [lsb.empty_bins(nT, cells, dev)]
+            ms_bin = timed(lambda: lsb.bin_points(pts, region, levels=(cells,), out=bins, stream=stream), reps)
+            h = torch.empty((nT, cells, cells), dtype=torch.float32, device=dev)
+            c = torch.empty((nT, cells, cells, 3), dtype=torch.uint8, device=dev)
+            ms_fill = timed(lambda: lsb.fill_sparse(s, region, res=cells, height=h, rgb=c, stream=stream), reps)
+            im = lsb.fill_interp(s, region, res=pres, pad_cm=16000, maps=("nn_height", "lin_height"), stream=stream)
+            ms_interp = timed(lambda: lsb.fill_interp(s, region, res=pres, pad_cm=16000, out=im,
+                                                      maps=("nn_height", "lin_height"), stream=stream), reps)
+        torch.cuda.synchronize()
+        assert lsb.last_error() == 0
+        b = bins[0]
+        cnt = b["count"].to(torch.float64)
+        m = cnt > 0
+        th = b["zsum"].to(torch.float64) / cnt.clamp(min=1) * region.z_scale + region.z_offset
+        rm = lambda x: float(torch.sqrt(((x.to(torch.float64) - th)[m] ** 2).mean()))  # noqa: E731
+        crop = lambda x: x[:, a:a + cells, a:a + cells]  # noqa: E731
+        rows.append({"texel_m": texel_cm / 100, "texels_per_tile": cells * cells,
+                     "bin_ms": round(ms_bin, 3), "bin_points_per_s": round(n_points / (ms_bin * 1e-3), 1),
+                     "gaussian_fill_ms": round(ms_fill, 3), "gaussian_fill_tiles_per_s": round(nT / (ms_fill * 1e-3), 1),
+                     "interp_ms": round(ms_interp, 3), "interp_patches_per_s": round(nT / (ms_interp * 1e-3), 1),
+                     "truth_texels_with_points": round(float(m.to(torch.float32).mean()), 4),
+                     "height_rmse_m": {"gaussian": round(rm(h), 4), "nn": round(rm(crop(im["nn_height"])), 4),
+                                       "linear": round(rm(crop(im["lin_height"])), 4)}})
+        del bins, b, h, c, im, cnt, th, m
+        torch.cuda.empty_cache()
+    return {"workload": f"20x20 tiles at 4 pts/m^2 ({n_points} points, {int(s['x'].numel())} chunk samples), "
+                        "all tiles; patches of the Alg. 1 maps = tile + 160 m",
+            "rows": rows}
 
 
 def run_e2e(lsb, region, counts, pts, step, stream, steps, world):

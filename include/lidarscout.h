@@ -85,7 +85,8 @@ typedef struct {
 
 /* Gaussian-fill parameters (radius 120 m, sigma 40 m in the reference workload). */
 typedef struct {
-  int32_t res;       /* texels per tile side, tile_cm divisible by it, 8..256   */
+  int32_t res;       /* texels per tile side, tile_cm divisible by it, 8..1024
+                        (multiple of 8)                                          */
   int32_t radius_cm; /* splat radius R, 1..tile_cm (inclusive d <= R)          */
   float sigma_cm;    /* Gaussian sigma, > 0                                      */
 } ls_fill_params;
@@ -221,7 +222,7 @@ ls_status ls_update_tile(const ls_bins *bins, const ls_region *region, const int
  *   clockwise global sample indices; -1 - c for window corner c, c = 0..3 at
  *   (0, 0), (W, 0), (W, W), (0, W)), tri_count int32[n_out]: the number of triangles
  *   (corner triangles included), -1 for a patch not triangulated.
- * Limits: res a multiple of 8 in [8, 128]; 0 <= pad_cm <= tile_cm; W divisible by
+ * Limits: res a multiple of 8 in [8, 1024]; 0 <= pad_cm <= tile_cm; W divisible by
  *   res and at most 131072 cm (INVALID_ARG / UNSUPPORTED otherwise); |z| < 2^28 (a
  *   patch with a larger |z| gets LS_ERR_UNSUPPORTED in the sticky status, tri_count
  *   -1 and lin = nn); at most 1536 samples per window (more: LS_ERR_OUT_OF_RANGE in

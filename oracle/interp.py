@@ -109,8 +109,10 @@ def interp_tile(samples, region, t, res=96, pad_cm=16000):
     # nearest point (exact int64 squared distance; ties to the lowest sample index)
     if len(sel):
         P = np.array(pts, dtype=np.int64)
-        d2 = (GX[..., None] - P[:, 0]) ** 2 + (GY[..., None] - P[:, 1]) ** 2
-        k = np.argmin(d2, axis=-1)  # first minimum = lowest index (sel is increasing)
+        k = np.empty((res, res), dtype=np.int64)
+        for i in range(res):  # one texel row at a time (memory res x n at any res)
+            d2 = (gx[:, None] - P[:, 0]) ** 2 + (gx[i] - P[:, 1]) ** 2
+            k[i] = np.argmin(d2, axis=-1)  # first minimum = lowest index (sel is increasing)
         out["nn_height"] = z[k] * region.z_scale + region.z_offset
         out["nn_rgb8"] = rgb[k] / 256.0
         out["lin_height"] = out["nn_height"].copy()

@@ -499,7 +499,7 @@ ls_status fill_launch(const ls_points* samples, const ls_region* region, const l
     return LS_ERR_INVALID_ARG;
   const int64_t T = (int64_t)region->tiles_x * region->tiles_y;
   if (!tile_ids && n_out != T) return LS_ERR_INVALID_ARG;
-  if (params->res < 8 || params->res > 256 || params->res % 8 || region->tile_cm % params->res)
+  if (params->res < 8 || params->res > 1024 || params->res % 8 || region->tile_cm % params->res)
     return LS_ERR_INVALID_ARG;
   if (params->radius_cm < 1 || params->radius_cm > region->tile_cm) return LS_ERR_UNSUPPORTED;
   if (!(params->sigma_cm > 0.f)) return LS_ERR_INVALID_ARG;

@@ -27,7 +27,8 @@
 namespace ls {
 namespace {
 
-constexpr int kInterpMaxRes = 128;
+constexpr int kInterpMaxRes = 1024;
+constexpr int kInterpHintRes = 128;  // up to this resolution walks start from the block above
 constexpr int kInterpSmallCap = 96;     // window samples per patch, small tier
 constexpr int kInterpSmallWarps = 4;    // patches (warps) per CTA, small tier
 constexpr int kInterpBigCap = 1536;     // big tier: one warp per CTA
@@ -54,7 +55,7 @@ struct InterpWarp {
   int32_t gidx[CAP];     // global sample index
   uint16_t list[NT];     // cavity triangles; later the NN candidates of a block
   __align__(16) uint8_t bytes[224];  // one texel block's colours (NN, lin) and flags
-  uint16_t hints[kInterpMaxRes / 8][32];  // per block column and lane: the last triangle
+  uint16_t hints[kInterpHintRes / 8][32];  // per block column and lane: the last triangle
 };
 
 struct InterpArgs {
@@ -351,10 +352,12 @@ __device__ void texel_maps(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o, i
   int hint = 0;
   // blocks row by row (whole 32-byte sectors of every output row are written by
   // consecutive blocks); a lane's walk starts from the triangle it found in the block
-  // above (4 texels up), in the first block row from the block to the left
+  // above (4 texels up), in the first block row and above 128 texels per side from
+  // the block to the left
   for (int blk = 0; blk < nblk; ++blk) {
     const int bj = (blk % bxn) * 8, bi = (blk / bxn) * 4;
-    if (bi > 0) hint = s.hints[bj >> 3][lane];
+    const bool keep_hint = res <= kInterpHintRes;
+    if (bi > 0 && keep_hint) hint = s.hints[bj >> 3][lane];
     const int jj = bj + (lane & 7), ii = bi + (lane >> 3);
     const int gxa = cell * bj + h, gxb = gxa + 7 * cell, gya = cell * bi + h, gyb = gya + 3 * cell;
     long long U = LLONG_MAX;
@@ -403,7 +406,7 @@ __device__ void texel_maps(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o, i
       int t = locate(s, g, hint, T, w);
       if (t >= 0) {
         hint = t;
-        s.hints[bj >> 3][lane] = (uint16_t)t;
+        if (keep_hint) s.hints[bj >> 3][lane] = (uint16_t)t;
         if (!real_tri(s.tv[t])) {
           t = (w[0] == 0 || w[1] == 0 || w[2] == 0) ? real_neighbour(s, t, w, T) : -1;
           if (t >= 0) {

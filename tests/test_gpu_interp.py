@@ -33,18 +33,18 @@ def _round8(x):
     return np.minimum(np.floor(x + 0.5), 255).astype(np.uint8)
 
 
-def run_gpu(lsb, samples, region, tile_ids=None, tri_cap=4096):
+def run_gpu(lsb, samples, region, tile_ids=None, tri_cap=4096, res=RES):
     import torch
     d = to_device(samples)
     tid = None if tile_ids is None else torch.as_tensor(np.asarray(tile_ids, np.int32))
-    out = lsb.fill_interp(d, region, tile_ids=tid, res=RES, pad_cm=PAD, tri_cap=tri_cap)
+    out = lsb.fill_interp(d, region, tile_ids=tid, res=res, pad_cm=PAD, tri_cap=tri_cap)
     torch.cuda.synchronize()
     st = lsb.last_error()
     return {k: v.cpu().numpy() for k, v in out.items()}, st
 
 
-def check_patch(got, o, samples, region, t, msg=""):
-    ref = oi.interp_tile(samples, region, t, res=RES, pad_cm=PAD)
+def check_patch(got, o, samples, region, t, msg="", res=RES):
+    ref = oi.interp_tile(samples, region, t, res=res, pad_cm=PAD)
     # triangulation: the same set of counter-clockwise triangles
     cnt = int(got["tri_count"][o])
     assert cnt == len(ref["triangles"]), f"{msg} triangle count {cnt} vs {len(ref['triangles'])}"
