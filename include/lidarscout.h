@@ -250,6 +250,71 @@ ls_status ls_fill_interp(const ls_points *samples, const ls_region *region,
                          const ls_interp_outputs *out, ls_stream_t stream);
 
 /* ---------------------------------------------------------------------------------
+ * Software rasterizers into a headless framebuffer (Sec. 3.5, rendering): points
+ * with a 64-bit depth|colour atomicMin per pixel, heightmaps as triangle meshes with
+ * the same per-fragment atomicMin, and a resolve pass that extracts the colours into
+ * an RGBA8 image (the paper resolves into an OpenGL texture; here a device buffer).
+ *
+ * Framebuffer: uint64[height][width], row 0 at the bottom (screen y upwards).  A word
+ * is (float bits of the depth d in [0, 1]) << 32 | R | G << 8 | B << 16 | 255 << 24;
+ * ls_render_clear sets every word to UINT64_MAX (empty).  The smallest word wins: the
+ * nearest fragment, equal depths the smaller colour word.  The result does not
+ * depend on the order of the fragments (bit-exact).
+ *
+ * Vertex arithmetic, float32 with one IEEE rounding per operation and no fused
+ * operations, in this order:
+ *  - camera frame (cm): q = ((float)(x - ox), (float)(y - oy), (float)(z - oz)) for a
+ *    point with LAS integers x, y, z (int64 differences); for heightmap texel (i, j)
+ *    of tile t with height h (metres): x = x0_cm + tx * tile_cm + cell * j + cell / 2
+ *    and y likewise (integers, cell = tile_cm / res), q.z = ((h - (float)z_offset) *
+ *    (float)(1 / z_scale)) - (float)oz; a NaN height drops the texel's triangles;
+ *  - clip c_r = ((M[r][0] q.x + M[r][1] q.y) + M[r][2] q.z) + M[r][3], M row-major;
+ *  - visible iff c_w > 0; ndc = c_xyz / c_w; screen sx = (ndc_x * 0.5 + 0.5) * width,
+ *    sy = (ndc_y * 0.5 + 0.5) * height; depth d = ndc_z * 0.5 + 0.5, kept iff
+ *    0 <= d <= 1;
+ *  - colours: 16-bit point colours round half up to 8 bits; heightmap colours as given.
+ * Points: the pixel (floor(sx), floor(sy)) if inside the framebuffer.
+ * Heightmap triangles: each quad of adjacent texel centres (i, j), (i, j + 1),
+ *   (i + 1, j + 1), (i + 1, j) gives the triangles (v00, v01, v11) and (v00, v11, v10);
+ *   a triangle is drawn when its three vertices are kept.  With A = (x1 - x0)(y2 - y0)
+ *   - (y1 - y0)(x2 - x0) (A = 0: nothing) and the pixel centre p = (ix + 0.5, iy + 0.5):
+ *   e0 = (x2 - x1)(py - y1) - (y2 - y1)(px - x1), e1 = (x0 - x2)(py - y2) - (y0 - y2)(px - x2),
+ *   e2 = (x1 - x0)(py - y0) - (y1 - y0)(px - x0), all negated with A when A < 0; the
+ *   pixel is covered iff e0, e1, e2 >= 0 (pixels with floor(min x) <= ix <= floor(max x),
+ *   likewise for y, inside the framebuffer, are tested).  l_k = e_k / A; depth
+ *   (l0 d0 + l1 d1) + l2 d2; colour channel floor(((l0 c0 + l1 c1) + l2 c2) + 0.5)
+ *   clamped to [0, 255].
+ * ------------------------------------------------------------------------------- */
+typedef struct {
+  int64_t origin_cm[3];  /* camera-frame origin in LAS centimetres                  */
+  float view_proj[16];   /* row-major 4x4: camera frame (cm) to clip space           */
+  int32_t width, height; /* framebuffer size in pixels, 1..16384                      */
+} ls_camera;
+
+/* Every framebuffer word to UINT64_MAX. */
+ls_status ls_render_clear(uint64_t *fb, int32_t width, int32_t height, ls_stream_t stream);
+
+/* Points (e.g. the chunk samples or full-resolution points): pts->tile_offsets is
+ * ignored.  fb: uint64[camera->height][camera->width] (device, 8-byte aligned). */
+ls_status ls_render_points(const ls_points *pts, const ls_camera *camera, uint64_t *fb,
+                           ls_stream_t stream);
+
+/* Heightmaps: height float[n][res][res] (metres, NaN = no data) and rgb
+ * uint8[n][res][res][3] of the tiles tile_ids[n] (device int32, or NULL for 0..n-1) of
+ * the region; res in [2, 1024] dividing tile_cm.  Triangles covering more than 1024
+ * candidate pixels are drawn by a whole CTA from a shared queue, the others by one
+ * thread each. */
+ls_status ls_render_heightmaps(const float *height, const uint8_t *rgb, const int32_t *tile_ids,
+                               int64_t n, int32_t res, const ls_region *region,
+                               const ls_camera *camera, uint64_t *fb, ls_stream_t stream);
+
+/* RGBA8 image uint8[height][width][4] (device, 4-byte aligned) from the framebuffer:
+ * the colour word of covered pixels, background (R | G << 8 | B << 16 | A << 24)
+ * elsewhere. */
+ls_status ls_render_resolve(const uint64_t *fb, int32_t width, int32_t height, uint32_t background,
+                            uint8_t *rgba, ls_stream_t stream);
+
+/* ---------------------------------------------------------------------------------
  * Tensor-core 3x3 convolution of the learned filler (Sec. 3.4: a U-Net-inspired CNN
  * refines the heightmaps).  Stride 1, zero padding 1, NHWC BF16 activations, FP32
  * accumulation (tcgen05 kind::f16, M = 128 pixels, N = c_out, K = 9 * c_in).

@@ -8,6 +8,8 @@ may import this package.  The product path (paper_2509_20198_b300) never does.
 * unet.py: FP64 numpy U-Net forward/backward, loss, AdamW, learned-input raster.
 * interp.py: the interpolated heightmaps of Alg. 1 (nearest-neighbour and
   Delaunay-linear maps of a padded patch), exact integer predicates in Python.
+* render.py: the point and heightmap rasterizers into a 64-bit depth|colour
+  framebuffer and the resolve (numpy float32, one rounding per operation).
 
 Parity status of each function (what pins it) is listed in the tests under
 tests/test_oracle_*.py.
