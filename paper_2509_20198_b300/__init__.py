@@ -18,7 +18,8 @@ import torch
 from . import _native as N
 
 __all__ = ["bin_points", "bin_stats", "extract_samples", "extract_samples_into", "fill_sparse", "fill_interp",
-           "update_tile", "last_error",
+           "update_tile", "render_framebuffer", "render_clear", "render_points", "render_heightmaps",
+           "render_resolve", "last_error",
            "release_workspace", "empty_bins", "BIN_KEYS", "Filler", "FillerFn", "filler_loss", "adamw_step",
            "learned_inputs", "learned_targets", "learned_finish", "fill_learned"]
 
@@ -200,6 +201,58 @@ def fill_interp(samples, region, tile_ids=None, res=96, pad_cm=16000, maps=INTER
     N.check("ls_fill_interp", N.lib().ls_fill_interp(ctypes.byref(pts), ctypes.byref(reg), ctypes.byref(prm),
                                                     _ptr(tile_ids), n, ctypes.byref(o), _stream(stream)))
     return res_maps
+
+
+def _camera(cam):
+    """ls_camera from a dict with origin_cm (3 ints), view_proj (16 floats, row-major),
+    width and height."""
+    return N.LsCamera((N.I64 * 3)(*[int(v) for v in cam["origin_cm"]]),
+                      (N.FLT * 16)(*[float(v) for v in cam["view_proj"]]), int(cam["width"]), int(cam["height"]))
+
+
+def render_framebuffer(cam, device="cuda"):
+    """An empty framebuffer (uint64 words stored in an int64 tensor [height, width])."""
+    fb = torch.empty((int(cam["height"]), int(cam["width"])), dtype=torch.int64, device=device)
+    return render_clear(fb)
+
+
+def render_clear(fb, stream=None):
+    N.check("ls_render_clear", N.lib().ls_render_clear(_ptr(_dev(fb, "fb")), fb.shape[1], fb.shape[0],
+                                                      _stream(stream)))
+    return fb
+
+
+def render_points(points, cam, fb, stream=None):
+    """Draw points (dict of x, y, z, r, g, b tensors) into the framebuffer."""
+    pts = _points(points)
+    c = _camera(cam)
+    N.check("ls_render_points", N.lib().ls_render_points(ctypes.byref(pts), ctypes.byref(c),
+                                                        _ptr(_dev(fb, "fb")), _stream(stream)))
+    return fb
+
+
+def render_heightmaps(height, rgb, region, cam, fb, tile_ids=None, stream=None):
+    """Draw heightmaps (height float32 [n, res, res] metres, rgb uint8 [n, res, res, 3])
+    of the tiles tile_ids (default 0..n-1) as triangle meshes."""
+    n, res = height.shape[0], height.shape[1]
+    if tile_ids is not None:
+        tile_ids = _dev(tile_ids.to(device=height.device, dtype=torch.int32).contiguous(), "tile_ids")
+    c = _camera(cam)
+    reg = _region(region)
+    N.check("ls_render_heightmaps", N.lib().ls_render_heightmaps(
+        _ptr(_dev(height, "height")), _ptr(_dev(rgb, "rgb")), _ptr(tile_ids), n, res, ctypes.byref(reg),
+        ctypes.byref(c), _ptr(_dev(fb, "fb")), _stream(stream)))
+    return fb
+
+
+def render_resolve(fb, background=0, out=None, stream=None):
+    """RGBA8 image uint8 [height, width, 4] of the framebuffer."""
+    H, W = fb.shape
+    if out is None:
+        out = torch.empty((H, W, 4), dtype=torch.uint8, device=fb.device)
+    N.check("ls_render_resolve", N.lib().ls_render_resolve(_ptr(_dev(fb, "fb")), W, H, int(background),
+                                                          _ptr(_dev(out, "rgba")), _stream(stream)))
+    return out
 
 
 def update_tile(bins, region, tile_ids, height, rgb, stream=None):

@@ -43,6 +43,10 @@ class LsInterpOutputs(ctypes.Structure):
                 ("triangles", VP), ("tri_count", VP), ("tri_cap", I32)]
 
 
+class LsCamera(ctypes.Structure):
+    _fields_ = [("origin_cm", I64 * 3), ("view_proj", FLT * 16), ("width", I32), ("height", I32)]
+
+
 class LsConvShape(ctypes.Structure):
     _fields_ = [("n", I32), ("h", I32), ("w", I32), ("cin", I32), ("cout", I32)]
 
@@ -60,6 +64,10 @@ SIGNATURES = {
     "ls_fill_sparse": ([P(LsPoints), P(LsRegion), P(LsFillParams), VP, I64, VP, VP, VP], I32),
     "ls_update_tile": ([P(LsBins), P(LsRegion), VP, I64, VP, VP, VP], I32),
     "ls_fill_interp": ([P(LsPoints), P(LsRegion), P(LsInterpParams), VP, I64, P(LsInterpOutputs), VP], I32),
+    "ls_render_clear": ([VP, I32, I32, VP], I32),
+    "ls_render_points": ([P(LsPoints), P(LsCamera), VP, VP], I32),
+    "ls_render_heightmaps": ([VP, VP, VP, I64, I32, P(LsRegion), P(LsCamera), VP, VP], I32),
+    "ls_render_resolve": ([VP, I32, I32, ctypes.c_uint32, VP, VP], I32),
     "ls_conv3x3_packed_elems": ([I32, I32], I64),
     "ls_conv3x3_pack": ([VP, I32, I32, I32, VP, VP], I32),
     "ls_conv3x3_forward": ([VP, VP, VP, VP, I32, P(LsConvShape), VP, VP], I32),

@@ -4,6 +4,7 @@
 #include "ls_bin.cu"
 #include "ls_fill.cu"
 #include "ls_interp.cu"
+#include "ls_render.cu"
 #include "ls_conv.cu"
 #include "ls_wgrad.cu"
 #include "ls_unet.cu"
