@@ -254,6 +254,7 @@ def run_b300(args, rank, world):
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline(pts, counts, region, budget_s=args.cpu_seconds)
     if args.overview:
+        out["render_points"] = run_render_points(lsb, region, pts, stream, args.steps, hbm, peak_kind)
         del pts, step, graph
         torch.cuda.empty_cache()
         out["overview"] = run_overview(lsb, args, dev, stream)
@@ -294,6 +295,27 @@ def run_overview(lsb, args, dev, stream):
 
     with torch.cuda.stream(stream):
         ms_gauss = timed(lambda: lsb.fill_sparse(s, region, height=h, rgb=c, stream=stream), args.steps)
+    # the viewer's frame: every tile's Gaussian-fill heightmap as a mesh plus the chunk
+    # samples, 1080p, oblique view of the whole region
+    cam = region_camera(region)
+    with torch.cuda.stream(stream):
+        fb = lsb.render_framebuffer(cam)
+        img = lsb.render_resolve(fb, stream=stream)
+
+        def frame():
+            lsb.render_clear(fb, stream=stream)
+            lsb.render_heightmaps(h, c, region, cam, fb, stream=stream)
+            lsb.render_points(s, cam, fb, stream=stream)
+            lsb.render_resolve(fb, out=img, stream=stream)
+        ms_frame = timed(frame, args.steps)
+        ms_mesh = timed(lambda: lsb.render_heightmaps(h, c, region, cam, fb, stream=stream), args.steps)
+    assert lsb.last_error() == 0
+    render = {"frame_ms": round(ms_frame, 3), "heightmaps_ms": round(ms_mesh, 3),
+              "triangles": nT * 63 * 63 * 2,
+              "triangles_per_s": round(nT * 63 * 63 * 2 / (ms_mesh * 1e-3), 1),
+              "covered_pixels": round(float((fb != -1).to(torch.float32).mean()), 4),
+              "view": "1920x1080, oblique view of the whole region; 40,000 heightmaps of 64x64 + 1.32M samples"}
+    del fb, img
     # Alg. 1 maps (nearest-neighbour and Delaunay-linear) on the 96 x 96 padded patches
     with torch.cuda.stream(stream):
         im = lsb.fill_interp(s, region, res=96, pad_cm=16000, stream=stream)
@@ -351,6 +373,7 @@ def run_overview(lsb, args, dev, stream):
     return {"workload": "overview 200x200 tiles, 4 pts/m^2, 33 samples/tile (1.32M samples)",
             "gaussian_fill": {"tiles_per_s": round(nT / (ms_gauss * 1e-3), 1), "ms": round(ms_gauss, 3),
                               "height_rmse_m": round(rm(h[sub_t]), 4), "rgb_rmse_8bit": round(rc(c[sub_t]), 3)},
+            "render": render,
             "interp_fill": {"tiles_per_s": round(nT / (ms_interp * 1e-3), 1), "ms": round(ms_interp, 3),
                             "patch": "96x96 texels of 10 m (tile + 160 m padding), Alg. 1",
                             "nn_height_rmse_m": round(rm(crop(im["nn_height"])), 4),
@@ -378,6 +401,74 @@ def run_overview(lsb, args, dev, stream):
                          "loss_first": [round(v, 7) for v in hist[0]],
                          "loss_last": [round(v, 7) for v in hist[-1]], "loss_parts": "total, height, colour, bound"},
             "truth": "per-texel mean of the full-resolution points, 400 seeded tiles"}
+
+
+def look_at(eye, target, fovy_deg, aspect, near=100.0, far=1e8):
+    """OpenGL-style view-projection (row-major float32 list) for a camera at `eye`
+    looking at `target` (cm, camera frame), z up."""
+    eye, target = np.asarray(eye, np.float64), np.asarray(target, np.float64)
+    f = (target - eye) / np.linalg.norm(target - eye)
+    sd = np.cross(f, (0.0, 0.0, 1.0))
+    sd /= np.linalg.norm(sd)
+    u = np.cross(sd, f)
+    V = np.eye(4)
+    V[0, :3], V[1, :3], V[2, :3] = sd, u, -f
+    V[:3, 3] = -V[:3, :3] @ eye
+    t = 1.0 / np.tan(np.radians(fovy_deg) / 2)
+    P = np.zeros((4, 4))
+    P[0, 0], P[1, 1] = t / aspect, t
+    P[2, 2], P[2, 3] = (far + near) / (near - far), 2 * far * near / (near - far)
+    P[3, 2] = -1.0
+    return (P @ V).astype(np.float32).ravel().tolist()
+
+
+def region_camera(region, width=1920, height=1080):
+    """Oblique view of the whole region from beyond its south-west corner."""
+    ext_x, ext_y = region.tiles_x * region.tile_cm, region.tiles_y * region.tile_cm
+    eye = (-0.35 * ext_x, -0.45 * ext_y, 0.6 * max(ext_x, ext_y))
+    target = (0.5 * ext_x, 0.5 * ext_y, 40000.0)
+    return {"origin_cm": (region.x0_cm, region.y0_cm, 0), "width": width, "height": height,
+            "view_proj": look_at(eye, target, 55.0, width / height)}
+
+
+def _timed(fn, reps, stream):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_render_points(lsb, region, pts, stream, steps, hbm, peak_kind):
+    """The point rasterizer on every full-resolution point of the region, 1080p:
+    clear, points, resolve per frame.  The points (18 B each) are read once per frame."""
+    import torch
+    cam = region_camera(region)
+    with torch.cuda.stream(stream):
+        fb = lsb.render_framebuffer(cam)
+        img = lsb.render_resolve(fb, stream=stream)
+
+        def frame():
+            lsb.render_clear(fb, stream=stream)
+            lsb.render_points(pts, cam, fb, stream=stream)
+            lsb.render_resolve(fb, out=img, stream=stream)
+        ms = _timed(frame, steps, stream)
+        ms_pts = _timed(lambda: lsb.render_points(pts, cam, fb, stream=stream), steps, stream)
+    assert lsb.last_error() == 0
+    n = int(pts["x"].numel())
+    covered = float((fb != -1).to(torch.float32).mean())
+    achieved = 18 * n / (ms_pts * 1e-3) / 1e9
+    return {"workload": f"{n} full-resolution points, 1920x1080, oblique view of the region",
+            "frame_ms": round(ms, 3), "points_ms": round(ms_pts, 3),
+            "points_per_s": round(n / (ms_pts * 1e-3), 1), "covered_pixels": round(covered, 4),
+            "roofline": {"bound": "hbm", "kernel": "k_points", "achieved": round(achieved, 1), "peak": hbm,
+                         "unit": "GB/s", "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
+                         "algorithmic_bytes": 18 * n}}
 
 
 def run_resolutions(lsb, args, dev, stream):
@@ -626,6 +717,38 @@ def run_interp_case(args):
     return 0 if st == 0 else 1
 
 
+def run_render_case(args):
+    """Profiling case for the rasterizers: the full-resolution points of a k x k-tile
+    lognormal region and the Gaussian-fill heightmaps (64 x 64) of a 4k x 4k-tile overview
+    region, one 1080p frame each."""
+    import torch
+    import paper_2509_20198_b300 as lsb
+    import synth
+    import synth.gpu as sg
+    from paper_2509_20198_b300 import build
+    build.build_library()
+    build.build_synth()
+    k = args.case_tiles
+    region = synth.Region(tiles_x=k, tiles_y=k)
+    pts = sg.region_points(SEED, region, synth.lognormal_counts(SEED, k * k))
+    cam = region_camera(region)
+    fb = lsb.render_framebuffer(cam)
+    for _ in range(args.steps):
+        lsb.render_points(pts, cam, fb)
+    del pts
+    oreg, ocounts = synth.overview_workload(tiles=4 * k)
+    s = sg.region_samples(3, oreg, ocounts)
+    h, c = lsb.fill_sparse(s, oreg)
+    ocam = region_camera(oreg)
+    ofb = lsb.render_framebuffer(ocam)
+    for _ in range(args.steps):
+        lsb.render_heightmaps(h, c, oreg, ocam, ofb)
+    torch.cuda.synchronize()
+    st = lsb.last_error()
+    print(json.dumps({"case": "render", "points_tiles": k * k, "heightmaps": oreg.n_tiles, "status": st}))
+    return 0 if st == 0 else 1
+
+
 def run_learned_case(args):
     """Profiling case for the learned filler: one forward pass and one training step
     (forward, loss, backward, AdamW) of the U-Net on a batch of random bf16 inputs, with
@@ -666,7 +789,7 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--overview", type=int, default=1, help="also time the 40,000-tile overview fills")
-    ap.add_argument("--case", default="", choices=["", "bin-small", "learned", "fill", "interp"],
+    ap.add_argument("--case", default="", choices=["", "bin-small", "learned", "fill", "interp", "render"],
                     help="profiling case instead of the bench")
     ap.add_argument("--case-tiles", type=int, default=3, help="tiles per side of the profiling case")
     ap.add_argument("--train-tiles", type=int, default=4096)
@@ -680,6 +803,8 @@ def main():
         sys.exit(run_fill_case(args))
     if args.case == "interp":
         sys.exit(run_interp_case(args))
+    if args.case == "render":
+        sys.exit(run_render_case(args))
     if args.case:
         sys.exit(run_profile_case(args))
     if args.impl == "reference":

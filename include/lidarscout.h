@@ -269,7 +269,8 @@ ls_status ls_fill_interp(const ls_points *samples, const ls_region *region,
  *    and y likewise (integers, cell = tile_cm / res), q.z = ((h - (float)z_offset) *
  *    (float)(1 / z_scale)) - (float)oz; a NaN height drops the texel's triangles;
  *  - clip c_r = ((M[r][0] q.x + M[r][1] q.y) + M[r][2] q.z) + M[r][3], M row-major;
- *  - visible iff c_w > 0; ndc = c_xyz / c_w; screen sx = (ndc_x * 0.5 + 0.5) * width,
+ *  - visible iff c_w > 0; ndc = c_xyz * r with r = 1 / c_w (the correctly rounded
+ *    reciprocal); screen sx = (ndc_x * 0.5 + 0.5) * width,
  *    sy = (ndc_y * 0.5 + 0.5) * height; depth d = ndc_z * 0.5 + 0.5, kept iff
  *    0 <= d <= 1;
  *  - colours: 16-bit point colours round half up to 8 bits; heightmap colours as given.

@@ -44,9 +44,20 @@ __device__ __forceinline__ float f_div(float a, float b) {
   asm("div.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
   return r;
 }
-__device__ __forceinline__ float f_of(long long v) {
+__device__ __forceinline__ float f_rcp(float a) {
   float r;
-  asm("cvt.rn.f32.s64 %0, %1;" : "=f"(r) : "l"(v));
+  asm("rcp.rn.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+__device__ __forceinline__ float f_of(long long v) {
+  // the 32-bit conversion when the value fits (the same rounded value, a cheaper
+  // instruction than the 64-bit one)
+  float r;
+  if (v == (long long)(int)v) {
+    asm("cvt.rn.f32.s32 %0, %1;" : "=f"(r) : "r"((int)v));
+  } else {
+    asm("cvt.rn.f32.s64 %0, %1;" : "=f"(r) : "l"(v));
+  }
   return r;
 }
 __device__ __forceinline__ bool finite_f(float v) { return (__float_as_uint(v) & 0x7f800000u) != 0x7f800000u; }
@@ -63,7 +74,8 @@ struct Vtx {
 };
 
 // Camera frame (cm) to screen: clip rows ((M0 qx + M1 qy) + M2 qz) + M3, perspective
-// division, viewport; kept when c_w > 0 and 0 <= d <= 1.
+// division as products with the reciprocal of c_w, viewport; kept when c_w > 0 and
+// 0 <= d <= 1.
 __device__ __forceinline__ Vtx project(const Cam& c, float qx, float qy, float qz) {
   float cl[4];
 #pragma unroll
@@ -72,7 +84,8 @@ __device__ __forceinline__ Vtx project(const Cam& c, float qx, float qy, float q
                   c.M[4 * r + 3]);
   Vtx v;
   v.kept = cl[3] > 0.f;
-  const float nx = f_div(cl[0], cl[3]), ny = f_div(cl[1], cl[3]), nz = f_div(cl[2], cl[3]);
+  const float rw = f_rcp(cl[3]);
+  const float nx = f_mul(cl[0], rw), ny = f_mul(cl[1], rw), nz = f_mul(cl[2], rw);
   v.x = f_mul(f_add(f_mul(nx, 0.5f), 0.5f), (float)c.W);
   v.y = f_mul(f_add(f_mul(ny, 0.5f), 0.5f), (float)c.H);
   v.d = f_add(f_mul(nz, 0.5f), 0.5f);
