@@ -458,7 +458,15 @@ def run_render_points(lsb, region, pts, stream, steps, hbm, peak_kind):
             lsb.render_points(pts, cam, fb, stream=stream)
             lsb.render_resolve(fb, out=img, stream=stream)
         ms = _timed(frame, steps, stream)
-        ms_pts = _timed(lambda: lsb.render_points(pts, cam, fb, stream=stream), steps, stream)
+        # the point pass alone, each time into a cleared framebuffer (as in a frame)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
+        for k in range(steps):
+            lsb.render_clear(fb, stream=stream)
+            ev[2 * k].record(stream)
+            lsb.render_points(pts, cam, fb, stream=stream)
+            ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize()
+        ms_pts = float(np.mean([ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(steps)]))
     assert lsb.last_error() == 0
     n = int(pts["x"].numel())
     covered = float((fb != -1).to(torch.float32).mean())

@@ -296,7 +296,9 @@ typedef struct {
 ls_status ls_render_clear(uint64_t *fb, int32_t width, int32_t height, ls_stream_t stream);
 
 /* Points (e.g. the chunk samples or full-resolution points): pts->tile_offsets is
- * ignored.  fb: uint64[camera->height][camera->width] (device, 8-byte aligned). */
+ * ignored.  fb: uint64[camera->height][camera->width] (device, 8-byte aligned).  The
+ * origin must lie in the int32 range and every point within 2^31 - 1 cm of it on each
+ * axis (the differences are taken in 32 bits). */
 ls_status ls_render_points(const ls_points *pts, const ls_camera *camera, uint64_t *fb,
                            ls_stream_t stream);
 

@@ -4,9 +4,10 @@
 //
 // Design (B300):
 //  * points: grid-stride over the point arrays (coalesced 4- and 2-byte loads); a
-//    fragment reads the pixel's word first and issues the atomicMin only when it is
-//    smaller (words only decrease, so the skipped ones could never win).  A 1080p
-//    framebuffer (16.6 MB) stays in L2, where the atomics resolve;
+//    fragment reads the pixel's word first, loads its colour only when its depth is
+//    not behind that word, and issues the atomicMin only when its word is smaller
+//    (words only decrease, so the skipped ones could never win).  A 1080p framebuffer
+//    (16.6 MB) stays in L2, where the atomics resolve;
 //  * heightmaps: the mesh is implicit (two triangles per quad of adjacent texel
 //    centres), so there is no triangle list in memory.  Persistent CTAs of 128 threads
 //    take 128 quads at a time; a thread projects its quad's four vertices and draws
@@ -102,18 +103,38 @@ __device__ __forceinline__ void frag(unsigned long long* fb, size_t p, unsigned 
   if (w < *reinterpret_cast<volatile unsigned long long*>(fb + p)) atomicMin(fb + p, w);
 }
 
+// Points: every coordinate difference to the origin fits int32 (checked on the host
+// for the origin; a point farther than 2^31 - 1 cm on an axis is outside the camera's
+// range), so it is one 32-bit subtraction and conversion.  floor(s) in [0, W) is
+// tested as s in [0, W), which also rejects non-finite coordinates.
+template <typename Index>
 __global__ void __launch_bounds__(kRenderThreads) k_points(ls_points pts, Cam c, unsigned long long* fb) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < pts.n; i += stride) {
-    const float qx = f_of((long long)pts.x[i] - c.ox);
-    const float qy = f_of((long long)pts.y[i] - c.oy);
-    const float qz = f_of((long long)pts.z[i] - c.oz);
-    const Vtx v = project(c, qx, qy, qz);
-    if (!v.kept) continue;
-    const float fx = floorf(v.x), fy = floorf(v.y);
-    if (!(fx >= 0.f && fx < (float)c.W && fy >= 0.f && fy < (float)c.H)) continue;
+  const Index n = (Index)pts.n, stride = (Index)gridDim.x * blockDim.x;
+  const uint32_t ox = (uint32_t)c.ox, oy = (uint32_t)c.oy, oz = (uint32_t)c.oz;
+  const float W = (float)c.W, H = (float)c.H;
+  for (Index i = (Index)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float qx = (float)(int)((uint32_t)pts.x[i] - ox);
+    const float qy = (float)(int)((uint32_t)pts.y[i] - oy);
+    const float qz = (float)(int)((uint32_t)pts.z[i] - oz);
+    float cl[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      cl[r] = f_add(f_add(f_add(f_mul(c.M[4 * r], qx), f_mul(c.M[4 * r + 1], qy)), f_mul(c.M[4 * r + 2], qz)),
+                    c.M[4 * r + 3]);
+    const float rw = f_rcp(cl[3]);
+    const float sx = f_mul(f_add(f_mul(f_mul(cl[0], rw), 0.5f), 0.5f), W);
+    const float sy = f_mul(f_add(f_mul(f_mul(cl[1], rw), 0.5f), 0.5f), H);
+    const float d = f_add(f_mul(f_mul(cl[2], rw), 0.5f), 0.5f);
+    if (!(cl[3] > 0.f && d >= 0.f && d <= 1.f && sx >= 0.f && sx < W && sy >= 0.f && sy < H)) continue;
+    // depth first: a fragment strictly behind the pixel's current word cannot win (words
+    // only decrease), and then its colour is never loaded
+    const uint32_t p = (uint32_t)(int)sy * (uint32_t)c.W + (uint32_t)(int)sx;
+    const unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(fb + p);
+    const uint32_t dbits = __float_as_uint(d);
+    if (dbits > (uint32_t)(cur >> 32)) continue;
     const uint32_t col = to8(pts.r[i]) | (to8(pts.g[i]) << 8) | (to8(pts.b[i]) << 16) | (255u << 24);
-    frag(fb, (size_t)(int)fy * c.W + (int)fx, ((unsigned long long)__float_as_uint(v.d) << 32) | col);
+    const unsigned long long w = ((unsigned long long)dbits << 32) | col;
+    if (w < cur) atomicMin(fb + p, w);
   }
 }
 
@@ -302,8 +323,15 @@ extern "C" ls_status ls_render_points(const ls_points* pts, const ls_camera* cam
   if (reinterpret_cast<uintptr_t>(fb) & 7u) return LS_ERR_INVALID_ARG;
   if (pts->n == 0) return LS_OK;
   if (!pts->x || !pts->y || !pts->z || !pts->r || !pts->g || !pts->b) return LS_ERR_INVALID_ARG;
-  k_points<<<grid_cap((pts->n + kRenderThreads - 1) / kRenderThreads, kSmCount * 8), kRenderThreads, 0,
-             reinterpret_cast<cudaStream_t>(stream)>>>(*pts, c, reinterpret_cast<unsigned long long*>(fb));
+  for (int k = 0; k < 3; ++k)
+    if (camera->origin_cm[k] < INT32_MIN || camera->origin_cm[k] > INT32_MAX) return LS_ERR_INVALID_ARG;
+  const int grid = grid_cap((pts->n + kRenderThreads - 1) / kRenderThreads, kSmCount * 8);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned long long* f = reinterpret_cast<unsigned long long*>(fb);
+  if (pts->n < (int64_t(1) << 31) - (int64_t)grid * kRenderThreads)
+    k_points<int><<<grid, kRenderThreads, 0, s>>>(*pts, c, f);
+  else
+    k_points<long long><<<grid, kRenderThreads, 0, s>>>(*pts, c, f);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 
