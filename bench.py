@@ -474,7 +474,7 @@ def run_render_points(lsb, region, pts, stream, steps, hbm, peak_kind):
     return {"workload": f"{n} full-resolution points, 1920x1080, oblique view of the region",
             "frame_ms": round(ms, 3), "points_ms": round(ms_pts, 3),
             "points_per_s": round(n / (ms_pts * 1e-3), 1), "covered_pixels": round(covered, 4),
-            "roofline": {"bound": "hbm", "kernel": "k_points", "achieved": round(achieved, 1), "peak": hbm,
+            "roofline": {"bound": "hbm", "kernel": "k_render_points", "achieved": round(achieved, 1), "peak": hbm,
                          "unit": "GB/s", "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
                          "algorithmic_bytes": 18 * n}}
 

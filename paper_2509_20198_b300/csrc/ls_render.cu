@@ -103,38 +103,73 @@ __device__ __forceinline__ void frag(unsigned long long* fb, size_t p, unsigned 
   if (w < *reinterpret_cast<volatile unsigned long long*>(fb + p)) atomicMin(fb + p, w);
 }
 
-// Points: every coordinate difference to the origin fits int32 (checked on the host
+// Screen pixel and depth bits of a point with LAS integers (x, y, z); false when it is
+// not drawn.  Every coordinate difference to the origin fits int32 (checked on the host
 // for the origin; a point farther than 2^31 - 1 cm on an axis is outside the camera's
-// range), so it is one 32-bit subtraction and conversion.  floor(s) in [0, W) is
-// tested as s in [0, W), which also rejects non-finite coordinates.
-template <typename Index>
-__global__ void __launch_bounds__(kRenderThreads) k_points(ls_points pts, Cam c, unsigned long long* fb) {
-  const Index n = (Index)pts.n, stride = (Index)gridDim.x * blockDim.x;
-  const uint32_t ox = (uint32_t)c.ox, oy = (uint32_t)c.oy, oz = (uint32_t)c.oz;
-  const float W = (float)c.W, H = (float)c.H;
-  for (Index i = (Index)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const float qx = (float)(int)((uint32_t)pts.x[i] - ox);
-    const float qy = (float)(int)((uint32_t)pts.y[i] - oy);
-    const float qz = (float)(int)((uint32_t)pts.z[i] - oz);
-    float cl[4];
+// range), so it is one 32-bit subtraction and conversion.  floor(s) in [0, W) is tested
+// as s in [0, W), which also rejects non-finite coordinates.
+__device__ __forceinline__ bool point_pixel(const Cam& c, int x, int y, int z, uint32_t& p, uint32_t& dbits) {
+  const float qx = (float)(int)((uint32_t)x - (uint32_t)c.ox);
+  const float qy = (float)(int)((uint32_t)y - (uint32_t)c.oy);
+  const float qz = (float)(int)((uint32_t)z - (uint32_t)c.oz);
+  float cl[4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
-      cl[r] = f_add(f_add(f_add(f_mul(c.M[4 * r], qx), f_mul(c.M[4 * r + 1], qy)), f_mul(c.M[4 * r + 2], qz)),
-                    c.M[4 * r + 3]);
-    const float rw = f_rcp(cl[3]);
-    const float sx = f_mul(f_add(f_mul(f_mul(cl[0], rw), 0.5f), 0.5f), W);
-    const float sy = f_mul(f_add(f_mul(f_mul(cl[1], rw), 0.5f), 0.5f), H);
-    const float d = f_add(f_mul(f_mul(cl[2], rw), 0.5f), 0.5f);
-    if (!(cl[3] > 0.f && d >= 0.f && d <= 1.f && sx >= 0.f && sx < W && sy >= 0.f && sy < H)) continue;
-    // depth first: a fragment strictly behind the pixel's current word cannot win (words
-    // only decrease), and then its colour is never loaded
-    const uint32_t p = (uint32_t)(int)sy * (uint32_t)c.W + (uint32_t)(int)sx;
-    const unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(fb + p);
-    const uint32_t dbits = __float_as_uint(d);
-    if (dbits > (uint32_t)(cur >> 32)) continue;
-    const uint32_t col = to8(pts.r[i]) | (to8(pts.g[i]) << 8) | (to8(pts.b[i]) << 16) | (255u << 24);
-    const unsigned long long w = ((unsigned long long)dbits << 32) | col;
-    if (w < cur) atomicMin(fb + p, w);
+  for (int r = 0; r < 4; ++r)
+    cl[r] = f_add(f_add(f_add(f_mul(c.M[4 * r], qx), f_mul(c.M[4 * r + 1], qy)), f_mul(c.M[4 * r + 2], qz)),
+                  c.M[4 * r + 3]);
+  const float rw = f_rcp(cl[3]);
+  const float W = (float)c.W, H = (float)c.H;
+  const float sx = f_mul(f_add(f_mul(f_mul(cl[0], rw), 0.5f), 0.5f), W);
+  const float sy = f_mul(f_add(f_mul(f_mul(cl[1], rw), 0.5f), 0.5f), H);
+  const float d = f_add(f_mul(f_mul(cl[2], rw), 0.5f), 0.5f);
+  p = (uint32_t)(int)fmaxf(0.f, fminf(sy, H - 1.f)) * (uint32_t)c.W + (uint32_t)(int)fmaxf(0.f, fminf(sx, W - 1.f));
+  dbits = __float_as_uint(d);
+  return cl[3] > 0.f && d >= 0.f && d <= 1.f && sx >= 0.f && sx < W && sy >= 0.f && sy < H;
+}
+
+// The fragment of point i after its pixel's word `cur` was read: a fragment strictly
+// behind that word cannot win (words only decrease) and never loads its colour.
+template <typename Index>
+__device__ __forceinline__ void point_fragment(const ls_points& pts, unsigned long long* fb, Index i, uint32_t p,
+                                               uint32_t dbits, unsigned long long cur) {
+  if (dbits > (uint32_t)(cur >> 32)) return;
+  const uint32_t col = to8(pts.r[i]) | (to8(pts.g[i]) << 8) | (to8(pts.b[i]) << 16) | (255u << 24);
+  const unsigned long long w = ((unsigned long long)dbits << 32) | col;
+  if (w < cur) atomicMin(fb + p, w);
+}
+
+// Four consecutive points per thread: their coordinates come with one 16-byte load per
+// array (the arrays are 16-byte aligned: VEC), the four pixel reads are issued together,
+// then the fragments; the tail (and unaligned arrays) go point by point.
+template <typename Index, bool VEC>
+__global__ void __launch_bounds__(kRenderThreads) k_render_points(ls_points pts, Cam c, unsigned long long* fb) {
+  const Index n = (Index)pts.n, tid = (Index)blockIdx.x * blockDim.x + threadIdx.x;
+  const Index threads = (Index)gridDim.x * blockDim.x;
+  const volatile unsigned long long* vfb = fb;
+  Index done = 0;
+  if (VEC) {
+    const Index groups = n / 4;
+    for (Index g = tid; g < groups; g += threads) {
+      const int4 x = __ldcs(reinterpret_cast<const int4*>(pts.x) + g);
+      const int4 y = __ldcs(reinterpret_cast<const int4*>(pts.y) + g);
+      const int4 z = __ldcs(reinterpret_cast<const int4*>(pts.z) + g);
+      const int xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w}, zs[4] = {z.x, z.y, z.z, z.w};
+      uint32_t p[4], db[4];
+      bool on[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) on[k] = point_pixel(c, xs[k], ys[k], zs[k], p[k], db[k]);
+      unsigned long long cur[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cur[k] = on[k] ? vfb[p[k]] : 0ull;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (on[k]) point_fragment(pts, fb, 4 * g + k, p[k], db[k], cur[k]);
+    }
+    done = groups * 4;
+  }
+  for (Index i = done + tid; i < n; i += threads) {
+    uint32_t p, db;
+    if (point_pixel(c, pts.x[i], pts.y[i], pts.z[i], p, db)) point_fragment(pts, fb, i, p, db, vfb[p]);
   }
 }
 
@@ -244,7 +279,7 @@ __device__ __forceinline__ bool mesh_tri(const MeshArgs& a, int64_t q, int half,
   return ok;
 }
 
-__global__ void __launch_bounds__(kMeshThreads) k_mesh(MeshArgs a) {
+__global__ void __launch_bounds__(kMeshThreads) k_render_mesh(MeshArgs a) {
   __shared__ unsigned long long queue[2 * kMeshThreads];  // (quad << 1) | half
   __shared__ int qn;
   const int64_t total = a.quads;
@@ -285,7 +320,7 @@ __global__ void __launch_bounds__(kMeshThreads) k_mesh(MeshArgs a) {
   }
 }
 
-__global__ void k_resolve(const unsigned long long* __restrict__ fb, int64_t n, uint32_t background,
+__global__ void k_render_resolve(const unsigned long long* __restrict__ fb, int64_t n, uint32_t background,
                           uint32_t* __restrict__ rgba) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
     const unsigned long long w = fb[p];
@@ -325,13 +360,18 @@ extern "C" ls_status ls_render_points(const ls_points* pts, const ls_camera* cam
   if (!pts->x || !pts->y || !pts->z || !pts->r || !pts->g || !pts->b) return LS_ERR_INVALID_ARG;
   for (int k = 0; k < 3; ++k)
     if (camera->origin_cm[k] < INT32_MIN || camera->origin_cm[k] > INT32_MAX) return LS_ERR_INVALID_ARG;
-  const int grid = grid_cap((pts->n + kRenderThreads - 1) / kRenderThreads, kSmCount * 8);
+  const int grid = grid_cap((pts->n / 4 + kRenderThreads - 1) / kRenderThreads, kSmCount * 8);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   unsigned long long* f = reinterpret_cast<unsigned long long*>(fb);
-  if (pts->n < (int64_t(1) << 31) - (int64_t)grid * kRenderThreads)
-    k_points<int><<<grid, kRenderThreads, 0, s>>>(*pts, c, f);
-  else
-    k_points<long long><<<grid, kRenderThreads, 0, s>>>(*pts, c, f);
+  const bool vec = ((reinterpret_cast<uintptr_t>(pts->x) | reinterpret_cast<uintptr_t>(pts->y) |
+                     reinterpret_cast<uintptr_t>(pts->z)) & 15u) == 0;
+  if (pts->n < (int64_t(1) << 31) - (int64_t)grid * kRenderThreads * 4) {
+    if (vec) k_render_points<int, true><<<grid, kRenderThreads, 0, s>>>(*pts, c, f);
+    else k_render_points<int, false><<<grid, kRenderThreads, 0, s>>>(*pts, c, f);
+  } else {
+    if (vec) k_render_points<long long, true><<<grid, kRenderThreads, 0, s>>>(*pts, c, f);
+    else k_render_points<long long, false><<<grid, kRenderThreads, 0, s>>>(*pts, c, f);
+  }
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 
@@ -363,7 +403,7 @@ extern "C" ls_status ls_render_heightmaps(const float* height, const uint8_t* rg
   a.ozf = (float)camera->origin_cm[2];
   a.c = c;
   a.fb = reinterpret_cast<unsigned long long*>(fb);
-  k_mesh<<<grid_cap((a.quads + kMeshThreads - 1) / kMeshThreads, kSmCount * 12), kMeshThreads, 0,
+  k_render_mesh<<<grid_cap((a.quads + kMeshThreads - 1) / kMeshThreads, kSmCount * 12), kMeshThreads, 0,
            reinterpret_cast<cudaStream_t>(stream)>>>(a);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
@@ -373,7 +413,7 @@ extern "C" ls_status ls_render_resolve(const uint64_t* fb, int32_t width, int32_
   if (!fb || !rgba || width < 1 || height < 1 || width > 16384 || height > 16384) return LS_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(fb) & 7u) || (reinterpret_cast<uintptr_t>(rgba) & 3u)) return LS_ERR_INVALID_ARG;
   const int64_t n = (int64_t)width * height;
-  k_resolve<<<grid_cap((n + 255) / 256, kSmCount * 8), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+  k_render_resolve<<<grid_cap((n + 255) / 256, kSmCount * 8), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
       reinterpret_cast<const unsigned long long*>(fb), n, background, reinterpret_cast<uint32_t*>(rgba));
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }

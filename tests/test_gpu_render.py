@@ -165,3 +165,21 @@ def test_points_over_heightmaps_and_order_independence(lsb):
     ref = R.render_heightmaps(R.clear(200, 160), h.cpu().numpy(), c.cpu().numpy(), range(4), region, cam)
     ref = R.render_points(ref, s, cam)
     np.testing.assert_array_equal(as_u64(a), ref)
+
+
+def test_points_unaligned_arrays_and_tail(lsb):
+    """Arrays that are not 16-byte aligned (the point-by-point path) and a count that is
+    not a multiple of 4 (the tail of the vector path)."""
+    import torch
+    region = synth.Region(tiles_x=2, tiles_y=1)
+    pts = synth.region_points(5, region, np.array([30_001, 20_002], np.int64))
+    del pts["tile_offsets"]
+    cam = camera(region, (-100, -300, 700), (640, 320, 400), 160, 120)
+    d = to_device(pts)
+    ref = R.render_points(R.clear(160, 120), {k: v[1:] for k, v in pts.items()}, cam)
+    for sub in ({k: v[1:] for k, v in d.items()},                      # 4-byte aligned only
+                {k: v[1:].clone() for k, v in d.items()}):             # aligned, n % 4 == 2
+        fb = gpu_fb(lsb, cam)
+        lsb.render_points(sub, cam, fb)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(as_u64(fb), ref)
