@@ -10,6 +10,8 @@ may import this package.  The product path (paper_2509_20198_b300) never does.
   Delaunay-linear maps of a padded patch), exact integer predicates in Python.
 * render.py: the point and heightmap rasterizers into a 64-bit depth|colour
   framebuffer and the resolve (numpy float32, one rounding per operation).
+* cnn.py: FP64 forward/backward of the paper's own network variant (per-input
+  encoders, fully connected merge, two decoders, skip concat, final CNN, crop).
 
 Parity status of each function (what pins it) is listed in the tests under
 tests/test_oracle_*.py.
