@@ -250,6 +250,54 @@ ls_status ls_fill_interp(const ls_points *samples, const ls_region *region,
                          const ls_interp_outputs *out, ls_stream_t stream);
 
 /* ---------------------------------------------------------------------------------
+ * The paper's own network variant (Sec. 3.4): the linear and NN heightmaps and textures
+ * of Alg. 1 (ls_fill_interp) on a res x res patch, encoded independently by four
+ * encoders, merged by fully connected layers in two steps, decoded by separate height
+ * and texture CNNs, concatenated with the original inputs (the one skip connection),
+ * reduced by a final CNN to 5 outputs (height, R, G, B in patch space, and an error
+ * bound) and cropped to the centre res/2 x res/2.  The text fixes no layer sizes; the
+ * ones used (2,481,733 parameters at res 128, the paper's 2.5M):
+ *   encoder (per input: lin height, NN height, lin RGB, NN RGB): 3x3 conv + ReLU + 2x2
+ *     max pool with 16, 32, 64, 64 channels, then 3x3 conv + ReLU to 16 at res/16;
+ *   fc1 (per input): 16 (res/16)^2 -> 256 + ReLU; fc2: 1024 -> 16 (res/16)^2 + ReLU;
+ *   decoder (height, texture): 3x3 conv + ReLU with 64, 32, 32, 16 channels, each
+ *     followed by 2x nearest upsampling, then 3x3 conv + ReLU to 16 at res;
+ *   final: concat [input 8, height 16, texture 16], 3x3 conv + ReLU to 32 and to 16,
+ *     1x1 head to 5.
+ * Flat fp32 parameters in that layer order (ls_cnn_layer_info gives kind 0 = 3x3 conv
+ * [C_out][3][3][C_in], 1 = fully connected [out][in], 2 = 1x1 head [5][16], each weight
+ * block followed by its bias).  x: bf16 [n][res][res][8] (ls_cnn_inputs); y: fp32
+ * [n][res/2][res/2][5].  res is 32, 64 or 128; n (and max_batch) a multiple of
+ * 128 / (res/16)^2 (2 at res 128).  Every 3x3 convolution, forward and backward, runs on
+ * the tensor-core kernels (bf16 operands, fp32 accumulation); the fully connected
+ * layers in fp32.  ls_cnn_backward needs a model created with training != 0 and the
+ * activations of the last forward (same n).  Loss and optimiser: ls_filler_loss with a
+ * zero base, ls_adamw_step.
+ * ------------------------------------------------------------------------------- */
+typedef struct ls_cnn ls_cnn;
+
+ls_status ls_cnn_create(int32_t res, int32_t max_batch, int32_t training, ls_cnn **out);
+void ls_cnn_destroy(ls_cnn *model);
+int64_t ls_cnn_param_count(const ls_cnn *model);
+int32_t ls_cnn_layer_count(const ls_cnn *model);
+ls_status ls_cnn_layer_info(const ls_cnn *model, int32_t layer, int32_t *kind, int32_t *cin, int32_t *cout,
+                            int64_t *w_offset, int64_t *b_offset);
+/* Pack the conv weights of params into the model's tensor-core operands. */
+ls_status ls_cnn_load(ls_cnn *model, const float *params, ls_stream_t stream);
+ls_status ls_cnn_forward(ls_cnn *model, const float *params, const uint16_t *x, int32_t n, float *y,
+                         ls_stream_t stream);
+/* grads (fp32, n_params) = dL/dparams given dy = dL/dy of the last forward. */
+ls_status ls_cnn_backward(ls_cnn *model, const float *params, const float *dy, int32_t n, float *grads,
+                          ls_stream_t stream);
+/* Network input from the Alg. 1 maps of n patches (lin/nn height float [n][res][res]
+ * metres, lin/nn rgb uint8 [n][res][res][3]): heights (h - c_z) / r_m with c_z the mean of
+ * the linear map's 4 central texels (cz fp32 [n] out), colours / 255, NaN heights 0;
+ * x bf16 [n][res][res][8] (16-byte aligned). */
+ls_status ls_cnn_inputs(const float *lin_height, const float *nn_height, const uint8_t *lin_rgb,
+                        const uint8_t *nn_rgb, int64_t n, int32_t res, float r_m, uint16_t *x, float *cz,
+                        ls_stream_t stream);
+
+/* ---------------------------------------------------------------------------------
  * Software rasterizers into a headless framebuffer (Sec. 3.5, rendering): points
  * with a 64-bit depth|colour atomicMin per pixel, heightmaps as triangle meshes with
  * the same per-fragment atomicMin, and a resolve pass that extracts the colours into

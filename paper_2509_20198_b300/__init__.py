@@ -19,7 +19,7 @@ from . import _native as N
 
 __all__ = ["bin_points", "bin_stats", "extract_samples", "extract_samples_into", "fill_sparse", "fill_interp",
            "update_tile", "render_framebuffer", "render_clear", "render_points", "render_heightmaps",
-           "render_resolve", "last_error",
+           "render_resolve", "PaperCNN", "PaperCNNFn", "cnn_inputs", "last_error",
            "release_workspace", "empty_bins", "BIN_KEYS", "Filler", "FillerFn", "filler_loss", "adamw_step",
            "learned_inputs", "learned_targets", "learned_finish", "fill_learned"]
 
@@ -346,6 +346,84 @@ class FillerFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, dy):
         return ctx.filler.backward(dy), None, None
+
+
+class PaperCNN:
+    """Native handle (ls_cnn) of the paper's network variant plus its flat fp32
+    parameters: four encoders, two fully connected merge steps, height and texture
+    decoders, skip concat with the inputs, final CNN, centre crop (see
+    include/lidarscout.h).  Input: bf16 bits [n, res, res, 8] (cnn_inputs); output fp32
+    [n, res/2, res/2, 5]."""
+
+    def __init__(self, res=128, max_batch=256, training=True, device="cuda"):
+        self.res, self.max_batch, self.training = res, max_batch, training
+        self.device = torch.device(device)
+        h = ctypes.c_void_p()
+        N.check("ls_cnn_create", N.lib().ls_cnn_create(res, max_batch, int(training), ctypes.byref(h)))
+        self._h = h
+        self.n_params = N.lib().ls_cnn_param_count(h)
+        self.params = torch.zeros(self.n_params, dtype=torch.float32, device=self.device)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            N.lib().ls_cnn_destroy(h)
+            self._h = None
+
+    def layers(self):
+        """[(kind, cin, cout, w_offset, b_offset)] in parameter order (kind 0: 3x3 conv,
+        1: fully connected, 2: 1x1 head)."""
+        out = []
+        for i in range(N.lib().ls_cnn_layer_count(self._h)):
+            a = [ctypes.c_int32() for _ in range(3)] + [ctypes.c_int64() for _ in range(2)]
+            N.check("ls_cnn_layer_info", N.lib().ls_cnn_layer_info(self._h, i, *[ctypes.byref(v) for v in a]))
+            out.append(tuple(v.value for v in a))
+        return out
+
+    def load(self, stream=None):
+        N.check("ls_cnn_load", N.lib().ls_cnn_load(self._h, _ptr(self.params), _stream(stream)))
+
+    def forward(self, x, stream=None):
+        n = x.shape[0]
+        y = torch.empty((n, self.res // 2, self.res // 2, 5), dtype=torch.float32, device=x.device)
+        N.check("ls_cnn_forward", N.lib().ls_cnn_forward(self._h, _ptr(self.params), _ptr(_dev(x, "x")), n, _ptr(y),
+                                                        _stream(stream)))
+        return y
+
+    def backward(self, dy, grads=None, stream=None):
+        n = dy.shape[0]
+        if grads is None:
+            grads = torch.empty_like(self.params)
+        N.check("ls_cnn_backward", N.lib().ls_cnn_backward(self._h, _ptr(self.params), _ptr(_dev(dy.contiguous(), "dy")),
+                                                          n, _ptr(grads), _stream(stream)))
+        return grads
+
+
+class PaperCNNFn(torch.autograd.Function):
+    """torch.autograd.Function over the library's kernels: y = cnn(params; x)."""
+
+    @staticmethod
+    def forward(ctx, params, x, cnn):
+        ctx.cnn = cnn
+        cnn.load()
+        return cnn.forward(x)
+
+    @staticmethod
+    def backward(ctx, dy):
+        return ctx.cnn.backward(dy), None, None
+
+
+def cnn_inputs(maps, r_m=320.0, stream=None):
+    """Network input of the paper's variant from ls_fill_interp maps (lin/nn height and
+    rgb of n patches).  Returns (x bf16 bits int16 [n, res, res, 8], cz [n])."""
+    lh = _dev(maps["lin_height"], "lin_height")
+    n, res = lh.shape[0], lh.shape[1]
+    x = torch.empty((n, res, res, 8), dtype=torch.int16, device=lh.device)
+    cz = torch.empty(n, dtype=torch.float32, device=lh.device)
+    N.check("ls_cnn_inputs", N.lib().ls_cnn_inputs(
+        _ptr(lh), _ptr(_dev(maps["nn_height"], "nn_height")), _ptr(_dev(maps["lin_rgb"], "lin_rgb")),
+        _ptr(_dev(maps["nn_rgb"], "nn_rgb")), n, res, float(r_m), _ptr(x), _ptr(cz), _stream(stream)))
+    return x, cz
 
 
 def filler_loss(y, base, target, mask, bound_weight=1.0, stream=None):

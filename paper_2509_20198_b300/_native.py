@@ -64,6 +64,15 @@ SIGNATURES = {
     "ls_fill_sparse": ([P(LsPoints), P(LsRegion), P(LsFillParams), VP, I64, VP, VP, VP], I32),
     "ls_update_tile": ([P(LsBins), P(LsRegion), VP, I64, VP, VP, VP], I32),
     "ls_fill_interp": ([P(LsPoints), P(LsRegion), P(LsInterpParams), VP, I64, P(LsInterpOutputs), VP], I32),
+    "ls_cnn_create": ([I32, I32, I32, P(VP)], I32),
+    "ls_cnn_destroy": ([VP], None),
+    "ls_cnn_param_count": ([VP], I64),
+    "ls_cnn_layer_count": ([VP], I32),
+    "ls_cnn_layer_info": ([VP, I32, P(I32), P(I32), P(I32), P(I64), P(I64)], I32),
+    "ls_cnn_load": ([VP, VP, VP], I32),
+    "ls_cnn_forward": ([VP, VP, VP, I32, VP, VP], I32),
+    "ls_cnn_backward": ([VP, VP, VP, I32, VP, VP], I32),
+    "ls_cnn_inputs": ([VP, VP, VP, VP, I64, I32, FLT, VP, VP, VP], I32),
     "ls_render_clear": ([VP, I32, I32, VP], I32),
     "ls_render_points": ([P(LsPoints), P(LsCamera), VP, VP], I32),
     "ls_render_heightmaps": ([VP, VP, VP, I64, I32, P(LsRegion), P(LsCamera), VP, VP], I32),

@@ -8,4 +8,5 @@
 #include "ls_conv.cu"
 #include "ls_wgrad.cu"
 #include "ls_unet.cu"
+#include "ls_cnn.cu"
 #include "ls_learned.cu"
