@@ -370,10 +370,14 @@ def run_overview(lsb, args, dev, stream):
     crop = lambda a: a[sub_t][:, 16:80, 16:80]  # the tile's 64 x 64 texels inside the patch  # noqa: E731
     inside = float(im["inside"][:, 16:80, 16:80].to(torch.float32).mean())
     interp_bytes = nT * 96 * 96 * (4 + 4 + 3 + 3 + 1)
+    del im
+    torch.cuda.empty_cache()
+    paper = run_paper_cnn(lsb, args, dev, stream, s, region, nT, sub_t, rm, rc, timed)
     return {"workload": "overview 200x200 tiles, 4 pts/m^2, 33 samples/tile (1.32M samples)",
             "gaussian_fill": {"tiles_per_s": round(nT / (ms_gauss * 1e-3), 1), "ms": round(ms_gauss, 3),
                               "height_rmse_m": round(rm(h[sub_t]), 4), "rgb_rmse_8bit": round(rc(c[sub_t]), 3)},
             "render": render,
+            "paper_cnn": paper,
             "interp_fill": {"tiles_per_s": round(nT / (ms_interp * 1e-3), 1), "ms": round(ms_interp, 3),
                             "patch": "96x96 texels of 10 m (tile + 160 m padding), Alg. 1",
                             "nn_height_rmse_m": round(rm(crop(im["nn_height"])), 4),
@@ -541,6 +545,83 @@ def run_resolutions(lsb, args, dev, stream):
     return {"workload": f"20x20 tiles at 4 pts/m^2 ({n_points} points, {int(s['x'].numel())} chunk samples), "
                         "all tiles; patches of the Alg. 1 maps = tile + 160 m",
             "rows": rows}
+
+
+def paper_cnn_flops(cnn):
+    """Useful FLOPs of one forward pass of the paper's variant (true input channels, not
+    the padded operands): 3x3 convs 2*9*cin*cout*h^2, fully connected 2*in*out, head."""
+    R = cnn.res
+    total = 0
+    sizes = []
+    for k in range(4):
+        sizes += [R >> l for l in range(4)] + [R // 16]
+    sizes += [0] * 5
+    for j in range(2):
+        sizes += [(R // 16) << l for l in range(5)]
+    sizes += [R, R, R]
+    for (kind, cin, cout, _, _), h in zip(cnn.layers(), sizes):
+        total += 2 * 9 * cin * cout * h * h if kind == 0 else (2 * cin * cout if kind == 1 else 2 * cin * cout * h * h)
+    return total
+
+
+def run_paper_cnn(lsb, args, dev, stream, s, region, nT, sub_t, rm, rc, timed):
+    """The paper's own network variant: trained on self-generated pairs (Alg. 1 maps of
+    128 x 128 patches against full-resolution means, seeds disjoint from the overview),
+    then the overview's 40,000 tiles in batches of 4096: maps, input raster, forward."""
+    import torch
+    from paper_2509_20198_b300 import train as T
+    t0 = time.perf_counter()
+    data = T.synthetic_patches(args.train_tiles, seed0=100, res=128, device=dev)
+    torch.cuda.synchronize()
+    data_s = time.perf_counter() - t0
+    cnn = lsb.PaperCNN(res=128, max_batch=256, training=True, device=dev)
+    T.init_cnn_params(cnn, seed=0)
+    t1 = time.perf_counter()
+    hist = T.train_cnn(cnn, data, epochs=args.cnn_epochs, batch=256, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    steps = (len(data) // 256) * 256 * args.cnn_epochs
+    flops = paper_cnn_flops(cnn)
+    params = cnn.params.clone()
+    del data, cnn
+    torch.cuda.empty_cache()
+    B = 4096
+    inf = lsb.PaperCNN(res=128, max_batch=B, training=False, device=dev)
+    inf.params.copy_(params)
+    inf.load()
+    r_m = 0.5 * region.tile_cm * region.z_scale
+    ids_all = torch.arange(nT, dtype=torch.int32, device=dev)
+    out_h = torch.empty((nT, 64, 64), dtype=torch.float32, device=dev)
+    out_c = torch.empty((nT, 64, 64, 3), dtype=torch.float32, device=dev)
+    xb = {}
+
+    def fill():
+        for a in range(0, nT, B):
+            ids = ids_all[a:a + B]
+            x, cz = T.patch_inputs(s, region, ids, res=128, stream=stream)
+            y = inf.forward(x, stream=stream)
+            out_h[a:a + len(ids)] = y[..., 0] * r_m + cz[:, None, None]
+            out_c[a:a + len(ids)] = y[..., 1:4] * 255.0
+            xb["x"] = x
+    with torch.cuda.stream(stream):
+        ms_fill = timed(fill, max(1, args.steps // 10))
+        x = xb["x"][:B] if xb["x"].shape[0] >= B else xb["x"]
+        ms_fwd = timed(lambda: inf.forward(x, stream=stream), max(1, args.steps // 10))
+    assert lsb.last_error() == 0
+    nfwd = x.shape[0]
+    tf = flops * nfwd / (ms_fwd * 1e-3) / 1e12
+    return {"parameters": int(params.numel()), "forward_gflop_per_tile": round(flops / 1e9, 3),
+            "fill_tiles_per_s": round(nT / (ms_fill * 1e-3), 1), "fill_ms": round(ms_fill, 3),
+            "forward_tiles_per_s": round(nfwd / (ms_fwd * 1e-3), 1), "forward_tflops": round(tf, 1),
+            "forward_frac_of_bf16_sustained": round(tf / bf16_sustained(), 4),
+            "height_rmse_m": round(rm(out_h[sub_t]), 4), "rgb_rmse_8bit": round(rc(out_c[sub_t]), 3),
+            "training": {"tiles": args.train_tiles, "epochs": args.cnn_epochs, "batch": 256,
+                         "seconds": round(train_s, 2), "data_seconds": round(data_s, 2),
+                         "tiles_per_s": round(steps / train_s, 1),
+                         "tflops": round(3 * flops * steps / train_s / 1e12, 1),
+                         "loss_first": [round(v, 7) for v in hist[0]],
+                         "loss_last": [round(v, 7) for v in hist[-1]]},
+            "input": "Alg. 1 NN + linear maps of the 128 x 128 patch (tile + 320 m), output the tile's 64 x 64"}
 
 
 def run_e2e(lsb, region, counts, pts, step, stream, steps, world):
@@ -802,6 +883,7 @@ def main():
     ap.add_argument("--case-tiles", type=int, default=3, help="tiles per side of the profiling case")
     ap.add_argument("--train-tiles", type=int, default=4096)
     ap.add_argument("--train-epochs", type=int, default=60)
+    ap.add_argument("--cnn-epochs", type=int, default=30, help="epochs of the paper's network variant")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -399,7 +399,10 @@ ls_status ls_conv3x3_forward(const uint16_t *x, const uint16_t *packed, const fl
  * dw[(tap * c_in + i) * c_out + o] += sum_p x_shift(tap)[p][i] * dz[p][o] with tap =
  * 3 * ky + kx (zero padding), db[o] += sum_p dz[p][o] (db may be NULL).  x: layer
  * input bf16 [n][h][w][c_in]; dz: output gradient bf16 [n][h][w][c_out].  dw and db are
- * fp32 and accumulated into (zero them first). */
+ * fp32 and accumulated into (zero them first).  Shapes: c_in a multiple of 8; c_out a
+ * multiple of 16 in [16, 128]; w a power of two <= 128; h * w a multiple of 64, or a
+ * divisor of 64 whose quotient divides n (64-pixel stages: half rows at w = 128, whole
+ * rows, or whole images). */
 ls_status ls_conv3x3_wgrad(const uint16_t *x, const uint16_t *dz, const ls_conv_shape *shape,
                            float *dw, float *db, ls_stream_t stream);
 

@@ -9,8 +9,8 @@
 // (pixels contiguous), so every stage is transposed once in shared memory:
 //  warp 0     TMA producer: the M tile's rows are 128 / cw blocks of cw channels of one
 //             tap (cw = 64, 32 or 8 dividing C_in): one 4-D tiled load per block of the
-//             tap-shifted input (cw channels x 64 pixels, zero-filled outside the image:
-//             the padding; rows of 128 / 64 bytes are written with the 128B / 64B
+//             tap-shifted input (cw channels x 64 pixels: whole rows, or half a row of a
+//             128-wide image; zero-filled outside the image: the padding; rows of 128 / 64 bytes are written with the 128B / 64B
 //             swizzle), and dZ in blocks of cwb output channels, into a raw ring;
 //  warps 1-4  transpose raw -> K-major core matrices with ldmatrix (8x8 b16 blocks:
 //             8 pixel rows of one 16-byte channel chunk, un-swizzled by address) and
@@ -48,7 +48,8 @@ struct WgArgs {
   float* __restrict__ part;  // [CTAs][128][cout] fp32 partial sums (CTA = slice * n_mtiles + tile)
   int32_t cw, cwb;                // channel block widths of the x and dZ loads
   int32_t h, w, cin, cout, rows;  // rows = 9*cin
-  int32_t rows_per_step;          // image rows per 64-pixel stage (64 / w, or h)
+  int32_t rows_per_step;          // image rows per 64-pixel stage (64 / w, 1, or h)
+  int32_t cols_per_step;          // pixels of a row per stage (w, or 64 when w = 128)
   int32_t imgs_per_step;          // images per stage (1, or 64 / (h * w))
   int64_t pix_total, pix_per_cta;
   int32_t n_mtiles;
@@ -117,7 +118,9 @@ __global__ void __launch_bounds__(kWgThreads, 1)
       const int n_ob = a.cout / a.cwb;
       const uint32_t bytes = (uint32_t)(n_valid * blk_a + n_ob * blk_b);
       int n0 = (int)(p_begin / hw);
-      int y0 = a.imgs_per_step > 1 ? 0 : (int)((p_begin - (int64_t)n0 * hw) / a.w);
+      const int64_t in_img = p_begin - (int64_t)n0 * hw;  // a multiple of the stage
+      int y0 = a.imgs_per_step > 1 ? 0 : (int)(in_img / a.w);
+      int x0 = a.imgs_per_step > 1 ? 0 : (int)(in_img - (int64_t)y0 * a.w);
       int slot = 0;
       uint32_t ph = 0;
       for (int s = 0; s < n_steps && !abort_flag; ++s) {
@@ -127,15 +130,21 @@ __global__ void __launch_bounds__(kWgThreads, 1)
         tc::mbar_arrive_expect_tx(&raw_full[slot], bytes);
 #pragma unroll
         for (int i = 0; i < 16; ++i)
-          if (i < n_valid) tc::tma_load_4d(RA + i * blk_a, &xmap, bc[i], bx[i], y0 + by[i], n0, &raw_full[slot]);
+          if (i < n_valid)
+            tc::tma_load_4d(RA + i * blk_a, &xmap, bc[i], x0 + bx[i], y0 + by[i], n0, &raw_full[slot]);
         for (int ob = 0; ob < n_ob; ++ob)
-          tc::tma_load_4d(RB + ob * blk_b, &dzmap, ob * a.cwb, 0, y0, n0, &raw_full[slot]);
-        // next 64 pixels: more rows of this image, or the next image(s)
+          tc::tma_load_4d(RB + ob * blk_b, &dzmap, ob * a.cwb, x0, y0, n0, &raw_full[slot]);
+        // next 64 pixels: the rest of this row, more rows of this image, or the next
+        // image(s)
         if (a.imgs_per_step > 1) {
           n0 += a.imgs_per_step;
         } else {
-          y0 += a.rows_per_step;
-          if (y0 >= a.h) { y0 = 0; ++n0; }
+          x0 += a.cols_per_step;
+          if (x0 >= a.w) {
+            x0 = 0;
+            y0 += a.rows_per_step;
+            if (y0 >= a.h) { y0 = 0; ++n0; }
+          }
         }
         if (++slot == kWgRaw) { slot = 0; ph ^= 1u; }
       }
@@ -314,14 +323,17 @@ ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int 
                        float* db, cudaStream_t stream) {
   if (!x || !dz || !dwt || n <= 0 || h <= 0 || w <= 0) return LS_ERR_INVALID_ARG;
   if (cin % 8 || cout < 16 || cout > 128 || cout % 16) return LS_ERR_UNSUPPORTED;
-  // a stage is 64 pixels: whole image rows of one image, or whole images
+  // a stage is 64 pixels: half a row (w = 128), whole image rows of one image, or
+  // whole images
   const int64_t hw = (int64_t)h * w;
-  if (w > kWgPix || kWgPix % w || (hw % kWgPix && kWgPix % hw)) return LS_ERR_UNSUPPORTED;
+  if ((w > kWgPix && w != 2 * kWgPix) || (w <= kWgPix && kWgPix % w) || (hw % kWgPix && kWgPix % hw))
+    return LS_ERR_UNSUPPORTED;
   if (hw < kWgPix && n % (kWgPix / hw)) return LS_ERR_UNSUPPORTED;
   if (((uintptr_t)x | (uintptr_t)dz) % 16) return LS_ERR_INVALID_ARG;
   WgArgs a = {};
   a.h = h; a.w = w; a.cin = cin; a.cout = cout; a.rows = 9 * cin;
-  a.rows_per_step = hw >= kWgPix ? kWgPix / w : h;
+  a.rows_per_step = hw >= kWgPix ? (w >= kWgPix ? 1 : kWgPix / w) : h;
+  a.cols_per_step = w > kWgPix ? kWgPix : w;
   a.imgs_per_step = hw >= kWgPix ? 1 : (int32_t)(kWgPix / hw);
   a.pix_total = (int64_t)n * h * w;
   a.n_mtiles = (a.rows + 127) / 128;
@@ -340,8 +352,10 @@ ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int 
   a.cw = cin % 64 == 0 ? 64 : cin % 32 == 0 ? 32 : 8;
   a.cwb = cout % 64 == 0 ? 64 : cout % 32 == 0 ? 32 : 8;
   CUtensorMap xmap, dzmap;
-  const uint32_t box[4] = {(uint32_t)a.cw, (uint32_t)w, (uint32_t)a.rows_per_step, (uint32_t)a.imgs_per_step};
-  const uint32_t boxb[4] = {(uint32_t)a.cwb, (uint32_t)w, (uint32_t)a.rows_per_step, (uint32_t)a.imgs_per_step};
+  const uint32_t box[4] = {(uint32_t)a.cw, (uint32_t)a.cols_per_step, (uint32_t)a.rows_per_step,
+                           (uint32_t)a.imgs_per_step};
+  const uint32_t boxb[4] = {(uint32_t)a.cwb, (uint32_t)a.cols_per_step, (uint32_t)a.rows_per_step,
+                            (uint32_t)a.imgs_per_step};
   const uint64_t xd[4] = {(uint64_t)cin, (uint64_t)w, (uint64_t)h, (uint64_t)n};
   const uint64_t xs[3] = {(uint64_t)cin * 2, (uint64_t)w * cin * 2, (uint64_t)h * w * cin * 2};
   const uint64_t zd[4] = {(uint64_t)cout, (uint64_t)w, (uint64_t)h, (uint64_t)n};

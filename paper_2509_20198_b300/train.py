@@ -15,8 +15,8 @@ import math
 import numpy as np
 import torch
 
-from . import (Filler, FillerFn, adamw_step, bin_points, filler_loss, learned_inputs, learned_targets,
-               learned_finish)
+from . import (Filler, FillerFn, PaperCNN, PaperCNNFn, adamw_step, bin_points, cnn_inputs, fill_interp, filler_loss,
+               learned_inputs, learned_targets, learned_finish)
 
 
 class FillerLossFn(torch.autograd.Function):
@@ -161,3 +161,105 @@ def init_params(filler: Filler, seed=0):
         flat[w_off:w_off + n] = torch.randn(n, generator=g) * math.sqrt(2.0 / (cin * k * k))
     filler.params.copy_(flat.to(filler.params.device))
     filler.load()
+
+
+# ------------------------------------------------------------------------------------
+# the paper's network variant: Alg. 1 maps of the padded patch in, 64 x 64 out
+# ------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class PatchSet:
+    x: torch.Tensor        # bf16 bits int16 [n, res, res, 8]
+    target: torch.Tensor   # [n, 64, 64, 4]
+    mask: torch.Tensor     # uint8 [n, 64, 64]
+    cz: torch.Tensor       # [n]
+
+    def __len__(self):
+        return self.x.shape[0]
+
+
+def patch_inputs(samples, region, tile_ids, res=128, stream=None):
+    """Alg. 1 maps of the res x res patches (10 m texels: the tile plus (res - 64) / 2
+    texels on every side) and the network input made from them."""
+    pad = (res - 64) // 2 * (region.tile_cm // 64)
+    maps = fill_interp(samples, region, tile_ids=tile_ids, res=res, pad_cm=pad,
+                       maps=("nn_height", "nn_rgb", "lin_height", "lin_rgb"), stream=stream)
+    x, cz = cnn_inputs(maps, r_m=0.5 * region.tile_cm * region.z_scale, stream=stream)
+    return x, cz
+
+
+def synthetic_patches(n_tiles, seed0, res=128, block=16, density=(3.0, 6.0), device="cuda"):
+    """Training pairs of the paper's variant on seeded synthetic terrain (regions of
+    (block + 4)^2 tiles, the inner block x block used: their padded patches see real
+    samples all around)."""
+    import synth
+    import synth.gpu as sg
+    parts, made, r = [], 0, 0
+    while made < n_tiles:
+        seed = seed0 + r
+        r += 1
+        side = block + 4
+        region = synth.Region(tiles_x=side, tiles_y=side)
+        rng = np.random.default_rng(seed)
+        counts = np.rint(rng.uniform(density[0], density[1], side * side) * 640 * 640).astype(np.int64)
+        inner = np.array([(ty * side + tx) for ty in range(2, side - 2) for tx in range(2, side - 2)], np.int64)
+        samples = sg.region_samples(seed, region, counts, device=device)
+        ids = torch.as_tensor(inner, dtype=torch.int32, device=device)
+        x, cz = patch_inputs(samples, region, ids, res=res)
+        full = np.zeros_like(counts)
+        full[inner] = counts[inner]
+        pts = sg.region_points(seed, region, full, device=device)
+        (b64,), _ = bin_points(pts, region, levels=(64,))
+        target, mask = learned_targets(b64, region, ids, cz)
+        del pts, b64
+        take = min(len(inner), n_tiles - made)
+        parts.append(PatchSet(x[:take], target[:take], mask[:take], cz[:take]))
+        made += take
+    cat = lambda k: torch.cat([getattr(p, k) for p in parts])  # noqa: E731
+    return PatchSet(*[cat(f.name) for f in dataclasses.fields(PatchSet)])
+
+
+def train_cnn(cnn: PaperCNN, data: PatchSet, epochs=20, batch=256, lr=1e-3, weight_decay=1e-2, betas=(0.9, 0.999),
+              eps=1e-5, milestones=(0.6, 0.85), gamma=0.1, bound_weight=1.0, seed=0, log=None):
+    """AdamW with a step schedule (Sec. 3.4) on the library's kernels; the outputs are
+    the patch-space height and colours directly (zero base).  Returns per-epoch mean
+    losses [total, height, colour, bound]."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    p = cnn.params
+    m, v = torch.zeros_like(p), torch.zeros_like(p)
+    base = torch.zeros((batch,) + tuple(data.target.shape[1:]), dtype=torch.float32, device=p.device)
+    steps_per_epoch = max(1, len(data) // batch)
+    total = epochs * steps_per_epoch
+    step, history = 0, []
+    for ep in range(epochs):
+        order = torch.randperm(len(data), generator=g).to(p.device)
+        acc = torch.zeros(4, device=p.device)
+        for k in range(steps_per_epoch):
+            idx = order[k * batch:(k + 1) * batch]
+            params = p.detach().requires_grad_(True)
+            y = PaperCNNFn.apply(params, data.x[idx].contiguous(), cnn)
+            loss = FillerLossFn.apply(y, base, data.target[idx].contiguous(), data.mask[idx].contiguous(),
+                                      bound_weight)
+            loss[0].backward()
+            step += 1
+            cur = lr * (gamma ** sum(step / total > mm for mm in milestones))
+            adamw_step(p, params.grad, m, v, step, lr=cur, betas=betas, eps=eps, weight_decay=weight_decay)
+            acc += loss.detach()
+        history.append([float(v) / steps_per_epoch for v in acc.tolist()])
+        if log:
+            log(f"epoch {ep + 1}/{epochs} loss {history[-1]}")
+    cnn.load()
+    return history
+
+
+def init_cnn_params(cnn: PaperCNN, seed=0):
+    """He-normal weights, zero biases; the head starts at zero."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    flat = torch.zeros(cnn.n_params)
+    for kind, cin, cout, w_off, b_off in cnn.layers():
+        if kind == 2:
+            continue
+        fan = cin * (9 if kind == 0 else 1)
+        flat[w_off:w_off + cout * fan] = torch.randn(cout * fan, generator=g) * math.sqrt(2.0 / fan)
+    cnn.params.copy_(flat.to(cnn.params.device))
+    cnn.load()

@@ -109,7 +109,8 @@ def test_input_gradient_via_flipped_weights(lib, shape):
 
 
 @pytest.mark.parametrize("shape", [(2, 64, 64, 8, 32), (2, 32, 32, 32, 64), (1, 16, 16, 64, 128),
-                                   (2, 32, 32, 192, 64), (1, 64, 64, 96, 32), (16, 4, 4, 16, 16)])
+                                   (2, 32, 32, 192, 64), (1, 64, 64, 96, 32), (16, 4, 4, 16, 16),
+                                   (2, 128, 128, 8, 16), (1, 128, 128, 48, 32)])
 def test_weight_gradient_matches_oracle(lib, shape):
     """dW, db of the tcgen05 weight-gradient GEMM against the FP64 oracle on the same
     bf16 operands; FP32 accumulation over n*h*w pixels: rel. L2 < 1e-4."""
