@@ -370,6 +370,10 @@ def run_overview(lsb, args, dev, stream):
     crop = lambda a: a[sub_t][:, 16:80, 16:80]  # the tile's 64 x 64 texels inside the patch  # noqa: E731
     inside = float(im["inside"][:, 16:80, 16:80].to(torch.float32).mean())
     interp_bytes = nT * 96 * 96 * (4 + 4 + 3 + 3 + 1)
+    interp_err = {"nn_height_rmse_m": round(rm(crop(im["nn_height"])), 4),
+                  "lin_height_rmse_m": round(rm(crop(im["lin_height"])), 4),
+                  "nn_rgb_rmse_8bit": round(rc(crop(im["nn_rgb"])), 3),
+                  "lin_rgb_rmse_8bit": round(rc(crop(im["lin_rgb"])), 3)}
     del im
     torch.cuda.empty_cache()
     paper = run_paper_cnn(lsb, args, dev, stream, s, region, nT, sub_t, rm, rc, timed)
@@ -380,10 +384,7 @@ def run_overview(lsb, args, dev, stream):
             "paper_cnn": paper,
             "interp_fill": {"tiles_per_s": round(nT / (ms_interp * 1e-3), 1), "ms": round(ms_interp, 3),
                             "patch": "96x96 texels of 10 m (tile + 160 m padding), Alg. 1",
-                            "nn_height_rmse_m": round(rm(crop(im["nn_height"])), 4),
-                            "lin_height_rmse_m": round(rm(crop(im["lin_height"])), 4),
-                            "nn_rgb_rmse_8bit": round(rc(crop(im["nn_rgb"])), 3),
-                            "lin_rgb_rmse_8bit": round(rc(crop(im["lin_rgb"])), 3),
+                            **interp_err,
                             "inside_fraction_of_tile": round(inside, 4),
                             # integer/latency-bound kernel: output bytes per second for scale
                             "output_gbs": round(interp_bytes / (ms_interp * 1e-3) / 1e9, 1)},
@@ -838,6 +839,28 @@ def run_render_case(args):
     return 0 if st == 0 else 1
 
 
+def run_paper_cnn_case(args):
+    """Profiling case for the paper's network variant: one forward and one backward
+    pass of a batch of --case-tiles 128 x 128 patches (He-initialised weights, random
+    inputs)."""
+    import torch
+    import paper_2509_20198_b300 as lsb
+    from paper_2509_20198_b300 import build, train as T
+    build.build_library()
+    n = args.case_tiles
+    cnn = lsb.PaperCNN(res=128, max_batch=n, training=True)
+    T.init_cnn_params(cnn, seed=0)
+    g = torch.Generator(device="cpu").manual_seed(1)
+    x = (torch.randn((n, 128, 128, 8), generator=g) * 0.5).to(torch.bfloat16).view(torch.int16).cuda()
+    for _ in range(args.steps):
+        y = cnn.forward(x)
+        cnn.backward(torch.ones_like(y) * 1e-3)
+    torch.cuda.synchronize()
+    st = lsb.last_error()
+    print(json.dumps({"case": "paper-cnn", "batch": n, "status": st}))
+    return 0 if st == 0 else 1
+
+
 def run_learned_case(args):
     """Profiling case for the learned filler: one forward pass and one training step
     (forward, loss, backward, AdamW) of the U-Net on a batch of random bf16 inputs, with
@@ -878,7 +901,7 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--overview", type=int, default=1, help="also time the 40,000-tile overview fills")
-    ap.add_argument("--case", default="", choices=["", "bin-small", "learned", "fill", "interp", "render"],
+    ap.add_argument("--case", default="", choices=["", "bin-small", "learned", "fill", "interp", "render", "paper-cnn"],
                     help="profiling case instead of the bench")
     ap.add_argument("--case-tiles", type=int, default=3, help="tiles per side of the profiling case")
     ap.add_argument("--train-tiles", type=int, default=4096)
@@ -895,6 +918,8 @@ def main():
         sys.exit(run_interp_case(args))
     if args.case == "render":
         sys.exit(run_render_case(args))
+    if args.case == "paper-cnn":
+        sys.exit(run_paper_cnn_case(args))
     if args.case:
         sys.exit(run_profile_case(args))
     if args.impl == "reference":
