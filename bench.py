@@ -156,6 +156,29 @@ class Step:
         lsb.update_tile(self.bins[1], self.region, None, self.height, self.rgb, stream=self.stream)
 
 
+def replica_seed(seed, rank):
+    """Points seed of a rank: every replica bins, fills and updates its own region (weak
+    scaling, no data exchange between ranks)."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(values, world, device="cpu"):
+    """Element-wise maximum over the ranks of a list of floats: a barrier-synchronised job
+    is as slow as its slowest replica.  One rank returns the values unchanged."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def job_rate(world, units_per_rank, ms):
+    """Whole-job throughput: the units all ranks processed per second of the slowest."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def run_b300(args, rank, world):
     import torch
     import paper_2509_20198_b300 as lsb
@@ -172,7 +195,7 @@ def run_b300(args, rank, world):
     T = region.n_tiles
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
-        pts = sg.region_points(SEED + 1000 * rank, region, counts, device=dev, stream=stream)
+        pts = sg.region_points(replica_seed(SEED, rank), region, counts, device=dev, stream=stream)
     stream.synchronize()
     step = Step(lsb, region, counts, pts, stream)
     # warm-up outside the graph (allocates the library workspace), then capture
@@ -219,10 +242,7 @@ def run_b300(args, rank, world):
     ms_bin = float(np.mean([bin_ev[2 * k].elapsed_time(bin_ev[2 * k + 1]) for k in range(args.steps)]))
     assert lsb.last_error() == 0
     ms_step = ms_total / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step, ms_bin], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step, ms_bin = float(t[0]), float(t[1])
+    ms_step, ms_bin = max_over_ranks([ms_step, ms_bin], world, device=dev)
 
     # ---- end-to-end through the public API with host buffers (pinned)
     e2e = run_e2e(lsb, region, counts, pts, step, stream, min(args.steps, 3), world)
@@ -232,14 +252,14 @@ def run_b300(args, rank, world):
     achieved = alg_bytes / (ms_bin * 1e-3) / 1e9
     tpp = bin_traffic_per_point()
     out = {
-        "metric": METRIC, "value": round(world * T / (ms_step * 1e-3), 1), "unit": "tiles/s",
+        "metric": METRIC, "value": round(job_rate(world, T, ms_step), 1), "unit": "tiles/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/int64 bins, f32 fill",
         "data": "synthetic (seeded fBm terrain, LAZ strip order)",
         "config": {"workload": WORKLOAD, "tiles_per_gpu": T, "points_per_gpu": n_points,
                    "fill_res": 64, "radius_m": 120, "sigma_m": 40, "parallelism": f"replicas{world}",
                    "l2": "inputs (~10 GB) larger than L2, no flush", "graph": "one CUDA graph per step"},
-        "points_binned_per_s": round(world * n_points / (ms_step * 1e-3), 1),
+        "points_binned_per_s": round(job_rate(world, n_points, ms_step), 1),
         "bin_only": {"ms": round(ms_bin, 4), "points_per_s": round(n_points / (ms_bin * 1e-3), 1)},
         "roofline": {"bound": "hbm", "kernel": "ls_bin_points (k_bin_prologue+k_bin_main+k_bin_finalize)",
                      "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
@@ -655,7 +675,8 @@ def run_e2e(lsb, region, counts, pts, step, stream, steps, world):
                 res_host[k].copy_(v, non_blocking=True)
         stream.synchronize()
     dt = (time.perf_counter() - t0) / steps
-    return {"value": round(world * region.n_tiles / dt, 1), "unit": "tiles/s",
+    (dt,) = max_over_ranks([dt], world, device=stream.device)
+    return {"value": round(job_rate(world, region.n_tiles, dt * 1e3), 1), "unit": "tiles/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps}
 
 
