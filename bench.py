@@ -273,7 +273,7 @@ def run_b300(args, rank, world):
     }
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline(pts, counts, region, budget_s=args.cpu_seconds)
-    if args.overview:
+    if args.overview and rank == 0:  # context measurements: one replica is enough
         out["render_points"] = run_render_points(lsb, region, pts, stream, args.steps, hbm, peak_kind)
         del pts, step, graph
         torch.cuda.empty_cache()
