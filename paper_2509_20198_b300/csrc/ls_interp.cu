@@ -18,8 +18,9 @@
 //    over the neighbour links from the lane's texel of the block above (exact int64
 //    orientations), then the barycentric interpolation from the exact numerator;
 //    outputs staged per block and stored as whole rows and 4-byte words.
-// Patches whose window holds more samples than the small tier's capacity are queued
-// on the device for a second launch with one warp per CTA and a larger capacity.
+// Patches whose window holds more samples than the small tier's capacity (96) are
+// queued on the device for a second launch with one warp per CTA and room for 384, and
+// those over that for a third with room for 1536 (one CTA per SM).
 #include <climits>
 
 #include "ls_internal.cuh"
@@ -31,7 +32,8 @@ constexpr int kInterpMaxRes = 1024;
 constexpr int kInterpHintRes = 128;  // up to this resolution walks start from the block above
 constexpr int kInterpSmallCap = 96;     // window samples per patch, small tier
 constexpr int kInterpSmallWarps = 4;    // patches (warps) per CTA, small tier
-constexpr int kInterpBigCap = 1536;     // big tier: one warp per CTA
+constexpr int kInterpMidCap = 384;      // medium tier: one warp per CTA, 4 CTAs per SM
+constexpr int kInterpBigCap = 1536;     // big tier: one warp per CTA, one CTA per SM
 constexpr int kInterpMaxWindow = 1 << 17;  // window side bound of the exact arithmetic
 constexpr int kInterpZBound = 1 << 28;     // |z| bound of the exact numerators
 
@@ -67,7 +69,9 @@ struct InterpArgs {
   double z_scale, z_offset;
   float zs_f, zo_f;
   ls_interp_outputs out;
-  int32_t* queue;  // [0]: patches queued for the big tier, [1..]: their ordinals
+  // two queues of n_out + 1 words: [0] the number of patches queued for the next
+  // tier (medium, then big), [1..] their ordinals
+  int32_t* queue;
 };
 
 __device__ __forceinline__ unsigned lanes_below() {
@@ -450,10 +454,10 @@ __device__ void texel_maps(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o, i
   __syncwarp();
 }
 
-// Alg. 1 for output ordinal o.  The small tier queues a patch with more than CAP
-// window samples for the big tier; the big tier reports it (LS_ERR_OUT_OF_RANGE) and
-// writes NaN heights.
-template <int CAP, bool BIG>
+// Alg. 1 for output ordinal o.  Tiers 0 and 1 queue a patch with more than CAP window
+// samples for the next tier; the last tier reports it (LS_ERR_OUT_OF_RANGE) and writes
+// NaN heights.
+template <int CAP, int TIER>
 __device__ void interp_patch(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanes_below();
@@ -505,10 +509,11 @@ __device__ void interp_patch(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o)
   }
   bool failed = false;
   if (n > CAP) {
-    if (!BIG) {
+    if (TIER < 2) {
       if (lane == 0) {
-        const int qpos = atomicAdd(a.queue, 1);
-        a.queue[1 + qpos] = (int)o;
+        int32_t* q = a.queue + (size_t)TIER * (a.n_out + 1);
+        const int qpos = atomicAdd(q, 1);
+        q[1 + qpos] = (int)o;
       }
       return;
     }
@@ -570,20 +575,23 @@ __device__ void interp_patch(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o)
   texel_maps(s, a, o, n, T);
 }
 
-template <int CAP, bool BIG>
-__global__ void __launch_bounds__(BIG ? 32 : 32 * kInterpSmallWarps) k_interp(InterpArgs a) {
+// Tier 0 takes every requested patch; tiers 1 and 2 the ones the previous tier queued
+// (written by the previous launch on the same stream).
+template <int CAP, int TIER>
+__global__ void __launch_bounds__(TIER > 0 ? 32 : 32 * kInterpSmallWarps) k_interp(InterpArgs a) {
   extern __shared__ __align__(16) unsigned char interp_dyn[];
   InterpWarp<CAP>& s = reinterpret_cast<InterpWarp<CAP>*>(interp_dyn)[threadIdx.x >> 5];
   const int wpc = blockDim.x >> 5;
   int64_t items = a.n_out;
-  if (BIG) {
-    const int queued = *reinterpret_cast<volatile int32_t*>(a.queue);
+  const int32_t* in = TIER > 0 ? a.queue + (size_t)(TIER - 1) * (a.n_out + 1) : nullptr;
+  if (TIER > 0) {
+    const int queued = *reinterpret_cast<const volatile int32_t*>(in);
     items = queued < a.n_out ? queued : a.n_out;
   }
   for (int64_t item = (int64_t)blockIdx.x * wpc + (threadIdx.x >> 5); item < items;
        item += (int64_t)gridDim.x * wpc) {
-    const int64_t o = BIG ? (int64_t)a.queue[1 + item] : item;
-    interp_patch<CAP, BIG>(s, a, o);
+    const int64_t o = TIER > 0 ? (int64_t)in[1 + item] : item;
+    interp_patch<CAP, TIER>(s, a, o);
   }
 }
 
@@ -619,12 +627,13 @@ extern "C" ls_status ls_fill_interp(const ls_points* samples, const ls_region* r
   if (n_out == 0) return LS_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   Rec* recs = static_cast<Rec*>(workspace(kWsInterpRecs, (size_t)(samples->n > 0 ? samples->n : 1) * sizeof(Rec)));
-  int32_t* queue = static_cast<int32_t*>(workspace(kWsInterpQueue, (size_t)(n_out + 1) * sizeof(int32_t)));
+  int32_t* queue = static_cast<int32_t*>(workspace(kWsInterpQueue, (size_t)2 * (n_out + 1) * sizeof(int32_t)));
   if (!recs || !queue) return LS_ERR_NO_MEMORY;
   if (samples->n > 0)
     k_pack<<<grid_cap((T + 7) / 8, kSmCount * 16), 256, 0, s>>>(*samples, T, region->x0_cm, region->y0_cm,
                                                                  region->tile_cm, region->tiles_x, recs);
   LS_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(int32_t), s));
+  LS_CUDA_TRY(cudaMemsetAsync(queue + n_out + 1, 0, sizeof(int32_t), s));
   InterpArgs a;
   a.toff = samples->tile_offsets;
   a.recs = recs;
@@ -645,28 +654,35 @@ extern "C" ls_status ls_fill_interp(const ls_points* samples, const ls_region* r
   a.out = *out;
   a.queue = queue;
   const size_t small_smem = sizeof(InterpWarp<kInterpSmallCap>) * kInterpSmallWarps;
+  const size_t mid_smem = sizeof(InterpWarp<kInterpMidCap>);
   const size_t big_smem = sizeof(InterpWarp<kInterpBigCap>);
   static bool attr_set[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return LS_ERR_CUDA;
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    LS_CUDA_TRY(cudaFuncSetAttribute(k_interp<kInterpSmallCap, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    LS_CUDA_TRY(cudaFuncSetAttribute(k_interp<kInterpSmallCap, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)small_smem));
-    LS_CUDA_TRY(cudaFuncSetAttribute(k_interp<kInterpBigCap, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    LS_CUDA_TRY(cudaFuncSetAttribute(k_interp<kInterpMidCap, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)mid_smem));
+    LS_CUDA_TRY(cudaFuncSetAttribute(k_interp<kInterpBigCap, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)big_smem));
     attr_set[dev] = true;
   }
-  static int small_per_sm[64] = {};
+  static int small_per_sm[64] = {}, mid_per_sm[64] = {};
   if (dev >= 0 && dev < 64 && small_per_sm[dev] == 0) {
-    int b = 0;
-    LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_interp<kInterpSmallCap, false>,
+    int b = 0, c = 0;
+    LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_interp<kInterpSmallCap, 0>,
                                                               32 * kInterpSmallWarps, small_smem));
+    LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_interp<kInterpMidCap, 1>, 32, mid_smem));
     small_per_sm[dev] = b > 0 ? b : 1;
+    mid_per_sm[dev] = c > 0 ? c : 1;
   }
-  const int per_sm = dev >= 0 && dev < 64 ? small_per_sm[dev] : 1;
-  k_interp<kInterpSmallCap, false>
+  const bool known = dev >= 0 && dev < 64;
+  const int per_sm = known ? small_per_sm[dev] : 1, mid_sm = known ? mid_per_sm[dev] : 1;
+  k_interp<kInterpSmallCap, 0>
       <<<grid_cap((n_out + kInterpSmallWarps - 1) / kInterpSmallWarps, (int64_t)kSmCount * per_sm),
          32 * kInterpSmallWarps, small_smem, s>>>(a);
-  k_interp<kInterpBigCap, true><<<grid_cap(n_out, kSmCount), 32, big_smem, s>>>(a);
+  k_interp<kInterpMidCap, 1><<<grid_cap(n_out, (int64_t)kSmCount * mid_sm), 32, mid_smem, s>>>(a);
+  k_interp<kInterpBigCap, 2><<<grid_cap(n_out, kSmCount), 32, big_smem, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
