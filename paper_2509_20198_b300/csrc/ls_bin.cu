@@ -90,6 +90,7 @@ struct BinArgs {
 // 16 bits (unsigned) and its high bits (signed), zsum = 65536 * sum(hi) + sum(lo),
 // both sums exact while a cell absorbs at most 65536 points.
 struct Smem {
+  uint32_t fa, fs;  // shared address of cnt[0]; byte stride between the eight fine arrays
   unsigned* cnt;  // [W*rstride]
   unsigned* rs;
   unsigned* gs;
@@ -145,6 +146,8 @@ __device__ __forceinline__ Smem carve(unsigned char* base, int WC, int CC) {
   s.cmn = reinterpret_cast<int*>(s.ccnt + CC);
   s.cmx = s.cmn + CC;
   s.sp = reinterpret_cast<unsigned*>(s.cmx + CC);
+  s.fa = (uint32_t)__cvta_generic_to_shared(s.cnt);
+  s.fs = (uint32_t)WC * 4u;
   return s;
 }
 
@@ -245,23 +248,24 @@ __device__ __forceinline__ int coarse_row_of(const BinArgs& a, int G) {
   return tile * a.ccells + (int)fdiv((uint32_t)row, a.div_f);
 }
 
-__device__ __forceinline__ uint32_t sh_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-// shared-memory reductions without a returned value (no scoreboard wait)
-__device__ __forceinline__ void red_add(unsigned* p, unsigned v) {
-  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(sh_addr(p)), "r"(v) : "memory");
+// shared-memory reductions at a 32-bit shared address, without a returned value (no
+// scoreboard wait)
+__device__ __forceinline__ void red_add_u(uint32_t p, unsigned v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ void red_add(int* p, int v) {
-  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(sh_addr(p)), "r"(v) : "memory");
+__device__ __forceinline__ void red_add_s(uint32_t p, int v) {
+  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ void red_min(int* p, int v) {
-  asm volatile("red.shared.min.s32 [%0], %1;" ::"r"(sh_addr(p)), "r"(v) : "memory");
+__device__ __forceinline__ void red_min_s(uint32_t p, int v) {
+  asm volatile("red.shared.min.s32 [%0], %1;" ::"r"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ void red_max(int* p, int v) {
-  asm volatile("red.shared.max.s32 [%0], %1;" ::"r"(sh_addr(p)), "r"(v) : "memory");
+__device__ __forceinline__ void red_max_s(uint32_t p, int v) {
+  asm volatile("red.shared.max.s32 [%0], %1;" ::"r"(p), "r"(v) : "memory");
 }
 
 // shared slot of fine column col in ring slot `slot` (padded layout, see BinArgs)
 __device__ __forceinline__ int sidx(const BinArgs& a, int slot, int col) {
+  if (a.gs == a.f) return slot * a.rstride + col;  // groups without padding
   const int cg = (int)fdiv((uint32_t)col, a.div_f);
   return slot * a.rstride + cg * a.gs + (col - cg * a.f);
 }
@@ -650,15 +654,16 @@ __device__ __forceinline__ void prefetch_batch(const BinArgs& a, int64_t i0, int
 
 __device__ __forceinline__ void accumulate(Smem& s, Meta& m, const BinArgs& a, int slot, int col, int z, uint32_t r,
                                            uint32_t g, uint32_t b) {
-  const int si = sidx(a, slot, col);
-  red_add(&s.cnt[si], 1u);
-  red_add(&s.rs[si], r);
-  red_add(&s.gs[si], g);
-  red_add(&s.bs[si], b);
-  red_add(&s.zlo[si], (unsigned)z & 0xffffu);
-  red_add(&s.zhi[si], z >> 16);
-  red_min(&s.mn[si], z);
-  red_max(&s.mx[si], z);
+  // the eight fine arrays lie s.fs bytes apart: cnt, rs, gs, bs, zlo, zhi, mn, mx
+  const uint32_t p = s.fa + 4u * (uint32_t)sidx(a, slot, col);
+  red_add_u(p, 1u);
+  red_add_u(p + s.fs, r);
+  red_add_u(p + 2u * s.fs, g);
+  red_add_u(p + 3u * s.fs, b);
+  red_add_u(p + 4u * s.fs, (unsigned)z & 0xffffu);
+  red_add_s(p + 5u * s.fs, z >> 16);
+  red_min_s(p + 6u * s.fs, z);
+  red_max_s(p + 7u * s.fs, z);
   m.touched[slot] = 1;
 }
 
