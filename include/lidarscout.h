@@ -129,6 +129,21 @@ ls_status ls_bin_points_fixed_scratch(const ls_points *pts, const ls_region *reg
                                       const ls_bins *levels, int32_t n_levels, uint64_t *dropped,
                                       ls_stream_t stream);
 
+/* ls_bin_points_accumulate -- ls_bin_points for points that arrive over several calls
+ * (Sec. 3.5: the full-resolution points of a tile reach the viewer chunk by chunk while
+ * it is on screen, and each chunk refines the tile's texels).  Adds this call's points
+ * into the existing accumulators of both levels: counts and the z and colour sums
+ * add, zmin / zmax take the minimum / maximum; cells without new points keep their
+ * values.  The bins must hold valid accumulators (an earlier ls_bin_points or
+ * ls_bin_points_accumulate call, or the empty-cell values).  The result equals one
+ * ls_bin_points call over the union of the points, bit for bit, in any split and
+ * order.  dropped: device uint64[1] or NULL, incremented by the number of this call's
+ * points outside the region.  Every touched row is merged with global atomics, so a
+ * call costs more per point than ls_bin_points.  Scratch and errors as ls_bin_points. */
+ls_status ls_bin_points_accumulate(const ls_points *pts, const ls_region *region,
+                                   const ls_bins *levels, int32_t n_levels, uint64_t *dropped,
+                                   ls_stream_t stream);
+
 /* Diagnostics of ls_bin_points, cumulative over calls (synchronous copy):
  * out[0] points that arrived after their row left the CTA's window (merged with
  * global atomics), out[1] waits on a row another CTA was writing, out[2] such waits

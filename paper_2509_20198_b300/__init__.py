@@ -77,10 +77,14 @@ def _bins_struct(b, cells):
     return N.LsBins(cells, *[_ptr(_dev(b[k], k)) for k in BIN_KEYS])
 
 
-def bin_points(points, region, levels=(640, 64), out=None, dropped=None, stream=None):
+def bin_points(points, region, levels=(640, 64), out=None, dropped=None, stream=None, accumulate=False):
     """Exact per-cell count / z-sum / z-min / z-max / RGB sums at one or two levels.
 
+    accumulate=True adds the points into the bins and the dropped count given in `out`
+    and `dropped` (points that arrive over several calls); both are then required.
     Returns (list of bin dicts, dropped tensor int64[1])."""
+    if accumulate and (out is None or dropped is None):
+        raise ValueError("accumulate=True needs the existing bins (out) and dropped counter")
     T = int(region.tiles_x) * int(region.tiles_y)
     dev = points["x"].device
     if out is None:
@@ -90,8 +94,9 @@ def bin_points(points, region, levels=(640, 64), out=None, dropped=None, stream=
     arr = (N.LsBins * len(levels))(*[_bins_struct(b, c) for b, c in zip(out, levels)])
     pts = _points(points)
     reg = _region(region)
-    N.check("ls_bin_points", N.lib().ls_bin_points(ctypes.byref(pts), ctypes.byref(reg), arr,
-                                                  len(levels), _ptr(dropped), _stream(stream)))
+    fn = "ls_bin_points_accumulate" if accumulate else "ls_bin_points"
+    N.check(fn, getattr(N.lib(), fn)(ctypes.byref(pts), ctypes.byref(reg), arr, len(levels), _ptr(dropped),
+                                     _stream(stream)))
     return out, dropped
 
 

@@ -59,6 +59,7 @@ P = ctypes.POINTER
 SIGNATURES = {
     "ls_bin_points": ([P(LsPoints), P(LsRegion), P(LsBins), I32, VP, VP], I32),
     "ls_bin_points_fixed_scratch": ([P(LsPoints), P(LsRegion), P(LsBins), I32, VP, VP], I32),
+    "ls_bin_points_accumulate": ([P(LsPoints), P(LsRegion), P(LsBins), I32, VP, VP], I32),
     "ls_bin_stats": ([VP, I32], I32),
     "ls_extract_samples": ([P(LsPoints), I64, I32, VP, P(LsSampleBuffers), I64, VP], I32),
     "ls_fill_sparse": ([P(LsPoints), P(LsRegion), P(LsFillParams), VP, I64, VP, VP, VP], I32),

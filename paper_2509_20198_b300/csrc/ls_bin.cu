@@ -83,6 +83,7 @@ struct BinArgs {
   // rows are rstride slots apart; the coarse partials split a coarse cell's f columns
   // at fh (gs and fh chosen against bank conflicts, see bin_coarse_layout)
   int32_t gs, rstride, fh;
+  int32_t accumulate;  // add into the existing bins: every flushed row merges with atomics
 };
 
 // shared-memory layout (dynamic).  Every fine accumulator is a 32-bit word (32-bit
@@ -272,9 +273,10 @@ __device__ __forceinline__ int sidx(const BinArgs& a, int slot, int col) {
 
 // A point whose row already left this CTA's window: claim the row if nobody has
 // written it yet (single thread writes sentinels), then merge with global atomics.
+// When accumulating, the row already holds valid bins: merge at once.
 __device__ void late_point(const BinArgs& a, int G, int col, int z, uint32_t r, uint32_t g, uint32_t b) {
   uint32_t* st = &a.row_state[G];
-  if (ld_acquire(st) != 2u) {
+  if (!a.accumulate && ld_acquire(st) != 2u) {
     if (atomicCAS(st, 0u, 1u) == 0u) {
       const int64_t base = (int64_t)G * a.cells;
       for (int c = 0; c < a.cells; ++c) store_empty_cell(a, base + c);
@@ -497,7 +499,7 @@ __device__ void evict_rows(const BinArgs& a, Smem& s, Meta& m, int ra, int rb, i
     const int slot = G & (W - 1);
     int mode = 0;
     if (m.touched[slot]) {
-      mode = (atomicCAS(&a.row_state[G], 0u, 1u) == 0u) ? 1 : 2;
+      mode = (!a.accumulate && atomicCAS(&a.row_state[G], 0u, 1u) == 0u) ? 1 : 2;
       m.touched[slot] = 0;
     }
     m.mode[threadIdx.x] = mode;
@@ -556,7 +558,7 @@ __device__ void evict_rows(const BinArgs& a, Smem& s, Meta& m, int ra, int rb, i
       if (m.mode[threadIdx.x] == 1) {
         __threadfence();
         atomicExch(&a.row_state[G], 2u);
-      } else if (m.mode[threadIdx.x] == 2) {
+      } else if (m.mode[threadIdx.x] == 2 && !a.accumulate) {
         wait_written(&a.row_state[G]);
       }
     }
@@ -837,18 +839,20 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
 }
 
 // Prologue: clear row states and the dropped counter; give the coarse level its
-// empty sentinels (it is only ever merged into with atomics).
+// empty sentinels (it is only ever merged into with atomics).  When accumulating, the
+// bins and the dropped counter keep their contents.
 __global__ void k_bin_prologue(BinArgs a, int64_t n_coarse) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n_rows; i += stride)
     a.row_state[i] = 0u;
+  if (a.accumulate) n_coarse = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_coarse; i += stride) {
     a.ccount[i] = 0u; a.czsum[i] = 0; a.czmin[i] = INT_MAX; a.czmax[i] = INT_MIN;
     a.crsum[i] = 0ull; a.cgsum[i] = 0ull; a.cbsum[i] = 0ull;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.row_state[a.n_rows] = 0u;  // span counter
-    if (a.dropped) *a.dropped = 0ull;
+    if (a.dropped && !a.accumulate) *a.dropped = 0ull;
   }
 }
 
@@ -992,7 +996,7 @@ ls_status bin_launch(BinArgs a, size_t smem, int64_t n_coarse, cudaStream_t stre
   if (a.n_items > 0) {
     k_bin_main<<<grid_cap(a.n_items, kSmCount), kBinThreads, smem, stream>>>(a);
   }
-  k_bin_finalize<<<grid_cap(a.n_rows, kSmCount * 16), 128, 0, stream>>>(a);
+  if (!a.accumulate) k_bin_finalize<<<grid_cap(a.n_rows, kSmCount * 16), 128, 0, stream>>>(a);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 
@@ -1015,6 +1019,20 @@ extern "C" ls_status ls_bin_points(const ls_points* pts, const ls_region* region
   int64_t n_coarse = 0;
   ls_status st = ls::bin_prepare(pts, region, levels, n_levels, dropped, &a, &smem, &n_coarse);
   if (st != LS_OK) return st;
+  a.row_state = static_cast<uint32_t*>(ls::workspace(ls::kWsBinRows, ((size_t)a.n_rows + 1) * 4));
+  if (!a.row_state) return LS_ERR_NO_MEMORY;
+  return ls::bin_launch(a, smem, n_coarse, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" ls_status ls_bin_points_accumulate(const ls_points* pts, const ls_region* region,
+                                              const ls_bins* levels, int32_t n_levels, uint64_t* dropped,
+                                              ls_stream_t stream) {
+  ls::BinArgs a;
+  size_t smem = 0;
+  int64_t n_coarse = 0;
+  ls_status st = ls::bin_prepare(pts, region, levels, n_levels, dropped, &a, &smem, &n_coarse);
+  if (st != LS_OK) return st;
+  a.accumulate = 1;
   a.row_state = static_cast<uint32_t*>(ls::workspace(ls::kWsBinRows, ((size_t)a.n_rows + 1) * 4));
   if (!a.row_state) return LS_ERR_NO_MEMORY;
   return ls::bin_launch(a, smem, n_coarse, reinterpret_cast<cudaStream_t>(stream));

@@ -1,6 +1,7 @@
 """GPU parity of ls_bin_points against the serial oracle: bit-exact on every
 accumulator, both levels, for stream order, shuffled order, unaligned pointers,
-empty input, and sampled tiles of the full-size 16x16-tile lognormal region."""
+empty input, points split over several accumulating calls, and sampled tiles of the
+full-size 16x16-tile lognormal region."""
 import numpy as np
 import pytest
 
@@ -86,6 +87,60 @@ def test_unaligned_pointers_use_scalar_path(lsb):
     ref = oracle.bin_points({k: pts[k][1:] for k in "xyzrgb"}, region, 640)
     assert_bins_equal(out[0], ref, msg="unaligned")
     assert int(dropped.item()) == ref["dropped"]
+
+
+def _accumulate_parts(lsb, region, parts, levels=(640, 64), out=None, dropped=None):
+    import torch
+    for i, part in enumerate(parts):
+        d = to_device(part)
+        if out is None:
+            out, dropped = lsb.bin_points(d, region, levels=levels)
+        else:
+            lsb.bin_points(d, region, levels=levels, out=out, dropped=dropped, accumulate=True)
+    torch.cuda.synchronize()
+    assert lsb.last_error() == 0
+    return out, dropped
+
+
+@pytest.mark.parametrize("cuts", [(0.3, 0.71), (0.5,), (1e-6, 0.999999)])
+def test_accumulate_over_split_calls_equals_one_call(lsb, cuts):
+    """Points that arrive over several calls (the first overwrites, the rest add):
+    the bins equal the oracle over the union of the points, bit for bit, at both
+    levels; splits fall inside strips, one part is empty and one holds a single point."""
+    region, pts = _small_region()
+    n = len(pts["x"])
+    idx = [0] + [int(c * n) for c in cuts] + [n]
+    parts = [{k: pts[k][a:b] for k in "xyzrgb"} for a, b in zip(idx[:-1], idx[1:])]
+    out, dropped = _accumulate_parts(lsb, region, parts)
+    for b, c in zip(out, (640, 64)):
+        ref = oracle.bin_points(pts, region, c)
+        assert_bins_equal(b, ref, msg=f"cuts={cuts} cells={c}")
+    assert int(dropped.item()) == ref["dropped"]
+
+
+def test_accumulate_shuffled_parts_onto_empty_bins(lsb):
+    """Accumulating into bins that hold the empty-cell values (and a dropped counter
+    that starts at 5) equals one call over all points; the parts are shuffled, so
+    rows are touched by several calls and late points occur within a call."""
+    import torch
+    region, pts = _small_region()
+    perm = np.random.default_rng(13).permutation(len(pts["x"]))
+    sh = {k: pts[k][perm] for k in "xyzrgb"}
+    T = region.n_tiles
+    out = []
+    for c in (640, 64):
+        b = lsb.empty_bins(T, c)
+        b["count"].zero_(); b["zsum"].zero_(); b["rsum"].zero_(); b["gsum"].zero_(); b["bsum"].zero_()
+        b["zmin"].fill_(np.iinfo(np.int32).max); b["zmax"].fill_(np.iinfo(np.int32).min)
+        out.append(b)
+    dropped = torch.full((1,), 5, dtype=torch.int64, device="cuda")
+    n = len(sh["x"])
+    parts = [{k: sh[k][a:b] for k in "xyzrgb"} for a, b in ((0, n // 3), (n // 3, n))]
+    out, dropped = _accumulate_parts(lsb, region, parts, out=out, dropped=dropped)
+    for b, c in zip(out, (640, 64)):
+        ref = oracle.bin_points(pts, region, c)
+        assert_bins_equal(b, ref, msg=f"shuffled parts cells={c}")
+    assert int(dropped.item()) == ref["dropped"] + 5
 
 
 def test_empty_input_gives_sentinels(lsb):
