@@ -198,6 +198,18 @@ def run_b300(args, rank, world):
         pts = sg.region_points(replica_seed(SEED, rank), region, counts, device=dev, stream=stream)
     stream.synchronize()
     step = Step(lsb, region, counts, pts, stream)
+    # launch shapes of the binning and the fill, measured on this workload (the graph
+    # below captures the launches with the shapes chosen here)
+    tuned = {}
+    with torch.cuda.stream(stream):
+        shape, ms, _, _ = lsb.tune_bin_points(pts, region, levels=(640, 64), out=step.bins, dropped=step.dropped,
+                                              reps=5, stream=stream)
+        tuned["bin"] = {**shape, "ms": round(ms, 4)}
+        lsb.extract_samples_into(pts, step.samples, step.cap, stream=stream)
+        shape, ms, _, _ = lsb.tune_fill_sparse(step.samples, region, height=step.height, rgb=step.rgb, reps=5,
+                                               stream=stream)
+        tuned["fill"] = {**shape, "ms": round(ms, 4)}
+    stream.synchronize()
     # warm-up outside the graph (allocates the library workspace), then capture
     lsb.bin_stats(reset=True)
     with torch.cuda.stream(stream):
@@ -272,7 +284,8 @@ def run_b300(args, rank, world):
         "data": "synthetic (seeded fBm terrain, LAZ strip order)",
         "config": {"workload": WORKLOAD, "tiles_per_gpu": T, "points_per_gpu": n_points,
                    "fill_res": 64, "radius_m": 120, "sigma_m": 40, "parallelism": f"replicas{world}",
-                   "l2": "inputs (~10 GB) larger than L2, no flush", "graph": "one CUDA graph per step"},
+                   "l2": "inputs (~10 GB) larger than L2, no flush", "graph": "one CUDA graph per step",
+                   "autotuned": tuned},
         "points_binned_per_s": round(job_rate(world, n_points, ms_step), 1),
         "bin_only": {"ms": round(ms_bin, 4), "points_per_s": round(n_points / (ms_bin * 1e-3), 1)},
         "bin_accumulate": {"calls": 4, "ms": round(ms_acc, 4), "points_per_s": round(n_points / (ms_acc * 1e-3), 1),

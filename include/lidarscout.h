@@ -205,6 +205,67 @@ ls_status ls_update_tile(const ls_bins *bins, const ls_region *region, const int
                          int64_t n, float *height, uint8_t *rgb, ls_stream_t stream);
 
 /* ---------------------------------------------------------------------------------
+ * Launch shapes and their autotuner.  The paper processes its patches in batches
+ * because batching pays off (Sec. 4.2); the batched launches here have shape
+ * parameters whose best values depend on the workload, chosen by measurement.
+ *
+ * A call's key is made of the arguments that decide its best shape: for binning the
+ * number of levels, their cell counts and floor(log2(n points)); for the fill the
+ * resolution, the radius, floor(log2(n_out)) and floor(log2(n samples)).  A table
+ * (per process, up to 256 keys, the oldest replaced) maps keys to shapes; a call whose
+ * key has no entry uses the default shape.  Lookups are host-only: calls stay
+ * asynchronous and capturable in CUDA graphs.
+ * ------------------------------------------------------------------------------- */
+typedef struct {
+  int32_t spans_per_cta;     /* work spans per CTA of the binning launch, 1..256 (default 16) */
+  int32_t prefetch_batches;  /* L2 prefetch distance of the point stream, in 4096-point
+                                batches, 1..4 (default 2) */
+} ls_bin_shape;
+
+typedef struct {
+  int32_t split;        /* CTAs per tile, each a band of res / split texel rows: 1, or 2
+                           or 4 when res is a multiple of 16 * split (default 4 for fewer
+                           than 592 tiles and res a multiple of 64, else 1) */
+  int32_t ctas_per_sm;  /* resident CTAs per SM the persistent grid is sized for: 1 or 2
+                           (default 2) */
+} ls_fill_shape;
+
+/* The shape a binning call with these arguments uses (the table's entry or the
+ * default).  Only pts->n, the levels' cells and n_levels are read (host memory). */
+ls_status ls_bin_shape_get(const ls_points *pts, const ls_bins *levels, int32_t n_levels,
+                           ls_bin_shape *out);
+/* Pins a shape for the key of these arguments; shape NULL removes the entry.
+ * LS_ERR_INVALID_ARG for a shape outside the ranges above. */
+ls_status ls_bin_shape_set(const ls_points *pts, const ls_bins *levels, int32_t n_levels,
+                           const ls_bin_shape *shape);
+/* The same for the fill (samples->n, params->res, params->radius_cm and n_out are read). */
+ls_status ls_fill_shape_get(const ls_points *samples, const ls_fill_params *params, int64_t n_out,
+                            ls_fill_shape *out);
+ls_status ls_fill_shape_set(const ls_points *samples, const ls_fill_params *params, int64_t n_out,
+                            const ls_fill_shape *shape);
+/* Removes every entry. */
+ls_status ls_tune_clear(void);
+
+/* Autotuners: time the call on the caller's own data with every candidate shape
+ * (binning: spans per CTA 8, 16, 32 x prefetch 1, 2, 3 batches; fill: split 1, 2, 4 x
+ * 1, 2 CTAs per SM, the valid ones), store the best for the call's key and return it
+ * with its median time in ms per call (best / best_ms may be NULL).  Each candidate
+ * runs once untimed, then the candidates are timed round-robin for `reps` rounds of
+ * two calls (CUDA events on `stream`), so drifts of clocks or cache state hit all of
+ * them alike; the score is the median over the rounds, and a candidate replaces the
+ * default shape only when its median is at least 1 % lower.  The outputs end as one
+ * call computes them: every shape gives the same results, bit for bit.  Synchronises
+ * the stream; LS_ERR_INVALID_ARG while the stream is being captured or for reps
+ * outside 1..1000; otherwise the errors of the tuned call. */
+ls_status ls_tune_bin_points(const ls_points *pts, const ls_region *region, const ls_bins *levels,
+                             int32_t n_levels, uint64_t *dropped, int32_t reps, ls_stream_t stream,
+                             ls_bin_shape *best, float *best_ms);
+ls_status ls_tune_fill_sparse(const ls_points *samples, const ls_region *region,
+                              const ls_fill_params *params, const int32_t *tile_ids, int64_t n_out,
+                              float *height, uint8_t *rgb, int32_t reps, ls_stream_t stream,
+                              ls_fill_shape *best, float *best_ms);
+
+/* ---------------------------------------------------------------------------------
  * ls_fill_interp -- the interpolated heightmaps of Alg. 1 (Sec. 3.3): for each
  * requested tile, the nearest-neighbour (NN) and the Delaunay-linear maps of the
  * samples in a padded patch, the network inputs of the paper's filler.

@@ -100,6 +100,93 @@ def bin_points(points, region, levels=(640, 64), out=None, dropped=None, stream=
     return out, dropped
 
 
+def _shape_points(points):
+    """An ls_points view for the shape table: only the count is read (host side)."""
+    return N.LsPoints(None, None, None, None, None, None, int(points["x"].numel()), None)
+
+
+def _level_structs(levels):
+    return (N.LsBins * len(levels))(*[N.LsBins(int(c), None, None, None, None, None, None, None) for c in levels])
+
+
+def bin_shape(points, levels=(640, 64)):
+    """Launch shape {spans_per_cta, prefetch_batches} that binning these points uses."""
+    out = N.LsBinShape()
+    N.check("ls_bin_shape_get", N.lib().ls_bin_shape_get(ctypes.byref(_shape_points(points)), _level_structs(levels),
+                                                        len(levels), ctypes.byref(out)))
+    return {"spans_per_cta": out.spans_per_cta, "prefetch_batches": out.prefetch_batches}
+
+
+def set_bin_shape(points, levels=(640, 64), shape=None):
+    """Pins a binning launch shape (dict) for calls like this one; None removes it."""
+    sh = None if shape is None else ctypes.byref(N.LsBinShape(int(shape["spans_per_cta"]),
+                                                              int(shape["prefetch_batches"])))
+    N.check("ls_bin_shape_set", N.lib().ls_bin_shape_set(ctypes.byref(_shape_points(points)), _level_structs(levels),
+                                                        len(levels), sh))
+
+
+def fill_shape(samples, n_out, res=64, radius_cm=12000, sigma_cm=4000.0):
+    """Launch shape {split, ctas_per_sm} of a Gaussian fill call like this one."""
+    out = N.LsFillShape()
+    prm = N.LsFillParams(res, radius_cm, sigma_cm)
+    N.check("ls_fill_shape_get", N.lib().ls_fill_shape_get(ctypes.byref(_shape_points(samples)), ctypes.byref(prm),
+                                                          int(n_out), ctypes.byref(out)))
+    return {"split": out.split, "ctas_per_sm": out.ctas_per_sm}
+
+
+def set_fill_shape(samples, n_out, res=64, radius_cm=12000, sigma_cm=4000.0, shape=None):
+    """Pins a fill launch shape (dict) for calls like this one; None removes it."""
+    prm = N.LsFillParams(res, radius_cm, sigma_cm)
+    sh = None if shape is None else ctypes.byref(N.LsFillShape(int(shape["split"]), int(shape["ctas_per_sm"])))
+    N.check("ls_fill_shape_set", N.lib().ls_fill_shape_set(ctypes.byref(_shape_points(samples)), ctypes.byref(prm),
+                                                          int(n_out), sh))
+
+
+def tune_clear():
+    """Forgets every tuned or pinned launch shape."""
+    N.check("ls_tune_clear", N.lib().ls_tune_clear())
+
+
+def tune_bin_points(points, region, levels=(640, 64), out=None, dropped=None, reps=5, stream=None):
+    """Times every candidate binning shape on these points, keeps the fastest for calls
+    like this one and leaves the bins computed.  Returns (shape dict, ms per call, out,
+    dropped)."""
+    T = int(region.tiles_x) * int(region.tiles_y)
+    dev = points["x"].device
+    if out is None:
+        out = [empty_bins(T, c, dev) for c in levels]
+    if dropped is None:
+        dropped = torch.empty(1, dtype=torch.int64, device=dev)
+    arr = (N.LsBins * len(levels))(*[_bins_struct(b, c) for b, c in zip(out, levels)])
+    best, ms = N.LsBinShape(), ctypes.c_float()
+    N.check("ls_tune_bin_points", N.lib().ls_tune_bin_points(
+        ctypes.byref(_points(points)), ctypes.byref(_region(region)), arr, len(levels), _ptr(dropped), int(reps),
+        _stream(stream), ctypes.byref(best), ctypes.byref(ms)))
+    return {"spans_per_cta": best.spans_per_cta, "prefetch_batches": best.prefetch_batches}, ms.value, out, dropped
+
+
+def tune_fill_sparse(samples, region, tile_ids=None, res=64, radius_cm=12000, sigma_cm=4000.0, height=None,
+                     rgb=None, reps=5, stream=None):
+    """Times every valid fill shape on these samples, keeps the fastest for calls like
+    this one and leaves the maps filled.  Returns (shape dict, ms per call, height, rgb)."""
+    T = int(region.tiles_x) * int(region.tiles_y)
+    dev = samples["x"].device
+    if tile_ids is not None:
+        tile_ids = _dev(tile_ids.to(device=dev, dtype=torch.int32).contiguous(), "tile_ids")
+    n = T if tile_ids is None else tile_ids.numel()
+    if height is None:
+        height = torch.empty((n, res, res), dtype=torch.float32, device=dev)
+    if rgb is None:
+        rgb = torch.empty((n, res, res, 3), dtype=torch.uint8, device=dev)
+    prm = N.LsFillParams(res, radius_cm, sigma_cm)
+    best, ms = N.LsFillShape(), ctypes.c_float()
+    N.check("ls_tune_fill_sparse", N.lib().ls_tune_fill_sparse(
+        ctypes.byref(_points(samples, need_offsets=True)), ctypes.byref(_region(region)), ctypes.byref(prm),
+        _ptr(tile_ids), n, _ptr(_dev(height, "height")), _ptr(_dev(rgb, "rgb")), int(reps), _stream(stream),
+        ctypes.byref(best), ctypes.byref(ms)))
+    return {"split": best.split, "ctas_per_sm": best.ctas_per_sm}, ms.value, height, rgb
+
+
 def bin_stats(reset=True):
     """Binning diagnostics: late points, cross-CTA waits, waits that ran out, in-place
     flushes (cumulative since the last reset)."""

@@ -51,6 +51,14 @@ class LsConvShape(ctypes.Structure):
     _fields_ = [("n", I32), ("h", I32), ("w", I32), ("cin", I32), ("cout", I32)]
 
 
+class LsBinShape(ctypes.Structure):
+    _fields_ = [("spans_per_cta", I32), ("prefetch_batches", I32)]
+
+
+class LsFillShape(ctypes.Structure):
+    _fields_ = [("split", I32), ("ctas_per_sm", I32)]
+
+
 class LsSampleBuffers(ctypes.Structure):
     _fields_ = [("x", VP), ("y", VP), ("z", VP), ("r", VP), ("g", VP), ("b", VP)]
 
@@ -61,6 +69,14 @@ SIGNATURES = {
     "ls_bin_points_fixed_scratch": ([P(LsPoints), P(LsRegion), P(LsBins), I32, VP, VP], I32),
     "ls_bin_points_accumulate": ([P(LsPoints), P(LsRegion), P(LsBins), I32, VP, VP], I32),
     "ls_bin_stats": ([VP, I32], I32),
+    "ls_bin_shape_get": ([P(LsPoints), P(LsBins), I32, P(LsBinShape)], I32),
+    "ls_bin_shape_set": ([P(LsPoints), P(LsBins), I32, P(LsBinShape)], I32),
+    "ls_fill_shape_get": ([P(LsPoints), P(LsFillParams), I64, P(LsFillShape)], I32),
+    "ls_fill_shape_set": ([P(LsPoints), P(LsFillParams), I64, P(LsFillShape)], I32),
+    "ls_tune_clear": ([], I32),
+    "ls_tune_bin_points": ([P(LsPoints), P(LsRegion), P(LsBins), I32, VP, I32, VP, P(LsBinShape), P(FLT)], I32),
+    "ls_tune_fill_sparse": ([P(LsPoints), P(LsRegion), P(LsFillParams), VP, I64, VP, VP, I32, VP, P(LsFillShape),
+                             P(FLT)], I32),
     "ls_extract_samples": ([P(LsPoints), I64, I32, VP, P(LsSampleBuffers), I64, VP], I32),
     "ls_fill_sparse": ([P(LsPoints), P(LsRegion), P(LsFillParams), VP, I64, VP, VP, VP], I32),
     "ls_update_tile": ([P(LsBins), P(LsRegion), VP, I64, VP, VP, VP], I32),

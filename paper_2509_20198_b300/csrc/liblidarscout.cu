@@ -3,6 +3,7 @@
 #include "ls_runtime.cu"
 #include "ls_bin.cu"
 #include "ls_fill.cu"
+#include "ls_tune.cu"
 #include "ls_interp.cu"
 #include "ls_render.cu"
 #include "ls_conv.cu"

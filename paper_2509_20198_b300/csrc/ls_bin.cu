@@ -43,8 +43,6 @@ constexpr int kMaxW = 64;
 constexpr int kCW = 4;  // coarse ring rows
 constexpr int kMaxWFlush = 8;  // window rows (W <= 8)
 constexpr int kBinSmemAttr = 224 * 1024;  // dynamic shared memory allowed (budget + margin)
-constexpr int kPfDist = 2;  // batches prefetched into L2 ahead of the loads
-constexpr int kSpansPerCta = 16;  // dynamic load balance vs. rows shared at span ends
 
 struct BinArgs {
   const int32_t* __restrict__ x;
@@ -84,6 +82,7 @@ struct BinArgs {
   // at fh (gs and fh chosen against bank conflicts, see bin_coarse_layout)
   int32_t gs, rstride, fh;
   int32_t accumulate;  // add into the existing bins: every flushed row merges with atomics
+  int32_t pf_dist;     // batches prefetched into L2 ahead of the loads (launch shape, 1..4)
 };
 
 // shared-memory layout (dynamic).  Every fine accumulator is a 32-bit word (32-bit
@@ -669,6 +668,9 @@ __device__ __forceinline__ void accumulate(Smem& s, Meta& m, const BinArgs& a, i
   m.touched[slot] = 1;
 }
 
+// PF: batches prefetched into L2 ahead of the loads (a launch-shape parameter, compiled
+// in so that it costs no register).
+template <int PF>
 __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Meta m;
@@ -700,10 +702,10 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
     int clo = -1;  // lowest coarse row of the coarse ring
     int batch = 0;
     Raw cur;
-    for (int d = 1; d < kPfDist; ++d) prefetch_batch(a, p0 + (int64_t)d * kBatch, p1);
+    for (int d = 1; d < PF; ++d) prefetch_batch(a, p0 + (int64_t)d * kBatch, p1);
     for (int64_t b0 = p0; b0 < p1; b0 += kBatch, ++batch) {
-      // keep the L2 kPfDist batches ahead of the loads
-      prefetch_batch(a, b0 + (int64_t)kPfDist * kBatch, p1);
+      // keep the L2 PF batches ahead of the loads
+      prefetch_batch(a, b0 + (int64_t)PF * kBatch, p1);
       load_raw(a, cur, b0 + (int64_t)threadIdx.x * kPtsPerThread, p1);
       int G[kPtsPerThread], col[kPtsPerThread];
       unsigned pend = 0;
@@ -971,9 +973,13 @@ ls_status bin_prepare(const ls_points* pts, const ls_region* region, const ls_bi
   a.y0_32 = a.narrow ? (int32_t)region->y0_cm : 0;
   a.vec = (((uintptr_t)a.x | (uintptr_t)a.y | (uintptr_t)a.z) % 16 == 0) &&
           (((uintptr_t)a.r | (uintptr_t)a.g | (uintptr_t)a.b) % 8 == 0);
-  // spans: about kSpansPerCta per CTA, multiples of the batch size
+  // launch shape: tuned for this key (ls_tune_bin_points / ls_bin_shape_set) or the default
+  BinShape shape;
+  bin_shape_lookup(bin_shape_key(pts->n, levels, n_levels), &shape);
+  a.pf_dist = shape.prefetch_batches;
+  // spans: about shape.spans_per_cta per CTA, multiples of the batch size
   const int64_t grid = kSmCount;
-  int64_t span = (a.n + grid * kSpansPerCta - 1) / (grid * kSpansPerCta);
+  int64_t span = (a.n + grid * shape.spans_per_cta - 1) / (grid * shape.spans_per_cta);
   span = (span + kBatch - 1) / kBatch * kBatch;
   if (span < kBatch) span = kBatch;
   a.span = span;
@@ -987,14 +993,22 @@ ls_status bin_launch(BinArgs a, size_t smem, int64_t n_coarse, cudaStream_t stre
   int dev = 0;
   LS_CUDA_TRY(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    LS_CUDA_TRY(cudaFuncSetAttribute(k_bin_main, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kBinSmemAttr));
+    LS_CUDA_TRY(cudaFuncSetAttribute(k_bin_main<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBinSmemAttr));
+    LS_CUDA_TRY(cudaFuncSetAttribute(k_bin_main<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBinSmemAttr));
+    LS_CUDA_TRY(cudaFuncSetAttribute(k_bin_main<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBinSmemAttr));
+    LS_CUDA_TRY(cudaFuncSetAttribute(k_bin_main<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBinSmemAttr));
     attr_set[dev] = true;
   }
   const int64_t work = a.n_rows > n_coarse ? a.n_rows : n_coarse;
   k_bin_prologue<<<grid_cap((work + 255) / 256, kSmCount * 8), 256, 0, stream>>>(a, n_coarse);
   if (a.n_items > 0) {
-    k_bin_main<<<grid_cap(a.n_items, kSmCount), kBinThreads, smem, stream>>>(a);
+    const int grid = grid_cap(a.n_items, kSmCount);
+    switch (a.pf_dist) {
+      case 1: k_bin_main<1><<<grid, kBinThreads, smem, stream>>>(a); break;
+      case 3: k_bin_main<3><<<grid, kBinThreads, smem, stream>>>(a); break;
+      case 4: k_bin_main<4><<<grid, kBinThreads, smem, stream>>>(a); break;
+      default: k_bin_main<2><<<grid, kBinThreads, smem, stream>>>(a); break;
+    }
   }
   if (!a.accumulate) k_bin_finalize<<<grid_cap(a.n_rows, kSmCount * 16), 128, 0, stream>>>(a);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;

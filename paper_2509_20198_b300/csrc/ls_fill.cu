@@ -539,9 +539,14 @@ ls_status fill_launch(const ls_points* samples, const ls_region* region, const l
       return LS_ERR_CUDA;
     attr_set[dev] = true;
   }
-  // few tiles: split each over 4 CTAs (bands of res / 4 texel rows, whole 4-row blocks)
-  f.split = (n_out < 4 * kSmCount && params->res % 64 == 0) ? 4 : 1;
-  k_fill<<<grid_cap(n_out * f.split, kSmCount * 2), kFillThreads, kStageCap * sizeof(Rec), s>>>(f);
+  // launch shape: tuned for this key (ls_tune_fill_sparse / ls_fill_shape_set), else the
+  // default: few tiles are split over 4 CTAs (bands of res / 4 texel rows, whole 4-row
+  // blocks), and the persistent grid assumes 2 resident CTAs per SM
+  FillShape shape;
+  fill_shape_lookup(fill_shape_key(samples->n, n_out, params), params->res, n_out, &shape);
+  f.split = shape.split;
+  k_fill<<<grid_cap(n_out * f.split, (int64_t)kSmCount * shape.ctas_per_sm), kFillThreads,
+           kStageCap * sizeof(Rec), s>>>(f);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 }  // namespace ls

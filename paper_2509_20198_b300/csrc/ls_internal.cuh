@@ -64,6 +64,21 @@ enum WorkspaceSlot {
 // Returns a device pointer of at least `bytes` for the given slot (nullptr on failure).
 void* workspace(WorkspaceSlot slot, size_t bytes);
 
+// ---------------------------------------------------------------------------------
+// Launch shapes and their autotuner (ls_tune.cu).  A call's key groups the arguments
+// that decide which shape is fastest; a table (per process) maps keys to the shape
+// ls_tune_* measured best or ls_*_shape_set pinned.  Keys without an entry use the
+// defaults.  Lookups are host-only and never synchronise (capturable in graphs).
+// ---------------------------------------------------------------------------------
+using BinShape = ls_bin_shape;
+using FillShape = ls_fill_shape;
+uint64_t bin_shape_key(int64_t n_points, const ls_bins* levels, int32_t n_levels);
+uint64_t fill_shape_key(int64_t n_samples, int64_t n_out, const ls_fill_params* params);
+void bin_shape_lookup(uint64_t key, BinShape* out);
+void fill_shape_lookup(uint64_t key, int32_t res, int64_t n_out, FillShape* out);
+bool bin_shape_valid(const BinShape& s);
+bool fill_shape_valid(const FillShape& s, int32_t res);
+
 inline int grid_cap(int64_t blocks, int64_t cap) {
   if (blocks < 1) blocks = 1;
   return (int)(blocks < cap ? blocks : cap);
