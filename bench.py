@@ -453,8 +453,28 @@ def run_overview(lsb, args, dev, stream):
                          "tiles_per_s": round(tile_steps / train_s, 1),
                          "tflops": round(TRAIN_FLOP_PER_TILE * tile_steps / train_s / 1e12, 1),
                          "loss_first": [round(v, 7) for v in hist[0]],
-                         "loss_last": [round(v, 7) for v in hist[-1]], "loss_parts": "total, height, colour, bound"},
+                         "loss_last": [round(v, 7) for v in hist[-1]], "loss_parts": "total, height, colour, bound",
+                         "recompute_per_level": recompute_study(lsb, filler, dev, stream)},
             "truth": "per-texel mean of the full-resolution points, 400 seeded tiles"}
+
+
+def recompute_study(lsb, trained, dev, stream, batch=256, reps=10):
+    """One training step (forward + backward) of the U-Net at batch 256 with every
+    activation kept and with activation recomputation per level: device memory of the
+    model and time per step (the gradients are bit-identical, tested)."""
+    import torch
+    out = {"batch": batch}
+    x = torch.randn((batch, 64, 64, 8), device=dev).to(torch.bfloat16).view(torch.int16)
+    dy = torch.randn((batch, 64, 64, 5), device=dev)
+    for name, rec in (("keep", False), ("recompute", True)):
+        f = lsb.Filler(max_batch=batch, device=dev, recompute=rec)
+        f.params.copy_(trained.params)
+        f.load(stream=stream)
+        with torch.cuda.stream(stream):
+            ms = _timed(lambda: (f.forward(x, stream=stream), f.backward(dy, stream=stream)), reps, stream)
+        out[name] = {"device_mb": round(f.device_bytes / 2 ** 20, 1), "ms_per_step": round(ms, 3)}
+        del f
+    return out
 
 
 def look_at(eye, target, fovy_deg, aspect, near=100.0, far=1e8):

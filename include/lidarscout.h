@@ -497,6 +497,18 @@ typedef struct ls_model ls_model;
 
 ls_status ls_model_create(int32_t levels, const int32_t *widths, int32_t res, int32_t max_batch,
                           ls_model **out);
+/* ls_model_create with options.  LS_MODEL_RECOMPUTE: activation recomputation per
+ * level, to bound the training memory at large batches (batch 256 in the workload).
+ * The first conv output of every level (e{l}a, d{l}a) lives in one buffer shared by
+ * all levels; ls_filler_forward consumes it at once and ls_filler_backward recomputes
+ * it from the level's stored input, one extra conv per level.  The kernels are
+ * deterministic, so outputs and gradients are bit-identical to those without the flag.
+ * Other flag bits: LS_ERR_INVALID_ARG. */
+#define LS_MODEL_RECOMPUTE 1
+ls_status ls_model_create_opts(int32_t levels, const int32_t *widths, int32_t res, int32_t max_batch,
+                               int32_t flags, ls_model **out);
+/* Device memory the model holds (packed weights, activations, gradient buffers). */
+size_t ls_model_device_bytes(const ls_model *model);
 void ls_model_destroy(ls_model *model);
 int64_t ls_model_param_count(const ls_model *model);
 int32_t ls_model_layer_count(const ls_model *model);

@@ -380,13 +380,17 @@ class Filler:
     Layer order and layout as in include/lidarscout.h; ``params`` is a plain CUDA
     tensor that the caller may update (then call :meth:`load`)."""
 
-    def __init__(self, widths=(32, 64, 128), res=64, max_batch=256, device="cuda"):
+    def __init__(self, widths=(32, 64, 128), res=64, max_batch=256, device="cuda", recompute=False):
+        """recompute=True: activation recomputation per level (less device memory, one
+        extra conv per level in backward, bit-identical results)."""
         self.widths, self.res, self.max_batch = tuple(widths), res, max_batch
         self.device = torch.device(device)
         h = ctypes.c_void_p()
         w = (ctypes.c_int32 * len(widths))(*widths)
-        N.check("ls_model_create", N.lib().ls_model_create(len(widths), w, res, max_batch, ctypes.byref(h)))
+        N.check("ls_model_create_opts", N.lib().ls_model_create_opts(len(widths), w, res, max_batch,
+                                                                    1 if recompute else 0, ctypes.byref(h)))
         self._h = h
+        self.device_bytes = N.lib().ls_model_device_bytes(h)
         self.n_params = N.lib().ls_model_param_count(h)
         self.params = torch.zeros(self.n_params, dtype=torch.float32, device=self.device)
 

@@ -99,6 +99,8 @@ SIGNATURES = {
     "ls_conv3x3_forward": ([VP, VP, VP, VP, I32, P(LsConvShape), VP, VP], I32),
     "ls_conv3x3_wgrad": ([VP, VP, P(LsConvShape), VP, VP, VP], I32),
     "ls_model_create": ([I32, VP, I32, I32, P(VP)], I32),
+    "ls_model_create_opts": ([I32, VP, I32, I32, I32, P(VP)], I32),
+    "ls_model_device_bytes": ([VP], ctypes.c_size_t),
     "ls_model_destroy": ([VP], None),
     "ls_model_param_count": ([VP], I64),
     "ls_model_layer_count": ([VP], I32),

@@ -363,6 +363,8 @@ struct ls_model {
   float* w0pad = nullptr;     // first layer weights padded to 8 input channels
   const uint16_t* x = nullptr;  // input of the last forward
   int last_n = 0;
+  int recompute = 0;           // e{l}a and d{l}a share one buffer; backward recomputes them
+  size_t device_bytes = 0;     // size of the arena
 };
 
 namespace ls {
@@ -384,9 +386,10 @@ int grid_for(int64_t work, int threads) { return grid_cap((work + threads - 1) /
 
 using namespace ls;
 
-extern "C" ls_status ls_model_create(int32_t levels, const int32_t* widths, int32_t res, int32_t max_batch,
-                                     ls_model** out) {
+extern "C" ls_status ls_model_create_opts(int32_t levels, const int32_t* widths, int32_t res, int32_t max_batch,
+                                          int32_t flags, ls_model** out) {
   if (!out || !widths || levels < 2 || levels > 4 || max_batch <= 0 || res <= 0) return LS_ERR_INVALID_ARG;
+  if (flags & ~LS_MODEL_RECOMPUTE) return LS_ERR_INVALID_ARG;
   if (res % (1 << (levels - 1))) return LS_ERR_INVALID_ARG;
   for (int l = 0; l < levels; ++l)
     if (widths[l] < 16 || widths[l] > 128 || widths[l] % 16) return LS_ERR_UNSUPPORTED;
@@ -395,6 +398,7 @@ extern "C" ls_status ls_model_create(int32_t levels, const int32_t* widths, int3
   m->levels = levels;
   m->res = res;
   m->max_batch = max_batch;
+  m->recompute = (flags & LS_MODEL_RECOMPUTE) ? 1 : 0;
   for (int l = 0; l < levels; ++l) m->widths[l] = widths[l];
   int64_t off = 0;
   auto add = [&](int cin, int cout, int k, int level, int h) {
@@ -448,7 +452,21 @@ extern "C" ls_status ls_model_create(int32_t levels, const int32_t* widths, int3
   size_t bytes = 0;
   auto take = [&](size_t nbytes) { size_t o = bytes; bytes += (nbytes + 255) / 256 * 256; return o; };
   std::vector<size_t> act_off;
-  for (auto& a : acts) act_off.push_back(take((size_t)a.second * 2));
+  // with recomputation the first conv output of every level (e{l}a, d{l}a) lives in one
+  // shared buffer: the forward consumes it at once, the backward recomputes it
+  int64_t max_first = 0;
+  for (int l = 1; l <= levels; ++l) {
+    const int64_t hw = (int64_t)(res >> (l - 1)) * (res >> (l - 1));
+    max_first = std::max<int64_t>(max_first, B * hw * widths[l - 1]);
+  }
+  const size_t first_off = m->recompute ? take((size_t)max_first * 2) : 0;
+  auto shared_first = [&](int slot) {
+    if (!m->recompute) return false;
+    for (int l = 1; l <= levels; ++l)
+      if (slot == slot_ea(l) || (l < levels && slot == slot_da(l))) return true;
+    return false;
+  };
+  for (auto& a : acts) act_off.push_back(shared_first(a.first) ? first_off : take((size_t)a.second * 2));
   size_t g_off[3];
   for (int i = 0; i < 3; ++i) g_off[i] = take((size_t)max_act * 2);
   size_t gs_off[4] = {0, 0, 0, 0};
@@ -474,6 +492,7 @@ extern "C" ls_status ls_model_create(int32_t levels, const int32_t* widths, int3
     return LS_ERR_NO_MEMORY;
   }
   char* base = static_cast<char*>(m->arena);
+  m->device_bytes = bytes;
   for (size_t i = 0; i < acts.size(); ++i) m->act[acts[i].first] = reinterpret_cast<uint16_t*>(base + act_off[i]);
   for (int i = 0; i < 3; ++i) m->gbuf[i] = reinterpret_cast<uint16_t*>(base + g_off[i]);
   for (int l = 1; l < levels; ++l) m->gskip[l - 1] = reinterpret_cast<uint16_t*>(base + gs_off[l - 1]);
@@ -489,6 +508,13 @@ extern "C" ls_status ls_model_create(int32_t levels, const int32_t* widths, int3
   *out = m;
   return LS_OK;
 }
+
+extern "C" ls_status ls_model_create(int32_t levels, const int32_t* widths, int32_t res, int32_t max_batch,
+                                     ls_model** out) {
+  return ls_model_create_opts(levels, widths, res, max_batch, 0, out);
+}
+
+extern "C" size_t ls_model_device_bytes(const ls_model* m) { return m ? m->device_bytes : 0; }
 
 extern "C" void ls_model_destroy(ls_model* m) {
   if (!m) return;
@@ -628,6 +654,15 @@ extern "C" ls_status ls_filler_backward(ls_model* m, const float* params, const 
     const LayerDesc& d = m->layers[li];
     return conv3x3_launch(dz, d.wpk_t, nullptr, mask, 0, n, d.h, d.h, d.cout, d.cin, dx, s);
   };
+  // recomputation: the first conv (layer li) of a level again, from its stored input,
+  // into the shared buffer; the kernel is deterministic, so the activation and every
+  // gradient equal those of a model that kept it
+  auto recompute = [&](int li) -> ls_status {
+    if (!m->recompute) return LS_OK;
+    const LayerDesc& d = m->layers[li];
+    return conv3x3_launch(lin[li], d.wpk, params + d.b_off, nullptr, 1, n, d.h, d.h, d.cin_pad, d.cout,
+                          const_cast<uint16_t*>(lin[li + 1]), s);
+  };
   ls_status st;
   // head
   uint16_t* gz = m->gbuf[0];
@@ -646,6 +681,7 @@ extern "C" ls_status ls_filler_backward(ls_model* m, const float* params, const 
   for (int l = 1; l < L; ++l, li -= 2) {
     const int h = R >> (l - 1);
     // layer li = d{l}b, li-1 = d{l}a
+    if ((st = recompute(li - 1)) != LS_OK) return st;
     if ((st = wgrad(li, gz)) != LS_OK) return st;
     uint16_t* gz2 = m->gbuf[(gi + 1) % 3];
     if ((st = dgrad(li, gz, lin[li], gz2)) != LS_OK) return st;  // masked by d{l}a > 0
@@ -673,6 +709,7 @@ extern "C" ls_status ls_filler_backward(ls_model* m, const float* params, const 
       gi = (gi + 1) % 3;
       gz = dz;
     }
+    if ((st = recompute(li - 1)) != LS_OK) return st;
     if ((st = wgrad(li, gz)) != LS_OK) return st;
     uint16_t* gz2 = m->gbuf[(gi + 1) % 3];
     if ((st = dgrad(li, gz, lin[li], gz2)) != LS_OK) return st;  // masked by e{l}a > 0

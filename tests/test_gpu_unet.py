@@ -147,6 +147,28 @@ def test_backward_matches_oracle_and_torch(lsb):
         assert rb < bar, (name, msg, rb, bar)
 
 
+@pytest.mark.parametrize("widths", [(32, 64, 128), (16, 32)])
+def test_recompute_per_level_is_bit_identical_and_smaller(lsb, widths):
+    """Activation recomputation per level: the outputs and every gradient equal those
+    of the model that keeps all activations, bit for bit, in less device memory."""
+    import torch
+    n = 8
+    f, layers, params, q, xb, xo = _setup(lsb, widths, n, seed=5)
+    g = lsb.Filler(widths=widths, res=64, max_batch=max(n, 2), recompute=True)
+    g.params.copy_(f.params)
+    g.load()
+    assert g.device_bytes < f.device_bytes
+    x = torch.from_numpy(xb.view(np.int16)).cuda()
+    dy = torch.from_numpy(np.random.default_rng(6).standard_normal((n, 64, 64, 5)).astype(np.float32)).cuda()
+    y1, y2 = f.forward(x), g.forward(x)
+    g1, g2 = f.backward(dy), g.backward(dy)
+    torch.cuda.synchronize()
+    assert lsb.last_error() == 0
+    assert torch.equal(y1, y2)
+    assert torch.equal(g1, g2)
+    assert float(g1.abs().sum()) > 0
+
+
 def test_loss_and_adamw_match_oracle(lsb):
     import torch
     rng = np.random.default_rng(7)
