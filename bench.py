@@ -234,13 +234,14 @@ def run_b300(args, rank, world):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev.index) as clocks:
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
+        # an event between consecutive replays: the whole region and every single step
+        step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        t0, t1 = step_ev[0], step_ev[-1]
         with torch.cuda.stream(stream):
             t0.record(stream)
             for k in range(args.steps):
                 graph.replay()
-            t1.record(stream)
+                step_ev[k + 1].record(stream)
         torch.cuda.synchronize()
         # binning alone (its own timing pass, same stream, not graph-fused with the rest)
         for k in range(args.steps):
@@ -264,6 +265,7 @@ def run_b300(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     ms_total = t0.elapsed_time(t1)
+    step_ms = sorted(step_ev[k].elapsed_time(step_ev[k + 1]) for k in range(args.steps))
     ms_bin = float(np.mean([bin_ev[2 * k].elapsed_time(bin_ev[2 * k + 1]) for k in range(args.steps)]))
     ms_acc = acc_ev[0].elapsed_time(acc_ev[1]) / n_acc
     assert lsb.last_error() == 0
@@ -287,6 +289,8 @@ def run_b300(args, rank, world):
                    "l2": "inputs (~10 GB) larger than L2, no flush", "graph": "one CUDA graph per step",
                    "autotuned": tuned},
         "points_binned_per_s": round(job_rate(world, n_points, ms_step), 1),
+        "step_ms": {"median": round(step_ms[len(step_ms) // 2], 4), "best": round(step_ms[0], 4),
+                    "worst": round(step_ms[-1], 4), "rank": 0},
         "bin_only": {"ms": round(ms_bin, 4), "points_per_s": round(n_points / (ms_bin * 1e-3), 1)},
         "bin_accumulate": {"calls": 4, "ms": round(ms_acc, 4), "points_per_s": round(n_points / (ms_acc * 1e-3), 1),
                            "note": "the same points in four calls, three of them adding into the bins"},
