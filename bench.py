@@ -348,6 +348,7 @@ def run_overview(lsb, args, dev, stream):
 
     with torch.cuda.stream(stream):
         ms_gauss = timed(lambda: lsb.fill_sparse(s, region, height=h, rgb=c, stream=stream), args.steps)
+    fill_bytes = 7 * nT * 64 * 64 + 32 * int(s["x"].numel())
     # the viewer's frame: every tile's Gaussian-fill heightmap as a mesh plus the chunk
     # samples, 1080p, oblique view of the whole region
     cam = region_camera(region)
@@ -432,7 +433,11 @@ def run_overview(lsb, args, dev, stream):
     paper = run_paper_cnn(lsb, args, dev, stream, s, region, nT, sub_t, rm, rc, timed)
     return {"workload": "overview 200x200 tiles, 4 pts/m^2, 33 samples/tile (1.32M samples)",
             "gaussian_fill": {"tiles_per_s": round(nT / (ms_gauss * 1e-3), 1), "ms": round(ms_gauss, 3),
-                              "height_rmse_m": round(rm(h[sub_t]), 4), "rgb_rmse_8bit": round(rc(c[sub_t]), 3)},
+                              "height_rmse_m": round(rm(h[sub_t]), 4), "rgb_rmse_8bit": round(rc(c[sub_t]), 3),
+                              # algorithmic bytes: 7 B per texel written, 32 B per packed sample read
+                              "achieved_gbs": round(fill_bytes / (ms_gauss * 1e-3) / 1e9, 1),
+                              "frac_of_hbm": round(fill_bytes / (ms_gauss * 1e-3) / 1e9 / peaks()[0], 4),
+                              "bound": "issue (about 10 candidate tests and 3.6 exp per texel)"},
             "render": render,
             "paper_cnn": paper,
             "interp_fill": {"tiles_per_s": round(nT / (ms_interp * 1e-3), 1), "ms": round(ms_interp, 3),
