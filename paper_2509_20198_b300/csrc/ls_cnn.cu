@@ -51,26 +51,30 @@ struct CnnLayer {
 
 // ---- fp32 tiled GEMM: C[m][n] = act(sum_k A(m,k) B(k,n) + bias[n]) * [mask(m,n) > 0]
 // with A(m,k) = A[m sam + k sak], B(k,n) = B[k sbk + n sbn]; one thread per 4 x 4 block
-// of C, k in increasing order (deterministic).
+// of C, k in increasing order (deterministic).  With split-K (gridDim.z > 1) the CTAs
+// of slice z sum k in [z kc, (z + 1) kc) into part[z][M][N] (no bias, activation or
+// mask), and k_gemm_reduce adds the slices in increasing z: still one fixed order.
 constexpr int kGt = 64, kGk = 16;
 __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float* __restrict__ A, int64_t sam,
                                               int64_t sak, const float* __restrict__ B, int64_t sbk, int64_t sbn,
                                               float* __restrict__ C, int64_t ldc, const float* __restrict__ bias,
-                                              int relu, const float* __restrict__ mask, int64_t ldm) {
+                                              int relu, const float* __restrict__ mask, int64_t ldm, int kc,
+                                              float* __restrict__ part) {
   __shared__ float As[kGk][kGt + 1], Bs[kGk][kGt + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.y * kGt, n0 = blockIdx.x * kGt;
+  const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
   float acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += kGk) {
+  for (int k0 = kb; k0 < ke; k0 += kGk) {
     for (int e = threadIdx.x; e < kGt * kGk; e += blockDim.x) {
-      const int mm = e / kGk, ka = e % kGk, kb = e / kGt, nn = e % kGt;
-      const int gm = m0 + mm, gka = k0 + ka, gkb = k0 + kb, gn = n0 + nn;
-      As[ka][mm] = (gm < M && gka < K) ? A[gm * sam + gka * sak] : 0.f;
-      Bs[kb][nn] = (gkb < K && gn < N) ? B[gkb * sbk + gn * sbn] : 0.f;
+      const int mm = e / kGk, ka = e % kGk, kb2 = e / kGt, nn = e % kGt;
+      const int gm = m0 + mm, gka = k0 + ka, gkb = k0 + kb2, gn = n0 + nn;
+      As[ka][mm] = (gm < M && gka < ke) ? A[gm * sam + gka * sak] : 0.f;
+      Bs[kb2][nn] = (gkb < ke && gn < N) ? B[gkb * sbk + gn * sbn] : 0.f;
     }
     __syncthreads();
 #pragma unroll
@@ -94,11 +98,31 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float* 
     for (int j = 0; j < 4; ++j) {
       const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
       if (m >= M || n >= N) continue;
+      if (part) {
+        part[((int64_t)blockIdx.z * M + m) * N + n] = acc[i][j];
+        continue;
+      }
       float v = acc[i][j] + (bias ? bias[n] : 0.f);
       if (relu) v = fmaxf(v, 0.f);
       if (mask && !(mask[m * ldm + n] > 0.f)) v = 0.f;
       C[m * ldc + n] = v;
     }
+}
+
+// C[m][n] = act(sum over z in increasing order of part[z][m][n] + bias[n]) * mask
+__global__ void k_gemm_reduce(int M, int N, int splits, const float* __restrict__ part, float* __restrict__ C,
+                              int64_t ldc, const float* __restrict__ bias, int relu, const float* __restrict__ mask,
+                              int64_t ldm) {
+  const int64_t total = (int64_t)M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(e / N), n = (int)(e - (int64_t)m * N);
+    float v = 0.f;
+    for (int z = 0; z < splits; ++z) v += part[(int64_t)z * total + e];
+    v += bias ? bias[n] : 0.f;
+    if (relu) v = fmaxf(v, 0.f);
+    if (mask && !(mask[m * ldm + n] > 0.f)) v = 0.f;
+    C[m * ldc + n] = v;
+  }
 }
 
 // column sums of a [rows][cols] block (leading dimension lda), rows in order
@@ -476,11 +500,28 @@ extern "C" ls_status ls_cnn_load(ls_cnn* m, const float* params, ls_stream_t str
 
 namespace {
 
+// Few output tiles (batch 256: a 256 x 256 output is 16 CTAs) split K into slices of
+// a multiple of 64 so that about two CTAs per SM run; the slices are added in order.
 ls_status gemm(int M, int N, int K, const float* A, int64_t sam, int64_t sak, const float* B, int64_t sbk,
                int64_t sbn, float* C, int64_t ldc, const float* bias, int relu, const float* mask, int64_t ldm,
                cudaStream_t s) {
-  dim3 grid((N + kGt - 1) / kGt, (M + kGt - 1) / kGt);
-  k_gemm<<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, relu, mask, ldm);
+  const int gx = (N + kGt - 1) / kGt, gy = (M + kGt - 1) / kGt;
+  int splits = 1;
+  if ((int64_t)gx * gy < 2 * kSmCount && K >= 128) {
+    splits = (int)((2 * kSmCount + (int64_t)gx * gy - 1) / ((int64_t)gx * gy));
+    splits = std::min(splits, K / 64);
+  }
+  const int kc = (K + splits * 64 - 1) / (splits * 64) * 64;  // slice length, multiple of 64
+  splits = (K + kc - 1) / kc;
+  float* part = nullptr;
+  if (splits > 1) {
+    part = static_cast<float*>(workspace(kWsGemmPart, (size_t)splits * M * N * 4));
+    if (!part) return LS_ERR_NO_MEMORY;
+  }
+  dim3 grid(gx, gy, splits);
+  k_gemm<<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, relu, mask, ldm, kc, part);
+  if (splits > 1)
+    k_gemm_reduce<<<cnn_grid((int64_t)M * N), 256, 0, s>>>(M, N, splits, part, C, ldc, bias, relu, mask, ldm);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 

@@ -59,7 +59,8 @@ enum WorkspaceSlot {
   kWsHeadPart = 4,
   kWsInterpRecs = 5,
   kWsInterpQueue = 6,
-  kWsSlots = 7
+  kWsGemmPart = 7,
+  kWsSlots = 8
 };
 // Returns a device pointer of at least `bytes` for the given slot (nullptr on failure).
 void* workspace(WorkspaceSlot slot, size_t bytes);
