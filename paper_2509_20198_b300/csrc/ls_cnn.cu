@@ -36,6 +36,9 @@ constexpr int kCnnFc1 = 256;
 constexpr int kCnnDecW[5] = {64, 32, 32, 16, 16};
 constexpr int kCnnEncC0[4] = {0, 1, 2, 5};
 constexpr int kCnnEncCk[4] = {1, 1, 3, 3};
+// the four encoders' first layers read the same 8-channel input: the forward runs them
+// as one convolution with 4 x 16 output channels, written to the four encoders' buffers
+constexpr int kCnnE0Fused = 4 * 16;
 
 enum CnnKind { kCnnConv = 0, kCnnFc = 1, kCnnHead = 2 };
 
@@ -311,6 +314,10 @@ struct ls_cnn {
   uint16_t* dgd[2] = {};    // decoder input gradients [B][b][b][16]
   float* dyfull = nullptr, *dg = nullptr, *dzc = nullptr, *dh = nullptr, *df = nullptr;
   float* dwt = nullptr, *dbs = nullptr, *wpad = nullptr;
+  // fused first encoder layers: packed operand, bias, padded fp32 weights [64][3][3][8]
+  uint16_t* wpk_e0 = nullptr;
+  float* bias_e0 = nullptr, *wpad_e0 = nullptr;
+  int64_t e0_plane = 0;  // elements between ez[k][0] and ez[k + 1][0]
   const uint16_t* x = nullptr;  // input of the last forward
   int last_n = 0;
 };
@@ -364,9 +371,12 @@ extern "C" ls_status ls_cnn_create(int32_t res, int32_t max_batch, int32_t train
   size_t bytes = 0;
   auto take = [&](size_t nbytes) { size_t o = bytes; bytes += (nbytes + 255) / 256 * 256; return o; };
   size_t o_ez[4][5], o_ep[4][4], o_f1[4], o_dz[2][5], o_du[2][4];
+  // the four encoders' first-layer outputs back to back (the fused layer's output groups)
+  const int64_t e0_plane = B * R * R * kCnnEncW[0];
+  const size_t o_e0 = take((size_t)4 * e0_plane * 2);
   for (int k = 0; k < 4; ++k) {
     for (int l = 0; l < 4; ++l) {
-      o_ez[k][l] = take((size_t)B * (R >> l) * (R >> l) * kCnnEncW[l] * 2);
+      o_ez[k][l] = l == 0 ? o_e0 + (size_t)k * e0_plane * 2 : take((size_t)B * (R >> l) * (R >> l) * kCnnEncW[l] * 2);
       o_ep[k][l] = take((size_t)B * (R >> (l + 1)) * (R >> (l + 1)) * kCnnEncW[l] * 2);
     }
     o_ez[k][4] = take((size_t)B * flat * 2);
@@ -406,6 +416,8 @@ extern "C" ls_status ls_cnn_create(int32_t res, int32_t max_batch, int32_t train
   }
   const size_t o_dwt = take((size_t)9 * 64 * 64 * 4), o_dbs = take(256 * 4);
   const size_t o_wpad = take((size_t)9 * kCatPad * 32 * 4);
+  const size_t o_wpk_e0 = take((size_t)ls_conv3x3_packed_elems(kCnnIn, kCnnE0Fused) * 2);
+  const size_t o_bias_e0 = take((size_t)kCnnE0Fused * 4), o_wpad_e0 = take((size_t)kCnnE0Fused * 9 * kCnnIn * 4);
   if (cudaMalloc(&m->arena, bytes) != cudaSuccess) {
     cudaGetLastError();
     delete m;
@@ -451,6 +463,10 @@ extern "C" ls_status ls_cnn_create(int32_t res, int32_t max_batch, int32_t train
   m->dwt = fp(o_dwt);
   m->dbs = fp(o_dbs);
   m->wpad = fp(o_wpad);
+  m->wpk_e0 = bf(o_wpk_e0);
+  m->bias_e0 = fp(o_bias_e0);
+  m->wpad_e0 = fp(o_wpad_e0);
+  m->e0_plane = e0_plane;
   *out = m;
   return LS_OK;
 }
@@ -479,9 +495,19 @@ extern "C" ls_status ls_cnn_layer_info(const ls_cnn* m, int32_t i, int32_t* kind
 extern "C" ls_status ls_cnn_load(ls_cnn* m, const float* params, ls_stream_t stream) {
   if (!m || !params) return LS_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  for (auto& d : m->layers) {
+  for (size_t li = 0; li < m->layers.size(); ++li) {
+    const CnnLayer& d = m->layers[li];
     if (d.kind != kCnnConv) continue;
     const float* w = params + d.w_off;
+    if (li < 20 && li % 5 == 0) {
+      // first layer of encoder li / 5: its padded weights and bias into the fused layer
+      const int k = (int)li / 5;
+      k_cnn_pad_w<<<cnn_grid((int64_t)d.cout * 9 * d.cin_pad), 256, 0, s>>>(
+          w, d.cout, d.cin, d.cin_pad, d.c0, m->wpad_e0 + (size_t)k * d.cout * 9 * d.cin_pad);
+      LS_CUDA_TRY(cudaMemcpyAsync(m->bias_e0 + k * d.cout, params + d.b_off, (size_t)d.cout * 4,
+                                  cudaMemcpyDeviceToDevice, s));
+      continue;
+    }
     if (d.cin != d.cin_pad) {
       k_cnn_pad_w<<<cnn_grid((int64_t)d.cout * 9 * d.cin_pad), 256, 0, s>>>(w, d.cout, d.cin, d.cin_pad, d.c0,
                                                                           m->wpad);
@@ -495,6 +521,8 @@ extern "C" ls_status ls_cnn_load(ls_cnn* m, const float* params, ls_stream_t str
       if (st != LS_OK) return st;
     }
   }
+  const ls_status st = ls_conv3x3_pack(m->wpad_e0, kCnnIn, kCnnE0Fused, 0, m->wpk_e0, stream);
+  if (st != LS_OK) return st;
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 
@@ -537,12 +565,17 @@ extern "C" ls_status ls_cnn_forward(ls_cnn* m, const float* params, const uint16
     return conv3x3_launch(in, d.wpk, params + d.b_off, nullptr, 1, n, d.h, d.h, d.cin_pad, d.cout, out, s);
   };
   ls_status st;
+  // the four encoders' first layers: one convolution, output groups of 16 channels into
+  // ez[0..3][0]
+  if ((st = conv3x3_launch_groups(x, m->wpk_e0, m->bias_e0, nullptr, 1, n, R, R, kCnnIn, kCnnE0Fused, m->ez[0][0],
+                                  kCnnEncW[0], m->e0_plane, s)) != LS_OK)
+    return st;
   int li = 0;
   for (int k = 0; k < 4; ++k) {
     const uint16_t* in = x;
     for (int l = 0; l < 4; ++l) {
       const CnnLayer& d = m->layers[li++];
-      if ((st = conv(d, in, m->ez[k][l])) != LS_OK) return st;
+      if (l > 0 && (st = conv(d, in, m->ez[k][l])) != LS_OK) return st;
       const int h = R >> l;
       k_maxpool<<<cnn_grid((int64_t)n * (h / 2) * (h / 2) * (d.cout / 8)), 256, 0, s>>>(m->ez[k][l], n, h, h, d.cout,
                                                                                      m->ep[k][l]);

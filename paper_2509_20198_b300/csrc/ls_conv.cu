@@ -68,6 +68,10 @@ struct ConvArgs {
   int32_t cin, cout, cpt, kc_real, kc, n_stages, n_mtiles;
   int32_t tiles_per_img, rows_per_tile, imgs_per_tile;
   int32_t relu;
+  // output: channel group g (ygroup channels, a multiple of 16) of every pixel goes to
+  // tensor g, ygstride elements after tensor g - 1 (one tensor: ygroup = cout)
+  int32_t ygroup;
+  int64_t ygstride;
   uint32_t acc_cols, tmem_cols, stage_bytes, idesc;
   int32_t ring;  // stages in use (<= kConvStages)
   // A operand: cw-channel blocks of one tap per TMA load (cw = 64 or 32: rows of
@@ -205,9 +209,10 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       if (!tc::mbar_wait(&tfull[acc], aph)) { abort_flag = 1; break; }
       tc::fence_after();
       const size_t pix = (size_t)m * 128 + row;
-      uint16_t* yp = a.y + pix * a.cout;
       const uint16_t* mp = a.mask ? a.mask + pix * a.cout : nullptr;
       for (int c0 = 0; c0 < a.cout; c0 += 16) {
+        const int g = c0 / a.ygroup;
+        uint16_t* yp = a.y + ((int64_t)g * a.ygstride + (int64_t)pix * a.ygroup + (c0 - g * a.ygroup));
         float v[16];
         tc::tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * a.acc_cols + (uint32_t)c0, v);
         if (a.bias) {
@@ -235,8 +240,8 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         o0.z = pack_bf16x2(v[4], v[5]); o0.w = pack_bf16x2(v[6], v[7]);
         o1.x = pack_bf16x2(v[8], v[9]); o1.y = pack_bf16x2(v[10], v[11]);
         o1.z = pack_bf16x2(v[12], v[13]); o1.w = pack_bf16x2(v[14], v[15]);
-        *reinterpret_cast<uint4*>(yp + c0) = o0;
-        *reinterpret_cast<uint4*>(yp + c0 + 8) = o1;
+        *reinterpret_cast<uint4*>(yp) = o0;
+        *reinterpret_cast<uint4*>(yp + 8) = o1;
       }
       tc::fence_before();
       tc::mbar_arrive(&tempty[acc]);
@@ -284,11 +289,17 @@ int chunk_count(int cin) {
 
 }  // namespace
 
-// Shared with the model code: validated launch of one convolution.
-ls_status conv3x3_launch(const uint16_t* x, const uint16_t* wpk, const float* bias, const uint16_t* mask, int relu,
-                         int n, int h, int w, int cin, int cout, uint16_t* y, cudaStream_t stream) {
+// Shared with the model code: validated launch of one convolution whose output
+// channels go to cout / ygroup tensors of ygroup channels each, ygstride elements apart
+// (ygroup = cout: one NHWC tensor).  Without a mask only (a mask is one NHWC tensor).
+ls_status conv3x3_launch_groups(const uint16_t* x, const uint16_t* wpk, const float* bias, const uint16_t* mask,
+                                int relu, int n, int h, int w, int cin, int cout, uint16_t* y, int ygroup,
+                                int64_t ygstride, cudaStream_t stream) {
   if (!x || !wpk || !y || n <= 0 || h <= 0 || w <= 0) return LS_ERR_INVALID_ARG;
   if (cin < 8 || cin % 8 || cin > 256 || cout < 16 || cout > 256 || cout % 16) return LS_ERR_UNSUPPORTED;
+  if (ygroup < 16 || ygroup % 16 || cout % ygroup ||
+      (ygroup != cout && (mask || ygstride % 8 || ygstride < (int64_t)n * h * w * ygroup)))
+    return LS_ERR_INVALID_ARG;
   if (w > 128 || 128 % w) return LS_ERR_UNSUPPORTED;
   if (((uintptr_t)x | (uintptr_t)wpk | (uintptr_t)y | (uintptr_t)mask) % 16) return LS_ERR_INVALID_ARG;
   ConvArgs a = {};
@@ -314,6 +325,7 @@ ls_status conv3x3_launch(const uint16_t* x, const uint16_t* wpk, const float* bi
   if (P % 128 || P / 128 > (int64_t)INT32_MAX) return LS_ERR_UNSUPPORTED;
   a.n_mtiles = (int32_t)(P / 128);
   a.wpk = wpk; a.bias = bias; a.mask = mask; a.y = y; a.relu = relu;
+  a.ygroup = ygroup; a.ygstride = ygroup == cout ? 0 : ygstride;
   a.cin = cin; a.cout = cout; a.cpt = cin / 8;
   a.kc_real = 9 * a.cpt;
   a.kc = chunk_count(cin);
@@ -349,6 +361,11 @@ ls_status conv3x3_launch(const uint16_t* x, const uint16_t* wpk, const float* bi
   }
   k_conv3x3<<<grid_cap(a.n_mtiles, kSmCount), kConvThreads, smem, stream>>>(map, a);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
+}
+
+ls_status conv3x3_launch(const uint16_t* x, const uint16_t* wpk, const float* bias, const uint16_t* mask, int relu,
+                         int n, int h, int w, int cin, int cout, uint16_t* y, cudaStream_t stream) {
+  return conv3x3_launch_groups(x, wpk, bias, mask, relu, n, h, w, cin, cout, y, cout, 0, stream);
 }
 
 }  // namespace ls
