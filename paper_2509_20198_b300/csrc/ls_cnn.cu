@@ -204,8 +204,9 @@ __global__ void k_cnn_uncrop(const float* __restrict__ dy, int n, int R, float* 
 
 // backward of 2x2 max pooling without a skip: route each pooled gradient to the first
 // maximum (row-major window order), times the ReLU derivative of the pooled input
+// dx: c channels of every pixel at dx[pixel * dx_ld + dx_off] (dense: dx_ld = c, dx_off = 0)
 __global__ void k_maxpool_bwd_relu(const uint16_t* __restrict__ x, const uint16_t* __restrict__ dpool, int n, int h,
-                                   int w, int c, uint16_t* __restrict__ dx) {
+                                   int w, int c, uint16_t* __restrict__ dx, int dx_ld, int dx_off) {
   const int ho = h / 2, wo = w / 2, g = c / 8;
   const int64_t total = (int64_t)n * ho * wo * g;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -228,7 +229,7 @@ __global__ void k_maxpool_bwd_relu(const uint16_t* __restrict__ x, const uint16_
       float o[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) o[i] = (v[k][i] > 0.f && arg[i] == k) ? dp[i] : 0.f;
-      *reinterpret_cast<uint4*>(dx + ip * c + gi * 8) = pack8(o);
+      *reinterpret_cast<uint4*>(dx + ip * dx_ld + dx_off + gi * 8) = pack8(o);
     }
   }
 }
@@ -244,14 +245,15 @@ __global__ void k_cnn_pad_w(const float* __restrict__ w, int cout, int cin, int 
 }
 
 // dW^T [9*cin_pad][cout] (+ db), the layer's channels [c0, c0 + cin), into the gradient
+// (dW^T rows of ld columns, the layer's outputs at columns [o0, o0 + cout))
 __global__ void k_cnn_dwt_to_grad(const float* __restrict__ dwt, const float* __restrict__ db, int cin_pad, int cin,
-                                  int c0, int cout, float* __restrict__ gw, float* __restrict__ gb) {
+                                  int c0, int cout, int ld, int o0, float* __restrict__ gw, float* __restrict__ gb) {
   const int total = cout * 9 * cin;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const int ci = e % cin, tap = (e / cin) % 9, o = e / (9 * cin);
-    gw[e] = dwt[(tap * cin_pad + c0 + ci) * cout + o];
+    gw[e] = dwt[(tap * cin_pad + c0 + ci) * ld + o0 + o];
   }
-  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < cout; o += gridDim.x * blockDim.x) gb[o] = db[o];
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < cout; o += gridDim.x * blockDim.x) gb[o] = db[o0 + o];
 }
 
 // network input from the Alg. 1 maps: (h - c_z) / r for both heights (c_z the mean of
@@ -318,6 +320,7 @@ struct ls_cnn {
   uint16_t* wpk_e0 = nullptr;
   float* bias_e0 = nullptr, *wpad_e0 = nullptr;
   int64_t e0_plane = 0;  // elements between ez[k][0] and ez[k + 1][0]
+  uint16_t* dz_e0 = nullptr;  // training: their output gradients interleaved [B][R][R][64]
   const uint16_t* x = nullptr;  // input of the last forward
   int last_n = 0;
 };
@@ -414,6 +417,7 @@ extern "C" ls_status ls_cnn_create(int32_t res, int32_t max_batch, int32_t train
     o_dh = take((size_t)B * kCnnFc1 * 4);
     o_df = take((size_t)B * flat * 4);
   }
+  const size_t o_dz_e0 = training ? take((size_t)B * R * R * kCnnE0Fused * 2) : 0;
   const size_t o_dwt = take((size_t)9 * 64 * 64 * 4), o_dbs = take(256 * 4);
   const size_t o_wpad = take((size_t)9 * kCatPad * 32 * 4);
   const size_t o_wpk_e0 = take((size_t)ls_conv3x3_packed_elems(kCnnIn, kCnnE0Fused) * 2);
@@ -459,6 +463,7 @@ extern "C" ls_status ls_cnn_create(int32_t res, int32_t max_batch, int32_t train
     m->dzc = fp(o_dzc);
     m->dh = fp(o_dh);
     m->df = fp(o_df);
+    m->dz_e0 = bf(o_dz_e0);
   }
   m->dwt = fp(o_dwt);
   m->dbs = fp(o_dbs);
@@ -637,7 +642,8 @@ extern "C" ls_status ls_cnn_backward(ls_cnn* m, const float* params, const float
     ls_status st = wgrad_launch(in, dz, n, d.h, d.h, d.cin_pad, d.cout, m->dwt, m->dbs, s);
     if (st != LS_OK) return st;
     k_cnn_dwt_to_grad<<<cnn_grid((int64_t)d.cout * 9 * d.cin), 256, 0, s>>>(m->dwt, m->dbs, d.cin_pad, d.cin, d.c0,
-                                                                          d.cout, grads + d.w_off, grads + d.b_off);
+                                                                          d.cout, d.cout, 0, grads + d.w_off,
+                                                                          grads + d.b_off);
     return LS_OK;
   };
   auto dgrad = [&](const CnnLayer& d, const uint16_t* dz, const uint16_t* mask, uint16_t* dx) -> ls_status {
@@ -710,22 +716,36 @@ extern "C" ls_status ls_cnn_backward(ls_cnn* m, const float* params, const float
     // ---- encoder k, from its last conv back to the first
     uint16_t* gz = m->gbuf[0];
     k_f32_to_bf16_masked<<<cnn_grid((int64_t)n * flat), 256, 0, s>>>(m->df, nullptr, (int64_t)n * flat, gz);
-    for (int l = 4; l >= 0; --l) {
+    for (int l = 4; l >= 1; --l) {
       const CnnLayer& d2 = m->layers[5 * k + l];
-      const uint16_t* in = l == 0 ? m->x : m->ep[k][l - 1];
+      const uint16_t* in = m->ep[k][l - 1];
       if ((st = wgrad(d2, in, gz)) != LS_OK) return st;
-      if (l == 0) break;
       uint16_t* gp = m->gbuf[1];
       if ((st = dgrad(d2, gz, nullptr, gp)) != LS_OK) return st;  // d(pooled), raw
       const CnnLayer& prev = m->layers[5 * k + l - 1];
       const int h = prev.h;
+      // the first layer's output gradient goes to channels [16 k, 16 k + 16) of dz_e0
+      const bool first = l == 1;
       k_maxpool_bwd_relu<<<cnn_grid((int64_t)n * (h / 2) * (h / 2) * (prev.cout / 8)), 256, 0, s>>>(
-          m->ez[k][l - 1], gp, n, h, h, prev.cout, m->gbuf[2]);
+          m->ez[k][l - 1], gp, n, h, h, prev.cout, first ? m->dz_e0 : m->gbuf[2], first ? kCnnE0Fused : prev.cout,
+          first ? prev.cout * k : 0);
+      if (first) break;
       gz = m->gbuf[2];
       // keep gz out of the buffers the next layer writes
       uint16_t* t = m->gbuf[0];
       m->gbuf[0] = m->gbuf[2];
       m->gbuf[2] = t;
+    }
+  }
+  // the four encoders' first layers: one weight gradient with 64 output channels, split
+  {
+    if (cudaMemsetAsync(m->dwt, 0, (size_t)9 * kCnnIn * kCnnE0Fused * 4, s) != cudaSuccess) return LS_ERR_CUDA;
+    if (cudaMemsetAsync(m->dbs, 0, (size_t)kCnnE0Fused * 4, s) != cudaSuccess) return LS_ERR_CUDA;
+    if ((st = wgrad_launch(m->x, m->dz_e0, n, R, R, kCnnIn, kCnnE0Fused, m->dwt, m->dbs, s)) != LS_OK) return st;
+    for (int k = 0; k < 4; ++k) {
+      const CnnLayer& d = m->layers[5 * k];
+      k_cnn_dwt_to_grad<<<cnn_grid((int64_t)d.cout * 9 * d.cin), 256, 0, s>>>(
+          m->dwt, m->dbs, d.cin_pad, d.cin, d.c0, d.cout, kCnnE0Fused, d.cout * k, grads + d.w_off, grads + d.b_off);
     }
   }
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
