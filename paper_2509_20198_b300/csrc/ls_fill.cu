@@ -270,7 +270,7 @@ __device__ void nearest_far(const FillArgs& f, int tx, int ty, int cx, int cy, L
   }
 }
 
-__global__ void __launch_bounds__(kFillThreads) k_fill(FillArgs f) {
+__global__ void __launch_bounds__(kFillThreads, 2) k_fill(FillArgs f) {  // 2 CTAs per SM (shared memory)
   extern __shared__ __align__(128) unsigned char fill_dyn[];
   Rec* stage = reinterpret_cast<Rec*>(fill_dyn);  // kStageCap records (dynamic)
   __shared__ __align__(16) float out_h[kOutStageRes * kOutStageRes];
