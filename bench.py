@@ -67,8 +67,8 @@ def bin_traffic_per_point():
     src_hash = hashlib.sha256(open(BIN_SRC, "rb").read()).hexdigest()[:16]
     vals = {}
     for line in open(p):
-        if ":" in line:
-            k, v = line.split(":", 1)
+        if ": " in line:  # "key: value" (keys may hold a colon, as in "sha256[:16]")
+            k, v = line.split(": ", 1)
             vals[k.strip()] = v.strip()
     if vals.get("ls_bin.cu sha256[:16]") != src_hash:
         return None
