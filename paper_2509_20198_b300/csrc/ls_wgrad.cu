@@ -18,8 +18,10 @@
 //             to the tensor core (fence.proxy.async);
 //             at the end they read the accumulator from TMEM (one row per thread);
 //  warp 5     issues tcgen05.mma kind::f16 (M=128, N=C_out, K=16) and commits.
-// The bias gradient is a column sum of dZ (k_colsum, per-block partials, then k_dbsum
-// in block order).
+// The bias gradient is a column sum of dZ.  When 9*C_in leaves padding rows in the last
+// M tile, the first padding row of every A stage is set to ones, so the same MMAs sum
+// dZ over the pixels into that row and k_wsum passes it on as the bias gradient;
+// otherwise k_colsum (per-block partials) and k_dbsum (in block order) compute it.
 #include <cuda_bf16.h>
 
 #include "ls_tc.cuh"
@@ -53,6 +55,7 @@ struct WgArgs {
   int32_t imgs_per_step;          // images per stage (1, or 64 / (h * w))
   int64_t pix_total, pix_per_cta;
   int32_t n_mtiles;
+  int32_t ones_row;  // row k = rows of the last tile set to ones (bias gradient), or -1
   uint32_t idesc, tmem_cols, b_bytes;
 };
 
@@ -178,6 +181,16 @@ __global__ void __launch_bounds__(kWgThreads, 1)
         }
       }
     }
+    // the ones row (local row lr of this tile): its two halves of 4 pixel groups belong
+    // to items 2 g1 and 2 g1 + 1, written by the warps that transpose those items
+    const int lr = a.ones_row - m0;
+    const bool has_ones = a.ones_row >= 0 && lr >= 0 && lr < 128;
+    const int g1 = lr >> 3, rr = lr & 7;
+    int ones_h = -1;  // half (pixel groups 4 h .. 4 h + 3) this warp writes
+    if (has_ones) {
+      if ((2 * g1) % 4 == tw) ones_h = 0;
+      else if ((2 * g1 + 1) % 4 == tw) ones_h = 1;
+    }
     for (int s = 0; s < n_steps && !abort_flag; ++s) {
       const int rs = s % kWgRaw, os = s % kWgOps;
       if (!tc::mbar_wait(&raw_full[rs], (uint32_t)(s / kWgRaw) & 1u)) { abort_flag = 1; break; }
@@ -197,6 +210,15 @@ __global__ void __launch_bounds__(kWgThreads, 1)
             if (q0 + q < mine) tc::stmatrix_x4_trans(OA + dst[q0 + q], r[q]);
         }
       }
+      if (ones_h >= 0) {
+        __syncwarp();
+        if (lane < 4) {
+          const uint32_t one2 = 0x3F803F80u;  // two bf16 1.0
+          const uint32_t adr = OA + (uint32_t)(g1 * 128 + (ones_h * 4 + lane) * 2048 + rr * 16);
+          asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(adr), "r"(one2) : "memory");
+        }
+        __syncwarp();
+      }
       tc::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
@@ -213,7 +235,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
       for (int c0 = 0; c0 < a.cout; c0 += 16) {
         float v[16];
         tc::tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-        if (m0 + row < a.rows) {
+        if (m0 + row < a.rows || m0 + row == a.ones_row) {
 #pragma unroll
           for (int i = 0; i < 16; i += 4)
             *reinterpret_cast<float4*>(out + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
@@ -248,9 +270,10 @@ __global__ void __launch_bounds__(kWgThreads, 1)
 
 // dW^T[k][o] += sum over slices of the CTA partials, slices in increasing order (loads
 // issued eight ahead of the in-order additions).
+// With db, row `rows` of the partials (the ones row) is the bias gradient: into db.
 __global__ void k_wsum(const float* __restrict__ part, int slices, int n_mtiles, int rows, int cout,
-                       float* __restrict__ dwt) {
-  const int total = rows * cout;
+                       float* __restrict__ dwt, float* __restrict__ db) {
+  const int total = (rows + (db ? 1 : 0)) * cout;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const int k = e / cout, o = e - k * cout;
     const int mt = k >> 7, row = k & 127;
@@ -266,7 +289,8 @@ __global__ void k_wsum(const float* __restrict__ part, int slices, int n_mtiles,
       for (int i = 0; i < 8; ++i) s += v[i];
     }
     for (; sl < slices; ++sl) s += p[(size_t)sl * stride];
-    dwt[e] += s;
+    if (k < rows) dwt[e] += s;
+    else db[o] += s;
   }
 }
 
@@ -337,6 +361,7 @@ ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int 
   a.imgs_per_step = hw >= kWgPix ? 1 : (int32_t)(kWgPix / hw);
   a.pix_total = (int64_t)n * h * w;
   a.n_mtiles = (a.rows + 127) / 128;
+  a.ones_row = (db && a.rows % 128) ? a.rows : -1;
   // about 2 waves of CTAs over the SMs, slices a multiple of the stage
   int64_t slices = (2 * kSmCount + a.n_mtiles - 1) / a.n_mtiles;
   int64_t per = (a.pix_total + slices - 1) / slices;
@@ -378,9 +403,10 @@ ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int 
     attr_set[dev] = true;
   }
   k_wgrad<<<(unsigned)ctas, kWgThreads, smem, stream>>>(xmap, dzmap, a);
-  k_wsum<<<grid_cap((a.rows * cout + 255) / 256, kSmCount * 4), 256, 0, stream>>>(a.part, (int)slices, a.n_mtiles,
-                                                                                   a.rows, cout, dwt);
-  if (db) {
+  const bool ones = a.ones_row >= 0;
+  k_wsum<<<grid_cap(((a.rows + 1) * cout + 255) / 256, kSmCount * 4), 256, 0, stream>>>(
+      a.part, (int)slices, a.n_mtiles, a.rows, cout, dwt, ones ? db : nullptr);
+  if (db && !ones) {
     float* dbp = reinterpret_cast<float*>(ws + part_bytes);
     const int threads = 256 - 256 % (cout / 8);  // whole pixel lanes of cout/8 threads
     k_colsum<<<kColsumBlocks, threads, 0, stream>>>(dz, a.pix_total, cout, dbp);
