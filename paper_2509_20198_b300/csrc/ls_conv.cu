@@ -74,8 +74,8 @@ struct ConvArgs {
   int64_t ygstride;
   uint32_t acc_cols, tmem_cols, stage_bytes, idesc;
   int32_t ring;  // stages in use (<= kConvStages)
-  // A operand: cw-channel blocks of one tap per TMA load (cw = 64 or 32: rows of
-  // 128 / 64 bytes, 128B / 64B swizzle; cw = 8: 8 unswizzled chunks per stage)
+  // A operand: cw-channel blocks of one tap per TMA load (cw = 64, 32 or 16: rows of
+  // 128 / 64 / 32 bytes, 128B / 64B / 32B swizzle; cw = 8: 8 unswizzled chunks per stage)
   int32_t cw, cblocks, blocks_per_stage, n_blocks;
   uint32_t blk_bytes, sbo_a, swz;
 };
@@ -331,13 +331,13 @@ ls_status conv3x3_launch_groups(const uint16_t* x, const uint16_t* wpk, const fl
   a.kc = chunk_count(cin);
   a.n_stages = (a.kc + kChunksPerStage - 1) / kChunksPerStage;
   // widest channel block per TMA load: fewer, longer rows for the TMA unit
-  a.cw = cin % 64 == 0 ? 64 : cin % 32 == 0 ? 32 : 8;
+  a.cw = cin % 64 == 0 ? 64 : cin % 32 == 0 ? 32 : cin % 16 == 0 ? 16 : 8;
   a.cblocks = cin / a.cw;
   a.blocks_per_stage = 64 / a.cw;
   a.n_blocks = 9 * a.cblocks;
   a.blk_bytes = (uint32_t)(128 * a.cw * 2);
   a.sbo_a = (uint32_t)(8 * a.cw * 2);  // 8 rows of one swizzle atom
-  a.swz = a.cw == 64 ? 2u : a.cw == 32 ? 4u : 0u;
+  a.swz = a.cw == 64 ? 2u : a.cw == 32 ? 4u : a.cw == 16 ? 6u : 0u;  // 128B, 64B, 32B swizzle
   box[0] = (uint32_t)a.cw;
   a.acc_cols = 32;
   while ((int)a.acc_cols < cout) a.acc_cols <<= 1;

@@ -8,7 +8,7 @@
 // Both operands are stored pixel-minor (NHWC), while the MMA reads K-major tiles
 // (pixels contiguous), so every stage is transposed once in shared memory:
 //  warp 0     TMA producer: the M tile's rows are 128 / cw blocks of cw channels of one
-//             tap (cw = 64, 32 or 8 dividing C_in): one 4-D tiled load per block of the
+//             tap (cw = 64, 32, 16 or 8 dividing C_in): one 4-D tiled load per block of the
 //             tap-shifted input (cw channels x 64 pixels: whole rows, or half a row of a
 //             128-wide image; zero-filled outside the image: the padding; rows of 128 / 64 bytes are written with the 128B / 64B
 //             swizzle), and dZ in blocks of cwb output channels, into a raw ring;
@@ -37,12 +37,13 @@ constexpr int kWgABytes = 128 * kWgPix * 2;
 
 // Byte offset in a raw stage of channel ch (multiple of 8) of pixel px, the stage being
 // a sequence of blocks of cw channels x 64 pixels as the TMA wrote them: pixel rows of
-// 2*cw bytes; 16-byte chunk c of row px sits at chunk c ^ (px & 7) (128B swizzle, cw 64)
-// or c ^ ((px >> 1) & 3) (64B swizzle, cw 32); cw 8 rows are plain 16-byte rows.
+// 2*cw bytes; 16-byte chunk c of row px sits at chunk c ^ (px & 7) (128B swizzle, cw 64),
+// c ^ ((px >> 1) & 3) (64B swizzle, cw 32) or c ^ ((px >> 2) & 1) (32B swizzle, cw 16);
+// cw 8 rows are plain 16-byte rows.
 __device__ __forceinline__ uint32_t raw_off(int ch, int px, int cw) {
   const int blk = ch / cw, c = (ch - blk * cw) >> 3;
   const uint32_t base = (uint32_t)blk * (kWgPix * cw * 2) + (uint32_t)px * (uint32_t)(cw * 2);
-  const int sc = cw == 64 ? (c ^ (px & 7)) : cw == 32 ? (c ^ ((px >> 1) & 3)) : c;
+  const int sc = cw == 64 ? (c ^ (px & 7)) : cw == 32 ? (c ^ ((px >> 1) & 3)) : cw == 16 ? (c ^ ((px >> 2) & 1)) : c;
   return base + (uint32_t)sc * 16u;
 }
 
@@ -374,8 +375,8 @@ ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int 
   while ((int)a.tmem_cols < cout) a.tmem_cols <<= 1;
   a.b_bytes = (uint32_t)cout * kWgPix * 2;
   // widest channel blocks per TMA load (fewer, longer rows), dividing the channel counts
-  a.cw = cin % 64 == 0 ? 64 : cin % 32 == 0 ? 32 : 8;
-  a.cwb = cout % 64 == 0 ? 64 : cout % 32 == 0 ? 32 : 8;
+  a.cw = cin % 64 == 0 ? 64 : cin % 32 == 0 ? 32 : cin % 16 == 0 ? 16 : 8;
+  a.cwb = cout % 64 == 0 ? 64 : cout % 32 == 0 ? 32 : cout % 16 == 0 ? 16 : 8;
   CUtensorMap xmap, dzmap;
   const uint32_t box[4] = {(uint32_t)a.cw, (uint32_t)a.cols_per_step, (uint32_t)a.rows_per_step,
                            (uint32_t)a.imgs_per_step};

@@ -65,6 +65,8 @@ SHAPES = [
     (1, 64, 64, 96, 32),
     (16, 4, 4, 8, 16),      # several whole images per 128-pixel tile
     (2, 16, 16, 128, 256),
+    (2, 64, 64, 16, 32),    # 16-channel blocks (32-byte swizzle)
+    (1, 128, 128, 48, 32),  # the skip concat: 16-channel blocks, 128-wide rows
 ]
 
 
@@ -110,7 +112,7 @@ def test_input_gradient_via_flipped_weights(lib, shape):
 
 @pytest.mark.parametrize("shape", [(2, 64, 64, 8, 32), (2, 32, 32, 32, 64), (1, 16, 16, 64, 128),
                                    (2, 32, 32, 192, 64), (1, 64, 64, 96, 32), (16, 4, 4, 16, 16),
-                                   (2, 128, 128, 8, 16), (1, 128, 128, 48, 32)])
+                                   (2, 128, 128, 8, 16), (1, 128, 128, 48, 32), (2, 64, 64, 16, 48)])
 def test_weight_gradient_matches_oracle(lib, shape):
     """dW, db of the tcgen05 weight-gradient GEMM against the FP64 oracle on the same
     bf16 operands; FP32 accumulation over n*h*w pixels: rel. L2 < 1e-4."""
