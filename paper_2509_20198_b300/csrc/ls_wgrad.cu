@@ -30,8 +30,12 @@ namespace ls {
 namespace {
 
 constexpr int kWgThreads = 192;
-constexpr int kWgRaw = 3;   // raw (TMA) stages
-constexpr int kWgOps = 3;   // operand (K-major) stages
+// Two raw and two operand stages: at C_out <= 64 a CTA then needs at most 96 KB of
+// shared memory and two or three CTAs share an SM, whose independent pipelines hide the
+// load and transpose latency better than deeper rings in one CTA (measured: 3 + 3
+// stages, one CTA per SM, made the weight gradients 25 % slower)
+constexpr int kWgRaw = 2;   // raw (TMA) stages
+constexpr int kWgOps = 2;   // operand (K-major) stages
 constexpr int kWgPix = 64;  // pixels (K) per stage
 constexpr int kWgABytes = 128 * kWgPix * 2;
 
