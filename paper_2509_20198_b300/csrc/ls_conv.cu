@@ -5,9 +5,10 @@
 // with transposed and flipped weights, in the input-gradient pass of training.
 //
 // Per CTA (persistent over 128-pixel tiles, 6 warps, a ring of up to 8 operand stages):
-// two CTAs per SM with about 108 KB of stages each where both accumulator pairs fit the
-// TMEM (C_out <= 128), else one CTA with about 200 KB.  Two independent pipelines per SM
-// hide the TMA and epilogue latency better than one deeper ring.
+// three CTAs per SM with about 70 KB of stages each where their accumulator pairs fit
+// the TMEM together (C_out <= 64), two with about 108 KB (C_out <= 128), else one with
+// about 200 KB.  Independent pipelines per SM hide the TMA and epilogue latency better
+// than one deeper ring (four CTAs per SM measured slower than three).
 //  warp 0  TMA producer: per 8-channel chunk of one tap, one 4-D tiled TMA load of
 //          the shifted 128-pixel slab (out-of-range rows/columns are zero-filled by
 //          the TMA unit: that is the padding) and one 1-D bulk copy of the
@@ -59,6 +60,7 @@ constexpr int kConvThreads = 192;
 constexpr int kConvStages = 8;            // most stages; a launch uses as many as fit
 constexpr size_t kConvSmemBudget = 200 * 1024;
 constexpr size_t kConvSmemBudget2 = 108 * 1024;  // per CTA with two CTAs per SM
+constexpr size_t kConvSmemBudget3 = 70 * 1024;   // per CTA with three CTAs per SM
 constexpr int kChunksPerStage = 8;
 constexpr int kAStageBytes = kChunksPerStage * 2048;
 constexpr int kMaxLoads = 9 * 256 / 8;  // TMA loads per 128-pixel tile at most (C_in <= 256)
@@ -353,7 +355,7 @@ ls_status conv3x3_launch_groups(const uint16_t* x, const uint16_t* wpk, const fl
   if (!encode_tmap_bf16_4d(&map, x, dims, strides, box, a.cw == 8 ? 0 : a.cw * 2)) return LS_ERR_CUDA;
   // two CTAs per SM where their accumulators fit the TMEM together (tmem_cols <= 256):
   // each gets half the shared-memory budget
-  const size_t budget = a.tmem_cols <= 256 ? kConvSmemBudget2 : kConvSmemBudget;
+  const size_t budget = a.tmem_cols <= 128 ? kConvSmemBudget3 : a.tmem_cols <= 256 ? kConvSmemBudget2 : kConvSmemBudget;
   a.ring = (int32_t)std::min<size_t>(kConvStages, budget / a.stage_bytes);
   if (a.ring < 2) return LS_ERR_UNSUPPORTED;
   const size_t smem = (size_t)a.ring * a.stage_bytes;
@@ -365,7 +367,7 @@ ls_status conv3x3_launch_groups(const uint16_t* x, const uint16_t* wpk, const fl
                                      (int)kConvSmemBudget));
     attr_set[dev] = true;
   }
-  const int per_sm = a.tmem_cols <= 256 ? 2 : 1;
+  const int per_sm = a.tmem_cols <= 128 ? 3 : a.tmem_cols <= 256 ? 2 : 1;
   k_conv3x3<<<grid_cap(a.n_mtiles, (int64_t)kSmCount * per_sm), kConvThreads, smem, stream>>>(map, a);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
