@@ -303,7 +303,7 @@ ls_status ls_tune_fill_sparse(const ls_points *samples, const ls_region *region,
  *   patch with a larger |z| gets LS_ERR_UNSUPPORTED in the sticky status, tri_count
  *   -1 and lin = nn); at most 1536 samples per window (more: LS_ERR_OUT_OF_RANGE in
  *   the sticky status and NaN maps for that patch).
- * Uses library scratch of 32 bytes per sample and 8 bytes per requested tile.
+ * Uses library scratch of 32 bytes per sample and 12 bytes per requested tile.
  * ------------------------------------------------------------------------------- */
 typedef struct {
   int32_t res;    /* texels per patch side (96) */

@@ -19,8 +19,9 @@
 //    orientations), then the barycentric interpolation from the exact numerator;
 //    outputs staged per block and stored as whole rows and 4-byte words.
 // Patches whose window holds more samples than the small tier's capacity (96) are
-// queued on the device for a second launch with one warp per CTA and room for 384, and
-// those over that for a third with room for 1536 (one CTA per SM).
+// queued on the device for a second launch with one warp per CTA and room for 192 (about
+// nine CTAs per SM), those over that for a third with room for 384 (four per SM), and
+// those over that for a fourth with room for 1536 (one per SM).
 #include <climits>
 
 #include "ls_internal.cuh"
@@ -32,7 +33,8 @@ constexpr int kInterpMaxRes = 1024;
 constexpr int kInterpHintRes = 128;  // up to this resolution walks start from the block above
 constexpr int kInterpSmallCap = 96;     // window samples per patch, small tier
 constexpr int kInterpSmallWarps = 4;    // patches (warps) per CTA, small tier
-constexpr int kInterpMidCap = 384;      // medium tier: one warp per CTA, 4 CTAs per SM
+constexpr int kInterpMid1Cap = 192;     // first medium tier: one warp per CTA
+constexpr int kInterpMidCap = 384;      // second medium tier: one warp per CTA, 4 CTAs per SM
 constexpr int kInterpBigCap = 1536;     // big tier: one warp per CTA, one CTA per SM
 constexpr int kInterpMaxWindow = 1 << 17;  // window side bound of the exact arithmetic
 constexpr int kInterpZBound = 1 << 28;     // |z| bound of the exact numerators
@@ -69,8 +71,8 @@ struct InterpArgs {
   double z_scale, z_offset;
   float zs_f, zo_f;
   ls_interp_outputs out;
-  // two queues of n_out + 1 words: [0] the number of patches queued for the next
-  // tier (medium, then big), [1..] their ordinals
+  // three queues of n_out + 1 words: [0] the number of patches queued for the next
+  // tier (the two medium tiers, then big), [1..] their ordinals
   int32_t* queue;
 };
 
@@ -454,7 +456,7 @@ __device__ void texel_maps(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o, i
   __syncwarp();
 }
 
-// Alg. 1 for output ordinal o.  Tiers 0 and 1 queue a patch with more than CAP window
+// Alg. 1 for output ordinal o.  Tiers 0, 1 and 2 queue a patch with more than CAP window
 // samples for the next tier; the last tier reports it (LS_ERR_OUT_OF_RANGE) and writes
 // NaN heights.
 template <int CAP, int TIER>
@@ -509,7 +511,7 @@ __device__ void interp_patch(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o)
   }
   bool failed = false;
   if (n > CAP) {
-    if (TIER < 2) {
+    if (TIER < 3) {
       if (lane == 0) {
         int32_t* q = a.queue + (size_t)TIER * (a.n_out + 1);
         const int qpos = atomicAdd(q, 1);
@@ -575,7 +577,7 @@ __device__ void interp_patch(InterpWarp<CAP>& s, const InterpArgs& a, int64_t o)
   texel_maps(s, a, o, n, T);
 }
 
-// Tier 0 takes every requested patch; tiers 1 and 2 the ones the previous tier queued
+// Tier 0 takes every requested patch; tiers 1 to 3 the ones the previous tier queued
 // (written by the previous launch on the same stream).
 template <int CAP, int TIER>
 __global__ void __launch_bounds__(TIER > 0 ? 32 : 32 * kInterpSmallWarps) k_interp(InterpArgs a) {
@@ -627,13 +629,14 @@ extern "C" ls_status ls_fill_interp(const ls_points* samples, const ls_region* r
   if (n_out == 0) return LS_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   Rec* recs = static_cast<Rec*>(workspace(kWsInterpRecs, (size_t)(samples->n > 0 ? samples->n : 1) * sizeof(Rec)));
-  int32_t* queue = static_cast<int32_t*>(workspace(kWsInterpQueue, (size_t)2 * (n_out + 1) * sizeof(int32_t)));
+  int32_t* queue = static_cast<int32_t*>(workspace(kWsInterpQueue, (size_t)3 * (n_out + 1) * sizeof(int32_t)));
   if (!recs || !queue) return LS_ERR_NO_MEMORY;
   if (samples->n > 0)
     k_pack<<<grid_cap((T + 7) / 8, kSmCount * 16), 256, 0, s>>>(*samples, T, region->x0_cm, region->y0_cm,
                                                                  region->tile_cm, region->tiles_x, recs);
   LS_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(int32_t), s));
   LS_CUDA_TRY(cudaMemsetAsync(queue + n_out + 1, 0, sizeof(int32_t), s));
+  LS_CUDA_TRY(cudaMemsetAsync(queue + 2 * (n_out + 1), 0, sizeof(int32_t), s));
   InterpArgs a;
   a.toff = samples->tile_offsets;
   a.recs = recs;
@@ -654,6 +657,7 @@ extern "C" ls_status ls_fill_interp(const ls_points* samples, const ls_region* r
   a.out = *out;
   a.queue = queue;
   const size_t small_smem = sizeof(InterpWarp<kInterpSmallCap>) * kInterpSmallWarps;
+  const size_t mid1_smem = sizeof(InterpWarp<kInterpMid1Cap>);
   const size_t mid_smem = sizeof(InterpWarp<kInterpMidCap>);
   const size_t big_smem = sizeof(InterpWarp<kInterpBigCap>);
   static bool attr_set[64] = {};
@@ -662,27 +666,33 @@ extern "C" ls_status ls_fill_interp(const ls_points* samples, const ls_region* r
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
     LS_CUDA_TRY(cudaFuncSetAttribute(k_interp<kInterpSmallCap, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)small_smem));
-    LS_CUDA_TRY(cudaFuncSetAttribute(k_interp<kInterpMidCap, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    LS_CUDA_TRY(cudaFuncSetAttribute(k_interp<kInterpMid1Cap, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)mid1_smem));
+    LS_CUDA_TRY(cudaFuncSetAttribute(k_interp<kInterpMidCap, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)mid_smem));
-    LS_CUDA_TRY(cudaFuncSetAttribute(k_interp<kInterpBigCap, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    LS_CUDA_TRY(cudaFuncSetAttribute(k_interp<kInterpBigCap, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)big_smem));
     attr_set[dev] = true;
   }
-  static int small_per_sm[64] = {}, mid_per_sm[64] = {};
+  static int small_per_sm[64] = {}, mid1_per_sm[64] = {}, mid_per_sm[64] = {};
   if (dev >= 0 && dev < 64 && small_per_sm[dev] == 0) {
-    int b = 0, c = 0;
+    int b = 0, c1 = 0, c = 0;
     LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_interp<kInterpSmallCap, 0>,
                                                               32 * kInterpSmallWarps, small_smem));
-    LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_interp<kInterpMidCap, 1>, 32, mid_smem));
+    LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c1, k_interp<kInterpMid1Cap, 1>, 32, mid1_smem));
+    LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_interp<kInterpMidCap, 2>, 32, mid_smem));
     small_per_sm[dev] = b > 0 ? b : 1;
+    mid1_per_sm[dev] = c1 > 0 ? c1 : 1;
     mid_per_sm[dev] = c > 0 ? c : 1;
   }
   const bool known = dev >= 0 && dev < 64;
   const int per_sm = known ? small_per_sm[dev] : 1, mid_sm = known ? mid_per_sm[dev] : 1;
+  const int mid1_sm = known ? mid1_per_sm[dev] : 1;
   k_interp<kInterpSmallCap, 0>
       <<<grid_cap((n_out + kInterpSmallWarps - 1) / kInterpSmallWarps, (int64_t)kSmCount * per_sm),
          32 * kInterpSmallWarps, small_smem, s>>>(a);
-  k_interp<kInterpMidCap, 1><<<grid_cap(n_out, (int64_t)kSmCount * mid_sm), 32, mid_smem, s>>>(a);
-  k_interp<kInterpBigCap, 2><<<grid_cap(n_out, kSmCount), 32, big_smem, s>>>(a);
+  k_interp<kInterpMid1Cap, 1><<<grid_cap(n_out, (int64_t)kSmCount * mid1_sm), 32, mid1_smem, s>>>(a);
+  k_interp<kInterpMidCap, 2><<<grid_cap(n_out, (int64_t)kSmCount * mid_sm), 32, mid_smem, s>>>(a);
+  k_interp<kInterpBigCap, 3><<<grid_cap(n_out, kSmCount), 32, big_smem, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
