@@ -8,7 +8,7 @@ multiply-add), in the order the rasterizer's definition fixes:
 
   camera frame  q = ((f32)(x - ox), (f32)(y - oy), (f32)(z - oz)) in cm
   clip          c_r = ((M[r,0] q.x + M[r,1] q.y) + M[r,2] q.z) + M[r,3]
-  kept          c_w > 0, ndc = c * (1 / c_w), d = ndc_z * 0.5 + 0.5 in [0, 1]
+  kept          c_w > 0, ndc = c / c_w, d = ndc_z * 0.5 + 0.5 in [0, 1]
   screen        sx = (ndc_x * 0.5 + 0.5) * width, sy = (ndc_y * 0.5 + 0.5) * height
   word          bits(d) << 32 | R | G << 8 | B << 16 | 255 << 24
 
@@ -36,8 +36,7 @@ def _project(q, M, width, height):
     c = [((M[r, 0] * q[:, 0] + M[r, 1] * q[:, 1]) + M[r, 2] * q[:, 2]) + M[r, 3] for r in range(4)]
     cw = c[3]
     with np.errstate(divide="ignore", invalid="ignore"):
-        rw = F(1) / cw  # the correctly rounded reciprocal
-        ndc = [c[k] * rw for k in range(3)]
+        ndc = [c[k] / cw for k in range(3)]  # the perspective division, one IEEE quotient each
     half = F(0.5)
     sx = (ndc[0] * half + half) * F(width)
     sy = (ndc[1] * half + half) * F(height)

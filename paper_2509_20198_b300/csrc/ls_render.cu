@@ -45,11 +45,6 @@ __device__ __forceinline__ float f_div(float a, float b) {
   asm("div.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
   return r;
 }
-__device__ __forceinline__ float f_rcp(float a) {
-  float r;
-  asm("rcp.rn.f32 %0, %1;" : "=f"(r) : "f"(a));
-  return r;
-}
 __device__ __forceinline__ float f_of(long long v) {
   // the 32-bit conversion when the value fits (the same rounded value, a cheaper
   // instruction than the 64-bit one)
@@ -75,8 +70,7 @@ struct Vtx {
 };
 
 // Camera frame (cm) to screen: clip rows ((M0 qx + M1 qy) + M2 qz) + M3, perspective
-// division as products with the reciprocal of c_w, viewport; kept when c_w > 0 and
-// 0 <= d <= 1.
+// division (IEEE quotients c / c_w), viewport; kept when c_w > 0 and 0 <= d <= 1.
 __device__ __forceinline__ Vtx project(const Cam& c, float qx, float qy, float qz) {
   float cl[4];
 #pragma unroll
@@ -85,8 +79,7 @@ __device__ __forceinline__ Vtx project(const Cam& c, float qx, float qy, float q
                   c.M[4 * r + 3]);
   Vtx v;
   v.kept = cl[3] > 0.f;
-  const float rw = f_rcp(cl[3]);
-  const float nx = f_mul(cl[0], rw), ny = f_mul(cl[1], rw), nz = f_mul(cl[2], rw);
+  const float nx = f_div(cl[0], cl[3]), ny = f_div(cl[1], cl[3]), nz = f_div(cl[2], cl[3]);
   v.x = f_mul(f_add(f_mul(nx, 0.5f), 0.5f), (float)c.W);
   v.y = f_mul(f_add(f_mul(ny, 0.5f), 0.5f), (float)c.H);
   v.d = f_add(f_mul(nz, 0.5f), 0.5f);
@@ -117,11 +110,10 @@ __device__ __forceinline__ bool point_pixel(const Cam& c, int x, int y, int z, u
   for (int r = 0; r < 4; ++r)
     cl[r] = f_add(f_add(f_add(f_mul(c.M[4 * r], qx), f_mul(c.M[4 * r + 1], qy)), f_mul(c.M[4 * r + 2], qz)),
                   c.M[4 * r + 3]);
-  const float rw = f_rcp(cl[3]);
   const float W = (float)c.W, H = (float)c.H;
-  const float sx = f_mul(f_add(f_mul(f_mul(cl[0], rw), 0.5f), 0.5f), W);
-  const float sy = f_mul(f_add(f_mul(f_mul(cl[1], rw), 0.5f), 0.5f), H);
-  const float d = f_add(f_mul(f_mul(cl[2], rw), 0.5f), 0.5f);
+  const float sx = f_mul(f_add(f_mul(f_div(cl[0], cl[3]), 0.5f), 0.5f), W);
+  const float sy = f_mul(f_add(f_mul(f_div(cl[1], cl[3]), 0.5f), 0.5f), H);
+  const float d = f_add(f_mul(f_div(cl[2], cl[3]), 0.5f), 0.5f);
   p = (uint32_t)(int)fmaxf(0.f, fminf(sy, H - 1.f)) * (uint32_t)c.W + (uint32_t)(int)fmaxf(0.f, fminf(sx, W - 1.f));
   dbits = __float_as_uint(d);
   return cl[3] > 0.f && d >= 0.f && d <= 1.f && sx >= 0.f && sx < W && sy >= 0.f && sy < H;
@@ -252,25 +244,83 @@ __device__ __forceinline__ Vtx mesh_vertex(const MeshArgs& a, int64_t o, int tx,
   return project(a.c, f_of(xc - a.c.ox), f_of(yc - a.c.oy), qz);
 }
 
-// Triangle `half` (0: v00 v01 v11, 1: v00 v11 v10) of quad q.  Returns false when the
-// triangle is not drawn (a vertex not kept, a bad tile id).
-__device__ __forceinline__ bool mesh_tri(const MeshArgs& a, int64_t q, int half, Tri& t) {
+// Quad q: its heightmap, tile and texel (i, j); false (with the status set) for a bad
+// tile id.
+__device__ __forceinline__ bool mesh_quad_at(const MeshArgs& a, int64_t q, int64_t& o, int& tx, int& ty, int& i,
+                                             int& j) {
   const int qs = a.res - 1;
-  const int64_t o = q / ((int64_t)qs * qs);
-  const int rem = (int)(q - o * qs * qs), i = rem / qs, j = rem - i * qs;
+  o = q / ((int64_t)qs * qs);
+  const int rem = (int)(q - o * qs * qs);
+  i = rem / qs;
+  j = rem - i * qs;
   const int tile = a.tile_ids ? a.tile_ids[o] : (int)o;
   if (tile < 0 || tile >= a.tiles_x * a.tiles_y) {
     set_status(LS_ERR_INVALID_ARG);
     return false;
   }
-  const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-  // (v00, v01, v11) or (v00, v11, v10)
-  const int ii[3] = {i, half ? i + 1 : i, i + 1};
-  const int jj[3] = {j, j + 1, half ? j : j + 1};
+  tx = tile % a.tiles_x;
+  ty = tile / a.tiles_x;
+  return true;
+}
+
+// Corners c = 0..3 of a quad in the order v00, v01, v11, v10 (row offset c >> 1,
+// column offset 1 for c = 1, 2); triangle `half` (0: v00 v01 v11, 1: v00 v11 v10)
+// takes the corners 0, 1 + half, 2 + half.
+__device__ __forceinline__ int corner_di(int c) { return c >> 1; }
+__device__ __forceinline__ int corner_dj(int c) { return ((c + 1) >> 1) & 1; }
+__device__ __forceinline__ int tri_corner(int half, int k) { return k == 0 ? 0 : k + half; }
+
+// The four projected corners of quad q (each vertex projected once for both triangles).
+struct Quad {
+  Vtx v[4];
+  float r[4], g[4], b[4];
+};
+
+__device__ __forceinline__ bool mesh_quad(const MeshArgs& a, int64_t q, Quad& Q) {
+  int64_t o;
+  int tx, ty, i, j;
+  if (!mesh_quad_at(a, q, o, tx, ty, i, j)) return false;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Q.v[k] = mesh_vertex(a, o, tx, ty, i + corner_di(k), j + corner_dj(k), Q.r[k], Q.g[k], Q.b[k]);
+  return true;
+}
+
+// Triangle `half` of a projected quad; false when a vertex is not kept.  The corners
+// are chosen with selects, so the quad stays in registers.
+__device__ __forceinline__ void quad_corner(const Quad& Q, int c, Tri& t, int k, bool& ok) {
+  t.x[k] = Q.v[c].x;
+  t.y[k] = Q.v[c].y;
+  t.d[k] = Q.v[c].d;
+  t.r[k] = Q.r[c];
+  t.g[k] = Q.g[c];
+  t.b[k] = Q.b[c];
+  ok = ok && Q.v[c].kept;
+}
+
+__device__ __forceinline__ bool quad_tri(const Quad& Q, int half, Tri& t) {
+  bool ok = true;
+  quad_corner(Q, 0, t, 0, ok);
+  if (half) {
+    quad_corner(Q, 2, t, 1, ok);
+    quad_corner(Q, 3, t, 2, ok);
+  } else {
+    quad_corner(Q, 1, t, 1, ok);
+    quad_corner(Q, 2, t, 2, ok);
+  }
+  return ok;
+}
+
+// Triangle `half` of quad q, projected on its own (the CTA-wide path of large
+// triangles).
+__device__ __forceinline__ bool mesh_tri(const MeshArgs& a, int64_t q, int half, Tri& t) {
+  int64_t o;
+  int tx, ty, i, j;
+  if (!mesh_quad_at(a, q, o, tx, ty, i, j)) return false;
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const Vtx v = mesh_vertex(a, o, tx, ty, ii[k], jj[k], t.r[k], t.g[k], t.b[k]);
+    const int c = tri_corner(half, k);
+    const Vtx v = mesh_vertex(a, o, tx, ty, i + corner_di(c), j + corner_dj(c), t.r[k], t.g[k], t.b[k]);
     t.x[k] = v.x;
     t.y[k] = v.y;
     t.d[k] = v.d;
@@ -287,11 +337,12 @@ __global__ void __launch_bounds__(kMeshThreads) k_render_mesh(MeshArgs a) {
     if (threadIdx.x == 0) qn = 0;
     __syncthreads();
     const int64_t q = base + threadIdx.x;
-    if (q < total) {
+    Quad Q;
+    if (q < total && mesh_quad(a, q, Q)) {
 #pragma unroll 1
       for (int half = 0; half < 2; ++half) {
         Tri t;
-        if (!mesh_tri(a, q, half, t)) continue;
+        if (!quad_tri(Q, half, t)) continue;
         const TriSetup s = tri_setup(t, a.c.W, a.c.H);
         if (!s.ok) continue;
         const long long cand = (long long)(s.ixb - s.ixa + 1) * (s.iyb - s.iya + 1);
