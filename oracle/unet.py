@@ -268,3 +268,44 @@ def tile_inputs(res, tile_cm, cell_cm, tile_x0, tile_y0, z_scale, z_offset, radi
     x[..., 4] = (fill_h - cz) / r_m
     base_c = fill_c * 256.0 / 65535.0
     return x, base_c, cz, r_m
+
+
+# ------------------------------------------------------------------------------
+# finish (step a11): de-normalisation of the network output, the per-tile error
+# bound and the Gaussian fallback
+# ------------------------------------------------------------------------------
+
+def finish(y, base_h, base_c, cz, r_m, fill_h, fill_rgb, max_err_m):
+    """Final heights and 8-bit colours of a batch of tiles from the network output.
+
+    y [N,H,W,5] network output (residuals 0..3, error channel 4); base_h [N,H,W] the
+    Gaussian-fill height in patch space (fill - c_z)/r; base_c [N,H,W,3] the
+    Gaussian-fill colour in 0..1; cz [N] the patch centres in metres; r_m the patch
+    half side in metres; fill_h [N,H,W], fill_rgb [N,H,W,3] the Gaussian fill itself.
+
+    * de-normalisation (Sec. 3.3/3.4: patch space is (z - c_z)/r, so z = z'·r + c_z):
+      height = (base_h + y0)·r + c_z;
+    * colour: c = base_c + y1..3, clamped to 0..1, 8 bits by round half up of c·255;
+    * error bound (a reading; the paper has none): the root mean square of the
+      clamped error channel max(y4, 0) over the tile's texels, times r (a NaN in
+      the channel makes the bound NaN);
+    * fallback: a tile whose bound is not <= max_err_m (above it, or NaN) takes the
+      Gaussian fill unchanged.
+    Returns (height, rgb8, bound [N], used_fallback [N] in {0, 1})."""
+    n = y.shape[0]
+    height = np.empty(base_h.shape)
+    rgb = np.empty(base_c.shape, dtype=np.uint8)
+    bound = np.empty(n)
+    used = np.empty(n, dtype=np.uint8)
+    for o in range(n):
+        e = np.where(y[o, ..., 4] < 0.0, 0.0, y[o, ..., 4])  # a NaN output stays NaN
+        bound[o] = np.sqrt(np.mean(e * e)) * r_m
+        used[o] = 0 if bound[o] <= max_err_m else 1
+        if used[o]:
+            height[o] = fill_h[o]
+            rgb[o] = fill_rgb[o]
+            continue
+        height[o] = (base_h[o] + y[o, ..., 0]) * r_m + cz[o]
+        c = np.clip(base_c[o] + y[o, ..., 1:4], 0.0, 1.0)
+        rgb[o] = np.floor(c * 255.0 + 0.5).astype(np.uint8)
+    return height, rgb, bound, used

@@ -120,7 +120,8 @@ __global__ void __launch_bounds__(kLearnedThreads) k_finish(const float* __restr
   for (int64_t o = blockIdx.x; o < n; o += gridDim.x) {
     float s = 0.f;
     for (int e = threadIdx.x; e < np; e += blockDim.x) {
-      const float b = fmaxf(y[((size_t)o * np + e) * 5 + 4], 0.f);
+      const float v = y[((size_t)o * np + e) * 5 + 4];
+      const float b = v < 0.f ? 0.f : v;  // max(v, 0) that keeps a NaN (fmaxf would drop it)
       s += b * b;
     }
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);

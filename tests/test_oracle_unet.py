@@ -167,3 +167,45 @@ def test_tile_inputs_hand_case():
     assert x[0, 0, 3] == 1.5 and x[0, 1, 3] == 2.0 and x[5, 5, 3] == 0.0
     assert x[0, 0, 4] == pytest.approx(-0.1) and x[4, 4, 4] == 0.0
     assert bc[0, 0, 0] == pytest.approx(128 * 256 / 65535)
+
+
+def test_finish_hand_case():
+    """Step a11 by hand: de-normalisation z'·r + c_z, colour clamp and half-up rounding,
+    the bound as the RMS of the clamped error channel times r, and the fallback select
+    on both sides of 2 m and on a NaN bound."""
+    r = 320.0
+    n, res = 5, 4
+    y = np.zeros((n, res, res, 5))
+    base_h = np.full((n, res, res), 0.5)
+    base_c = np.full((n, res, res, 3), 0.25)
+    cz = np.array([100.0, -20.0, 7.0, 0.0, 3.0])
+    fill_h = np.full((n, res, res), -1.0)
+    fill_rgb = np.full((n, res, res, 3), 9, np.uint8)
+    y[..., 0] = 0.25                         # height = 0.75 * 320 + cz
+    y[0, 0, 0, 1:4] = [0.25, 0.95, -0.5]     # colour 0.5 -> 128 (half up), 1.2 -> 255, -0.25 -> 0
+    y[0, 0, 1, 1] = (63.5 - 1e-6) / 255.0 - 0.25   # just below a half level: rounds down to 63
+    # tile 0: error channel all negative -> bound 0
+    y[0, ..., 4] = -3.0
+    # tile 1: a constant error channel gives bound = value * r; just under 2 m
+    y[1, ..., 4] = (2.0 - 1e-9) / r
+    # tile 2: just over 2 m
+    y[2, ..., 4] = (2.0 + 1e-9) / r
+    # tile 3: one NaN in the error channel -> NaN bound -> fallback
+    y[3, 1, 2, 4] = np.nan
+    # tile 4: half the texels at e and half negative: RMS = e / sqrt(2)
+    y[4, :2, :, 4] = 2.0 * np.sqrt(2.0) / r * 0.999
+    y[4, 2:, :, 4] = -1.0
+    h, c, bound, used = U.finish(y, base_h, base_c, cz, r, fill_h, fill_rgb, 2.0)
+    assert bound[0] == 0.0
+    assert bound[1] == pytest.approx(2.0 - 1e-9, abs=1e-12) and used[1] == 0
+    assert bound[2] == pytest.approx(2.0 + 1e-9, abs=1e-12) and used[2] == 1
+    assert np.isnan(bound[3]) and used[3] == 1
+    assert bound[4] == pytest.approx(2.0 * 0.999) and used[4] == 0
+    assert list(used) == [0, 0, 1, 1, 0]
+    for o in (0, 1, 4):
+        np.testing.assert_allclose(h[o], 0.75 * r + cz[o], rtol=0, atol=1e-12)
+    for o in (2, 3):
+        assert (h[o] == -1.0).all() and (c[o] == 9).all()
+    assert list(c[0, 0, 0]) == [128, 255, 0]
+    assert c[0, 0, 1, 0] == 63
+    assert (c[1] == 64).all()            # 0.25 * 255 = 63.75 -> 64
