@@ -121,8 +121,9 @@ ls_status ls_bin_points(const ls_points *pts, const ls_region *region, const ls_
  * array of 2^20 rows (4 MiB) compiled into the library, held by every GPU that loads
  * it until the process exits; regions with more than 2^20 fine rows (tiles *
  * levels[0].cells) are rejected with LS_ERR_UNSUPPORTED.  Nothing is allocated: the
- * first call on a device looks up the array's device address (make that first call
- * before any stream capture).  All calls share the array, which keeps the last
+ * first call on a device looks up the array's device address and caches it (make
+ * that first call before any stream capture; ls_release_workspace drops the cache,
+ * which a device reset makes stale).  All calls share the array, which keeps the last
  * call's contents (every call clears the states it uses): calls that overlap on the
  * GPU, on any streams, race and must be serialised by the caller. */
 ls_status ls_bin_points_fixed_scratch(const ls_points *pts, const ls_region *region,
@@ -393,8 +394,8 @@ ls_status ls_cnn_inputs(const float *lin_height, const float *nn_height, const u
  *    and y likewise (integers, cell = tile_cm / res), q.z = ((h - (float)z_offset) *
  *    (float)(1 / z_scale)) - (float)oz; a NaN height drops the texel's triangles;
  *  - clip c_r = ((M[r][0] q.x + M[r][1] q.y) + M[r][2] q.z) + M[r][3], M row-major;
- *  - visible iff c_w > 0; ndc = c_xyz * r with r = 1 / c_w (the correctly rounded
- *    reciprocal); screen sx = (ndc_x * 0.5 + 0.5) * width,
+ *  - visible iff c_w > 0; ndc = c_xyz / c_w (three IEEE quotients); screen
+ *    sx = (ndc_x * 0.5 + 0.5) * width,
  *    sy = (ndc_y * 0.5 + 0.5) * height; depth d = ndc_z * 0.5 + 0.5, kept iff
  *    0 <= d <= 1;
  *  - colours: 16-bit point colours round half up to 8 bits; heightmap colours as given.
@@ -550,9 +551,14 @@ ls_status ls_learned_inputs(const ls_points *samples, const ls_region *region,
  * patch space with the tile's cz, mean R, G, B / 65535), mask = count > 0. */
 ls_status ls_learned_targets(const ls_bins *bins, const ls_region *region, const int32_t *tile_ids,
                              int64_t n, const float *cz, float *target, uint8_t *mask, ls_stream_t stream);
-/* height = (base + y0) * r + cz, colour = round(clamp(base + y1..3, 0, 1) * 255); tile
- * bound = RMS(max(y4, 0)) * r metres; tiles whose bound exceeds max_err_m (or is NaN)
- * take the Gaussian fill instead.  err_bound [n] and used_fallback [n] may be NULL. */
+/* Step a11 (Sec. 3.3/3.4 de-normalisation; the bound is this library's reading, the
+ * paper has none).  height = (base + y0) * r + cz, colour = floor(clamp(base + y1..3,
+ * 0, 1) * 255 + 0.5); tile bound = RMS(max(y4, 0)) * r metres, where a NaN in y4 makes
+ * the bound NaN; tiles whose bound is not <= max_err_m (above it, or NaN) take the
+ * Gaussian fill (fill_height, fill_rgb) unchanged.  y: fp32 [n][res][res][5]; base:
+ * fp32 [n][res][res][4] (Gaussian height in patch space, colour in 0..1); cz [n] metres;
+ * height/rgb may alias fill_height/fill_rgb.  err_bound [n] and used_fallback [n] may
+ * be NULL. */
 ls_status ls_learned_finish(const float *y, const float *base, const float *cz, int64_t n, int32_t res,
                             const ls_region *region, float max_err_m, const float *fill_height,
                             const uint8_t *fill_rgb, float *height, uint8_t *rgb, float *err_bound,
@@ -574,7 +580,26 @@ ls_status ls_fill_learned(ls_model *model, const float *params, const ls_points 
 const char *ls_status_string(ls_status s);
 /* Synchronises the current device, returns and clears its sticky device status. */
 ls_status ls_last_error(void);
-/* Frees the library scratch workspace of the current device (synchronises it). */
+/* Failure detection without a GPU fault (the paper has no counterpart).  Every wait
+ * of the library's kernels on another thread's progress (binning row states, the
+ * fill's and the tensor-core kernels' mbarriers) gives up after a number of polls,
+ * sets LS_ERR_TIMEOUT in the sticky status and lets the kernel return.
+ * ls_set_spin_limit sets that number for the current device (polls <= 0 restores the
+ * default, 2^22); it synchronises the device first, so no kernel of the library runs
+ * while the limit changes.  A short limit is meant for tests only: with it, an
+ * ordinary wait can run out, and the results of that call are then undefined (the
+ * status says so).  Only binning and ls_probe_wait, whose waits poll global memory
+ * with no copy in flight, should run under a short limit.
+ * ls_probe_wait runs the binning's row wait once, in one thread, on the caller's
+ * device flag (4-byte aligned): it returns when *flag == 2, or sets LS_ERR_TIMEOUT
+ * when the limit runs out first.  Either way the kernel ends and the context stays
+ * usable; the wait counts in ls_bin_stats (out[1], and out[2] when it ran out). */
+ls_status ls_set_spin_limit(int32_t polls);
+ls_status ls_probe_wait(const uint32_t *flag, ls_stream_t stream);
+/* Frees the library scratch workspace of the current device (synchronises it) and
+ * forgets the cached device address of the fixed binning scratch.  After a device
+ * reset (cudaDeviceReset) every device pointer the library cached is stale: call this
+ * before the next library call on that device. */
 ls_status ls_release_workspace(void);
 /* Library version as major * 10000 + minor * 100 + patch. */
 int32_t ls_version(void);

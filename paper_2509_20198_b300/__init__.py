@@ -366,6 +366,16 @@ def last_error():
     return N.lib().ls_last_error()
 
 
+def set_spin_limit(polls=0):
+    """Polls before any bounded device wait gives up (0 restores the default)."""
+    N.check("ls_set_spin_limit", N.lib().ls_set_spin_limit(int(polls)))
+
+
+def probe_wait(flag, stream=None):
+    """Run the binning's bounded row wait on a one-element int32 device tensor."""
+    N.check("ls_probe_wait", N.lib().ls_probe_wait(_ptr(_dev(flag, "flag")), _stream(stream)))
+
+
 def release_workspace():
     N.check("ls_release_workspace", N.lib().ls_release_workspace())
 

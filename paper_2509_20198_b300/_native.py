@@ -118,6 +118,8 @@ SIGNATURES = {
                          ctypes.c_size_t, VP], I32),
     "ls_status_string": ([I32], ctypes.c_char_p),
     "ls_last_error": ([], I32),
+    "ls_set_spin_limit": ([I32], I32),
+    "ls_probe_wait": ([VP, VP], I32),
     "ls_release_workspace": ([], I32),
     "ls_version": ([], I32),
 }

@@ -198,8 +198,9 @@ __device__ void wait_written(const uint32_t* state) {
   if (ld_acquire(state) == 2u) return;
   atomicAdd(&g_bin_stats[1], 1ull);
   int it = 0;
+  const int limit = spin_limit();
   while (ld_acquire(state) != 2u) {
-    if (++it > kSpinLimit) {
+    if (++it > limit) {
       set_status(LS_ERR_TIMEOUT);
       atomicAdd(&g_bin_stats[2], 1ull);
       return;
@@ -989,16 +990,17 @@ ls_status bin_prepare(const ls_points* pts, const ls_region* region, const ls_bi
 }
 
 ls_status bin_launch(BinArgs a, size_t smem, int64_t n_coarse, cudaStream_t stream) {
-  static bool attr_set[64] = {};
+  static DeviceOnce once;
   int dev = 0;
   LS_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    LS_CUDA_TRY(cudaFuncSetAttribute(k_bin_main<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBinSmemAttr));
-    LS_CUDA_TRY(cudaFuncSetAttribute(k_bin_main<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBinSmemAttr));
-    LS_CUDA_TRY(cudaFuncSetAttribute(k_bin_main<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBinSmemAttr));
-    LS_CUDA_TRY(cudaFuncSetAttribute(k_bin_main<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBinSmemAttr));
-    attr_set[dev] = true;
-  }
+  const bool ok = device_once(once, dev, [] {
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    return cudaFuncSetAttribute(k_bin_main<1>, attr, kBinSmemAttr) == cudaSuccess &&
+           cudaFuncSetAttribute(k_bin_main<2>, attr, kBinSmemAttr) == cudaSuccess &&
+           cudaFuncSetAttribute(k_bin_main<3>, attr, kBinSmemAttr) == cudaSuccess &&
+           cudaFuncSetAttribute(k_bin_main<4>, attr, kBinSmemAttr) == cudaSuccess;
+  });
+  if (!ok) return LS_ERR_CUDA;
   const int64_t work = a.n_rows > n_coarse ? a.n_rows : n_coarse;
   k_bin_prologue<<<grid_cap((work + 255) / 256, kSmCount * 8), 256, 0, stream>>>(a, n_coarse);
   if (a.n_items > 0) {
@@ -1015,6 +1017,21 @@ ls_status bin_launch(BinArgs a, size_t smem, int64_t n_coarse, cudaStream_t stre
 }
 
 }  // namespace ls
+
+namespace ls {
+namespace {
+// One thread runs the binning's bounded row wait on a caller's flag.
+__global__ void k_probe_wait(const uint32_t* flag) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) wait_written(flag);
+}
+}  // namespace
+}  // namespace ls
+
+extern "C" ls_status ls_probe_wait(const uint32_t* flag, ls_stream_t stream) {
+  if (!flag || (reinterpret_cast<uintptr_t>(flag) & 3u)) return LS_ERR_INVALID_ARG;
+  ls::k_probe_wait<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(flag);
+  return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
+}
 
 extern "C" ls_status ls_bin_stats(uint64_t* out, int32_t reset) {
   if (!out) return LS_ERR_INVALID_ARG;
@@ -1067,6 +1084,11 @@ static __device__ __align__(256) uint32_t g_bin_rows_fixed[kFixedBinRows + 64]; 
 std::mutex g_fixed_mu;
 uint32_t* g_fixed_ptr[64] = {};
 }  // namespace
+
+void forget_fixed_scratch(int dev) {
+  std::lock_guard<std::mutex> lock(g_fixed_mu);
+  if (dev >= 0 && dev < 64) g_fixed_ptr[dev] = nullptr;
+}
 }  // namespace ls
 
 extern "C" ls_status ls_bin_points_fixed_scratch(const ls_points* pts, const ls_region* region,

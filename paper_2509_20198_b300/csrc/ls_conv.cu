@@ -31,16 +31,17 @@ namespace ls {
 
 bool encode_tmap_bf16_4d(CUtensorMap* map, const void* base, const uint64_t dims[4], const uint64_t strides[3],
                          const uint32_t box[4], int swizzle_bytes) {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  // looked up once (a function-local static: thread-safe initialisation)
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     cudaDriverEntryPointQueryResult q;
     void* p = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
             cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !p)
-      return false;
-    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  if (!fn) return false;
   cuuint64_t d[4] = {dims[0], dims[1], dims[2], dims[3]};
   cuuint64_t s[3] = {strides[0], strides[1], strides[2]};
   cuuint32_t b[4] = {box[0], box[1], box[2], box[3]};
@@ -359,14 +360,14 @@ ls_status conv3x3_launch_groups(const uint16_t* x, const uint16_t* wpk, const fl
   a.ring = (int32_t)std::min<size_t>(kConvStages, budget / a.stage_bytes);
   if (a.ring < 2) return LS_ERR_UNSUPPORTED;
   const size_t smem = (size_t)a.ring * a.stage_bytes;
-  static bool attr_set[64] = {};
+  static DeviceOnce once;
   int dev = 0;
   LS_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    LS_CUDA_TRY(cudaFuncSetAttribute(k_conv3x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kConvSmemBudget));
-    attr_set[dev] = true;
-  }
+  if (!device_once(once, dev, [] {
+        return cudaFuncSetAttribute(k_conv3x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kConvSmemBudget) == cudaSuccess;
+      }))
+    return LS_ERR_CUDA;
   const int per_sm = a.tmem_cols <= 128 ? 3 : a.tmem_cols <= 256 ? 2 : 1;
   k_conv3x3<<<grid_cap(a.n_mtiles, (int64_t)kSmCount * per_sm), kConvThreads, smem, stream>>>(map, a);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;

@@ -330,9 +330,10 @@ __global__ void __launch_bounds__(kFillThreads, 2) k_fill(FillArgs f) {  // 2 CT
     __syncthreads();
     const bool use_stage = staged;
     if (use_stage && stage_n > 0) {
-      int it = 0;
+      int it = 0, limit = 0;
       while (!mbar_try_wait(&bar, phase)) {
-        if (++it > kSpinLimit) { set_status(LS_ERR_TIMEOUT); break; }
+        if (it == 0) limit = spin_limit();
+        if (++it > limit) { set_status(LS_ERR_TIMEOUT); break; }
       }
       phase ^= 1u;
     }
@@ -530,15 +531,14 @@ ls_status fill_launch(const ls_points* samples, const ls_region* region, const l
   f.rgb = rgb;
   f.aux_hc = aux_hc;
   f.aux_d = aux_d;
-  static bool attr_set[64] = {};
+  static DeviceOnce once;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return LS_ERR_CUDA;
-  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    if (cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kStageCap * sizeof(Rec))) != cudaSuccess)
-      return LS_ERR_CUDA;
-    attr_set[dev] = true;
-  }
+  if (!device_once(once, dev, [] {
+        return cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(kStageCap * sizeof(Rec))) == cudaSuccess;
+      }))
+    return LS_ERR_CUDA;
   // launch shape: tuned for this key (ls_tune_fill_sparse / ls_fill_shape_set), else the
   // default: few tiles are split over 4 CTAs (bands of res / 4 texel rows, whole 4-row
   // blocks), and the persistent grid assumes 2 resident CTAs per SM

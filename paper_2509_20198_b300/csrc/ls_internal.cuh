@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "lidarscout.h"
 
 namespace ls {
@@ -19,8 +21,13 @@ __device__ int g_status = 0;
 
 __device__ __forceinline__ void set_status(int code) { atomicCAS(&g_status, 0, code); }
 
-// Bounded spin limit for every device-side wait (iterations of >= 64 ns each).
-constexpr int kSpinLimit = 1 << 22;
+// Bounded spin limit for every device-side wait, in polls (the binning's row waits
+// sleep 64 ns between polls).  A device variable, so that tests of failure detection
+// can shorten it (ls_set_spin_limit).  Kernels read it only once a wait's first poll
+// has failed, so the fast path of a wait costs no load.
+constexpr int kSpinLimitDefault = 1 << 22;
+__device__ int g_spin_limit = kSpinLimitDefault;
+__device__ __forceinline__ int spin_limit() { return g_spin_limit; }
 
 // ---------------------------------------------------------------------------------
 // Unsigned 32-bit division by a run-time invariant divisor, after Granlund and
@@ -64,6 +71,9 @@ enum WorkspaceSlot {
 };
 // Returns a device pointer of at least `bytes` for the given slot (nullptr on failure).
 void* workspace(WorkspaceSlot slot, size_t bytes);
+// Forgets the cached device address of the fixed binning scratch of a device, so that
+// the next call looks it up again (ls_release_workspace; after a device reset).
+void forget_fixed_scratch(int dev);
 
 // ---------------------------------------------------------------------------------
 // Launch shapes and their autotuner (ls_tune.cu).  A call's key groups the arguments
@@ -79,6 +89,25 @@ void bin_shape_lookup(uint64_t key, BinShape* out);
 void fill_shape_lookup(uint64_t key, int32_t res, int64_t n_out, FillShape* out);
 bool bin_shape_valid(const BinShape& s);
 bool fill_shape_valid(const FillShape& s, int32_t res);
+
+// One-time set-up per device (kernel attributes, occupancy queries).  The first
+// caller on a device runs `fn` under a lock; callers from other host threads wait for
+// it and then see its effects.  `fn` returns false on failure, and the next call
+// tries again.  Devices beyond the table run `fn` on every call.
+constexpr int kMaxDevicesOnce = 64;
+struct DeviceOnce {
+  std::mutex mu;
+  bool done[kMaxDevicesOnce] = {};
+};
+template <class F>
+inline bool device_once(DeviceOnce& o, int dev, F&& fn) {
+  if (dev < 0 || dev >= kMaxDevicesOnce) return fn();
+  std::lock_guard<std::mutex> lock(o.mu);
+  if (o.done[dev]) return true;
+  if (!fn()) return false;
+  o.done[dev] = true;
+  return true;
+}
 
 inline int grid_cap(int64_t blocks, int64_t cap) {
   if (blocks < 1) blocks = 1;

@@ -660,32 +660,34 @@ extern "C" ls_status ls_fill_interp(const ls_points* samples, const ls_region* r
   const size_t mid1_smem = sizeof(InterpWarp<kInterpMid1Cap>);
   const size_t mid_smem = sizeof(InterpWarp<kInterpMidCap>);
   const size_t big_smem = sizeof(InterpWarp<kInterpBigCap>);
-  static bool attr_set[64] = {};
+  // kernel attributes and resident CTAs per SM of the tiers, once per device
+  static DeviceOnce once;
+  static int small_per_sm[kMaxDevicesOnce] = {}, mid1_per_sm[kMaxDevicesOnce] = {}, mid_per_sm[kMaxDevicesOnce] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return LS_ERR_CUDA;
-  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    LS_CUDA_TRY(cudaFuncSetAttribute(k_interp<kInterpSmallCap, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)small_smem));
-    LS_CUDA_TRY(cudaFuncSetAttribute(k_interp<kInterpMid1Cap, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)mid1_smem));
-    LS_CUDA_TRY(cudaFuncSetAttribute(k_interp<kInterpMidCap, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)mid_smem));
-    LS_CUDA_TRY(cudaFuncSetAttribute(k_interp<kInterpBigCap, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)big_smem));
-    attr_set[dev] = true;
-  }
-  static int small_per_sm[64] = {}, mid1_per_sm[64] = {}, mid_per_sm[64] = {};
-  if (dev >= 0 && dev < 64 && small_per_sm[dev] == 0) {
+  const bool known = dev >= 0 && dev < kMaxDevicesOnce;
+  const bool ok = device_once(once, dev, [&] {
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (cudaFuncSetAttribute(k_interp<kInterpSmallCap, 0>, attr, (int)small_smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_interp<kInterpMid1Cap, 1>, attr, (int)mid1_smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_interp<kInterpMidCap, 2>, attr, (int)mid_smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_interp<kInterpBigCap, 3>, attr, (int)big_smem) != cudaSuccess)
+      return false;
     int b = 0, c1 = 0, c = 0;
-    LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_interp<kInterpSmallCap, 0>,
-                                                              32 * kInterpSmallWarps, small_smem));
-    LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c1, k_interp<kInterpMid1Cap, 1>, 32, mid1_smem));
-    LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_interp<kInterpMidCap, 2>, 32, mid_smem));
-    small_per_sm[dev] = b > 0 ? b : 1;
-    mid1_per_sm[dev] = c1 > 0 ? c1 : 1;
-    mid_per_sm[dev] = c > 0 ? c : 1;
-  }
-  const bool known = dev >= 0 && dev < 64;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_interp<kInterpSmallCap, 0>, 32 * kInterpSmallWarps,
+                                                      small_smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c1, k_interp<kInterpMid1Cap, 1>, 32, mid1_smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_interp<kInterpMidCap, 2>, 32, mid_smem) != cudaSuccess)
+      return false;
+    if (known) {
+      small_per_sm[dev] = b > 0 ? b : 1;
+      mid1_per_sm[dev] = c1 > 0 ? c1 : 1;
+      mid_per_sm[dev] = c > 0 ? c : 1;
+    }
+    return true;
+  });
+  if (!ok) return LS_ERR_CUDA;
   const int per_sm = known ? small_per_sm[dev] : 1, mid_sm = known ? mid_per_sm[dev] : 1;
   const int mid1_sm = known ? mid1_per_sm[dev] : 1;
   k_interp<kInterpSmallCap, 0>

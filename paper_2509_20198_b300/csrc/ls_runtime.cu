@@ -77,7 +77,14 @@ ls_status ls_release_workspace(void) {
     ls::g_ws[dev].ptr[s] = nullptr;
     ls::g_ws[dev].size[s] = 0;
   }
+  ls::forget_fixed_scratch(dev);
   return LS_OK;
+}
+
+ls_status ls_set_spin_limit(int32_t polls) {
+  const int v = polls > 0 ? polls : ls::kSpinLimitDefault;
+  if (cudaDeviceSynchronize() != cudaSuccess) return LS_ERR_CUDA;
+  return cudaMemcpyToSymbol(ls::g_spin_limit, &v, sizeof(int)) == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 
 int32_t ls_version(void) { return 100; }

@@ -43,7 +43,9 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
 // Bounded wait for the phase of the given parity; false (and the sticky status set)
 // when the limit runs out.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < kSpinLimit; ++it)
+  if (mbar_test(bar, parity)) return true;
+  const int limit = spin_limit();
+  for (int it = 1; it < limit; ++it)
     if (mbar_test(bar, parity)) return true;
   set_status(LS_ERR_TIMEOUT);
   return false;

@@ -401,14 +401,14 @@ ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int 
   uint8_t* ws = static_cast<uint8_t*>(workspace(kWsGradPart, part_bytes + db_bytes));
   if (!ws) return LS_ERR_NO_MEMORY;
   a.part = reinterpret_cast<float*>(ws);
-  static bool attr_set[64] = {};
+  static DeviceOnce once;
   int dev = 0;
   LS_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    LS_CUDA_TRY(cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (kWgRaw + kWgOps) * (kWgABytes + 128 * kWgPix * 2)));
-    attr_set[dev] = true;
-  }
+  if (!device_once(once, dev, [] {
+        return cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (kWgRaw + kWgOps) * (kWgABytes + 128 * kWgPix * 2)) == cudaSuccess;
+      }))
+    return LS_ERR_CUDA;
   k_wgrad<<<(unsigned)ctas, kWgThreads, smem, stream>>>(xmap, dzmap, a);
   const bool ones = a.ones_row >= 0;
   k_wsum<<<grid_cap(((a.rows + 1) * cout + 255) / 256, kSmCount * 4), 256, 0, stream>>>(

@@ -1,13 +1,16 @@
 """ls_bin_points_fixed_scratch: the binning entry point for callers that cannot
 allocate device memory during the call (its per-row scratch is a fixed array inside
 the library).  Called through the C ABI, twice in a row, it must give exactly the
-results of ls_bin_points (binning is bit-exact).  This file is collected last."""
+results of ls_bin_points and of the oracle (binning is bit-exact), and the device's
+free memory must not change across the two calls.  This file is collected last."""
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
+from tests.helpers import assert_bins_equal
 
 pytestmark = pytest.mark.gpu
 
@@ -42,18 +45,28 @@ def test_fixed_scratch_binning_matches_ls_bin_points_twice():
     dref = torch.zeros(1, dtype=torch.int64, device="cuda")
     N.check("ls_bin_points", L.ls_bin_points(ctypes.byref(P), ctypes.byref(R), arr_ref, 2,
                                             ctypes.c_void_p(dref.data_ptr()), None))
-    for call in range(2):
-        got, arr = _levels(N, torch, T, (640, 64))
-        dg = torch.full((1,), 99, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    # outputs of both calls allocated up front; the library's own workspace released,
+    # so that an allocation inside the calls would show in the device's free memory
+    outs = [_levels(N, torch, T, (640, 64)) + (torch.full((1,), 99, dtype=torch.int64, device="cuda"),)
+            for _ in range(2)]
+    N.check("ls_release_workspace", L.ls_release_workspace())
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for call, (got, arr, dg) in enumerate(outs):
         N.check("ls_bin_points_fixed_scratch",
                 L.ls_bin_points_fixed_scratch(ctypes.byref(P), ctypes.byref(R), arr, 2,
                                               ctypes.c_void_p(dg.data_ptr()), None))
         torch.cuda.synchronize()
         assert L.ls_last_error() == 0
+    assert torch.cuda.mem_get_info()[0] == free0, "the fixed-scratch calls allocated device memory"
+    for call, (got, arr, dg) in enumerate(outs):
         for lv in range(2):
             for k in KEYS:
                 assert torch.equal(got[lv][k], ref[lv][k]), (call, lv, k)
         assert int(dg.item()) == int(dref.item())
+    for lv, cells in enumerate((640, 64)):
+        assert_bins_equal(outs[1][0][lv], oracle.bin_points(pts, region, cells), msg=f"oracle cells={cells}")
 
 
 def test_fixed_scratch_rejects_regions_over_the_limit():
