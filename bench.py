@@ -887,9 +887,10 @@ def run_profile_case(args):
     return 0 if st == 0 else 1
 
 
-def run_fill_case(args):
+def run_fill_case(args, overview=False):
     """Profiling case for the Gaussian fill: the chunk samples of a k x k-tile region at
-    the batched-region densities, filled at 64x64 (R 120 m, sigma 40 m)."""
+    the batched-region densities (or, overview=True, at the overview's 4 pts/m^2, 33
+    samples per tile), filled at 64x64 (R 120 m, sigma 40 m)."""
     import torch
     import paper_2509_20198_b300 as lsb
     import synth
@@ -899,7 +900,7 @@ def run_fill_case(args):
     build.build_synth()
     k = args.case_tiles
     region = synth.Region(tiles_x=k, tiles_y=k)
-    counts = synth.lognormal_counts(SEED, k * k)
+    counts = synth.uniform_counts(k * k, 4.0) if overview else synth.lognormal_counts(SEED, k * k)
     s = sg.region_samples(SEED, region, counts)
     h, c = lsb.fill_sparse(s, region)
     for _ in range(args.steps):
@@ -1027,7 +1028,8 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--overview", type=int, default=1, help="also time the 40,000-tile overview fills")
-    ap.add_argument("--case", default="", choices=["", "bin-small", "learned", "fill", "interp", "render", "paper-cnn"],
+    ap.add_argument("--case", default="", choices=["", "bin-small", "learned", "fill", "fill-overview", "interp", "render",
+                                                   "paper-cnn"],
                     help="profiling case instead of the bench")
     ap.add_argument("--case-tiles", type=int, default=3, help="tiles per side of the profiling case")
     ap.add_argument("--train-tiles", type=int, default=4096)
@@ -1038,8 +1040,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.case == "learned":
         sys.exit(run_learned_case(args))
-    if args.case == "fill":
-        sys.exit(run_fill_case(args))
+    if args.case in ("fill", "fill-overview"):
+        sys.exit(run_fill_case(args, overview=args.case == "fill-overview"))
     if args.case == "interp":
         sys.exit(run_interp_case(args))
     if args.case == "render":

@@ -34,8 +34,10 @@ struct __align__(16) Rec {
 static_assert(sizeof(Rec) == 32, "record size");
 
 constexpr int kFillThreads = 256;
-constexpr int kStageCap = 2048;  // staged samples per tile (64 KB)
+constexpr int kStageCap = 2048;  // most staged samples per tile (64 KB)
 constexpr int kOutStageRes = 64; // texel maps up to 64x64 are staged in shared memory
+constexpr int kCandCap = 256;    // candidate list of a block row (indices into the stage)
+constexpr int kFillMaxCtasPerSm = 3;
 
 // ---------------------------------------------------------------------------------
 // extraction
@@ -112,9 +114,11 @@ struct FillArgs {
   int64_t n_out;
   int64_t n_samples;  // records in recs
   int32_t tiles_x, tiles_y, tile_cm, res, cell_cm;
-  int64_t R2;
+  uint32_t R2u;  // R^2 (R < 65536)
   int32_t R;
-  float k_exp;  // 1 / (2 sigma^2)
+  float k2;     // log2(e) / (2 sigma^2): w = 2^(-d^2 k2)
+  float zs_f;   // z_scale in FP32
+  int32_t stage_cap;  // records the dynamic shared stage holds
   double z_scale, z_offset;
   float* height;
   uint8_t* rgb;
@@ -179,21 +183,34 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 struct LaneAcc {
   float sw, swz, swr, swg, swb;
-  long long bd2;  // nearest squared distance (-1: none yet)
-  int bidx;
-  int bz;
-  uint32_t brg, bb;
+  long long bd2;  // nearest squared distance (LLONG_MAX: none yet)
+  int bidx;       // its sample index (records are indexed by sample)
 };
 
-__device__ __forceinline__ void consider_nearest(LaneAcc& a, long long d2, const Rec& q) {
-  if (a.bd2 < 0 || d2 < a.bd2 || (d2 == a.bd2 && q.idx < a.bidx)) {
-    a.bd2 = d2; a.bidx = q.idx; a.bz = q.z; a.brg = q.rg; a.bb = q.b;
+// One sample for this lane's texel: the nearest by exact squared distance (ties: lower
+// sample index), and, within R, the Gaussian weight on height (relative to the tile's
+// reference zref) and colour.  R^2 <= tile_cm^2 < 2^32, so an in-radius d2 converts
+// to float from 32 bits.
+__device__ __forceinline__ void weigh(const Rec& q, int cx, int cy, int zref, uint32_t R2, float k2, LaneAcc& a) {
+  const int dx = q.lx - cx, dy = q.ly - cy;
+  const long long d2 = (long long)dx * dx + (long long)dy * dy;
+  if (d2 < a.bd2 || (d2 == a.bd2 && q.idx < a.bidx)) {
+    a.bd2 = d2;
+    a.bidx = q.idx;
+  }
+  if (d2 <= (long long)R2) {
+    const float w = exp2f(-__uint2float_rn((uint32_t)d2) * k2);
+    a.sw += w;
+    a.swz = fmaf(w, (float)(q.z - zref), a.swz);
+    a.swr = fmaf(w, (float)(q.rg & 0xffffu), a.swr);
+    a.swg = fmaf(w, (float)(q.rg >> 16), a.swg);
+    a.swb = fmaf(w, (float)q.b, a.swb);
   }
 }
 
-// Weigh the samples recs[0..n) that fall in the warp's box for this lane's texel.
-__device__ __forceinline__ void splat_range(const Rec* recs, int n, int bx0, int bx1, int by0, int by1,
-                                            int cx, int cy, const FillArgs& f, int& zref, LaneAcc& a) {
+// Weigh, for this lane's texel, the samples recs[0..n) that fall in the warp's box.
+__device__ __forceinline__ void splat_range(const Rec* recs, int n, int bx0, int bx1, int by0, int by1, int cx,
+                                            int cy, int zref, uint32_t R2, float k2, LaneAcc& a) {
   const int lane = threadIdx.x & 31;
   for (int base = 0; base < n; base += 32) {
     bool in = false;
@@ -205,19 +222,28 @@ __device__ __forceinline__ void splat_range(const Rec* recs, int n, int bx0, int
     while (mask) {
       const int src = __ffs(mask) - 1;
       mask &= mask - 1;
-      const Rec q = recs[base + src];
-      if (zref == INT_MIN) zref = q.z;  // warp-uniform provisional height reference
-      const int dx = q.lx - cx, dy = q.ly - cy;
-      const long long d2 = (long long)dx * dx + (long long)dy * dy;
-      consider_nearest(a, d2, q);
-      if (d2 <= f.R2) {
-        const float w = __expf(-(float)d2 * f.k_exp);
-        a.sw += w;
-        a.swz = fmaf(w, (float)(q.z - zref), a.swz);
-        a.swr = fmaf(w, (float)(q.rg & 0xffffu), a.swr);
-        a.swg = fmaf(w, (float)(q.rg >> 16), a.swg);
-        a.swb = fmaf(w, (float)q.b, a.swb);
-      }
+      weigh(recs[base + src], cx, cy, zref, R2, k2, a);
+    }
+  }
+}
+
+// The same over a candidate list (indices into the staged records).
+__device__ __forceinline__ void splat_list(const Rec* stage, const uint16_t* cand, int n, int bx0, int bx1, int by0,
+                                           int by1, int cx, int cy, int zref, uint32_t R2, float k2, LaneAcc& a) {
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < n; base += 32) {
+    bool in = false;
+    int k = 0;
+    if (base + lane < n) {
+      k = cand[base + lane];
+      const int2 xy = *reinterpret_cast<const int2*>(&stage[k]);
+      in = xy.x >= bx0 && xy.x <= bx1 && xy.y >= by0 && xy.y <= by1;
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, in);
+    while (mask) {
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1;
+      weigh(stage[__shfl_sync(0xffffffffu, k, src)], cx, cy, zref, R2, k2, a);
     }
   }
 }
@@ -241,7 +267,11 @@ __device__ __forceinline__ void nearest_range(const Rec* recs, int n, bool need,
       const Rec q = recs[base + src];
       if (need) {
         const int dx = q.lx - cx, dy = q.ly - cy;
-        consider_nearest(a, (long long)dx * dx + (long long)dy * dy, q);
+        const long long d2 = (long long)dx * dx + (long long)dy * dy;
+        if (d2 < a.bd2 || (d2 == a.bd2 && q.idx < a.bidx)) {
+          a.bd2 = d2;
+          a.bidx = q.idx;
+        }
       }
     }
   }
@@ -262,26 +292,39 @@ __device__ void nearest_far(const FillArgs& f, int tx, int ty, int cx, int cy, L
         for (int64_t q = f.toff[u] < 0 ? 0 : f.toff[u]; q < q1; ++q) {
           const Rec rc = f.recs[q];
           const int dx = rc.lx - cx, dy = rc.ly - cy;
-          consider_nearest(a, (long long)dx * dx + (long long)dy * dy, rc);
+          const long long d2 = (long long)dx * dx + (long long)dy * dy;
+          if (d2 < a.bd2 || (d2 == a.bd2 && rc.idx < a.bidx)) {
+            a.bd2 = d2;
+            a.bidx = rc.idx;
+          }
         }
       }
     }
-    if (a.bd2 >= 0 && a.bd2 <= (long long)m * f.tile_cm * (long long)m * f.tile_cm) return;
+    if (a.bd2 != LLONG_MAX && a.bd2 <= (long long)m * f.tile_cm * (long long)m * f.tile_cm) return;
   }
 }
 
-__global__ void __launch_bounds__(kFillThreads, 2) k_fill(FillArgs f) {  // 2 CTAs per SM (shared memory)
+// One CTA per tile (or per band of a tile when f.split > 1), 8 warps.  Each warp takes
+// whole rows of 8 x 4-texel blocks.  For a block row it lists once the staged samples
+// within R of the row's texels (a candidate list in shared memory, ~20 samples in the
+// overview against ~300 staged), and each block of the row ballots over that list only.
+// Heights are blended relative to the tile's reference z (the first staged sample), so
+// the per-texel arithmetic is FP32; the tile's base height z_ref * z_scale + z_offset
+// is formed once in FP64.
+__global__ void __launch_bounds__(kFillThreads, kFillMaxCtasPerSm) k_fill(FillArgs f) {
   extern __shared__ __align__(128) unsigned char fill_dyn[];
-  Rec* stage = reinterpret_cast<Rec*>(fill_dyn);  // kStageCap records (dynamic)
+  Rec* stage = reinterpret_cast<Rec*>(fill_dyn);  // f.stage_cap records (dynamic)
   __shared__ __align__(16) float out_h[kOutStageRes * kOutStageRes];
   __shared__ __align__(16) uint8_t out_c[kOutStageRes * kOutStageRes * 3];
+  __shared__ __align__(16) uint16_t cand_all[kFillThreads / 32][kCandCap];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int64_t rng_lo[3], rng_n[3];
-  __shared__ int stage_n, staged;
+  __shared__ int stage_n, staged, zref_s;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int res = f.res, cell = f.cell_cm;
   const bool stage_out = res <= kOutStageRes;
+  uint16_t* cand = cand_all[warp];
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -315,8 +358,13 @@ __global__ void __launch_bounds__(kFillThreads, 2) k_fill(FillArgs f) {  // 2 CT
         rng_lo[k] = a0; rng_n[k] = a1 - a0;
         total += a1 - a0;
       }
-      stage_n = (int)(total < kStageCap ? total : kStageCap);
-      staged = total <= kStageCap;
+      stage_n = (int)(total < f.stage_cap ? total : f.stage_cap);
+      staged = total <= f.stage_cap;
+      // the tile's height reference: the first sample of its neighbourhood
+      int zr = 0;
+      for (int k = 0; k < 3; ++k)
+        if (rng_n[k] > 0) { zr = f.recs[rng_lo[k]].z; break; }
+      zref_s = zr;
       if (staged && total > 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive_expect_tx(&bar, (uint32_t)(total * sizeof(Rec)));
@@ -329,6 +377,9 @@ __global__ void __launch_bounds__(kFillThreads, 2) k_fill(FillArgs f) {  // 2 CT
     }
     __syncthreads();
     const bool use_stage = staged;
+    const int zref = zref_s;
+    // base height of the tile, FP64 once; texels add (blended z - zref) * z_scale in FP32
+    const float base_h = (float)((double)zref * f.z_scale + f.z_offset);
     if (use_stage && stage_n > 0) {
       int it = 0, limit = 0;
       while (!mbar_try_wait(&bar, phase)) {
@@ -337,87 +388,114 @@ __global__ void __launch_bounds__(kFillThreads, 2) k_fill(FillArgs f) {  // 2 CT
       }
       phase ^= 1u;
     }
-    // ---- texel blocks of 8 x 4 per warp
-    const int bw = res / 8, nblk = bw * (res / 4);
-    const int blk0 = part * (nblk / f.split), blk1 = blk0 + nblk / f.split;  // whole block rows
-    for (int blk = blk0 + warp; blk < blk1; blk += kFillThreads / 32) {
-      const int bj = (blk % bw) * 8, bi = (blk / bw) * 4;
-      const int j = bj + (lane & 7), i = bi + (lane >> 3);
-      const int cx = tx * f.tile_cm + cell * j + cell / 2;
-      const int cy = ty * f.tile_cm + cell * i + cell / 2;
-      const int x0b = tx * f.tile_cm + cell * bj + cell / 2, y0b = ty * f.tile_cm + cell * bi + cell / 2;
-      const int bx0 = x0b - f.R, bx1 = x0b + 7 * cell + f.R;
-      const int by0 = y0b - f.R, by1 = y0b + 3 * cell + f.R;
-      LaneAcc a = {0.f, 0.f, 0.f, 0.f, 0.f, -1ll, INT_MAX, 0, 0u, 0u};
-      int zref = INT_MIN;
+    // ---- rows of 8 x 4-texel blocks, one row per warp at a time
+    const int bw = res / 8, nbr = res / 4;
+    const int br0 = part * (nbr / f.split), br1 = br0 + nbr / f.split;  // this part's block rows
+    for (int br = br0 + warp; br < br1; br += kFillThreads / 32) {
+      const int bi = br * 4;
+      const int y0b = ty * f.tile_cm + cell * bi + cell / 2;
+      const int rx0 = tx * f.tile_cm + cell / 2 - f.R, rx1 = tx * f.tile_cm + (res - 1) * cell + cell / 2 + f.R;
+      const int ry0 = y0b - f.R, ry1 = y0b + 3 * cell + f.R;
+      // candidate list of the row (staged samples within R of any of its texels' box)
+      int n_cand = 0;
       if (use_stage) {
-        splat_range(stage, stage_n, bx0, bx1, by0, by1, cx, cy, f, zref, a);
-      } else {
-        for (int k = 0; k < 3; ++k)
-          splat_range(f.recs + rng_lo[k], (int)rng_n[k], bx0, bx1, by0, by1, cx, cy, f, zref, a);
-      }
-      const bool need = !(a.sw > 0.f);
-      if (__any_sync(0xffffffffu, need)) {
-        // grow the box to the largest current best distance of the lanes in need
-        // (in-box samples were all considered above); a lane without any in-box
-        // sample makes the search unbounded
-        const bool unbounded = need && a.bd2 < 0;
-        const long long bd = need && a.bd2 >= 0 ? a.bd2 : 0;
-        long long wmax = bd;
-        for (int off = 16; off > 0; off >>= 1) {
-          const long long o = __shfl_xor_sync(0xffffffffu, wmax, off);
-          wmax = o > wmax ? o : wmax;
+        for (int base = 0; base < stage_n; base += 32) {
+          bool in = false;
+          if (base + lane < stage_n) {
+            const int2 xy = *reinterpret_cast<const int2*>(&stage[base + lane]);
+            in = xy.x >= rx0 && xy.x <= rx1 && xy.y >= ry0 && xy.y <= ry1;
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, in);
+          const int pos = n_cand + __popc(m & ((1u << lane) - 1u));
+          if (in && pos < kCandCap) cand[pos] = (uint16_t)(base + lane);
+          n_cand += __popc(m);
         }
-        int grow = (int)ceilf(sqrtf((float)wmax)) + 1;
-        if (__any_sync(0xffffffffu, unbounded) || grow > 2 * f.tile_cm) grow = 2 * f.tile_cm;
-        const int gx0 = x0b - grow, gx1 = x0b + 7 * cell + grow;
-        const int gy0 = y0b - grow, gy1 = y0b + 3 * cell + grow;
-        if (use_stage) {
-          nearest_range(stage, stage_n, need, cx, cy, gx0, gx1, gy0, gy1, a);
+        __syncwarp();
+      }
+      const bool use_list = use_stage && n_cand <= kCandCap;
+      for (int bj8 = 0; bj8 < bw; ++bj8) {
+        const int bj = bj8 * 8;
+        const int j = bj + (lane & 7), i = bi + (lane >> 3);
+        const int cx = tx * f.tile_cm + cell * j + cell / 2;
+        const int cy = ty * f.tile_cm + cell * i + cell / 2;
+        const int x0b = tx * f.tile_cm + cell * bj + cell / 2;
+        const int bx0 = x0b - f.R, bx1 = x0b + 7 * cell + f.R;
+        const int by0 = ry0, by1 = ry1;
+        LaneAcc a = {0.f, 0.f, 0.f, 0.f, 0.f, LLONG_MAX, INT_MAX};
+        if (use_list) {
+          splat_list(stage, cand, n_cand, bx0, bx1, by0, by1, cx, cy, zref, f.R2u, f.k2, a);
+        } else if (use_stage) {
+          splat_range(stage, stage_n, bx0, bx1, by0, by1, cx, cy, zref, f.R2u, f.k2, a);
         } else {
           for (int k = 0; k < 3; ++k)
-            nearest_range(f.recs + rng_lo[k], (int)rng_n[k], need, cx, cy, gx0, gx1, gy0, gy1, a);
+            splat_range(f.recs + rng_lo[k], (int)rng_n[k], bx0, bx1, by0, by1, cx, cy, zref, f.R2u, f.k2, a);
+        }
+        const bool need = !(a.sw > 0.f);
+        if (__any_sync(0xffffffffu, need)) {
+          // grow the box to the largest current best distance of the lanes in need
+          // (in-box samples were all considered above); a lane without any in-box
+          // sample makes the search unbounded
+          const bool unbounded = need && a.bd2 == LLONG_MAX;
+          const long long bd = need && a.bd2 != LLONG_MAX ? a.bd2 : 0;
+          long long wmax = bd;
+          for (int off = 16; off > 0; off >>= 1) {
+            const long long ov = __shfl_xor_sync(0xffffffffu, wmax, off);
+            wmax = ov > wmax ? ov : wmax;
+          }
+          int grow = (int)ceilf(sqrtf((float)wmax)) + 1;
+          if (__any_sync(0xffffffffu, unbounded) || grow > 2 * f.tile_cm) grow = 2 * f.tile_cm;
+          const int gx0 = x0b - grow, gx1 = x0b + 7 * cell + grow;
+          const int gy0 = y0b - grow, gy1 = y0b + 3 * cell + grow;
+          if (use_stage) {
+            nearest_range(stage, stage_n, need, cx, cy, gx0, gx1, gy0, gy1, a);
+          } else {
+            for (int k = 0; k < 3; ++k)
+              nearest_range(f.recs + rng_lo[k], (int)rng_n[k], need, cx, cy, gx0, gx1, gy0, gy1, a);
+          }
+        }
+        if (need && !(a.bd2 != LLONG_MAX && a.bd2 <= (long long)f.tile_cm * f.tile_cm))
+          nearest_far(f, tx, ty, cx, cy, a);
+        float h;
+        float c3[3];
+        if (!need) {
+          const float inv = 1.0f / a.sw;
+          h = fmaf(a.swz * inv, f.zs_f, base_h);
+          c3[0] = a.swr * inv * (1.0f / 256.0f);
+          c3[1] = a.swg * inv * (1.0f / 256.0f);
+          c3[2] = a.swb * inv * (1.0f / 256.0f);
+        } else if (a.bd2 != LLONG_MAX) {
+          const Rec q = f.recs[a.bidx];  // records are indexed by sample
+          h = fmaf((float)(q.z - zref), f.zs_f, base_h);
+          c3[0] = (float)(q.rg & 0xffffu) * (1.0f / 256.0f);
+          c3[1] = (float)(q.rg >> 16) * (1.0f / 256.0f);
+          c3[2] = (float)q.b * (1.0f / 256.0f);
+        } else {
+          h = __int_as_float(0x7fc00000);
+          c3[0] = c3[1] = c3[2] = 0.f;
+        }
+        if (f.aux_hc) {
+          const size_t ae = (size_t)o * res * res + (size_t)i * res + j;
+          f.aux_hc[ae] = make_float4(h, c3[0] * (256.0f / 65535.0f), c3[1] * (256.0f / 65535.0f),
+                                     c3[2] * (256.0f / 65535.0f));
+          f.aux_d[ae] = a.bd2 != LLONG_MAX ? sqrtf((float)a.bd2) : __int_as_float(0x7f800000);
+        }
+        uint8_t q8[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float v = floorf(c3[c] + 0.5f);
+          q8[c] = (uint8_t)(v > 255.f ? 255.f : v);
+        }
+        const int e = i * res + j;
+        if (stage_out) {
+          out_h[e] = h;
+          out_c[3 * e] = q8[0]; out_c[3 * e + 1] = q8[1]; out_c[3 * e + 2] = q8[2];
+        } else {
+          f.height[o * res * res + e] = h;
+          uint8_t* dst = f.rgb + (o * res * res + e) * 3;
+          dst[0] = q8[0]; dst[1] = q8[1]; dst[2] = q8[2];
         }
       }
-      if (need && !(a.bd2 >= 0 && a.bd2 <= (long long)f.tile_cm * f.tile_cm)) nearest_far(f, tx, ty, cx, cy, a);
-      float h;
-      float c3[3];
-      if (!need) {
-        h = (float)(((double)zref + (double)(a.swz / a.sw)) * f.z_scale + f.z_offset);
-        const float inv = 1.0f / a.sw;
-        c3[0] = a.swr * inv * (1.0f / 256.0f);
-        c3[1] = a.swg * inv * (1.0f / 256.0f);
-        c3[2] = a.swb * inv * (1.0f / 256.0f);
-      } else if (a.bd2 >= 0) {
-        h = (float)((double)a.bz * f.z_scale + f.z_offset);
-        c3[0] = (float)(a.brg & 0xffffu) * (1.0f / 256.0f);
-        c3[1] = (float)(a.brg >> 16) * (1.0f / 256.0f);
-        c3[2] = (float)a.bb * (1.0f / 256.0f);
-      } else {
-        h = __int_as_float(0x7fc00000);
-        c3[0] = c3[1] = c3[2] = 0.f;
-      }
-      if (f.aux_hc) {
-        const size_t ae = (size_t)o * res * res + (size_t)i * res + j;
-        f.aux_hc[ae] = make_float4(h, c3[0] * (256.0f / 65535.0f), c3[1] * (256.0f / 65535.0f),
-                                   c3[2] * (256.0f / 65535.0f));
-        f.aux_d[ae] = a.bd2 >= 0 ? sqrtf((float)a.bd2) : __int_as_float(0x7f800000);
-      }
-      uint8_t q8[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float v = floorf(c3[c] + 0.5f);
-        q8[c] = (uint8_t)(v > 255.f ? 255.f : v);
-      }
-      const int e = i * res + j;
-      if (stage_out) {
-        out_h[e] = h;
-        out_c[3 * e] = q8[0]; out_c[3 * e + 1] = q8[1]; out_c[3 * e + 2] = q8[2];
-      } else {
-        f.height[o * res * res + e] = h;
-        uint8_t* dst = f.rgb + (o * res * res + e) * 3;
-        dst[0] = q8[0]; dst[1] = q8[1]; dst[2] = q8[2];
-      }
+      __syncwarp();  // the next row's list overwrites this one
     }
     __syncthreads();
     if (stage_out) {
@@ -502,7 +580,8 @@ ls_status fill_launch(const ls_points* samples, const ls_region* region, const l
   if (!tile_ids && n_out != T) return LS_ERR_INVALID_ARG;
   if (params->res < 8 || params->res > 1024 || params->res % 8 || region->tile_cm % params->res)
     return LS_ERR_INVALID_ARG;
-  if (params->radius_cm < 1 || params->radius_cm > region->tile_cm) return LS_ERR_UNSUPPORTED;
+  if (params->radius_cm < 1 || params->radius_cm > region->tile_cm || params->radius_cm > 65535)
+    return LS_ERR_UNSUPPORTED;
   if (!(params->sigma_cm > 0.f)) return LS_ERR_INVALID_ARG;
   if (n_out == 0) return LS_OK;
   Rec* recs = static_cast<Rec*>(workspace(kWsFillPacked, (size_t)(samples->n > 0 ? samples->n : 1) * sizeof(Rec)));
@@ -523,8 +602,17 @@ ls_status fill_launch(const ls_points* samples, const ls_region* region, const l
   f.res = params->res;
   f.cell_cm = region->tile_cm / params->res;
   f.R = params->radius_cm;
-  f.R2 = (int64_t)params->radius_cm * params->radius_cm;
-  f.k_exp = (float)(1.0 / (2.0 * (double)params->sigma_cm * (double)params->sigma_cm));
+  f.R2u = (uint32_t)params->radius_cm * (uint32_t)params->radius_cm;
+  f.k2 = (float)(1.4426950408889634 / (2.0 * (double)params->sigma_cm * (double)params->sigma_cm));
+  f.zs_f = (float)region->z_scale;
+  // stage: room for 1.5 x the average 3 x 3 neighbourhood (a power of two, 256..2048
+  // records); a tile whose neighbourhood does not fit reads it from global memory
+  {
+    const int64_t want = (samples->n * 27 + 2 * T - 1) / (2 * T);
+    int cap = 256;
+    while (cap < want && cap < kStageCap) cap *= 2;
+    f.stage_cap = cap;
+  }
   f.z_scale = region->z_scale;
   f.z_offset = region->z_offset;
   f.height = height;
@@ -532,21 +620,35 @@ ls_status fill_launch(const ls_points* samples, const ls_region* region, const l
   f.aux_hc = aux_hc;
   f.aux_d = aux_d;
   static DeviceOnce once;
+  static int occ[kMaxDevicesOnce + 1][5] = {};  // resident CTAs per SM by stage size (256 << k)
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return LS_ERR_CUDA;
-  if (!device_once(once, dev, [] {
-        return cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(kStageCap * sizeof(Rec))) == cudaSuccess;
+  const int di = dev >= 0 && dev < kMaxDevicesOnce ? dev : kMaxDevicesOnce;
+  if (!device_once(once, dev, [&] {
+        if (cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kStageCap * sizeof(Rec))) != cudaSuccess)
+          return false;
+        for (int k = 0; k < 5; ++k) {
+          int b = 0;
+          if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fill, kFillThreads,
+                                                            (size_t)(256 << k) * sizeof(Rec)) != cudaSuccess)
+            return false;
+          occ[di][k] = b > 0 ? b : 1;
+        }
+        return true;
       }))
     return LS_ERR_CUDA;
+  int ks = 0;
+  while ((256 << ks) < f.stage_cap) ++ks;
   // launch shape: tuned for this key (ls_tune_fill_sparse / ls_fill_shape_set), else the
   // default: few tiles are split over 4 CTAs (bands of res / 4 texel rows, whole 4-row
-  // blocks), and the persistent grid assumes 2 resident CTAs per SM
+  // blocks), and the persistent grid is sized for the CTAs that fit on an SM
   FillShape shape;
   fill_shape_lookup(fill_shape_key(samples->n, n_out, params), params->res, n_out, &shape);
   f.split = shape.split;
-  k_fill<<<grid_cap(n_out * f.split, (int64_t)kSmCount * shape.ctas_per_sm), kFillThreads,
-           kStageCap * sizeof(Rec), s>>>(f);
+  const int per_sm = shape.ctas_per_sm < occ[di][ks] ? shape.ctas_per_sm : occ[di][ks];
+  k_fill<<<grid_cap(n_out * f.split, (int64_t)kSmCount * per_sm), kFillThreads,
+           (size_t)f.stage_cap * sizeof(Rec), s>>>(f);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 }  // namespace ls
