@@ -227,8 +227,8 @@ typedef struct {
   int32_t split;        /* CTAs per tile, each a band of res / split texel rows: 1, or 2
                            or 4 when res is a multiple of 16 * split (default 4 for fewer
                            than 592 tiles and res a multiple of 64, else 1) */
-  int32_t ctas_per_sm;  /* resident CTAs per SM the persistent grid is sized for: 1..3
-                           (default 3), capped at what fits next to the launch's sample
+  int32_t ctas_per_sm;  /* resident CTAs per SM the persistent grid is sized for: 1..4
+                           (default 4), capped at what fits next to the launch's sample
                            stage (sized from the average samples per tile) */
 } ls_fill_shape;
 

@@ -37,7 +37,7 @@ constexpr int kFillThreads = 256;
 constexpr int kStageCap = 2048;  // most staged samples per tile (64 KB)
 constexpr int kOutStageRes = 64; // texel maps up to 64x64 are staged in shared memory
 constexpr int kCandCap = 256;    // candidate list of a block row (indices into the stage)
-constexpr int kFillMaxCtasPerSm = 3;
+constexpr int kFillMaxCtasPerSm = 4;
 
 // ---------------------------------------------------------------------------------
 // extraction
@@ -208,6 +208,115 @@ __device__ __forceinline__ void weigh(const Rec& q, int cx, int cy, int zref, ui
   }
 }
 
+// A staged record after the per-tile conversion: height relative to the tile's
+// reference and colours as floats, so that a hit needs no integer conversions.
+struct __align__(16) StRec {
+  int32_t lx, ly;
+  float fz;     // z - zref (cm)
+  int32_t idx;  // sample index
+  float fr, fg, fb;
+  uint32_t pad;
+};
+static_assert(sizeof(StRec) == sizeof(Rec), "staged records are converted in place");
+
+// Nearest of the staged samples as one 64-bit key: squared distance above the stage
+// index (stage order is sample order, so the smaller key also breaks ties by the
+// lower sample index).
+constexpr int kKeyShift = 11;  // stage indices < kStageCap = 2^11
+static_assert((1 << kKeyShift) >= kStageCap, "stage index field");
+
+struct LaneAccS {
+  float sw, swz, swr, swg, swb;
+  unsigned long long key;  // ~0: none yet
+};
+
+// A lane owns two texels of one column, 4 rows apart (an 8 x 8 block per warp): one
+// sample's x distance serves both.
+constexpr int kTexPerLane = 2;
+
+// One staged sample for this lane's texels (rows cy and cy + dyt).  kSmall: the
+// squared distance of every sample in the block's box fits 32 bits (checked on the
+// host).  Weights are branch-free: a sample beyond R gets weight 0 (the lanes of a warp
+// disagree often).
+template <bool kSmall>
+__device__ __forceinline__ void weigh_st(const StRec& q, int si, int cx, int cy, int dyt, uint32_t R2, float k2,
+                                         LaneAccS (&a)[kTexPerLane]) {
+  const int dx = q.lx - cx;
+#pragma unroll
+  for (int t = 0; t < kTexPerLane; ++t) {
+    const int dy = q.ly - cy - t * dyt;
+    unsigned long long d2;
+    if (kSmall) {
+      d2 = (uint32_t)dx * (uint32_t)dx + (uint32_t)dy * (uint32_t)dy;
+    } else {
+      d2 = (unsigned long long)((long long)dx * dx + (long long)dy * dy);
+    }
+    const unsigned long long key = (d2 << kKeyShift) | (unsigned)si;
+    a[t].key = key < a[t].key ? key : a[t].key;
+    float w = exp2f(-__uint2float_rn((uint32_t)d2) * k2);
+    w = d2 <= (unsigned long long)R2 ? w : 0.f;
+    a[t].sw += w;
+    a[t].swz = fmaf(w, q.fz, a[t].swz);
+    a[t].swr = fmaf(w, q.fr, a[t].swr);
+    a[t].swg = fmaf(w, q.fg, a[t].swg);
+    a[t].swb = fmaf(w, q.fb, a[t].swb);
+  }
+}
+
+// The staged samples of a candidate list (or of the whole stage, cand == nullptr) that
+// fall in the warp's box, for this lane's texels.
+template <bool kSmall>
+__device__ __forceinline__ void splat_st(const StRec* stage, const uint16_t* cand, int n, int bx0, int bx1, int by0,
+                                         int by1, int cx, int cy, int dyt, uint32_t R2, float k2,
+                                         LaneAccS (&a)[kTexPerLane]) {
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < n; base += 32) {
+    bool in = false;
+    int k = base + lane;
+    if (base + lane < n) {
+      if (cand) k = cand[base + lane];
+      const int2 xy = *reinterpret_cast<const int2*>(&stage[k]);
+      in = xy.x >= bx0 && xy.x <= bx1 && xy.y >= by0 && xy.y <= by1;
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, in);
+    while (mask) {
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const int si = __shfl_sync(0xffffffffu, k, src);
+      weigh_st<kSmall>(stage[si], si, cx, cy, dyt, R2, k2, a);
+    }
+  }
+}
+
+// Nearest staged sample for the lane's texels that need it (need bit t), within the
+// warp's block box grown by the caller.
+__device__ __forceinline__ void nearest_st(const StRec* stage, int n, unsigned need, int cx, int cy, int dyt,
+                                           int bx0, int bx1, int by0, int by1, LaneAccS (&a)[kTexPerLane]) {
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < n; base += 32) {
+    bool in = false;
+    if (base + lane < n) {
+      const int2 xy = *reinterpret_cast<const int2*>(&stage[base + lane]);
+      in = xy.x >= bx0 && xy.x <= bx1 && xy.y >= by0 && xy.y <= by1;
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, in);
+    while (mask) {
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const int2 xy = *reinterpret_cast<const int2*>(&stage[base + src]);
+#pragma unroll
+      for (int t = 0; t < kTexPerLane; ++t) {
+        if (need & (1u << t)) {
+          const int dx = xy.x - cx, dy = xy.y - cy - t * dyt;
+          const unsigned long long d2 = (unsigned long long)((long long)dx * dx + (long long)dy * dy);
+          const unsigned long long key = (d2 << kKeyShift) | (unsigned)(base + src);
+          a[t].key = key < a[t].key ? key : a[t].key;
+        }
+      }
+    }
+  }
+}
+
 // Weigh, for this lane's texel, the samples recs[0..n) that fall in the warp's box.
 __device__ __forceinline__ void splat_range(const Rec* recs, int n, int bx0, int bx1, int by0, int by1, int cx,
                                             int cy, int zref, uint32_t R2, float k2, LaneAcc& a) {
@@ -223,27 +332,6 @@ __device__ __forceinline__ void splat_range(const Rec* recs, int n, int bx0, int
       const int src = __ffs(mask) - 1;
       mask &= mask - 1;
       weigh(recs[base + src], cx, cy, zref, R2, k2, a);
-    }
-  }
-}
-
-// The same over a candidate list (indices into the staged records).
-__device__ __forceinline__ void splat_list(const Rec* stage, const uint16_t* cand, int n, int bx0, int bx1, int by0,
-                                           int by1, int cx, int cy, int zref, uint32_t R2, float k2, LaneAcc& a) {
-  const int lane = threadIdx.x & 31;
-  for (int base = 0; base < n; base += 32) {
-    bool in = false;
-    int k = 0;
-    if (base + lane < n) {
-      k = cand[base + lane];
-      const int2 xy = *reinterpret_cast<const int2*>(&stage[k]);
-      in = xy.x >= bx0 && xy.x <= bx1 && xy.y >= by0 && xy.y <= by1;
-    }
-    unsigned mask = __ballot_sync(0xffffffffu, in);
-    while (mask) {
-      const int src = __ffs(mask) - 1;
-      mask &= mask - 1;
-      weigh(stage[__shfl_sync(0xffffffffu, k, src)], cx, cy, zref, R2, k2, a);
     }
   }
 }
@@ -305,15 +393,18 @@ __device__ void nearest_far(const FillArgs& f, int tx, int ty, int cx, int cy, L
 }
 
 // One CTA per tile (or per band of a tile when f.split > 1), 8 warps.  Each warp takes
-// whole rows of 8 x 4-texel blocks.  For a block row it lists once the staged samples
-// within R of the row's texels (a candidate list in shared memory, ~20 samples in the
-// overview against ~300 staged), and each block of the row ballots over that list only.
+// whole rows of 8 x 8-texel blocks, two texels of a column per lane.  For a block row it
+// lists once the staged samples within R of the row's texels (a candidate list in shared
+// memory, ~25 samples in the overview against ~300 staged), and each block of the row
+// ballots over that list only.
 // Heights are blended relative to the tile's reference z (the first staged sample), so
 // the per-texel arithmetic is FP32; the tile's base height z_ref * z_scale + z_offset
 // is formed once in FP64.
+template <bool kSmall>
 __global__ void __launch_bounds__(kFillThreads, kFillMaxCtasPerSm) k_fill(FillArgs f) {
   extern __shared__ __align__(128) unsigned char fill_dyn[];
   Rec* stage = reinterpret_cast<Rec*>(fill_dyn);  // f.stage_cap records (dynamic)
+  StRec* st = reinterpret_cast<StRec*>(fill_dyn);  // the same records once converted
   __shared__ __align__(16) float out_h[kOutStageRes * kOutStageRes];
   __shared__ __align__(16) uint8_t out_c[kOutStageRes * kOutStageRes * 3];
   __shared__ __align__(16) uint16_t cand_all[kFillThreads / 32][kCandCap];
@@ -387,15 +478,27 @@ __global__ void __launch_bounds__(kFillThreads, kFillMaxCtasPerSm) k_fill(FillAr
         if (++it > limit) { set_status(LS_ERR_TIMEOUT); break; }
       }
       phase ^= 1u;
+      // convert the staged records in place: heights relative to zref and colours as
+      // floats (each thread its own records)
+      for (int k = threadIdx.x; k < stage_n; k += blockDim.x) {
+        const Rec r = stage[k];
+        StRec v;
+        v.lx = r.lx; v.ly = r.ly; v.fz = (float)(r.z - zref); v.idx = r.idx;
+        v.fr = (float)(r.rg & 0xffffu); v.fg = (float)(r.rg >> 16); v.fb = (float)r.b; v.pad = 0u;
+        st[k] = v;
+      }
+      __syncthreads();
     }
-    // ---- rows of 8 x 4-texel blocks, one row per warp at a time
-    const int bw = res / 8, nbr = res / 4;
+    // ---- rows of 8 x 8-texel blocks, one row per warp at a time; lane (r, c) of a
+    // block owns the texels (r, c) and (r + 4, c)
+    const int bw = res / 8, nbr = res / 8;
     const int br0 = part * (nbr / f.split), br1 = br0 + nbr / f.split;  // this part's block rows
+    const int dyt = 4 * cell;
     for (int br = br0 + warp; br < br1; br += kFillThreads / 32) {
-      const int bi = br * 4;
+      const int bi = br * 8;
       const int y0b = ty * f.tile_cm + cell * bi + cell / 2;
       const int rx0 = tx * f.tile_cm + cell / 2 - f.R, rx1 = tx * f.tile_cm + (res - 1) * cell + cell / 2 + f.R;
-      const int ry0 = y0b - f.R, ry1 = y0b + 3 * cell + f.R;
+      const int ry0 = y0b - f.R, ry1 = y0b + 7 * cell + f.R;
       // candidate list of the row (staged samples within R of any of its texels' box)
       int n_cand = 0;
       if (use_stage) {
@@ -415,84 +518,132 @@ __global__ void __launch_bounds__(kFillThreads, kFillMaxCtasPerSm) k_fill(FillAr
       const bool use_list = use_stage && n_cand <= kCandCap;
       for (int bj8 = 0; bj8 < bw; ++bj8) {
         const int bj = bj8 * 8;
-        const int j = bj + (lane & 7), i = bi + (lane >> 3);
+        const int j = bj + (lane & 7), i0 = bi + (lane >> 3);
         const int cx = tx * f.tile_cm + cell * j + cell / 2;
-        const int cy = ty * f.tile_cm + cell * i + cell / 2;
+        const int cy = ty * f.tile_cm + cell * i0 + cell / 2;
         const int x0b = tx * f.tile_cm + cell * bj + cell / 2;
         const int bx0 = x0b - f.R, bx1 = x0b + 7 * cell + f.R;
-        const int by0 = ry0, by1 = ry1;
-        LaneAcc a = {0.f, 0.f, 0.f, 0.f, 0.f, LLONG_MAX, INT_MAX};
-        if (use_list) {
-          splat_list(stage, cand, n_cand, bx0, bx1, by0, by1, cx, cy, zref, f.R2u, f.k2, a);
-        } else if (use_stage) {
-          splat_range(stage, stage_n, bx0, bx1, by0, by1, cx, cy, zref, f.R2u, f.k2, a);
-        } else {
-          for (int k = 0; k < 3; ++k)
-            splat_range(f.recs + rng_lo[k], (int)rng_n[k], bx0, bx1, by0, by1, cx, cy, zref, f.R2u, f.k2, a);
-        }
-        const bool need = !(a.sw > 0.f);
-        if (__any_sync(0xffffffffu, need)) {
-          // grow the box to the largest current best distance of the lanes in need
-          // (in-box samples were all considered above); a lane without any in-box
-          // sample makes the search unbounded
-          const bool unbounded = need && a.bd2 == LLONG_MAX;
-          const long long bd = need && a.bd2 != LLONG_MAX ? a.bd2 : 0;
-          long long wmax = bd;
-          for (int off = 16; off > 0; off >>= 1) {
-            const long long ov = __shfl_xor_sync(0xffffffffu, wmax, off);
-            wmax = ov > wmax ? ov : wmax;
-          }
-          int grow = (int)ceilf(sqrtf((float)wmax)) + 1;
-          if (__any_sync(0xffffffffu, unbounded) || grow > 2 * f.tile_cm) grow = 2 * f.tile_cm;
-          const int gx0 = x0b - grow, gx1 = x0b + 7 * cell + grow;
-          const int gy0 = y0b - grow, gy1 = y0b + 3 * cell + grow;
-          if (use_stage) {
-            nearest_range(stage, stage_n, need, cx, cy, gx0, gx1, gy0, gy1, a);
-          } else {
-            for (int k = 0; k < 3; ++k)
-              nearest_range(f.recs + rng_lo[k], (int)rng_n[k], need, cx, cy, gx0, gx1, gy0, gy1, a);
-          }
-        }
-        if (need && !(a.bd2 != LLONG_MAX && a.bd2 <= (long long)f.tile_cm * f.tile_cm))
-          nearest_far(f, tx, ty, cx, cy, a);
-        float h;
-        float c3[3];
-        if (!need) {
-          const float inv = 1.0f / a.sw;
-          h = fmaf(a.swz * inv, f.zs_f, base_h);
-          c3[0] = a.swr * inv * (1.0f / 256.0f);
-          c3[1] = a.swg * inv * (1.0f / 256.0f);
-          c3[2] = a.swb * inv * (1.0f / 256.0f);
-        } else if (a.bd2 != LLONG_MAX) {
-          const Rec q = f.recs[a.bidx];  // records are indexed by sample
-          h = fmaf((float)(q.z - zref), f.zs_f, base_h);
-          c3[0] = (float)(q.rg & 0xffffu) * (1.0f / 256.0f);
-          c3[1] = (float)(q.rg >> 16) * (1.0f / 256.0f);
-          c3[2] = (float)q.b * (1.0f / 256.0f);
-        } else {
-          h = __int_as_float(0x7fc00000);
-          c3[0] = c3[1] = c3[2] = 0.f;
-        }
-        if (f.aux_hc) {
-          const size_t ae = (size_t)o * res * res + (size_t)i * res + j;
-          f.aux_hc[ae] = make_float4(h, c3[0] * (256.0f / 65535.0f), c3[1] * (256.0f / 65535.0f),
-                                     c3[2] * (256.0f / 65535.0f));
-          f.aux_d[ae] = a.bd2 != LLONG_MAX ? sqrtf((float)a.bd2) : __int_as_float(0x7f800000);
-        }
-        uint8_t q8[3];
+        LaneAcc a[kTexPerLane];
+        unsigned need = 0;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float v = floorf(c3[c] + 0.5f);
-          q8[c] = (uint8_t)(v > 255.f ? 255.f : v);
-        }
-        const int e = i * res + j;
-        if (stage_out) {
-          out_h[e] = h;
-          out_c[3 * e] = q8[0]; out_c[3 * e + 1] = q8[1]; out_c[3 * e + 2] = q8[2];
+        for (int t = 0; t < kTexPerLane; ++t) a[t] = LaneAcc{0.f, 0.f, 0.f, 0.f, 0.f, LLONG_MAX, INT_MAX};
+        if (use_stage) {
+          LaneAccS as[kTexPerLane];
+#pragma unroll
+          for (int t = 0; t < kTexPerLane; ++t) as[t] = LaneAccS{0.f, 0.f, 0.f, 0.f, 0.f, ~0ull};
+          splat_st<kSmall>(st, use_list ? cand : nullptr, use_list ? n_cand : stage_n, bx0, bx1, ry0, ry1, cx, cy,
+                           dyt, f.R2u, f.k2, as);
+#pragma unroll
+          for (int t = 0; t < kTexPerLane; ++t) need |= (as[t].sw > 0.f) ? 0u : (1u << t);
+          if (__any_sync(0xffffffffu, need != 0)) {
+            // grow the box to the largest current best distance of the texels in need
+            // (in-box samples were all considered above); a texel without any in-box
+            // sample makes the search unbounded
+            bool unbounded = false;
+            long long wmax = 0;
+#pragma unroll
+            for (int t = 0; t < kTexPerLane; ++t) {
+              if (!(need & (1u << t))) continue;
+              if (as[t].key == ~0ull) unbounded = true;
+              else wmax = max(wmax, (long long)(as[t].key >> kKeyShift));
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+              const long long ov = __shfl_xor_sync(0xffffffffu, wmax, off);
+              wmax = ov > wmax ? ov : wmax;
+            }
+            int grow = (int)ceilf(sqrtf((float)wmax)) + 1;
+            if (__any_sync(0xffffffffu, unbounded) || grow > 2 * f.tile_cm) grow = 2 * f.tile_cm;
+            nearest_st(st, stage_n, need, cx, cy, dyt, x0b - grow, x0b + 7 * cell + grow, y0b - grow,
+                       y0b + 7 * cell + grow, as);
+          }
+#pragma unroll
+          for (int t = 0; t < kTexPerLane; ++t) {
+            a[t].sw = as[t].sw; a[t].swz = as[t].swz; a[t].swr = as[t].swr; a[t].swg = as[t].swg;
+            a[t].swb = as[t].swb;
+            if (as[t].key != ~0ull) {
+              a[t].bd2 = (long long)(as[t].key >> kKeyShift);
+              // the sample index is needed only for a nearest-sample texel
+              if (need & (1u << t)) a[t].bidx = st[as[t].key & ((1u << kKeyShift) - 1)].idx;
+            }
+          }
         } else {
-          f.height[o * res * res + e] = h;
-          uint8_t* dst = f.rgb + (o * res * res + e) * 3;
-          dst[0] = q8[0]; dst[1] = q8[1]; dst[2] = q8[2];
+#pragma unroll
+          for (int t = 0; t < kTexPerLane; ++t) {
+            for (int k = 0; k < 3; ++k)
+              splat_range(f.recs + rng_lo[k], (int)rng_n[k], bx0, bx1, ry0, ry1, cx, cy + t * dyt, zref, f.R2u,
+                          f.k2, a[t]);
+            need |= (a[t].sw > 0.f) ? 0u : (1u << t);
+          }
+          if (__any_sync(0xffffffffu, need != 0)) {
+            bool unbounded = false;
+            long long wmax = 0;
+#pragma unroll
+            for (int t = 0; t < kTexPerLane; ++t) {
+              if (!(need & (1u << t))) continue;
+              if (a[t].bd2 == LLONG_MAX) unbounded = true;
+              else wmax = max(wmax, a[t].bd2);
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+              const long long ov = __shfl_xor_sync(0xffffffffu, wmax, off);
+              wmax = ov > wmax ? ov : wmax;
+            }
+            int grow = (int)ceilf(sqrtf((float)wmax)) + 1;
+            if (__any_sync(0xffffffffu, unbounded) || grow > 2 * f.tile_cm) grow = 2 * f.tile_cm;
+            const int gx0 = x0b - grow, gx1 = x0b + 7 * cell + grow;
+            const int gy0 = y0b - grow, gy1 = y0b + 7 * cell + grow;
+#pragma unroll
+            for (int t = 0; t < kTexPerLane; ++t)
+              for (int k = 0; k < 3; ++k)
+                nearest_range(f.recs + rng_lo[k], (int)rng_n[k], (need >> t) & 1u, cx, cy + t * dyt, gx0, gx1, gy0,
+                              gy1, a[t]);
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < kTexPerLane; ++t) {
+          const int i = i0 + 4 * t;
+          const int cyt = cy + t * dyt;
+          const bool nd = (need >> t) & 1u;
+          if (nd && !(a[t].bd2 != LLONG_MAX && a[t].bd2 <= (long long)f.tile_cm * f.tile_cm))
+            nearest_far(f, tx, ty, cx, cyt, a[t]);
+          float h;
+          float c3[3];
+          if (!nd) {
+            const float inv = 1.0f / a[t].sw;
+            h = fmaf(a[t].swz * inv, f.zs_f, base_h);
+            c3[0] = a[t].swr * inv * (1.0f / 256.0f);
+            c3[1] = a[t].swg * inv * (1.0f / 256.0f);
+            c3[2] = a[t].swb * inv * (1.0f / 256.0f);
+          } else if (a[t].bd2 != LLONG_MAX) {
+            const Rec q = f.recs[a[t].bidx];  // records are indexed by sample
+            h = fmaf((float)(q.z - zref), f.zs_f, base_h);
+            c3[0] = (float)(q.rg & 0xffffu) * (1.0f / 256.0f);
+            c3[1] = (float)(q.rg >> 16) * (1.0f / 256.0f);
+            c3[2] = (float)q.b * (1.0f / 256.0f);
+          } else {
+            h = __int_as_float(0x7fc00000);
+            c3[0] = c3[1] = c3[2] = 0.f;
+          }
+          if (f.aux_hc) {
+            const size_t ae = (size_t)o * res * res + (size_t)i * res + j;
+            f.aux_hc[ae] = make_float4(h, c3[0] * (256.0f / 65535.0f), c3[1] * (256.0f / 65535.0f),
+                                       c3[2] * (256.0f / 65535.0f));
+            f.aux_d[ae] = a[t].bd2 != LLONG_MAX ? sqrtf((float)a[t].bd2) : __int_as_float(0x7f800000);
+          }
+          uint8_t q8[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float v = floorf(c3[c] + 0.5f);
+            q8[c] = (uint8_t)(v > 255.f ? 255.f : v);
+          }
+          const int e = i * res + j;
+          if (stage_out) {
+            out_h[e] = h;
+            out_c[3 * e] = q8[0]; out_c[3 * e + 1] = q8[1]; out_c[3 * e + 2] = q8[2];
+          } else {
+            f.height[o * res * res + e] = h;
+            uint8_t* dst = f.rgb + (o * res * res + e) * 3;
+            dst[0] = q8[0]; dst[1] = q8[1]; dst[2] = q8[2];
+          }
         }
       }
       __syncwarp();  // the next row's list overwrites this one
@@ -625,14 +776,18 @@ ls_status fill_launch(const ls_points* samples, const ls_region* region, const l
   if (cudaGetDevice(&dev) != cudaSuccess) return LS_ERR_CUDA;
   const int di = dev >= 0 && dev < kMaxDevicesOnce ? dev : kMaxDevicesOnce;
   if (!device_once(once, dev, [&] {
-        if (cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kStageCap * sizeof(Rec))) != cudaSuccess)
+        const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        if (cudaFuncSetAttribute(k_fill<true>, attr, (int)(kStageCap * sizeof(Rec))) != cudaSuccess ||
+            cudaFuncSetAttribute(k_fill<false>, attr, (int)(kStageCap * sizeof(Rec))) != cudaSuccess)
           return false;
         for (int k = 0; k < 5; ++k) {
-          int b = 0;
-          if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fill, kFillThreads,
+          int b = 0, b2 = 0;
+          if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fill<true>, kFillThreads,
+                                                            (size_t)(256 << k) * sizeof(Rec)) != cudaSuccess ||
+              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_fill<false>, kFillThreads,
                                                             (size_t)(256 << k) * sizeof(Rec)) != cudaSuccess)
             return false;
+          b = b2 < b ? b2 : b;
           occ[di][k] = b > 0 ? b : 1;
         }
         return true;
@@ -647,8 +802,16 @@ ls_status fill_launch(const ls_points* samples, const ls_region* region, const l
   fill_shape_lookup(fill_shape_key(samples->n, n_out, params), params->res, n_out, &shape);
   f.split = shape.split;
   const int per_sm = shape.ctas_per_sm < occ[di][ks] ? shape.ctas_per_sm : occ[di][ks];
-  k_fill<<<grid_cap(n_out * f.split, (int64_t)kSmCount * per_sm), kFillThreads,
-           (size_t)f.stage_cap * sizeof(Rec), s>>>(f);
+  // 32-bit squared distances for every sample in a block's box: |dx|, |dy| <= R + 7
+  // cells from either texel of a lane
+  const uint64_t ex = (uint64_t)f.R + 7 * (uint64_t)f.cell_cm, ey = ex;
+  const bool small = ex * ex + ey * ey < (uint64_t(1) << 32);
+  const dim3 grid(grid_cap(n_out * f.split, (int64_t)kSmCount * per_sm));
+  const size_t smem = (size_t)f.stage_cap * sizeof(Rec);
+  if (small)
+    k_fill<true><<<grid, kFillThreads, smem, s>>>(f);
+  else
+    k_fill<false><<<grid, kFillThreads, smem, s>>>(f);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 }  // namespace ls

@@ -78,11 +78,11 @@ const BinShape kBinDefault = {16, 2};
 const int32_t kBinSpans[] = {8, 16, 32};
 const int32_t kBinPrefetch[] = {1, 2, 3};
 const int32_t kFillSplits[] = {1, 2, 4};
-const int32_t kFillCtas[] = {1, 2, 3};
+const int32_t kFillCtas[] = {1, 2, 3, 4};
 
 // the grid is sized for at most as many CTAs as fit on an SM with the launch's stage
 FillShape fill_default(int32_t res, int64_t n_out) {
-  return FillShape{(n_out < 4 * kSmCount && res % 64 == 0) ? 4 : 1, 3};
+  return FillShape{(n_out < 4 * kSmCount && res % 64 == 0) ? 4 : 1, 4};
 }
 
 // Timer of a sequence of library calls on one stream (CUDA events; synchronises).
@@ -173,9 +173,9 @@ bool bin_shape_valid(const BinShape& s) {
 }
 
 bool fill_shape_valid(const FillShape& s, int32_t res) {
-  if (s.ctas_per_sm < 1 || s.ctas_per_sm > 3) return false;
+  if (s.ctas_per_sm < 1 || s.ctas_per_sm > 4) return false;
   if (s.split == 1) return true;
-  // a band of res / split rows is made of whole 4-row texel blocks and starts its output
+  // a band of res / split rows is made of whole 8-row texel blocks and starts its output
   // rows at 16-byte boundaries
   return (s.split == 2 || s.split == 4) && res % (16 * s.split) == 0;
 }

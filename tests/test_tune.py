@@ -21,9 +21,9 @@ def _pts(n):
 
 def test_defaults(lsb):
     assert lsb.bin_shape(_pts(567_111_960)) == {"spans_per_cta": 16, "prefetch_batches": 2}
-    assert lsb.fill_shape(_pts(12_000), n_out=256) == {"split": 4, "ctas_per_sm": 3}
-    assert lsb.fill_shape(_pts(1_320_000), n_out=40_000) == {"split": 1, "ctas_per_sm": 3}
-    assert lsb.fill_shape(_pts(12_000), n_out=256, res=96) == {"split": 1, "ctas_per_sm": 3}
+    assert lsb.fill_shape(_pts(12_000), n_out=256) == {"split": 4, "ctas_per_sm": 4}
+    assert lsb.fill_shape(_pts(1_320_000), n_out=40_000) == {"split": 1, "ctas_per_sm": 4}
+    assert lsb.fill_shape(_pts(12_000), n_out=256, res=96) == {"split": 1, "ctas_per_sm": 4}
 
 
 def test_pinned_shape_applies_to_its_key_only(lsb):
@@ -37,7 +37,7 @@ def test_pinned_shape_applies_to_its_key_only(lsb):
     assert lsb.bin_shape(_pts(1_000_000)) == {"spans_per_cta": 16, "prefetch_batches": 2}
     lsb.set_fill_shape(_pts(5000), 300, shape={"split": 2, "ctas_per_sm": 1})
     assert lsb.fill_shape(_pts(5000), 300) == {"split": 2, "ctas_per_sm": 1}
-    assert lsb.fill_shape(_pts(5000), 300, radius_cm=8000) == {"split": 4, "ctas_per_sm": 3}
+    assert lsb.fill_shape(_pts(5000), 300, radius_cm=8000) == {"split": 4, "ctas_per_sm": 4}
 
 
 @pytest.mark.parametrize("shape", [{"spans_per_cta": 0, "prefetch_batches": 2},
@@ -51,7 +51,7 @@ def test_invalid_bin_shapes_are_rejected(lsb, shape):
 
 
 @pytest.mark.parametrize("res,shape", [(64, {"split": 3, "ctas_per_sm": 2}),
-                                       (64, {"split": 1, "ctas_per_sm": 4}),
+                                       (64, {"split": 1, "ctas_per_sm": 5}),
                                        (64, {"split": 1, "ctas_per_sm": 0}),
                                        (48, {"split": 4, "ctas_per_sm": 2}),   # 48 is no multiple of 64
                                        (80, {"split": 2, "ctas_per_sm": 2})])  # nor 80 of 32
@@ -66,7 +66,7 @@ def test_clear_forgets_every_entry(lsb):
     lsb.set_fill_shape(_pts(77), 7, shape={"split": 1, "ctas_per_sm": 1})
     lsb.tune_clear()
     assert lsb.bin_shape(_pts(77)) == {"spans_per_cta": 16, "prefetch_batches": 2}
-    assert lsb.fill_shape(_pts(77), 7) == {"split": 4, "ctas_per_sm": 3}
+    assert lsb.fill_shape(_pts(77), 7) == {"split": 4, "ctas_per_sm": 4}
 
 
 def test_tuner_rejects_bad_repetitions_before_touching_the_gpu():
