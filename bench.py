@@ -33,6 +33,7 @@ METRIC = "heightmap tiles/s (plain vs learned fill), full-res points binned/s, %
 WORKLOAD = "batched-region 16x16 tiles x 640 m, lognormal(ln4,0.8) pts/m^2, bin 640^2+64^2, extract, gaussian fill 64^2, tile update"
 SEED = 2
 BIN_SRC = os.path.join(ROOT, "paper_2509_20198_b300", "csrc", "ls_bin.cu")
+FILL_SRC = os.path.join(ROOT, "paper_2509_20198_b300", "csrc", "ls_fill.cu")
 
 
 # U-Net of the learned filler (64x64 input, widths 32/64/128): 3x3 convolutions
@@ -58,24 +59,45 @@ def peaks():
     return 6400.0, "fallback"
 
 
-def bin_traffic_per_point():
-    """DRAM bytes per launch of k_bin_main from the committed ncu summary, scaled per
-    point, or None when the summary is absent or the kernel source changed since."""
-    p = os.path.join(ROOT, "profiles", "k_bin_main_batched_region.txt")
+def profile_value(summary, src, key):
+    """A number from a committed ncu summary under profiles/ ("key: value" lines), or None
+    when the summary is absent or the kernel source changed since it was taken (the
+    summary records the source's sha256[:16])."""
+    p = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(p):
         return None
-    src_hash = hashlib.sha256(open(BIN_SRC, "rb").read()).hexdigest()[:16]
+    src_hash = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     vals = {}
     for line in open(p):
         if ": " in line:  # "key: value" (keys may hold a colon, as in "sha256[:16]")
             k, v = line.split(": ", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("ls_bin.cu sha256[:16]") != src_hash:
+    if vals.get(os.path.basename(src) + " sha256[:16]") != src_hash:
         return None
     try:
-        return float(vals["dram bytes per point (read+write)"])
-    except (KeyError, ValueError):
+        return float(vals[key].split()[0])
+    except (KeyError, ValueError, IndexError):
         return None
+
+
+def bin_traffic_per_point():
+    """DRAM bytes per launch of k_bin_main from the committed ncu summary, scaled per
+    point, or None when the summary is absent or the kernel source changed since."""
+    return profile_value("k_bin_main_batched_region.txt", BIN_SRC, "dram bytes per point (read+write)")
+
+
+def fill_issue_frac(texels, ms):
+    """Issue-bound fraction of the Gaussian fill: the warp instructions per texel of the
+    committed ncu summary times the texels, over the issue slots of the launch's time at
+    the maximum SM clock (148 SMs x 4 schedulers x 1 instruction per cycle)."""
+    ipt = profile_value("k_fill_overview_80x80_tiles.txt", FILL_SRC, "warp instructions per texel")
+    if ipt is None:
+        return None, None
+    mhz = 2032.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        mhz = float(json.load(open(p)).get("sm_max_mhz", mhz))
+    return round(ipt * texels / (ms * 1e-3 * 148 * 4 * mhz * 1e6), 4), ipt
 
 
 class ClockSampler:
@@ -431,13 +453,17 @@ def run_overview(lsb, args, dev, stream):
     del im
     torch.cuda.empty_cache()
     paper = run_paper_cnn(lsb, args, dev, stream, s, region, nT, sub_t, rm, rc, timed)
+    issue_frac, ipt = fill_issue_frac(nT * 64 * 64, ms_gauss)
     return {"workload": "overview 200x200 tiles, 4 pts/m^2, 33 samples/tile (1.32M samples)",
             "gaussian_fill": {"tiles_per_s": round(nT / (ms_gauss * 1e-3), 1), "ms": round(ms_gauss, 3),
                               "height_rmse_m": round(rm(h[sub_t]), 4), "rgb_rmse_8bit": round(rc(c[sub_t]), 3),
                               # algorithmic bytes: 7 B per texel written, 32 B per packed sample read
                               "achieved_gbs": round(fill_bytes / (ms_gauss * 1e-3) / 1e9, 1),
                               "frac_of_hbm": round(fill_bytes / (ms_gauss * 1e-3) / 1e9 / peaks()[0], 4),
-                              "bound": "issue (about 10 candidate tests and 3.6 exp per texel)"},
+                              "bound": "issue", "issue_frac": issue_frac,
+                              "warp_instructions_per_texel": ipt,
+                              "issue_note": "instructions per texel from profiles/k_fill_overview_80x80_tiles.txt "
+                                            "over 148 x 4 issue slots per cycle at the maximum SM clock"},
             "render": render,
             "paper_cnn": paper,
             "interp_fill": {"tiles_per_s": round(nT / (ms_interp * 1e-3), 1), "ms": round(ms_interp, 3),
