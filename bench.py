@@ -405,7 +405,7 @@ def run_overview(lsb, args, dev, stream):
     filler = lsb.Filler(max_batch=4096, device=dev)
     T.init_params(filler, seed=0)
     t1 = time.perf_counter()
-    hist = T.train(filler, train_set, epochs=args.train_epochs, batch=256, lr=1e-3)
+    hist = T.train(filler, train_set, epochs=args.train_epochs, batch=256, lr=T.LR)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t1
     tile_steps = (args.train_tiles // 256) * 256 * args.train_epochs
@@ -483,7 +483,7 @@ def run_overview(lsb, args, dev, stream):
                              "tflops": round(FWD_FLOP_PER_TILE * nT / (ms_learned * 1e-3) / 1e12, 1),
                              "frac_of_bf16_sustained": round(FWD_FLOP_PER_TILE * nT / (ms_learned * 1e-3) / 1e12
                                                              / bf16_sustained(), 4)},
-            "training": {"tiles": args.train_tiles, "epochs": args.train_epochs, "batch": 256,
+            "training": {"tiles": args.train_tiles, "epochs": args.train_epochs, "batch": 256, "lr": T.LR,
                          "seconds": round(train_s, 2), "data_seconds": round(data_s, 2),
                          "tiles_per_s": round(tile_steps / train_s, 1),
                          "tflops": round(TRAIN_FLOP_PER_TILE * tile_steps / train_s / 1e12, 1),
@@ -676,13 +676,13 @@ def run_paper_cnn(lsb, args, dev, stream, s, region, nT, sub_t, rm, rc, timed):
     import torch
     from paper_2509_20198_b300 import train as T
     t0 = time.perf_counter()
-    data = T.synthetic_patches(args.train_tiles, seed0=100, res=128, device=dev)
+    data = T.synthetic_patches(args.cnn_tiles, seed0=100, res=128, device=dev)
     torch.cuda.synchronize()
     data_s = time.perf_counter() - t0
     cnn = lsb.PaperCNN(res=128, max_batch=256, training=True, device=dev)
     T.init_cnn_params(cnn, seed=0)
     t1 = time.perf_counter()
-    hist = T.train_cnn(cnn, data, epochs=args.cnn_epochs, batch=256, lr=1e-3)
+    hist = T.train_cnn(cnn, data, epochs=args.cnn_epochs, batch=256, lr=T.LR)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t1
     steps = (len(data) // 256) * 256 * args.cnn_epochs
@@ -720,7 +720,7 @@ def run_paper_cnn(lsb, args, dev, stream, s, region, nT, sub_t, rm, rc, timed):
             "forward_tiles_per_s": round(nfwd / (ms_fwd * 1e-3), 1), "forward_tflops": round(tf, 1),
             "forward_frac_of_bf16_sustained": round(tf / bf16_sustained(), 4),
             "height_rmse_m": round(rm(out_h[sub_t]), 4), "rgb_rmse_8bit": round(rc(out_c[sub_t]), 3),
-            "training": {"tiles": args.train_tiles, "epochs": args.cnn_epochs, "batch": 256,
+            "training": {"tiles": args.cnn_tiles, "epochs": args.cnn_epochs, "batch": 256, "lr": T.LR,
                          "seconds": round(train_s, 2), "data_seconds": round(data_s, 2),
                          "tiles_per_s": round(steps / train_s, 1),
                          "tflops": round(3 * flops * steps / train_s / 1e12, 1),
@@ -1058,8 +1058,9 @@ def main():
                                                    "paper-cnn"],
                     help="profiling case instead of the bench")
     ap.add_argument("--case-tiles", type=int, default=3, help="tiles per side of the profiling case")
-    ap.add_argument("--train-tiles", type=int, default=4096)
-    ap.add_argument("--train-epochs", type=int, default=60)
+    ap.add_argument("--train-tiles", type=int, default=20000, help="training pairs of the learned filler")
+    ap.add_argument("--train-epochs", type=int, default=24)
+    ap.add_argument("--cnn-tiles", type=int, default=4096, help="training pairs of the paper's network variant")
     ap.add_argument("--cnn-epochs", type=int, default=30, help="epochs of the paper's network variant")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

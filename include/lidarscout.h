@@ -526,14 +526,17 @@ ls_status ls_filler_forward(ls_model *model, const float *params, const uint16_t
 ls_status ls_filler_backward(ls_model *model, const float *params, const float *dy, int32_t n,
                              float *grads, ls_stream_t stream);
 /* Loss of Sec. 3.4: masked MSE of height and colour (each squared error clipped to 1),
- * the two averaged, plus bound_weight * mean((y4 - |height error|)^2) (the error
- * target detached).  base, target:
+ * the two averaged, plus bound_weight * mean((y4 - b)^2) with the detached bound target
+ * b = |e| (the height error e = base + y0 - target), or, bound_excess = 1, the excess
+ * b = max(|e| - |base - target|, 0) of the learned height's error over the base fill's
+ * (the bound then predicts how much the learned fill may be worse than its base; the
+ * paper has no bound, this is the library's reading).  base, target:
  * [n_px][4] (normalised height, R, G, B in 0..1); mask [n_px] (0: texel without truth).
  * sums: device double[4] scratch; loss: device float[4] (total, height, colour,
  * bound) or NULL; dy: fp32 [n_px][5]. */
 ls_status ls_filler_loss(const float *y, const float *base, const float *target, const uint8_t *mask,
-                         int64_t n_px, float bound_weight, double *sums, float *loss, float *dy,
-                         ls_stream_t stream);
+                         int64_t n_px, float bound_weight, int32_t bound_excess, double *sums, float *loss,
+                         float *dy, ls_stream_t stream);
 /* AdamW with decoupled weight decay (Sec. 3.4 uses lr 1e-4, betas 0.9/0.999, eps 1e-5,
  * weight decay 1e-2); step counts from 1. */
 ls_status ls_adamw_step(float *p, const float *g, float *m, float *v, int64_t n, float lr, float beta1,

@@ -198,11 +198,13 @@ def backward(params, cache, dy, layers=LAYERS, store=None):
 
 # ------------------------------------------------------------------------------
 # loss (Sec. 3.4): masked, clipped MSE on height and colour, averaged; plus the
-# squared-error regression of the error-bound channel onto the (detached) absolute
-# height error (a reading: the paper has no bound), on the height term's scale.
+# squared-error regression of the error-bound channel onto a (detached) error target
+# (a reading: the paper has no bound), on the height term's scale.  The target is the
+# absolute height error |e|, or, with bound_excess, the excess max(|e| - |e_base|, 0)
+# of the learned height's error over the base fill's error e_base = base_h - t_h.
 # ------------------------------------------------------------------------------
 
-def loss_and_grad(y, base_h, base_c, t_h, t_c, mask, bound_weight=BOUND_WEIGHT):
+def loss_and_grad(y, base_h, base_c, t_h, t_c, mask, bound_weight=BOUND_WEIGHT, bound_excess=False):
     """y: [N,H,W,5] net output; base_h [N,H,W], base_c [N,H,W,3] the Gaussian-fill
     inputs the residuals are added to; t_h, t_c targets; mask [N,H,W] in {0,1}.
     Returns (loss, dL/dy, parts)."""
@@ -214,6 +216,8 @@ def loss_and_grad(y, base_h, base_c, t_h, t_c, mask, bound_weight=BOUND_WEIGHT):
     lh = (np.minimum(sh, 1.0) * m).sum() / cnt
     lc = (np.minimum(sc, 1.0) * m[..., None]).sum() / (3.0 * cnt)
     tb = np.abs(eh)                                  # detached target
+    if bound_excess:
+        tb = np.maximum(tb - np.abs(base_h - t_h), 0.0)
     db = y[..., 4] - tb
     lb = (db * db * m).sum() / cnt
     loss = 0.5 * (lh + lc) + bound_weight * lb

@@ -532,15 +532,16 @@ def cnn_inputs(maps, r_m=320.0, stream=None):
     return x, cz
 
 
-def filler_loss(y, base, target, mask, bound_weight=1.0, stream=None):
-    """Masked, clipped MSE of Sec. 3.4 (+ bound term).  Returns (loss[4], dL/dy)."""
+def filler_loss(y, base, target, mask, bound_weight=1.0, bound_excess=False, stream=None):
+    """Masked, clipped MSE of Sec. 3.4 (+ bound term; bound_excess: its target is the
+    excess of the learned height's error over the base fill's).  Returns (loss[4], dL/dy)."""
     n_px = mask.numel()
     sums = torch.empty(4, dtype=torch.float64, device=y.device)
     loss = torch.empty(4, dtype=torch.float32, device=y.device)
     dy = torch.empty_like(y)
     N.check("ls_filler_loss", N.lib().ls_filler_loss(_ptr(y), _ptr(base), _ptr(target), _ptr(mask), n_px,
-                                                    float(bound_weight), _ptr(sums), _ptr(loss), _ptr(dy),
-                                                    _stream(stream)))
+                                                    float(bound_weight), int(bool(bound_excess)), _ptr(sums),
+                                                    _ptr(loss), _ptr(dy), _stream(stream)))
     return loss, dy
 
 

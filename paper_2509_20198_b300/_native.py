@@ -108,7 +108,7 @@ SIGNATURES = {
     "ls_model_load": ([VP, VP, VP], I32),
     "ls_filler_forward": ([VP, VP, VP, I32, VP, VP], I32),
     "ls_filler_backward": ([VP, VP, VP, I32, VP, VP], I32),
-    "ls_filler_loss": ([VP, VP, VP, VP, I64, FLT, VP, VP, VP, VP], I32),
+    "ls_filler_loss": ([VP, VP, VP, VP, I64, FLT, I32, VP, VP, VP, VP], I32),
     "ls_adamw_step": ([VP, VP, VP, VP, I64, FLT, FLT, FLT, FLT, FLT, I32, VP], I32),
     "ls_learned_inputs": ([P(LsPoints), P(LsRegion), P(LsFillParams), VP, I64, VP, VP, VP, VP, VP, VP, VP], I32),
     "ls_learned_targets": ([P(LsBins), P(LsRegion), VP, I64, VP, VP, VP, VP], I32),

@@ -268,9 +268,16 @@ __global__ void k_pad_in(const float* __restrict__ w, int cout, int cin, int cin
 // 1, height and colour terms averaged; plus the squared error of the bound channel
 // against the detached absolute height error ---------------------------------------
 // y [P][5]; base [P][4] (normalised fill height, colour 0..1); target [P][4]; mask [P]
+// Detached target of the bound channel: |e|, or the excess max(|e| - |e_base|, 0) of
+// the learned height's error over the base fill's error (e_base = base - target).
+__device__ __forceinline__ float bound_target(float eh, float base_h, float t_h, int excess) {
+  const float a = fabsf(eh);
+  return excess ? fmaxf(a - fabsf(base_h - t_h), 0.f) : a;
+}
+
 __global__ void k_loss_sums(const float* __restrict__ y, const float* __restrict__ base,
                             const float* __restrict__ target, const uint8_t* __restrict__ mask, int64_t P,
-                            double* __restrict__ sums /* [4]: count, sh, sc, sb */) {
+                            int excess, double* __restrict__ sums /* [4]: count, sh, sc, sb */) {
   double s[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
     if (!mask[p]) continue;
@@ -281,7 +288,7 @@ __global__ void k_loss_sums(const float* __restrict__ y, const float* __restrict
       const float ec = base[p * 4 + k] + y[p * kOut + k] - target[p * 4 + k];
       s[2] += fminf(ec * ec, 1.f);
     }
-    const float db = y[p * kOut + 4] - fabsf(eh);
+    const float db = y[p * kOut + 4] - bound_target(eh, base[p * 4], target[p * 4], excess);
     s[3] += db * db;
   }
   for (int k = 0; k < 4; ++k) {
@@ -293,7 +300,7 @@ __global__ void k_loss_sums(const float* __restrict__ y, const float* __restrict
 
 __global__ void k_loss_grad(const float* __restrict__ y, const float* __restrict__ base,
                             const float* __restrict__ target, const uint8_t* __restrict__ mask, int64_t P,
-                            const double* __restrict__ sums, float bound_weight, float* __restrict__ dy,
+                            const double* __restrict__ sums, float bound_weight, int excess, float* __restrict__ dy,
                             float* __restrict__ loss /* [4] total, height, colour, bound */) {
   const double cnt = sums[0] > 1.0 ? sums[0] : 1.0;
   const float inv = (float)(1.0 / cnt), inv3 = (float)(1.0 / (3.0 * cnt));
@@ -311,7 +318,7 @@ __global__ void k_loss_grad(const float* __restrict__ y, const float* __restrict
         const float ec = base[p * 4 + k] + y[p * kOut + k] - target[p * 4 + k];
         g[k] = ec * ec < 1.f ? ec * inv3 : 0.f;
       }
-      const float db = y[p * kOut + 4] - fabsf(eh);
+      const float db = y[p * kOut + 4] - bound_target(eh, base[p * 4], target[p * 4], excess);
       g[4] = bound_weight * 2.f * db * inv;
     }
 #pragma unroll
@@ -725,14 +732,16 @@ extern "C" ls_status ls_filler_backward(ls_model* m, const float* params, const 
 }
 
 extern "C" ls_status ls_filler_loss(const float* y, const float* base, const float* target, const uint8_t* mask,
-                                    int64_t n_px, float bound_weight, double* sums, float* loss, float* dy,
-                                    ls_stream_t stream) {
+                                    int64_t n_px, float bound_weight, int32_t bound_excess, double* sums,
+                                    float* loss, float* dy, ls_stream_t stream) {
   if (!y || !base || !target || !mask || !sums || !dy || n_px <= 0) return LS_ERR_INVALID_ARG;
+  if (bound_excess != 0 && bound_excess != 1) return LS_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   LS_CUDA_TRY(cudaMemsetAsync(sums, 0, 4 * sizeof(double), s));
-  k_loss_sums<<<grid_cap((n_px + 255) / 256, kSmCount * 8), 256, 0, s>>>(y, base, target, mask, n_px, sums);
+  k_loss_sums<<<grid_cap((n_px + 255) / 256, kSmCount * 8), 256, 0, s>>>(y, base, target, mask, n_px, bound_excess,
+                                                                         sums);
   k_loss_grad<<<grid_cap((n_px + 255) / 256, kSmCount * 8), 256, 0, s>>>(y, base, target, mask, n_px, sums,
-                                                                         bound_weight, dy, loss);
+                                                                         bound_weight, bound_excess, dy, loss);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 

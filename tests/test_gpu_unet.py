@@ -236,16 +236,18 @@ def test_loss_and_adamw_match_oracle(lsb):
     tgt[0, :4, :4, 0] += 3.0     # clipped squared errors
     mask = (rng.random((n, 64, 64)) > 0.2).astype(np.uint8)
     T = lambda a: torch.from_numpy(a).cuda()  # noqa: E731
-    loss, dy = lsb.filler_loss(T(y), T(base), T(tgt), T(mask))
-    lr_, dyr, parts = U.loss_and_grad(y.astype(np.float64), base[..., 0].astype(np.float64),
-                                      base[..., 1:].astype(np.float64), tgt[..., 0].astype(np.float64),
-                                      tgt[..., 1:].astype(np.float64), mask)
-    l4 = loss.cpu().numpy()
-    assert l4[0] == pytest.approx(lr_, rel=1e-5)
-    assert l4[1] == pytest.approx(parts["height"], rel=1e-5)
-    # the bound gradient 2 (y4 - |e_h|)/n cancels in fp32 where y4 ~ |e_h|: absolute
-    # tolerance of a few fp32 ulps of |y4| / n
-    np.testing.assert_allclose(dy.cpu().numpy(), dyr, rtol=1e-5, atol=4e-6 / mask.sum())
+    for excess in (False, True):
+        loss, dy = lsb.filler_loss(T(y), T(base), T(tgt), T(mask), bound_excess=excess)
+        lr_, dyr, parts = U.loss_and_grad(y.astype(np.float64), base[..., 0].astype(np.float64),
+                                          base[..., 1:].astype(np.float64), tgt[..., 0].astype(np.float64),
+                                          tgt[..., 1:].astype(np.float64), mask, bound_excess=excess)
+        l4 = loss.cpu().numpy()
+        assert l4[0] == pytest.approx(lr_, rel=1e-5)
+        assert l4[1] == pytest.approx(parts["height"], rel=1e-5)
+        assert l4[3] == pytest.approx(parts["bound"], rel=1e-5)
+        # the bound gradient 2 (y4 - b)/n cancels in fp32 where y4 ~ b (b a difference
+        # of fp32 terms): absolute tolerance of a few fp32 ulps of |y4| / n
+        np.testing.assert_allclose(dy.cpu().numpy(), dyr, rtol=1e-5, atol=4e-6 / mask.sum())
     # AdamW
     p = rng.standard_normal(1000).astype(np.float32)
     pg, pm, pv = T(p.copy()), T(np.zeros(1000, np.float32)), T(np.zeros(1000, np.float32))

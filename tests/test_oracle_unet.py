@@ -69,6 +69,26 @@ def test_loss_hand_case():
     assert (dy[0, 0, 1] == 0).all()
 
 
+def test_loss_bound_excess_hand_case():
+    """The excess target max(|e| - |e_base|, 0): the learned height's error over the
+    base fill's error, zero where the learned height is the better one."""
+    y = np.zeros((1, 1, 3, 5))
+    y[0, 0, :, 0] = [0.3, -0.1, 0.0]             # residuals
+    y[0, 0, :, 4] = [0.05, 0.2, 0.0]
+    base_h = np.array([[[0.1, 0.5, -0.2]]])
+    t_h = np.array([[[0.2, 0.2, 0.0]]])          # base errors -0.1, 0.3, -0.2
+    z = np.zeros((1, 1, 3, 3))
+    m = np.ones((1, 1, 3))
+    # learned errors 0.2, 0.2, -0.2 -> excess 0.1, 0 (better than the base), 0
+    _, dy, parts = U.loss_and_grad(y, base_h, z, t_h, z, m, bound_excess=True)
+    tb = np.array([0.1, 0.0, 0.0])
+    assert parts["bound"] == pytest.approx(((y[0, 0, :, 4] - tb) ** 2).mean())
+    np.testing.assert_allclose(dy[0, 0, :, 4], 2.0 * (y[0, 0, :, 4] - tb) / 3.0, rtol=1e-12)
+    # the absolute target on the same case: |e| = 0.2, 0.2, 0.2
+    _, _, p_abs = U.loss_and_grad(y, base_h, z, t_h, z, m)
+    assert p_abs["bound"] == pytest.approx(((y[0, 0, :, 4] - 0.2) ** 2).mean())
+
+
 def _fd_check(widths, hw, n=2, seed=0, h=1e-6):
     layers = U.layer_table(widths)
     rng = np.random.default_rng(seed)
@@ -110,23 +130,30 @@ def test_backward_matches_finite_differences_three_level():
     assert _fd_check((4, 6, 8), 8, seed=3) < 1e-6
 
 
-def test_loss_gradient_matches_finite_differences():
+@pytest.mark.parametrize("excess", [False, True])
+def test_loss_gradient_matches_finite_differences(excess):
     rng = np.random.default_rng(5)
     y = rng.standard_normal((2, 4, 4, 5)) * 0.3
     bh, bc = rng.standard_normal((2, 4, 4)) * 0.2, rng.random((2, 4, 4, 3))
     th, tc = rng.standard_normal((2, 4, 4)) * 0.2, rng.random((2, 4, 4, 3))
     m = rng.random((2, 4, 4)) > 0.3
-    _, dy, _ = U.loss_and_grad(y, bh, bc, th, tc, m)
+    L = lambda yy: U.loss_and_grad(yy, bh, bc, th, tc, m, bound_excess=excess)  # noqa: E731
+    _, dy, _ = L(y)
+
+    def target(yy):
+        t = np.abs(bh + yy[..., 0] - th)
+        return np.maximum(t - np.abs(bh - th), 0.0) if excess else t
+
     h = 1e-7
     for _ in range(40):
         i = tuple(rng.integers(0, s) for s in y.shape)
         yp, ym = y.copy(), y.copy()
         yp[i] += h
         ym[i] -= h
-        fd = (U.loss_and_grad(yp, bh, bc, th, tc, m)[0] - U.loss_and_grad(ym, bh, bc, th, tc, m)[0]) / (2 * h)
+        fd = (L(yp)[0] - L(ym)[0]) / (2 * h)
         if i[3] == 0:
             # the bound term's detached target also moves with y0: remove it
-            db = lambda yy: ((yy[..., 4] - np.abs(bh + yy[..., 0] - th)) ** 2 * m).sum() / max(m.sum(), 1)  # noqa: E731
+            db = lambda yy: ((yy[..., 4] - target(yy)) ** 2 * m).sum() / max(m.sum(), 1)  # noqa: E731
             fd -= (db(yp) - db(ym)) / (2 * h)
         assert fd == pytest.approx(dy[i], abs=1e-7)
 
