@@ -768,26 +768,56 @@ def run_e2e(lsb, region, counts, pts, step, stream, steps, world):
 # CPU oracle (the baseline and the reference arm)
 # ------------------------------------------------------------------------------------
 
-def oracle_tiles_per_s(tiles_pts, region, budget_s):
-    """Time the oracle's whole path per tile (bin 640 + bin 64, extraction, FP64 fill
-    of the tile with its 3x3 neighbourhood samples, tile update) on host cores."""
+def neighbourhood(region, samples, t):
+    """The tiles of tile t's 3 x 3 block that exist, as a sub-region, with their chunk
+    samples (host arrays, CSR by sub-region tile) and the index of t inside it."""
+    import synth
+    tx, ty = t % region.tiles_x, t // region.tiles_x
+    xa, xb = max(tx - 1, 0), min(tx + 1, region.tiles_x - 1)
+    ya, yb = max(ty - 1, 0), min(ty + 1, region.tiles_y - 1)
+    sub = synth.Region(x0_cm=region.x0_cm + xa * region.tile_cm, y0_cm=region.y0_cm + ya * region.tile_cm,
+                       tile_cm=region.tile_cm, tiles_x=xb - xa + 1, tiles_y=yb - ya + 1,
+                       z_scale=region.z_scale, z_offset=region.z_offset)
+    offs = samples["tile_offsets"]
+    tiles = [uy * region.tiles_x + ux for uy in range(ya, yb + 1) for ux in range(xa, xb + 1)]
+    parts = {k: [samples[k][offs[u]:offs[u + 1]] for u in tiles] for k in "xyzrgb"}
+    center = (ty - ya) * sub.tiles_x + (tx - xa)
+    return sub, parts, center
+
+
+def oracle_tile(t, p, region, samples):
+    """The oracle's whole path for tile t of the region (bin 640 + bin 64 of its points,
+    extraction of its chunk samples, FP64 Gaussian fill of the tile over the samples of
+    its 3 x 3 neighbourhood, as the GPU blends them, tile update); seconds taken.  The
+    neighbours' samples are generated beforehand (they equal the extraction of their
+    points) and their gathering is not timed."""
     import oracle
     import synth
+    one = synth.Region(x0_cm=region.x0_cm + (t % region.tiles_x) * region.tile_cm,
+                       y0_cm=region.y0_cm + (t // region.tiles_x) * region.tile_cm,
+                       tile_cm=region.tile_cm, z_scale=region.z_scale, z_offset=region.z_offset)
+    sub, parts, center = neighbourhood(region, samples, t)
+    t0 = time.perf_counter()
+    oracle.bin_points(p, one, 640)
+    b64 = oracle.bin_points(p, one, 64)
+    idx, _ = oracle.extract_sample_indices(np.array([0, len(p["x"])], np.int64))
+    own = {k: p[k][idx] for k in "xyzrgb"}
+    s = {k: np.concatenate(parts[k][:center] + [own[k]] + parts[k][center + 1:]) for k in "xyzrgb"}
+    s["tile_offsets"] = np.concatenate([[0], np.cumsum([len(q) for q in parts["x"][:center]] + [len(own["x"])]
+                                                       + [len(q) for q in parts["x"][center + 1:]])])
+    f = oracle.fill_sparse(s, sub, tile_ids=np.array([center]))
+    oracle.update_tile(b64, one, [0], f["height"].astype(np.float32), f["rgb8"])
+    return time.perf_counter() - t0
+
+
+def oracle_tiles_per_s(tiles_pts, region, samples, budget_s):
+    """The oracle path per tile (oracle_tile) over the given tiles, serially on one host
+    core, until the budget has passed: tiles per second."""
     done = 0
     t_used = 0.0
     for t, p in tiles_pts:
-        one = synth.Region(x0_cm=region.x0_cm + (t % region.tiles_x) * region.tile_cm,
-                           y0_cm=region.y0_cm + (t // region.tiles_x) * region.tile_cm)
-        t0 = time.perf_counter()
-        b640 = oracle.bin_points(p, one, 640)
-        b64 = oracle.bin_points(p, one, 64)
-        idx, soffs = oracle.extract_sample_indices(np.array([0, len(p["x"])], np.int64))
-        s = {k: p[k][idx] for k in "xyzrgb"}
-        f = oracle.fill_sparse(s, one)
-        oracle.update_tile(b64, one, [0], f["height"].astype(np.float32), f["rgb8"])
-        t_used += time.perf_counter() - t0
+        t_used += oracle_tile(t, p, region, samples)
         done += 1
-        del b640
         if t_used >= budget_s:
             break
     return done / t_used, done, t_used
@@ -816,7 +846,7 @@ def _cpu_model():
     return "unknown"
 
 
-def oracle_tiles_per_s_parallel(tiles_pts, region, budget_s, threads):
+def oracle_tiles_per_s_parallel(tiles_pts, region, samples, budget_s, threads):
     """The same per-tile oracle path on `threads` host threads (the C oracle and numpy
     release the GIL), tiles taken round-robin from the preloaded list until the budget
     has passed; tiles per second of wall time."""
@@ -830,7 +860,7 @@ def oracle_tiles_per_s_parallel(tiles_pts, region, budget_s, threads):
             with lock:
                 i = state["next"]
                 state["next"] += 1
-            oracle_tiles_per_s([tiles_pts[i % len(tiles_pts)]], region, 0.0)
+            oracle_tiles_per_s([tiles_pts[i % len(tiles_pts)]], region, samples, 0.0)
             with lock:
                 state["done"] += 1
 
@@ -844,46 +874,70 @@ def oracle_tiles_per_s_parallel(tiles_pts, region, budget_s, threads):
     return state["done"] / wall, state["done"], wall
 
 
-def cpu_baseline(pts, counts, region, budget_s=12.0):
+def cpu_baseline(pts, counts, region, budget_s=12.0, seed=SEED):
+    import synth
+    samples = synth.region_samples(seed, region, counts)  # the chunk samples of every tile
     tiles = _sample_tiles_host(pts, counts, region, 256)
-    tps, done, used = oracle_tiles_per_s(tiles, region, budget_s)
+    tps, done, used = oracle_tiles_per_s(tiles, region, samples, budget_s)
     out = {"value": round(tps, 3), "unit": "tiles/s", "cores": 1, "kind": "oracle",
            "sample": f"{done} tiles of the batched region spread over the density range "
-                     f"(serial C oracle: bin 640+64, extract, FP64 fill, update), {used:.1f} s",
+                     f"(serial C oracle: bin 640+64, extract, FP64 fill over the 3x3 neighbourhood's "
+                     f"samples, update), {used:.1f} s",
            "cpu_model": _cpu_model()}
     # the same oracle over tiles on every host core (results are per tile, identical)
     threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     if threads > 1:
         pre = list(_sample_tiles_host(pts, counts, region, 32))
-        ptps, pdone, wall = oracle_tiles_per_s_parallel(pre, region, budget_s / 2, threads)
+        ptps, pdone, wall = oracle_tiles_per_s_parallel(pre, region, samples, budget_s / 2, threads)
         out["all_cores"] = {"value": round(ptps, 3), "unit": "tiles/s", "cores": threads,
                             "sample": f"{pdone} tile runs over 32 tiles of the density range, {wall:.1f} s wall"}
     return out
 
 
+REF_TILES = 16  # tiles of the reference arm's cycle, spread over the density range
+
+
 def run_reference(args, rank, world):
-    """The reference arm: the CPU oracle as it stands, on the same workload shape."""
+    """The reference arm: the CPU oracle as it stands (oracle_tile), on the batched
+    region.  A step is one tile of the region, serially on one host core; the steps
+    cycle through REF_TILES tiles at evenly spaced quantiles of the lognormal point
+    counts, so the timed steps cover the density range.  value = tiles per second of
+    the timed steps, ms_per_step their mean time (one tile each, not extrapolated)."""
     import synth
     region, counts = synth.batched_region_workload(seed=SEED)
-    times, done_all = [], 0
+    samples = synth.region_samples(SEED, region, counts)
     order = np.argsort(counts)
-    picks = [int(order[len(order) // 3]), int(order[len(order) // 2])]
-    tiles = [(t, dict(zip("xyzrgb", synth.tile_points(SEED, region, t, int(counts[t]))))) for t in picks]
+    picks = order[np.linspace(0, len(order) - 1, REF_TILES).astype(int)]
+    picks = picks[np.random.default_rng(0).permutation(REF_TILES)]  # few steps still span the range
+    cache = {}
+
+    def tile(t):
+        if t not in cache:
+            cache[t] = dict(zip("xyzrgb", synth.tile_points(SEED, region, t, int(counts[t]))))
+        return cache[t]
+
+    times, pts_timed = [], 0
     for step in range(args.warmup + args.steps):
-        tps, done, used = oracle_tiles_per_s([tiles[step % len(tiles)]], region, 0.0)
+        t = int(picks[step % REF_TILES])
+        dt = oracle_tile(t, tile(t), region, samples)
         if step >= args.warmup:
-            times.append(used / done)
-            done_all += done
+            times.append(dt)
+            pts_timed += int(counts[t])
     s_per_tile = float(np.mean(times))
     value = 1.0 / s_per_tile
     return {"metric": METRIC, "value": round(value, 3), "unit": "tiles/s", "impl": "reference",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(1000 * s_per_tile * region.n_tiles, 1),
+            "ms_per_step": round(1000 * s_per_tile, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64/f64",
             "data": "synthetic (seeded fBm terrain, LAZ strip order)",
-            "config": {"workload": WORKLOAD, "tiles_per_gpu": region.n_tiles},
+            "config": {"workload": WORKLOAD, "tiles_per_gpu": region.n_tiles,
+                       "step": "one tile of the region per step (bounded CPU sample); the GPU arm's step "
+                               "is the whole region"},
             "cpu_baseline": {"value": round(value, 3), "unit": "tiles/s", "cores": 1, "kind": "oracle",
-                             "sample": f"one of two mid-density tiles per step, {done_all} tiles timed"},
+                             "sample": f"{len(times)} timed tiles cycling through {REF_TILES} tiles at evenly "
+                                       f"spaced quantiles of the point counts ({pts_timed} points); serial C "
+                                       f"oracle: bin 640+64, extract, FP64 fill over the 3x3 neighbourhood's "
+                                       f"samples, update"},
             "e2e": {"value": round(value, 3), "unit": "tiles/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
