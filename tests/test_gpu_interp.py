@@ -93,8 +93,7 @@ def bucket(region, x, y, z, rgb=None, seed=0):
 
 def test_region_3x3_synthetic_samples(lsb):
     """9 tiles of the chunk-sample workload (about 2M points per tile, 40 samples per
-    tile, 60-140 per padded window): both the small tier (<= 96 window samples) and
-    the big tier run."""
+    tile, 60-140 per padded window): the 96- and 192-sample tiers run."""
     region = synth.Region(tiles_x=3, tiles_y=3, z_offset=120.25)
     counts = synth.lognormal_counts(5, 9, mu=np.log(5.0), sigma=0.5)
     samples = synth.region_samples(7, region, counts)
@@ -105,7 +104,8 @@ def test_region_3x3_synthetic_samples(lsb):
 
 
 def test_big_tier_dense_windows(lsb):
-    """Windows of 250-450 samples (big tier only), tile subset in reverse order."""
+    """Windows of 250-450 samples (the 384- and 1536-sample tiers), tile subset in
+    reverse order."""
     region = synth.Region(tiles_x=3, tiles_y=3)
     counts = np.full(9, 9_000_000, np.int64)
     samples = synth.region_samples(11, region, counts)
@@ -114,6 +114,25 @@ def test_big_tier_dense_windows(lsb):
     assert st == 0
     for o, t in enumerate(tiles):
         check_patch(got, o, samples, region, t, msg=f"tile {t}")
+
+
+@pytest.mark.parametrize("n", [96, 97, 192, 193, 384, 385])
+def test_tier_edges(lsb, n):
+    """A window holding exactly n samples, at and just past each tier's capacity (96,
+    192, 384 window samples; the next tier takes the patch from a device queue): the
+    centre tile of a 3x3 region holds all n samples, and its neighbours' windows see
+    the 160 m of it next to them."""
+    region = synth.Region(tiles_x=3, tiles_y=3, z_offset=7.5)
+    rng = np.random.default_rng(n)
+    x = region.x0_cm + region.tile_cm + rng.integers(0, region.tile_cm, n)
+    y = region.y0_cm + region.tile_cm + rng.integers(0, region.tile_cm, n)
+    z = rng.integers(-20000, 90000, n)
+    samples = bucket(region, x, y, z, seed=n)
+    tiles = [4, 1, 5]
+    got, st = run_gpu(lsb, samples, region, tile_ids=tiles)
+    assert st == 0
+    for o, t in enumerate(tiles):
+        check_patch(got, o, samples, region, t, msg=f"n={n} tile {t}")
 
 
 def _lattice_case(step, jitter_seed=None, dup=0, shuffle_seed=1):
