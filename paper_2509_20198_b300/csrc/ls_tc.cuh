@@ -93,9 +93,28 @@ __device__ __forceinline__ uint64_t sdesc_sw(uint32_t addr, uint32_t sbo, uint32
   d |= (uint64_t)(mode & 7u) << 61;
   return d;
 }
+// MN-major (the M or N index contiguous in a row), as a TMA tile load writes an NHWC
+// box of cw channels x pixels: rows of 2*cw bytes (one per K index), swizzled with
+// mode 2 (128-byte, cw 64), 4 (64-byte, cw 32), 6 (32-byte, cw 16) or 0 (none, cw 8).
+// With a swizzle, LBO is the byte stride between groups of cw MN indices and SBO
+// between groups of 8 K rows; without one the roles swap (SBO between 8-index MN groups,
+// LBO between 8-row K groups).
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t mode) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)(mode & 7u) << 61;
+  return d;
+}
 // kind::f16 instruction descriptor: BF16 A and B, FP32 accumulator, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+// The same with A and B MN-major (bits 15 and 16: the operands are read transposed).
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int m, int n) {
+  return idesc_bf16(m, n) | (1u << 15) | (1u << 16);
 }
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(

@@ -5,23 +5,23 @@
 // and stores its partial sums; k_wsum adds them to the FP32 gradient in a fixed order,
 // so the result does not depend on CTA scheduling (training is reproducible).
 //
-// Both operands are stored pixel-minor (NHWC), while the MMA reads K-major tiles
-// (pixels contiguous), so every stage is transposed once in shared memory:
+// Both operands are stored pixel-minor (NHWC): for a pixel (the GEMM's K index) the
+// channels (its M or N index) are contiguous.  That is the MN-major operand layout, so
+// the MMA reads the TMA boxes as they land, with no transposition:
 //  warp 0     TMA producer: the M tile's rows are 128 / cw blocks of cw channels of one
 //             tap (cw = 64, 32, 16 or 8 dividing C_in): one 4-D tiled load per block of the
 //             tap-shifted input (cw channels x 64 pixels: whole rows, or half a row of a
-//             128-wide image; zero-filled outside the image: the padding; rows of 128 / 64 bytes are written with the 128B / 64B
-//             swizzle), and dZ in blocks of cwb output channels, into a raw ring;
-//  warps 1-4  transpose raw -> K-major core matrices with ldmatrix (8x8 b16 blocks:
-//             8 pixel rows of one 16-byte channel chunk, un-swizzled by address) and
-//             stmatrix.trans, 4 blocks per instruction pair, then make the tile visible
-//             to the tensor core (fence.proxy.async);
-//             at the end they read the accumulator from TMEM (one row per thread);
-//  warp 5     issues tcgen05.mma kind::f16 (M=128, N=C_out, K=16) and commits.
+//             128-wide image; zero-filled outside the image: the padding; rows of
+//             128 / 64 / 32 bytes written with the matching swizzle), and dZ in blocks of
+//             cwb output channels, into a ring of stages;
+//  warp 5     issues tcgen05.mma kind::f16 (M=128, N=C_out, K=16) with both operands
+//             MN-major and commits each stage back to the producer;
+//  warps 1-4  read the accumulator from TMEM at the end (one row per thread).
 // The bias gradient is a column sum of dZ.  When 9*C_in leaves padding rows in the last
-// M tile, the first padding row of every A stage is set to ones, so the same MMAs sum
-// dZ over the pixels into that row and k_wsum passes it on as the bias gradient;
-// otherwise k_colsum (per-block partials) and k_dbsum (in block order) compute it.
+// M tile, the first padding row of every stage is set to ones once (no load writes the
+// padding blocks), so the same MMAs sum dZ over the pixels into that row and k_wsum
+// passes it on as the bias gradient; otherwise k_colsum (per-block partials) and k_dbsum
+// (in block order) compute it.
 #include <cuda_bf16.h>
 
 #include "ls_tc.cuh"
@@ -30,16 +30,14 @@ namespace ls {
 namespace {
 
 constexpr int kWgThreads = 192;
-// Two raw and two operand stages: at C_out <= 64 a CTA then needs at most 96 KB of
-// shared memory and two or three CTAs share an SM, whose independent pipelines hide the
-// load and transpose latency better than deeper rings in one CTA (measured: 3 + 3
-// stages, one CTA per SM, made the weight gradients 25 % slower)
-constexpr int kWgRaw = 2;   // raw (TMA) stages
-constexpr int kWgOps = 2;   // operand (K-major) stages
+// Four stages: at C_out <= 64 a CTA needs at most 96 KB of shared memory and two or
+// three CTAs share an SM, whose independent pipelines hide the load latency better than
+// deeper rings in one CTA
+constexpr int kWgStages = 4;
 constexpr int kWgPix = 64;  // pixels (K) per stage
 constexpr int kWgABytes = 128 * kWgPix * 2;
 
-// Byte offset in a raw stage of channel ch (multiple of 8) of pixel px, the stage being
+// Byte offset in a stage of channel ch (multiple of 8) of pixel px, the stage being
 // a sequence of blocks of cw channels x 64 pixels as the TMA wrote them: pixel rows of
 // 2*cw bytes; 16-byte chunk c of row px sits at chunk c ^ (px & 7) (128B swizzle, cw 64),
 // c ^ ((px >> 1) & 3) (64B swizzle, cw 32) or c ^ ((px >> 2) & 1) (32B swizzle, cw 16);
@@ -67,35 +65,55 @@ struct WgArgs {
 __global__ void __launch_bounds__(kWgThreads, 1)
     k_wgrad(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap dzmap, const WgArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t raw_full[kWgRaw], raw_empty[kWgRaw], op_full[kWgOps], op_empty[kWgOps], done;
+  __shared__ __align__(8) uint64_t full[kWgStages], empty[kWgStages], done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t stage_bytes = kWgABytes + a.b_bytes;
-  uint8_t* raw = smem;
-  uint8_t* ops = smem + (size_t)kWgRaw * stage_bytes;
   const int mt = blockIdx.x % a.n_mtiles;
   const int64_t slice = blockIdx.x / a.n_mtiles;
   const int64_t p_begin = slice * a.pix_per_cta;
   const int64_t p_end = min(p_begin + a.pix_per_cta, a.pix_total);
   const int n_steps = (int)((p_end - p_begin + kWgPix - 1) / kWgPix);
   const int m0 = mt * 128;
-  const int n_og = a.cout / 8;
+  const int blk_a = kWgPix * a.cw * 2, blk_b = kWgPix * a.cwb * 2;  // bytes per block load
+  // blocks of cw channels of the tile inside the 9*C_in rows (a block never straddles
+  // two taps: cw divides C_in); the rest of the tile is padding that no load writes
+  const int n_blocks = 128 / a.cw;
+  int n_valid = (a.rows - m0) / a.cw;
+  if (n_valid > n_blocks) n_valid = n_blocks;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kWgRaw; ++i) {
-      tc::mbar_init(&raw_full[i], 1);
-      tc::mbar_init(&raw_empty[i], 4);
-    }
-    for (int i = 0; i < kWgOps; ++i) {
-      tc::mbar_init(&op_full[i], 4);
-      tc::mbar_init(&op_empty[i], 1);
+    for (int i = 0; i < kWgStages; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
     }
     tc::mbar_init(&done, 1);
     abort_flag = 0;
     tc::mbar_fence_init();
     tc::prefetch_tmap(&xmap);
     tc::prefetch_tmap(&dzmap);
+  }
+  if (n_valid < n_blocks && warp >= 1 && warp <= 4) {
+    // padding blocks of every stage, once: zeros, and, for the bias gradient, the ones
+    // row (the tile's row `rows`: channel 0 of the first padding block) for all pixels
+    const int t = threadIdx.x - 32;
+    for (int s = 0; s < kWgStages; ++s) {
+      uint32_t* pad = reinterpret_cast<uint32_t*>(smem + (size_t)s * stage_bytes + (size_t)n_valid * blk_a);
+      const int words = (n_blocks - n_valid) * blk_a / 4;
+      for (int i = t; i < words; i += 128) pad[i] = 0u;
+    }
+    __syncwarp();
+    asm volatile("bar.sync 1, 128;" ::: "memory");  // the four padding warps
+    if (a.ones_row == a.rows && a.ones_row >= m0 && a.ones_row < m0 + 128) {
+      for (int i = t; i < kWgStages * kWgPix; i += 128) {
+        const int s = i / kWgPix, px = i - s * kWgPix;
+        uint16_t* one = reinterpret_cast<uint16_t*>(smem + (size_t)s * stage_bytes +
+                                                    raw_off(n_valid * a.cw, px, a.cw));
+        *one = 0x3F80u;  // bf16 1.0
+      }
+    }
+    tc::fence_proxy_async_smem();
   }
   if (warp == 5) tc::tmem_alloc(&tmem_base, a.tmem_cols);
   tc::fence_before();
@@ -108,19 +126,16 @@ __global__ void __launch_bounds__(kWgThreads, 1)
       // ---------------- TMA producer: the tile's block coordinates are fixed, the
       // pixel position advances by one stage (64 pixels) at a time
       const int64_t hw = (int64_t)a.h * a.w;
-      const int blk_a = kWgPix * a.cw * 2, blk_b = kWgPix * a.cwb * 2;  // bytes per block load
-      int n_valid = 0;  // blocks of the tile inside the 9*C_in rows
       int bc[16], bx[16], by[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        const int k = m0 + i * a.cw;  // a block never straddles two taps: cw divides C_in
+        const int k = m0 + i * a.cw;
         bc[i] = bx[i] = by[i] = 0;
-        if (i < 128 / a.cw && k < a.rows) {
+        if (i < n_valid) {
           const int tap = k / a.cin;
           bc[i] = k - tap * a.cin;
           by[i] = tap / 3 - 1;
           bx[i] = tap - (tap / 3) * 3 - 1;
-          ++n_valid;
         }
       }
       const int n_ob = a.cout / a.cwb;
@@ -132,16 +147,16 @@ __global__ void __launch_bounds__(kWgThreads, 1)
       int slot = 0;
       uint32_t ph = 0;
       for (int s = 0; s < n_steps && !abort_flag; ++s) {
-        if (!tc::mbar_wait(&raw_empty[slot], ph ^ 1u)) { abort_flag = 1; break; }
-        uint8_t* RA = raw + (size_t)slot * stage_bytes;
+        if (!tc::mbar_wait(&empty[slot], ph ^ 1u)) { abort_flag = 1; break; }
+        uint8_t* RA = smem + (size_t)slot * stage_bytes;
         uint8_t* RB = RA + kWgABytes;
-        tc::mbar_arrive_expect_tx(&raw_full[slot], bytes);
+        tc::mbar_arrive_expect_tx(&full[slot], bytes);
 #pragma unroll
         for (int i = 0; i < 16; ++i)
           if (i < n_valid)
-            tc::tma_load_4d(RA + i * blk_a, &xmap, bc[i], x0 + bx[i], y0 + by[i], n0, &raw_full[slot]);
+            tc::tma_load_4d(RA + i * blk_a, &xmap, bc[i], x0 + bx[i], y0 + by[i], n0, &full[slot]);
         for (int ob = 0; ob < n_ob; ++ob)
-          tc::tma_load_4d(RB + ob * blk_b, &dzmap, ob * a.cwb, x0, y0, n0, &raw_full[slot]);
+          tc::tma_load_4d(RB + ob * blk_b, &dzmap, ob * a.cwb, x0, y0, n0, &full[slot]);
         // next 64 pixels: the rest of this row, more rows of this image, or the next
         // image(s)
         if (a.imgs_per_step > 1) {
@@ -154,85 +169,12 @@ __global__ void __launch_bounds__(kWgThreads, 1)
             if (y0 >= a.h) { y0 = 0; ++n0; }
           }
         }
-        if (++slot == kWgRaw) { slot = 0; ph ^= 1u; }
+        if (++slot == kWgStages) { slot = 0; ph ^= 1u; }
       }
     }
   } else if (warp <= 4) {
-    // ---------------- transposers (warps 1-4), then epilogue
-    const int tw = warp - 1;
-    const int mi = lane >> 3, mj = lane & 7;  // matrix of this lane's row address, row within it
-    const int n_aitems = 32;                  // 16 row groups x 2 quads of pixel groups
-    const int n_items = n_aitems + n_og * 2;
-    // this warp's items (at most 8 of A and 8 of B): lane offsets from the raw stage's
-    // and the operand stage's bases, computed once
-    uint32_t src[16], dst[16];
-    int mine = 0;
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int it = tw + 4 * q;
-      src[q] = dst[q] = 0u;
-      if (it < n_items) {
-        ++mine;
-        if (it < n_aitems) {
-          // A block (row group g, pixel group pg): raw rows = pixels, K-major core
-          // matrix rows = channels (16 B = 8 pixels)
-          const int g = it >> 1, pg = (it & 1) * 4 + mi;
-          src[q] = raw_off(g * 8, pg * 8 + mj, a.cw);
-          dst[q] = g * 128 + pg * 2048 + mj * 16;
-        } else {
-          const int u = it - n_aitems, og = u >> 1, pg = (u & 1) * 4 + mi;
-          src[q] = kWgABytes + raw_off(og * 8, pg * 8 + mj, a.cwb);
-          dst[q] = kWgABytes + og * 128 + pg * (a.cout * 16) + mj * 16;
-        }
-      }
-    }
-    // the ones row (local row lr of this tile): its two halves of 4 pixel groups belong
-    // to items 2 g1 and 2 g1 + 1, written by the warps that transpose those items
-    const int lr = a.ones_row - m0;
-    const bool has_ones = a.ones_row >= 0 && lr >= 0 && lr < 128;
-    const int g1 = lr >> 3, rr = lr & 7;
-    int ones_h = -1;  // half (pixel groups 4 h .. 4 h + 3) this warp writes
-    if (has_ones) {
-      if ((2 * g1) % 4 == tw) ones_h = 0;
-      else if ((2 * g1 + 1) % 4 == tw) ones_h = 1;
-    }
-    for (int s = 0; s < n_steps && !abort_flag; ++s) {
-      const int rs = s % kWgRaw, os = s % kWgOps;
-      if (!tc::mbar_wait(&raw_full[rs], (uint32_t)(s / kWgRaw) & 1u)) { abort_flag = 1; break; }
-      if (!tc::mbar_wait(&op_empty[os], ((uint32_t)(s / kWgOps) & 1u) ^ 1u)) { abort_flag = 1; break; }
-      const uint32_t RA = tc::saddr(raw + (size_t)rs * stage_bytes);
-      const uint32_t OA = tc::saddr(ops + (size_t)os * stage_bytes);
-      // four loads in flight before their stores
-#pragma unroll
-      for (int q0 = 0; q0 < 16; q0 += 4) {
-        if (q0 < mine) {
-          uint32_t r[4][4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (q0 + q < mine) tc::ldmatrix_x4(RA + src[q0 + q], r[q]);
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (q0 + q < mine) tc::stmatrix_x4_trans(OA + dst[q0 + q], r[q]);
-        }
-      }
-      if (ones_h >= 0) {
-        __syncwarp();
-        if (lane < 4) {
-          const uint32_t one2 = 0x3F803F80u;  // two bf16 1.0
-          const uint32_t adr = OA + (uint32_t)(g1 * 128 + (ones_h * 4 + lane) * 2048 + rr * 16);
-          asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(adr), "r"(one2) : "memory");
-        }
-        __syncwarp();
-      }
-      tc::fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) {
-        tc::mbar_arrive(&raw_empty[rs]);
-        tc::mbar_arrive(&op_full[os]);
-      }
-    }
     // ---------------- epilogue: TMEM row per thread into this CTA's partial block
-    if (n_steps > 0 && !abort_flag && tc::mbar_wait(&done, 0)) {
+    if (n_steps > 0 && tc::mbar_wait(&done, 0) && !abort_flag) {
       tc::fence_after();
       const int q = warp & 3;
       const int row = q * 32 + lane;
@@ -248,20 +190,28 @@ __global__ void __launch_bounds__(kWgThreads, 1)
       }
     }
   } else if (lane == 0) {
-    // ---------------- MMA issuer (warp 5): descriptors are the stage's base + offsets
-    const uint32_t o0 = tc::saddr(ops);
-    const uint64_t adesc0 = tc::sdesc(o0, 2048, 128);
-    const uint64_t bdesc0 = tc::sdesc(o0 + kWgABytes, a.cout * 16, 128);
+    // ---------------- MMA issuer (warp 5): both operands MN-major, straight from the
+    // TMA boxes (NHWC: channels contiguous); K = 16 pixels per MMA is two 8-row groups
+    const uint32_t s0 = tc::saddr(smem);
+    const uint32_t mode_a = a.cw == 64 ? 2u : a.cw == 32 ? 4u : a.cw == 16 ? 6u : 0u;
+    const uint32_t mode_b = a.cwb == 64 ? 2u : a.cwb == 32 ? 4u : a.cwb == 16 ? 6u : 0u;
+    const uint32_t kgrp_a = 16u * (uint32_t)a.cw, kgrp_b = 16u * (uint32_t)a.cwb;  // bytes per 8 K rows
+    const uint64_t adesc0 = a.cw == 8 ? tc::sdesc_mn(s0, kgrp_a, (uint32_t)blk_a, 0u)
+                                      : tc::sdesc_mn(s0, (uint32_t)blk_a, kgrp_a, mode_a);
+    const uint64_t bdesc0 = a.cwb == 8 ? tc::sdesc_mn(s0 + kWgABytes, kgrp_b, (uint32_t)blk_b, 0u)
+                                       : tc::sdesc_mn(s0 + kWgABytes, (uint32_t)blk_b, kgrp_b, mode_b);
+    int slot = 0;
+    uint32_t ph = 0;
     for (int s = 0; s < n_steps && !abort_flag; ++s) {
-      const int os = s % kWgOps;
-      if (!tc::mbar_wait(&op_full[os], (uint32_t)(s / kWgOps) & 1u)) { abort_flag = 1; break; }
+      if (!tc::mbar_wait(&full[slot], ph)) { abort_flag = 1; break; }
       tc::fence_after();
-      const uint64_t so = (uint64_t)((os * stage_bytes) >> 4);
+      const uint64_t so = (uint64_t)((slot * stage_bytes) >> 4);
 #pragma unroll
       for (int j = 0; j < kWgPix / 16; ++j)
-        tc::mma_bf16(taddr, adesc0 + so + (uint64_t)(j * 4096 >> 4), bdesc0 + so + (uint64_t)((j * 2 * a.cout * 16) >> 4),
-                     a.idesc, (s > 0 || j > 0) ? 1u : 0u);
-      tc::mma_commit(&op_empty[os]);
+        tc::mma_bf16(taddr, adesc0 + so + (uint64_t)((j * 2 * kgrp_a) >> 4),
+                     bdesc0 + so + (uint64_t)((j * 2 * kgrp_b) >> 4), a.idesc, (s > 0 || j > 0) ? 1u : 0u);
+      tc::mma_commit(&empty[slot]);
+      if (++slot == kWgStages) { slot = 0; ph ^= 1u; }
     }
     if (n_steps > 0) tc::mma_commit(&done);
   }
@@ -376,7 +326,7 @@ ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int 
   if (per < 1024) per = 1024;
   a.pix_per_cta = per;
   slices = (a.pix_total + per - 1) / per;
-  a.idesc = tc::idesc_bf16(128, cout);
+  a.idesc = tc::idesc_bf16_mn(128, cout);
   a.tmem_cols = 32;
   while ((int)a.tmem_cols < cout) a.tmem_cols <<= 1;
   a.b_bytes = (uint32_t)cout * kWgPix * 2;
@@ -395,7 +345,7 @@ ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int 
   if (!encode_tmap_bf16_4d(&xmap, x, xd, xs, box, a.cw == 8 ? 0 : a.cw * 2) ||
       !encode_tmap_bf16_4d(&dzmap, dz, zd, zs, boxb, a.cwb == 8 ? 0 : a.cwb * 2))
     return LS_ERR_CUDA;
-  const size_t smem = (size_t)(kWgRaw + kWgOps) * (kWgABytes + a.b_bytes);
+  const size_t smem = (size_t)kWgStages * (kWgABytes + a.b_bytes);
   const int64_t ctas = slices * a.n_mtiles;
   const size_t part_bytes = (size_t)ctas * 128 * cout * 4, db_bytes = (size_t)kColsumBlocks * cout * 4;
   uint8_t* ws = static_cast<uint8_t*>(workspace(kWsGradPart, part_bytes + db_bytes));
@@ -406,7 +356,7 @@ ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int 
   LS_CUDA_TRY(cudaGetDevice(&dev));
   if (!device_once(once, dev, [] {
         return cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (kWgRaw + kWgOps) * (kWgABytes + 128 * kWgPix * 2)) == cudaSuccess;
+                                    kWgStages * (kWgABytes + 128 * kWgPix * 2)) == cudaSuccess;
       }))
     return LS_ERR_CUDA;
   k_wgrad<<<(unsigned)ctas, kWgThreads, smem, stream>>>(xmap, dzmap, a);
