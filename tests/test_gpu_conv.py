@@ -83,8 +83,8 @@ def test_forward_bias_relu(lib, shape):
     _close(g, ref)
 
 
-def test_mask_epilogue_and_no_bias(lib):
-    shape = (2, 32, 32, 64, 32)
+@pytest.mark.parametrize("shape", [(2, 32, 32, 64, 32), (2, 64, 64, 32, 32)])
+def test_mask_epilogue_and_no_bias(lib, shape):
     n, h, w, cin, cout = shape
     rng = np.random.default_rng(3)
     x = bf16_bits(rng.standard_normal((n, h, w, cin)).astype(np.float32))
