@@ -225,6 +225,10 @@ struct MeshArgs {
   const int32_t* __restrict__ tile_ids;
   int64_t n, quads;  // heightmaps; quads in all of them
   int res, cell, tile_cm, tiles_x, tiles_y;
+  // quad index -> heightmap and texel by 32-bit division by invariants when every quad
+  // index fits 32 bits (a 64-bit division is a long routine, partly on the FP64 pipe)
+  int q32;
+  FastDiv div_qsq, div_qs;
   long long x0, y0;
   float zo, izs, ozf;
   Cam c;
@@ -249,9 +253,17 @@ __device__ __forceinline__ Vtx mesh_vertex(const MeshArgs& a, int64_t o, int tx,
 __device__ __forceinline__ bool mesh_quad_at(const MeshArgs& a, int64_t q, int64_t& o, int& tx, int& ty, int& i,
                                              int& j) {
   const int qs = a.res - 1;
-  o = q / ((int64_t)qs * qs);
-  const int rem = (int)(q - o * qs * qs);
-  i = rem / qs;
+  int rem;
+  if (a.q32) {
+    const uint32_t oq = fdiv((uint32_t)q, a.div_qsq);
+    rem = (int)((uint32_t)q - oq * (uint32_t)(qs * qs));
+    o = oq;
+    i = (int)fdiv((uint32_t)rem, a.div_qs);
+  } else {
+    o = q / ((int64_t)qs * qs);
+    rem = (int)(q - o * qs * qs);
+    i = rem / qs;
+  }
   j = rem - i * qs;
   const int tile = a.tile_ids ? a.tile_ids[o] : (int)o;
   if (tile < 0 || tile >= a.tiles_x * a.tiles_y) {
@@ -442,6 +454,9 @@ extern "C" ls_status ls_render_heightmaps(const float* height, const uint8_t* rg
   a.tile_ids = tile_ids;
   a.n = n;
   a.quads = n * (int64_t)(res - 1) * (res - 1);
+  a.q32 = a.quads + kMeshThreads < (int64_t(1) << 32);
+  a.div_qsq = make_fastdiv((uint32_t)((res - 1) * (res - 1)));
+  a.div_qs = make_fastdiv((uint32_t)(res - 1));
   a.res = res;
   a.cell = region->tile_cm / res;
   a.tile_cm = region->tile_cm;
