@@ -796,7 +796,7 @@ ls_status fill_launch(const ls_points* samples, const ls_region* region, const l
   int ks = 0;
   while ((256 << ks) < f.stage_cap) ++ks;
   // launch shape: tuned for this key (ls_tune_fill_sparse / ls_fill_shape_set), else the
-  // default: few tiles are split over 4 CTAs (bands of res / 4 texel rows, whole 4-row
+  // default: few tiles are split over 4 CTAs (bands of res / 4 texel rows, whole 8-row
   // blocks), and the persistent grid is sized for the CTAs that fit on an SM
   FillShape shape;
   fill_shape_lookup(fill_shape_key(samples->n, n_out, params), params->res, n_out, &shape);
