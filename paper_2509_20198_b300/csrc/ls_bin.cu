@@ -9,14 +9,16 @@
 //    8 m scan strips.  "Global fine row" G = tile * cells + row is therefore almost
 //    monotone along the stream.  Each CTA streams a contiguous span of points with
 //    128-bit loads and accumulates into a shared-memory ring of W fine rows
-//    (32 bytes per cell: packed R|G, B|count, z-sum, z-min, z-max) with shared
-//    atomics.  When a point lands above the window, the window slides and the rows
-//    that leave are flushed.
+//    (eight 32-bit words per cell: count, R, G, B, low and high halves of z, z-min,
+//    z-max) with shared atomics.  When a point lands above the window, the window
+//    slides and the rows that leave are flushed.
 //  * Flush protocol per row (per-row state word in scratch: 0 free, 1 being
 //    written, 2 written): the first CTA to flush a row claims it (0 -> 1), writes
 //    all its cells with plain coalesced stores (empty cells get the sentinels),
 //    fences and publishes 2.  Any later contribution to that row (another CTA's
 //    part of a strip, or a late point) merges with global atomics after seeing 2.
+//    Late points (rows already below the window) are taken one row at a time by
+//    their whole warp: lane 0 claims or waits, the warp writes the row's sentinels.
 //    So every output byte is written once by a plain store in the common case and
 //    no memset pass is needed.  Rows that nobody touched get sentinels in a final
 //    pass.  Result is exact for ANY point order; only speed depends on the order.
@@ -24,8 +26,10 @@
 //    while they are flushed, accumulated in a small shared ring of coarse rows and
 //    merged with global atomics into the (L2-resident) coarse arrays, which a
 //    prologue kernel initialises.
-//  * Packed 32-bit colour sums in shared memory cannot overflow: a row is forced out
-//    of the window before it can have absorbed 65536 points (65536 * 65535 < 2^32).
+//  * The 32-bit sums in shared memory cannot overflow: no ring row absorbs more than
+//    65536 points (65536 * 65535 < 2^32).  The rows are counted when the fullest one
+//    could first reach that bound, and the window is flushed in place only when a
+//    row is near it.
 #include <algorithm>
 #include <climits>
 #include <mutex>
@@ -38,7 +42,8 @@ namespace {
 constexpr int kBinThreads = 1024;
 constexpr int kPtsPerThread = 4;
 constexpr int kBatch = kBinThreads * kPtsPerThread;  // 4096 points per batch
-constexpr int kResidLimitBatches = 65536 / kBatch;     // residency bound (batches)
+constexpr int kRowLimit = 65536;                      // residency bound: points per ring row
+constexpr int kResidLimitBatches = kRowLimit / kBatch;  // batches before the first row check
 constexpr int kMaxW = 64;
 constexpr int kCW = 4;  // coarse ring rows
 constexpr int kMaxWFlush = 8;  // window rows (W <= 8)
@@ -55,6 +60,7 @@ struct BinArgs {
   int64_t x0, y0;
   uint32_t ext_x, ext_y;
   FastDiv div_tile, div_cell, div_f;
+  FastDiv31 d31_tile, d31_cell;  // the same divisions for numerators < 2^31 (cell_cm >= 2)
   uint32_t tile_cm, cell_cm;
   int32_t tiles_x, cells, W, f, ccells, has_coarse;
   int32_t n_rows;  // T * cells
@@ -82,6 +88,7 @@ struct BinArgs {
   // at fh (gs and fh chosen against bank conflicts, see bin_coarse_layout)
   int32_t gs, rstride, fh;
   int32_t accumulate;  // add into the existing bins: every flushed row merges with atomics
+  int32_t vec_out;     // rows of 4-cell groups (16-byte shared and global alignment): 128-bit flush
   int32_t pf_dist;     // batches prefetched into L2 ahead of the loads (launch shape, 1..4)
 };
 
@@ -112,7 +119,7 @@ struct Smem {
 
 struct Meta {
   int touched[kMaxW];
-  int enter[kMaxW];  // batch index at which the row entered the window
+  unsigned rowc[kMaxW];  // points per ring row (scratch of the residency check)
   int mode[kMaxW];   // 0 none, 1 store, 2 merge
   int ckey[kMaxW];   // coarse row of each row being flushed
   int red[kBinThreads / 32];
@@ -120,7 +127,7 @@ struct Meta {
   int bcast, bcastx;
   int clo_old, clo_new;  // coarse ring scratch of evict_rows (not shared with block_min)
   int n_inplace;
-  int oldest;  // lowest entry batch over the window's slots
+  int next_check;  // batch after whose accumulation the rows are counted again (per span)
   long long item;  // span taken from the counter
   // rows this CTA claimed and stored in its last flush, published (state 2) later
   int pend_row[kMaxW];  // -1: none
@@ -180,6 +187,57 @@ __device__ __forceinline__ Cell read_cell(const Smem& s, int si) {
 __device__ __forceinline__ void reset_cell(Smem& s, int si) {
   s.cnt[si] = 0u; s.rs[si] = 0u; s.gs[si] = 0u; s.bs[si] = 0u;
   s.zlo[si] = 0u; s.zhi[si] = 0; s.mn[si] = INT_MAX; s.mx[si] = INT_MIN;
+}
+
+// Store ring slot `slot` as fine row `base / cells` (every cell, empty ones as the
+// sentinels) and reset it, four cells per thread with 128-bit shared and global
+// accesses (the row's cells are contiguous: no padding; a.vec_out checked the
+// alignment).  Threads t0, t0 + nt, ... take part.
+__device__ __forceinline__ void store_row_vec(const BinArgs& a, Smem& s, int slot, int64_t base, int t0, int nt) {
+  const int o = slot * a.rstride;
+  const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+  for (int q = t0; q < a.cells / 4; q += nt) {
+    const int si = o + 4 * q;
+    const int64_t o4 = base + 4 * q;
+    // one array at a time: load the 4 cells, store them, reset them
+    {
+      uint4* p = reinterpret_cast<uint4*>(s.cnt + si);
+      *reinterpret_cast<uint4*>(a.count + o4) = *p;
+      *p = z4;
+    }
+    {
+      uint4* pl = reinterpret_cast<uint4*>(s.zlo + si);
+      int4* ph = reinterpret_cast<int4*>(s.zhi + si);
+      const uint4 zl = *pl;
+      const int4 zh = *ph;
+      *reinterpret_cast<longlong2*>(a.zsum + o4) =
+          make_longlong2((long long)zh.x * 65536 + (long long)zl.x, (long long)zh.y * 65536 + (long long)zl.y);
+      *reinterpret_cast<longlong2*>(a.zsum + o4 + 2) =
+          make_longlong2((long long)zh.z * 65536 + (long long)zl.z, (long long)zh.w * 65536 + (long long)zl.w);
+      *pl = z4;
+      *reinterpret_cast<uint4*>(ph) = z4;
+    }
+    {
+      int4* p = reinterpret_cast<int4*>(s.mn + si);
+      *reinterpret_cast<int4*>(a.zmin + o4) = *p;
+      *p = make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX);
+    }
+    {
+      int4* p = reinterpret_cast<int4*>(s.mx + si);
+      *reinterpret_cast<int4*>(a.zmax + o4) = *p;
+      *p = make_int4(INT_MIN, INT_MIN, INT_MIN, INT_MIN);
+    }
+    unsigned* const src[3] = {s.rs, s.gs, s.bs};
+    uint64_t* const dst[3] = {a.rsum, a.gsum, a.bsum};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      uint4* p = reinterpret_cast<uint4*>(src[j] + si);
+      const uint4 v = *p;
+      *reinterpret_cast<ulonglong2*>(dst[j] + o4) = make_ulonglong2(v.x, v.y);
+      *reinterpret_cast<ulonglong2*>(dst[j] + o4 + 2) = make_ulonglong2(v.z, v.w);
+      *p = z4;
+    }
+  }
 }
 
 // Diagnostics of the last calls (cumulative until read): late points, waits on a
@@ -271,26 +329,59 @@ __device__ __forceinline__ int sidx(const BinArgs& a, int slot, int col) {
   return slot * a.rstride + cg * a.gs + (col - cg * a.f);
 }
 
-// A point whose row already left this CTA's window: claim the row if nobody has
-// written it yet (single thread writes sentinels), then merge with global atomics.
-// When accumulating, the row already holds valid bins: merge at once.
-__device__ void late_point(const BinArgs& a, int G, int col, int z, uint32_t r, uint32_t g, uint32_t b) {
+// Rows below this CTA's window (late points), one row at a time for the whole warp
+// (called by all 32 lanes, converged): lane 0 claims the row if nobody has written it
+// yet, and then the warp writes its empty cells and lane 0 publishes it; when another
+// claim holds the row, lane 0 waits (bounded) until it is written.  When accumulating,
+// the row already holds valid bins.  Afterwards the late point merges with atomics.
+__device__ void late_row_ready(const BinArgs& a, int G) {
+  if (a.accumulate) return;
+  const int lane = threadIdx.x & 31;
   uint32_t* st = &a.row_state[G];
-  if (!a.accumulate && ld_acquire(st) != 2u) {
-    if (atomicCAS(st, 0u, 1u) == 0u) {
-      const int64_t base = (int64_t)G * a.cells;
-      for (int c = 0; c < a.cells; ++c) store_empty_cell(a, base + c);
+  int act = 0;  // 0 written, 1 claimed here, 2 being written by another claim
+  if (lane == 0 && ld_acquire(st) != 2u) act = atomicCAS(st, 0u, 1u) == 0u ? 1 : 2;
+  act = __shfl_sync(0xffffffffu, act, 0);
+  if (act == 1) {
+    const int64_t base = (int64_t)G * a.cells;
+    for (int c = lane; c < a.cells; c += 32) store_empty_cell(a, base + c);
+    __syncwarp();
+    if (lane == 0) {
       __threadfence();
       atomicExch(st, 2u);
-    } else {
-      wait_written(st);
     }
+  } else if (act == 2) {
+    if (lane == 0) wait_written(st);
   }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void late_merge(const BinArgs& a, int G, int col, int z, uint32_t r, uint32_t g,
+                                           uint32_t b) {
   merge_fine(a, (int64_t)G * a.cells + col, 1u, z, z, z, r, g, b);
   if (a.has_coarse) {
     const int64_t o = (int64_t)coarse_row_of(a, G) * a.ccells + (int)fdiv((uint32_t)col, a.div_f);
     merge_coarse(a, o, 1u, z, z, z, r, g, b);
   }
+}
+
+// Largest point count over the W ring rows (every thread gets it; block-wide, with
+// barriers before and after).  Thread t sums the count words of row t / (threads / W).
+__device__ unsigned row_count_max(const BinArgs& a, const Smem& s, Meta& m) {
+  const int W = a.W;
+  const int per = (int)blockDim.x / W;  // threads per row (W divides 1024)
+  const int r = (int)threadIdx.x / per, t = (int)threadIdx.x - r * per;
+  __syncthreads();  // the accumulation before is complete
+  if (threadIdx.x < W) m.rowc[threadIdx.x] = 0u;
+  __syncthreads();
+  unsigned c = 0;
+  for (int i = t; i < a.rstride; i += per) c += s.cnt[r * a.rstride + i];  // padding slots hold 0
+  c = __reduce_add_sync(0xffffffffu, c);  // per divides into whole warps (per >= 128)
+  if ((threadIdx.x & 31) == 0) atomicAdd(&m.rowc[r], c);
+  __syncthreads();
+  unsigned mx = 0;
+  for (int k = 0; k < W; ++k) mx = max(mx, m.rowc[k]);
+  __syncthreads();  // m.rowc is read before anyone reuses it
+  return mx;
 }
 
 // Block-wide min and max (every thread gets both).
@@ -349,10 +440,11 @@ __device__ __forceinline__ void publish_pending(const BinArgs& a, Meta& m) {
   }
 }
 
-// Partial coarse cell.  32-bit fields suffice for any set of cells in the window:
-// the residency bound keeps the whole window below 65536 points, so count, colour
+// Partial coarse cell of one ring row.  32-bit fields suffice for any set of cells of
+// one row: the residency bound keeps a row at or below 65536 points, so count, colour
 // sums and the sum of the low z halves stay below 2^32 and the sum of the high z
-// halves inside int32.
+// halves inside int32.  Sums over several rows are only formed in the 64-bit coarse
+// ring and arrays.
 struct CAcc {
   unsigned cnt, zlo;
   int zhi, mn, mx;
@@ -442,34 +534,27 @@ __device__ void coarse_partials(const BinArgs& a, Smem& s, const Meta& m, int ra
   }
 }
 
-// Step 2 (threads < kCoarseThreads): one thread per coarse column walks the touched
-// rows' partials in order and emits a coarse cell whenever the coarse row changes.
+// Step 2 (threads < kCoarseThreads): one thread per coarse column adds the touched
+// rows' partials, one row at a time, to their coarse cells (the 64-bit coarse ring,
+// or the global coarse arrays for a coarse row outside it).
 __device__ void coarse_combine(const BinArgs& a, Smem& s, const Meta& m, int nr, int clo) {
   const int SC = a.W * a.ccells;
   for (int c = threadIdx.x; c < a.ccells; c += kCoarseThreads) {
-    CAcc v;
-    cacc_clear(v);
-    int key = -1;
-#pragma unroll
-    for (int rr = 0; rr < kMaxWFlush; ++rr) {
-      if (rr >= nr || m.mode[rr] == 0) continue;
-      const int kr = m.ckey[rr];
-      if (kr != key) {
-        if (key >= 0) cacc_emit(a, s, key, c, clo, v);
-        cacc_clear(v);
-        key = kr;
-      }
+#pragma unroll 1
+    for (int rr = 0; rr < nr; ++rr) {
+      if (m.mode[rr] == 0) continue;
       const int pc = rr * a.ccells + c;
-      v.cnt += s.sp[0 * SC + pc];
-      v.zlo += s.sp[1 * SC + pc];
-      v.zhi += (int)s.sp[2 * SC + pc];
-      v.mn = min(v.mn, (int)s.sp[3 * SC + pc]);
-      v.mx = max(v.mx, (int)s.sp[4 * SC + pc]);
-      v.r += s.sp[5 * SC + pc];
-      v.g += s.sp[6 * SC + pc];
-      v.b += s.sp[7 * SC + pc];
+      CAcc v;
+      v.cnt = s.sp[0 * SC + pc];
+      v.zlo = s.sp[1 * SC + pc];
+      v.zhi = (int)s.sp[2 * SC + pc];
+      v.mn = (int)s.sp[3 * SC + pc];
+      v.mx = (int)s.sp[4 * SC + pc];
+      v.r = s.sp[5 * SC + pc];
+      v.g = s.sp[6 * SC + pc];
+      v.b = s.sp[7 * SC + pc];
+      cacc_emit(a, s, m.ckey[rr], c, clo, v);
     }
-    if (key >= 0) cacc_emit(a, s, key, c, clo, v);
   }
 }
 
@@ -534,6 +619,7 @@ __device__ void evict_rows(const BinArgs& a, Smem& s, Meta& m, int ra, int rb, i
       const int G = ra + rr;
       const int slot = G & (W - 1);
       const int64_t base = (int64_t)G * a.cells;
+
       for (int c = threadIdx.x - st0; c < a.cells; c += nst) {
         const int si = sidx(a, slot, c);
         const Cell fc = read_cell(s, si);
@@ -670,8 +756,9 @@ __device__ __forceinline__ void accumulate(Smem& s, Meta& m, const BinArgs& a, i
 }
 
 // PF: batches prefetched into L2 ahead of the loads (a launch-shape parameter, compiled
-// in so that it costs no register).
-template <int PF>
+// in so that it costs no register).  kD31: cells of at least 2 cm, so the tile and cell
+// divisions take the two-instruction form.
+template <int PF, bool kD31>
 __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Meta m;
@@ -683,8 +770,8 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
     s.crs[i] = 0ull; s.cgs[i] = 0ull; s.cbs[i] = 0ull; s.czs[i] = 0ull;
     s.ccnt[i] = 0u; s.cmn[i] = INT_MAX; s.cmx[i] = INT_MIN;
   }
-  if (threadIdx.x < kMaxW) { m.touched[threadIdx.x] = 0; m.enter[threadIdx.x] = 0; m.pend_row[threadIdx.x] = -1; }
-  if (threadIdx.x == 0) { m.dropped = 0ull; m.n_late = 0ull; m.n_inplace = 0; m.oldest = 0; }
+  if (threadIdx.x < kMaxW) { m.touched[threadIdx.x] = 0; m.pend_row[threadIdx.x] = -1; }
+  if (threadIdx.x == 0) { m.dropped = 0ull; m.n_late = 0ull; m.n_inplace = 0; }
   __syncthreads();
   unsigned my_dropped = 0, my_late = 0;  // per thread: far below 2^32 points
   const int W = a.W;
@@ -702,6 +789,7 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
     int lo = -1;   // lowest fine row of the window (uniform); -1 = empty
     int clo = -1;  // lowest coarse row of the coarse ring
     int batch = 0;
+    if (threadIdx.x == 0) m.next_check = kResidLimitBatches - 1;  // the window starts empty
     Raw cur;
     for (int d = 1; d < PF; ++d) prefetch_batch(a, p0 + (int64_t)d * kBatch, p1);
     for (int64_t b0 = p0; b0 < p1; b0 += kBatch, ++batch) {
@@ -731,9 +819,18 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
           ++my_dropped;
           continue;
         }
-        const uint32_t tx = fdiv(ux, a.div_tile), ty = fdiv(uy, a.div_tile);
-        const uint32_t cx = fdiv(ux - tx * a.tile_cm, a.div_cell);
-        const uint32_t cy = fdiv(uy - ty * a.tile_cm, a.div_cell);
+        uint32_t tx, ty, cx, cy;
+        if constexpr (kD31) {  // ux, uy < ext < 2^31
+          tx = fdiv31(ux, a.d31_tile);
+          ty = fdiv31(uy, a.d31_tile);
+          cx = fdiv31(ux - tx * a.tile_cm, a.d31_cell);
+          cy = fdiv31(uy - ty * a.tile_cm, a.d31_cell);
+        } else {
+          tx = fdiv(ux, a.div_tile);
+          ty = fdiv(uy, a.div_tile);
+          cx = fdiv(ux - tx * a.tile_cm, a.div_cell);
+          cy = fdiv(uy - ty * a.tile_cm, a.div_cell);
+        }
         G[k] = ((int)ty * a.tiles_x + (int)tx) * a.cells + (int)cy;
         col[k] = (int)cx;
         pend |= 1u << k;
@@ -757,14 +854,26 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
         publish_pending(a, m);
         while (true) {
           if (lo >= 0) {
+            // late points (rows below the window), the warp's one at a time
 #pragma unroll
             for (int k = 0; k < kPtsPerThread; ++k) {
-              if (!(pend & (1u << k))) continue;
-              if (G[k] < lo) {
-                late_point(a, G[k], col[k], cur.z[k], half16(cur.r, k), half16(cur.g, k), half16(cur.b, k));
+              const bool late = (pend & (1u << k)) && G[k] < lo;
+              unsigned todo = __ballot_sync(0xffffffffu, late);
+              while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                late_row_ready(a, __shfl_sync(0xffffffffu, G[k], src));
+                if ((int)(threadIdx.x & 31) == src)
+                  late_merge(a, G[k], col[k], cur.z[k], half16(cur.r, k), half16(cur.g, k), half16(cur.b, k));
+              }
+              if (late) {
                 ++my_late;
                 pend &= ~(1u << k);
-              } else if (G[k] < lo + W) {
+              }
+            }
+#pragma unroll
+            for (int k = 0; k < kPtsPerThread; ++k) {
+              if ((pend & (1u << k)) && G[k] < lo + W) {
                 accumulate(s, m, a, G[k] & (W - 1), col[k], cur.z[k], half16(cur.r, k), half16(cur.g, k), half16(cur.b, k));
                 pend &= ~(1u << k);
               }
@@ -788,28 +897,21 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_bin_main(BinArgs a) {
             const int hi = (nlo < lo + W) ? nlo : lo + W;
             evict_rows(a, s, m, lo, hi, clo);
           }
-          if (threadIdx.x == 0) {
-            // rows [max(lo + W, nlo), nlo + W) enter; rows kept in the window keep their age
-            const int first_new = (lo >= 0 && lo + W > nlo) ? lo + W : nlo;
-            for (int G2 = first_new; G2 < nlo + W; ++G2) m.enter[G2 & (W - 1)] = batch;
-            int o = INT_MAX;
-            for (int k = 0; k < W; ++k) o = min(o, m.enter[k]);
-            m.oldest = o;
-          }
-          lo = nlo;
+          lo = nlo;  // the rows that enter are empty
           __syncthreads();
         }
       }
-      // ---- residency bound: before any row can have absorbed 65536 points the
-      // window is flushed in place (its rows stay in the window; their next flush
-      // merges), so strip-ordered input never produces late points
-      if (lo >= 0 && batch - m.oldest + 1 >= kResidLimitBatches) {
-        __syncthreads();
-        evict_rows(a, s, m, lo, lo + W, clo);
+      // ---- residency bound: no ring row may absorb more than kRowLimit points (the
+      // 32-bit sums of its cells stay exact).  A batch adds at most kBatch points to a
+      // row, so after a count of the rows the next one is due once the fullest row
+      // could reach the limit; rows that enter are empty.  Only when a row is near the
+      // limit is the window flushed in place (its rows stay; their next flush merges).
+      if (lo >= 0 && batch >= m.next_check) {
+        const int room = kRowLimit - (int)row_count_max(a, s, m);
+        if (room < 4 * kBatch) evict_rows(a, s, m, lo, lo + W, clo);
         if (threadIdx.x == 0) {
-          for (int k = 0; k < W; ++k) m.enter[k] = batch + 1;
-          m.oldest = batch + 1;
-          ++m.n_inplace;
+          m.n_inplace += room < 4 * kBatch;
+          m.next_check = batch + (room < 4 * kBatch ? kResidLimitBatches : room / kBatch);
         }
         __syncthreads();
       }
@@ -927,6 +1029,10 @@ ls_status bin_prepare(const ls_points* pts, const ls_region* region, const ls_bi
   a.cell_cm = (uint32_t)(region->tile_cm / L0.cells);
   a.div_tile = make_fastdiv(a.tile_cm);
   a.div_cell = make_fastdiv(a.cell_cm);
+  if (a.cell_cm >= 2) {  // then tile_cm >= 2 too; every numerator is below ext < 2^31
+    a.d31_tile = make_fastdiv31(a.tile_cm);
+    a.d31_cell = make_fastdiv31(a.cell_cm);
+  }
   a.tiles_x = region->tiles_x;
   a.cells = L0.cells;
   a.n_rows = (int32_t)n_rows;
@@ -967,6 +1073,11 @@ ls_status bin_prepare(const ls_points* pts, const ls_region* region, const ls_bi
   if (a.rstride < (a.cells / a.f) * a.gs || a.fh < 1 || a.fh > a.f) return LS_ERR_UNSUPPORTED;
   a.W = W;
   *smem = need(W);
+  // 128-bit row stores: contiguous rows of whole 4-cell groups, every fine output array
+  // and the shared arrays (WC words each, after the 64-bit coarse sums) 16-byte aligned
+  a.vec_out = a.gs == a.f && a.cells % 4 == 0 && a.rstride % 4 == 0 && (W * a.rstride) % 4 == 0 &&
+              (((uintptr_t)a.count | (uintptr_t)a.zsum | (uintptr_t)a.zmin | (uintptr_t)a.zmax |
+                (uintptr_t)a.rsum | (uintptr_t)a.gsum | (uintptr_t)a.bsum) % 16 == 0);
   // vector loads need 16-byte aligned int32 arrays and 8-byte aligned uint16 arrays
   a.narrow = region->x0_cm >= INT32_MIN && region->x0_cm <= INT32_MAX && region->y0_cm >= INT32_MIN &&
              region->y0_cm <= INT32_MAX;
@@ -995,21 +1106,34 @@ ls_status bin_launch(BinArgs a, size_t smem, int64_t n_coarse, cudaStream_t stre
   LS_CUDA_TRY(cudaGetDevice(&dev));
   const bool ok = device_once(once, dev, [] {
     const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    return cudaFuncSetAttribute(k_bin_main<1>, attr, kBinSmemAttr) == cudaSuccess &&
-           cudaFuncSetAttribute(k_bin_main<2>, attr, kBinSmemAttr) == cudaSuccess &&
-           cudaFuncSetAttribute(k_bin_main<3>, attr, kBinSmemAttr) == cudaSuccess &&
-           cudaFuncSetAttribute(k_bin_main<4>, attr, kBinSmemAttr) == cudaSuccess;
+    return cudaFuncSetAttribute(k_bin_main<1, true>, attr, kBinSmemAttr) == cudaSuccess &&
+           cudaFuncSetAttribute(k_bin_main<2, true>, attr, kBinSmemAttr) == cudaSuccess &&
+           cudaFuncSetAttribute(k_bin_main<3, true>, attr, kBinSmemAttr) == cudaSuccess &&
+           cudaFuncSetAttribute(k_bin_main<4, true>, attr, kBinSmemAttr) == cudaSuccess &&
+           cudaFuncSetAttribute(k_bin_main<1, false>, attr, kBinSmemAttr) == cudaSuccess &&
+           cudaFuncSetAttribute(k_bin_main<2, false>, attr, kBinSmemAttr) == cudaSuccess &&
+           cudaFuncSetAttribute(k_bin_main<3, false>, attr, kBinSmemAttr) == cudaSuccess &&
+           cudaFuncSetAttribute(k_bin_main<4, false>, attr, kBinSmemAttr) == cudaSuccess;
   });
   if (!ok) return LS_ERR_CUDA;
   const int64_t work = a.n_rows > n_coarse ? a.n_rows : n_coarse;
   k_bin_prologue<<<grid_cap((work + 255) / 256, kSmCount * 8), 256, 0, stream>>>(a, n_coarse);
   if (a.n_items > 0) {
     const int grid = grid_cap(a.n_items, kSmCount);
-    switch (a.pf_dist) {
-      case 1: k_bin_main<1><<<grid, kBinThreads, smem, stream>>>(a); break;
-      case 3: k_bin_main<3><<<grid, kBinThreads, smem, stream>>>(a); break;
-      case 4: k_bin_main<4><<<grid, kBinThreads, smem, stream>>>(a); break;
-      default: k_bin_main<2><<<grid, kBinThreads, smem, stream>>>(a); break;
+    const bool d31 = a.cell_cm >= 2;
+    switch (a.pf_dist * 2 + (d31 ? 1 : 0)) {
+      case 2: k_bin_main<1, false><<<grid, kBinThreads, smem, stream>>>(a); break;
+      case 3: k_bin_main<1, true><<<grid, kBinThreads, smem, stream>>>(a); break;
+      case 6: k_bin_main<3, false><<<grid, kBinThreads, smem, stream>>>(a); break;
+      case 7: k_bin_main<3, true><<<grid, kBinThreads, smem, stream>>>(a); break;
+      case 8: k_bin_main<4, false><<<grid, kBinThreads, smem, stream>>>(a); break;
+      case 9: k_bin_main<4, true><<<grid, kBinThreads, smem, stream>>>(a); break;
+      default:
+        if (d31)
+          k_bin_main<2, true><<<grid, kBinThreads, smem, stream>>>(a);
+        else
+          k_bin_main<2, false><<<grid, kBinThreads, smem, stream>>>(a);
+        break;
     }
   }
   if (!a.accumulate) k_bin_finalize<<<grid_cap(a.n_rows, kSmCount * 16), 128, 0, stream>>>(a);

@@ -55,6 +55,26 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
   return (t + ((n - t) >> f.s1)) >> f.s2;
 }
 
+// Numerators below 2^31 need no correction step: with s = ceil(log2 d) - 1 and
+// m = ceil(2^(32+s) / d) (below 2^32 because 2^s < d), the error e = m d - 2^(32+s)
+// is below d <= 2^(s+1), so n e < 2^(32+s) for every n < 2^31 and
+// q = mulhi(m, n) >> s = floor(n / d) (the round-up method of the same paper, Sec. 4).
+// d >= 2.
+struct FastDiv31 {
+  uint32_t m, s;
+};
+
+inline FastDiv31 make_fastdiv31(uint32_t d) {
+  FastDiv31 f;
+  uint32_t l = 0;
+  while ((uint64_t(1) << l) < d) ++l;
+  f.s = l - 1;
+  f.m = (uint32_t)(((uint64_t(1) << (32 + f.s)) + d - 1) / d);
+  return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv31(uint32_t n, const FastDiv31& f) { return __umulhi(f.m, n) >> f.s; }
+
 // ---------------------------------------------------------------------------------
 // Library scratch workspace (per device, grown on demand).
 // ---------------------------------------------------------------------------------
