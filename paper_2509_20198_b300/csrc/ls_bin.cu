@@ -749,7 +749,7 @@ __device__ __forceinline__ void accumulate(Smem& s, Meta& m, const BinArgs& a, i
   red_add_u(p + 2u * s.fs, g);
   red_add_u(p + 3u * s.fs, b);
   red_add_u(p + 4u * s.fs, (unsigned)z & 0xffffu);
-  red_add_s(p + 5u * s.fs, z >> 16);
+  if (z >> 16) red_add_s(p + 5u * s.fs, z >> 16);  // 0 <= z < 65536 cm: nothing to add
   red_min_s(p + 6u * s.fs, z);
   red_max_s(p + 7u * s.fs, z);
   m.touched[slot] = 1;
