@@ -21,6 +21,8 @@
 // Operands are K-major without swizzle: an A stage holds up to 8 chunks of
 // 128 rows x 16 bytes (LBO 2048 B between chunks, SBO 128 B between 8-row groups);
 // the packed weights of a stage are C_out rows x 8 chunks (LBO C_out*16 B, SBO 128 B).
+// Images 64 or 128 pixels wide (H a multiple of 64) take the halo form further down
+// (k_conv3x3_halo): one box per tile and channel block serves all nine taps.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -89,6 +91,39 @@ struct ConvArgs {
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// 16 accumulator columns of one output pixel: + bias, ReLU or the ReLU-derivative mask
+// (a bf16 mask value > 0 keeps the gradient), BF16 store of 32 bytes
+__device__ __forceinline__ void epilogue16(float (&v)[16], const float* bias, int relu, const uint16_t* mp,
+                                           uint16_t* yp) {
+  if (bias) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] += __ldg(bias + i);
+  }
+  if (relu) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
+  }
+  if (mp) {
+    const uint4 m0 = *reinterpret_cast<const uint4*>(mp);
+    const uint4 m1 = *reinterpret_cast<const uint4*>(mp + 8);
+    const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      // bf16 > 0: sign bit clear and not +0
+      const uint32_t lo = mw[i] & 0xffffu, hi = mw[i] >> 16;
+      if (!(lo != 0u && !(lo & 0x8000u))) v[2 * i] = 0.f;
+      if (!(hi != 0u && !(hi & 0x8000u))) v[2 * i + 1] = 0.f;
+    }
+  }
+  uint4 o0, o1;
+  o0.x = pack_bf16x2(v[0], v[1]); o0.y = pack_bf16x2(v[2], v[3]);
+  o0.z = pack_bf16x2(v[4], v[5]); o0.w = pack_bf16x2(v[6], v[7]);
+  o1.x = pack_bf16x2(v[8], v[9]); o1.y = pack_bf16x2(v[10], v[11]);
+  o1.z = pack_bf16x2(v[12], v[13]); o1.w = pack_bf16x2(v[14], v[15]);
+  *reinterpret_cast<uint4*>(yp) = o0;
+  *reinterpret_cast<uint4*>(yp + 8) = o1;
 }
 
 __global__ void __launch_bounds__(kConvThreads, 1)
@@ -221,33 +256,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         uint16_t* yp = a.y + ((int64_t)g * a.ygstride + (int64_t)pix * a.ygroup + (c0 - g * a.ygroup));
         float v[16];
         tc::tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * a.acc_cols + (uint32_t)c0, v);
-        if (a.bias) {
-#pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] += __ldg(a.bias + c0 + i);
-        }
-        if (a.relu) {
-#pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
-        }
-        if (mp) {
-          const uint4 m0 = *reinterpret_cast<const uint4*>(mp + c0);
-          const uint4 m1 = *reinterpret_cast<const uint4*>(mp + c0 + 8);
-          const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            // bf16 > 0: sign bit clear and not +0
-            const uint32_t lo = mw[i] & 0xffffu, hi = mw[i] >> 16;
-            if (!(lo != 0u && !(lo & 0x8000u))) v[2 * i] = 0.f;
-            if (!(hi != 0u && !(hi & 0x8000u))) v[2 * i + 1] = 0.f;
-          }
-        }
-        uint4 o0, o1;
-        o0.x = pack_bf16x2(v[0], v[1]); o0.y = pack_bf16x2(v[2], v[3]);
-        o0.z = pack_bf16x2(v[4], v[5]); o0.w = pack_bf16x2(v[6], v[7]);
-        o1.x = pack_bf16x2(v[8], v[9]); o1.y = pack_bf16x2(v[10], v[11]);
-        o1.z = pack_bf16x2(v[12], v[13]); o1.w = pack_bf16x2(v[14], v[15]);
-        *reinterpret_cast<uint4*>(yp) = o0;
-        *reinterpret_cast<uint4*>(yp + 8) = o1;
+        epilogue16(v, a.bias ? a.bias + c0 : nullptr, a.relu, mp ? mp + c0 : nullptr, yp);
       }
       tc::fence_before();
       tc::mbar_arrive(&tempty[acc]);
@@ -261,7 +270,183 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   }
 }
 
-// Pack fp32 OHWI weights into the K-major operand layout: chunk c (8 consecutive K
+// ---------------------------------------------------------------------------------
+// Halo form for images W = 64 or 128 wide (H a multiple of 64): the output is computed
+// on a grid of P = W + 2 slots per row (two junk slots per row, discarded), so that the
+// input pixel of output slot s under tap (ky, kx) is padded-input slot s + ky*P + kx,
+// a fixed row offset.  One TMA box of the padded rows around a 128-slot tile (x from
+// -1 to W, rows y0-1 .. y0+bh-2, zero-filled outside the image) then serves all nine
+// taps of one channel block: each MMA's A operand starts a whole number of 2*cw-byte
+// rows into the box (the swizzle is a function of the absolute shared address, so any
+// row offset reads the rows that the TMA wrote).  The packed weights of the layer stay
+// in shared memory for the whole launch, and the CTA runs up to four independent
+// pipelines that share them, one tcgen05.mma issuer each (one issuing thread is
+// accepted about one M=128 MMA per 150 cycles whatever N; the SM takes about four):
+//  warp 6g      TMA producer of pipeline g (one box per tile and channel block);
+//  warp 6g + 1  MMA issuer: 9 taps x cw/16 MMAs per box (8-channel inputs: two taps
+//               per K=16 MMA, the second tap's rows LBO bytes after the first's);
+//  warps 6g+2.. epilogue of pipeline g (one slot per thread; junk slots not stored).
+constexpr int kHaloMaxPipes = 4;
+constexpr int kHaloRing = 2;
+constexpr int kHaloThreadsPerPipe = 192;
+constexpr size_t kHaloSmemBudget = 224 * 1024;
+
+struct HaloArgs {
+  const uint16_t* __restrict__ wpk;
+  const float* __restrict__ bias;
+  const uint16_t* __restrict__ mask;
+  uint16_t* __restrict__ y;
+  int32_t cin, cout, cpt, cw, cblocks, relu, ygroup;
+  int64_t ygstride;
+  int32_t w, h, p, bh;          // image width, height, slots per row (w + 2), box rows
+  int32_t tiles_per_img, n_tiles, npipes;
+  uint32_t wbytes, box_bytes, box_stride, acc_cols, tmem_cols, idesc, swz, rowb;
+};
+
+__global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
+    k_conv3x3_halo(const __grid_constant__ CUtensorMap xmap, const HaloArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t full[kHaloMaxPipes][kHaloRing], empty[kHaloMaxPipes][kHaloRing];
+  __shared__ __align__(8) uint64_t tfull[kHaloMaxPipes][2], tempty[kHaloMaxPipes][2], wbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = warp / 6, role = warp - g * 6;  // pipeline and role within it
+  uint8_t* wsm = smem;                          // packed weights (a.wbytes)
+  uint8_t* boxes = smem + ((a.wbytes + 1023u) & ~1023u);  // 1024-aligned: the swizzle atoms
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < a.npipes; ++q) {
+      for (int i = 0; i < kHaloRing; ++i) {
+        tc::mbar_init(&full[q][i], 1);
+        tc::mbar_init(&empty[q][i], 1);
+      }
+      for (int i = 0; i < 2; ++i) {
+        tc::mbar_init(&tfull[q][i], 1);
+        tc::mbar_init(&tempty[q][i], 128);
+      }
+    }
+    tc::mbar_init(&wbar, 1);
+    abort_flag = 0;
+    tc::mbar_fence_init();
+    tc::prefetch_tmap(&xmap);
+  }
+  if (warp == 1) tc::tmem_alloc(&tmem_base, a.tmem_cols);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t taddr = tmem_base;
+  if (threadIdx.x == 0) {  // the layer's weights, once
+    tc::mbar_arrive_expect_tx(&wbar, a.wbytes);
+    tc::bulk_load(wsm, a.wpk, a.wbytes, &wbar);
+  }
+  const int stride = gridDim.x * a.npipes;  // tiles are dealt out pipeline by pipeline
+  const int first = blockIdx.x * a.npipes + g;
+  uint8_t* ring = boxes + (size_t)g * kHaloRing * a.box_stride;
+
+  if (role == 0 && lane == 0) {
+    // ---------------- TMA producer of pipeline g
+    int slot = 0;
+    uint32_t ph = 0;
+    for (int t = first; t < a.n_tiles && !abort_flag; t += stride) {
+      const int n = t / a.tiles_per_img;
+      const int y0 = (t - n * a.tiles_per_img) * 128 / a.p;  // first slot row of the tile
+      for (int b = 0; b < a.cblocks; ++b) {
+        if (!tc::mbar_wait(&empty[g][slot], ph ^ 1u)) { abort_flag = 1; break; }
+        tc::mbar_arrive_expect_tx(&full[g][slot], a.box_bytes);
+        // padded rows y0 .. y0 + bh - 1 = image rows y0 - 1 .. y0 + bh - 2, columns -1 .. w
+        tc::tma_load_4d(ring + (size_t)slot * a.box_stride, &xmap, b * a.cw, -1, y0 - 1, n, &full[g][slot]);
+        if (++slot == kHaloRing) { slot = 0; ph ^= 1u; }
+      }
+    }
+  } else if (role == 1 && lane == 0) {
+    // ---------------- MMA issuer of pipeline g
+    if (!tc::mbar_wait(&wbar, 0)) abort_flag = 1;
+    tc::fence_after();
+    const uint32_t wb = tc::saddr(wsm), rb = tc::saddr(ring);
+    const uint32_t chunkb = (uint32_t)a.cout * 16u;  // one packed chunk: C_out rows x 8 K
+    int slot = 0, ai = 0;
+    uint32_t ph = 0;
+    for (int t = first; t < a.n_tiles && !abort_flag; t += stride, ++ai) {
+      const int n = t / a.tiles_per_img;
+      const int s0 = (t - n * a.tiles_per_img) * 128;
+      const int o = s0 - (s0 / a.p) * a.p;  // the tile's first slot within the box's first row
+      const int acc = ai & 1;
+      const uint32_t aph = (uint32_t)(ai >> 1) & 1u;
+      if (!tc::mbar_wait(&tempty[g][acc], aph ^ 1u)) { abort_flag = 1; break; }
+      tc::fence_after();
+      const uint32_t d = taddr + (uint32_t)(g * 2 + acc) * a.acc_cols;
+      uint32_t accf = 0u;
+      for (int b = 0; b < a.cblocks; ++b) {
+        if (!tc::mbar_wait(&full[g][slot], ph)) { abort_flag = 1; break; }
+        tc::fence_after();
+        const uint32_t box = rb + (uint32_t)slot * a.box_stride;
+        if (a.cw == 8) {
+          // one 8-channel block (C_in = 8): chunk c is tap c, so a K=16 MMA takes taps
+          // 2i and 2i + 1 (the second 8 K-elements LBO bytes after the first); tap 9 is
+          // the zero chunk of the pack, read against tap 8's rows
+          for (int i = 0; i < 5; ++i) {
+            const int t0 = 2 * i, t1 = t0 + 1 < 9 ? t0 + 1 : t0;
+            const int r0 = o + (t0 / 3) * a.p + (t0 % 3), r1 = o + (t1 / 3) * a.p + (t1 % 3);
+            const uint64_t ad = tc::sdesc(box + (uint32_t)r0 * 16u, (uint32_t)(r1 - r0) * 16u, 128);
+            const uint64_t bd = tc::sdesc(wb + (uint32_t)t0 * chunkb, chunkb, 128);
+            tc::mma_bf16(d, ad, bd, a.idesc, accf);
+            accf = 1u;
+          }
+        } else {
+          for (int tap = 0; tap < 9; ++tap) {
+            const uint32_t arow = box + (uint32_t)(o + (tap / 3) * a.p + (tap % 3)) * a.rowb;
+            const uint32_t wrow = wb + (uint32_t)(tap * a.cpt + b * (a.cw / 8)) * chunkb;
+            for (int j = 0; j < a.cw / 16; ++j) {
+              const uint64_t ad = tc::sdesc_sw(arow + (uint32_t)j * 32u, 8u * a.rowb, a.swz);
+              const uint64_t bd = tc::sdesc(wrow + (uint32_t)(2 * j) * chunkb, chunkb, 128);
+              tc::mma_bf16(d, ad, bd, a.idesc, accf);
+              accf = 1u;
+            }
+          }
+        }
+        tc::mma_commit(&empty[g][slot]);
+        if (++slot == kHaloRing) { slot = 0; ph ^= 1u; }
+      }
+      tc::mma_commit(&tfull[g][acc]);
+    }
+  } else if (role >= 2) {
+    // ---------------- epilogue of pipeline g: slot 32q + lane of the tile per thread
+    const int q = warp & 3;
+    const int m = q * 32 + lane;
+    int ai = 0;
+    for (int t = first; t < a.n_tiles && !abort_flag; t += stride, ++ai) {
+      const int acc = ai & 1;
+      const uint32_t aph = (uint32_t)(ai >> 1) & 1u;
+      if (!tc::mbar_wait(&tfull[g][acc], aph)) { abort_flag = 1; break; }
+      tc::fence_after();
+      const int n = t / a.tiles_per_img;
+      const int s = (t - n * a.tiles_per_img) * 128 + m;
+      const int yy = s / a.p, xx = s - yy * a.p;
+      const bool real = xx < a.w;  // slots w and w + 1 of a row are not pixels
+      const size_t pix = ((size_t)n * a.h + yy) * a.w + (real ? xx : 0);
+      const uint16_t* mp = a.mask ? a.mask + pix * a.cout : nullptr;
+      for (int c0 = 0; c0 < a.cout; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * 2 + acc) * a.acc_cols + (uint32_t)c0, v);
+        if (real) {
+          const int gi = c0 / a.ygroup;
+          uint16_t* yp = a.y + ((int64_t)gi * a.ygstride + (int64_t)pix * a.ygroup + (c0 - gi * a.ygroup));
+          epilogue16(v, a.bias ? a.bias + c0 : nullptr, a.relu, mp ? mp + c0 : nullptr, yp);
+        }
+      }
+      tc::fence_before();
+      tc::mbar_arrive(&tempty[g][acc]);
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after();
+    tc::tmem_dealloc(taddr, a.tmem_cols);
+  }
+}
+
+
 // elements of one tap) is a block of C_out rows x 16 bytes, 8-row groups of 128 bytes.
 __global__ void k_pack_weights(const float* __restrict__ w, int cin, int cout, int tflip, int kc,
                                uint16_t* __restrict__ out) {
@@ -295,6 +480,62 @@ int chunk_count(int cin) {
 
 }  // namespace
 
+// The halo form (k_conv3x3_halo) when the shape allows it: W = 64 or 128 and H a
+// multiple of 64 (so that every 128-slot tile lies in one image), 8-channel inputs
+// only as a single block, and the layer's packed weights plus two pipelines' box rings
+// within the shared memory.  LS_ERR_UNSUPPORTED: use the per-tap form.
+ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const float* bias, const uint16_t* mask,
+                              int relu, int n, int h, int w, int cin, int cout, uint16_t* y, int ygroup,
+                              int64_t ygstride, cudaStream_t stream) {
+  if (!((w == 64 || w == 128) && h % 64 == 0)) return LS_ERR_UNSUPPORTED;
+  HaloArgs a = {};
+  a.cw = cin % 64 == 0 ? 64 : cin % 32 == 0 ? 32 : cin % 16 == 0 ? 16 : 8;
+  if (a.cw == 8 && cin != 8) return LS_ERR_UNSUPPORTED;
+  a.cin = cin; a.cout = cout; a.cpt = cin / 8; a.cblocks = cin / a.cw;
+  a.relu = relu; a.ygroup = ygroup; a.ygstride = ygstride;
+  a.wpk = wpk; a.bias = bias; a.mask = mask; a.y = y;
+  a.w = w; a.h = h; a.p = w + 2;
+  // rows of the box: the tile starts at most p - 1 slots into its first row and needs
+  // 128 + 2p + 2 slots from there
+  a.bh = ((a.p - 1) + 129 + 2 * a.p) / a.p + 1;
+  a.tiles_per_img = h * a.p / 128;
+  const int64_t nt = (int64_t)n * a.tiles_per_img;
+  if (nt > INT32_MAX) return LS_ERR_UNSUPPORTED;
+  a.n_tiles = (int32_t)nt;
+  a.rowb = (uint32_t)(2 * a.cw);
+  a.swz = a.cw == 64 ? 2u : a.cw == 32 ? 4u : a.cw == 16 ? 6u : 0u;
+  a.box_bytes = (uint32_t)a.bh * (uint32_t)a.p * a.rowb;
+  a.box_stride = (a.box_bytes + 1023u) & ~1023u;
+  a.wbytes = (uint32_t)chunk_count(cin) * (uint32_t)cout * 16u;
+  a.acc_cols = 32;
+  while ((int)a.acc_cols < cout) a.acc_cols <<= 1;
+  int np = kHaloMaxPipes;
+  while (np > 1 && (uint32_t)np * 2u * a.acc_cols > 512u) np >>= 1;
+  const size_t wsz = ((size_t)a.wbytes + 1023) & ~(size_t)1023;
+  while (np > 1 && wsz + (size_t)np * kHaloRing * a.box_stride > kHaloSmemBudget) np >>= 1;
+  if (np < 2 || wsz + (size_t)np * kHaloRing * a.box_stride > kHaloSmemBudget) return LS_ERR_UNSUPPORTED;
+  a.npipes = np;
+  a.tmem_cols = (uint32_t)np * 2u * a.acc_cols;
+  a.idesc = tc::idesc_bf16(128, cout);
+  const size_t smem = wsz + (size_t)np * kHaloRing * a.box_stride;
+  CUtensorMap map;
+  const uint64_t dims[4] = {(uint64_t)cin, (uint64_t)w, (uint64_t)h, (uint64_t)n};
+  const uint64_t strides[3] = {(uint64_t)cin * 2, (uint64_t)w * cin * 2, (uint64_t)h * w * cin * 2};
+  const uint32_t box[4] = {(uint32_t)a.cw, (uint32_t)a.p, (uint32_t)a.bh, 1};
+  if (!encode_tmap_bf16_4d(&map, x, dims, strides, box, a.cw == 8 ? 0 : a.cw * 2)) return LS_ERR_CUDA;
+  static DeviceOnce once;
+  int dev = 0;
+  LS_CUDA_TRY(cudaGetDevice(&dev));
+  if (!device_once(once, dev, [] {
+        return cudaFuncSetAttribute(k_conv3x3_halo, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kHaloSmemBudget) == cudaSuccess;
+      }))
+    return LS_ERR_CUDA;
+  const int grid = grid_cap(((int64_t)a.n_tiles + np - 1) / np, kSmCount);
+  k_conv3x3_halo<<<grid, np * kHaloThreadsPerPipe, smem, stream>>>(map, a);
+  return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
+}
+
 // Shared with the model code: validated launch of one convolution whose output
 // channels go to cout / ygroup tensors of ygroup channels each, ygstride elements apart
 // (ygroup = cout: one NHWC tensor).  Without a mask only (a mask is one NHWC tensor).
@@ -308,6 +549,11 @@ ls_status conv3x3_launch_groups(const uint16_t* x, const uint16_t* wpk, const fl
     return LS_ERR_INVALID_ARG;
   if (w > 128 || 128 % w) return LS_ERR_UNSUPPORTED;
   if (((uintptr_t)x | (uintptr_t)wpk | (uintptr_t)y | (uintptr_t)mask) % 16) return LS_ERR_INVALID_ARG;
+  {
+    const ls_status hs = conv3x3_halo_launch(x, wpk, bias, mask, relu, n, h, w, cin, cout, y, ygroup,
+                                             ygroup == cout ? 0 : ygstride, stream);
+    if (hs != LS_ERR_UNSUPPORTED) return hs;  // else the shape is not one for the halo form
+  }
   ConvArgs a = {};
   uint32_t box[4] = {8, (uint32_t)w, 1, 1};
   if (w * h >= 128) {

@@ -67,6 +67,9 @@ SHAPES = [
     (2, 16, 16, 128, 256),
     (2, 64, 64, 16, 32),    # 16-channel blocks (32-byte swizzle)
     (1, 128, 128, 48, 32),  # the skip concat: 16-channel blocks, 128-wide rows
+    (2, 64, 64, 64, 32),    # halo form, 64-channel blocks (128-byte swizzle), two pipelines
+    (2, 64, 64, 32, 64),    # halo form, four pipelines of 64 accumulator columns
+    (1, 128, 128, 8, 16),   # halo form, 8-channel input on 130-slot rows
 ]
 
 
