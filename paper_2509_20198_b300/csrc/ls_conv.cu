@@ -271,8 +271,9 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 }
 
 // ---------------------------------------------------------------------------------
-// Halo form for images W = 64 or 128 wide (H a multiple of 64): the output is computed
-// on a grid of P = W + 2 slots per row (two junk slots per row, discarded), so that the
+// Halo form for images W = 32, 64 or 128 wide: the output is computed on a grid of
+// P = W + 2 slots per row (two junk slots per row, discarded; an image's slots are
+// padded to whole 128-slot tiles, the slots beyond its last row junk too), so that the
 // input pixel of output slot s under tap (ky, kx) is padded-input slot s + ky*P + kx,
 // a fixed row offset.  One TMA box of the padded rows around a 128-slot tile (x from
 // -1 to W, rows y0-1 .. y0+bh-2, zero-filled outside the image) then serves all nine
@@ -422,8 +423,8 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
       const int n = t / a.tiles_per_img;
       const int s = (t - n * a.tiles_per_img) * 128 + m;
       const int yy = s / a.p, xx = s - yy * a.p;
-      const bool real = xx < a.w;  // slots w and w + 1 of a row are not pixels
-      const size_t pix = ((size_t)n * a.h + yy) * a.w + (real ? xx : 0);
+      const bool real = xx < a.w && yy < a.h;  // slots w, w + 1 of a row and rows >= h: junk
+      const size_t pix = ((size_t)n * a.h + (real ? yy : 0)) * a.w + (real ? xx : 0);
       const uint16_t* mp = a.mask ? a.mask + pix * a.cout : nullptr;
       for (int c0 = 0; c0 < a.cout; c0 += 16) {
         float v[16];
@@ -480,14 +481,14 @@ int chunk_count(int cin) {
 
 }  // namespace
 
-// The halo form (k_conv3x3_halo) when the shape allows it: W = 64 or 128 and H a
-// multiple of 64 (so that every 128-slot tile lies in one image), 8-channel inputs
-// only as a single block, and the layer's packed weights plus two pipelines' box rings
-// within the shared memory.  LS_ERR_UNSUPPORTED: use the per-tap form.
+// The halo form (k_conv3x3_halo) when the shape allows it: W = 32, 64 or 128 (narrower
+// rows would waste too many junk slots), 8-channel inputs only as a single block, and
+// the layer's packed weights plus two pipelines' box rings within the shared memory.
+// LS_ERR_UNSUPPORTED: use the per-tap form.
 ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const float* bias, const uint16_t* mask,
                               int relu, int n, int h, int w, int cin, int cout, uint16_t* y, int ygroup,
                               int64_t ygstride, cudaStream_t stream) {
-  if (!((w == 64 || w == 128) && h % 64 == 0)) return LS_ERR_UNSUPPORTED;
+  if (!(w == 32 || w == 64 || w == 128)) return LS_ERR_UNSUPPORTED;
   HaloArgs a = {};
   a.cw = cin % 64 == 0 ? 64 : cin % 32 == 0 ? 32 : cin % 16 == 0 ? 16 : 8;
   if (a.cw == 8 && cin != 8) return LS_ERR_UNSUPPORTED;
@@ -498,7 +499,7 @@ ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const floa
   // rows of the box: the tile starts at most p - 1 slots into its first row and needs
   // 128 + 2p + 2 slots from there
   a.bh = ((a.p - 1) + 129 + 2 * a.p) / a.p + 1;
-  a.tiles_per_img = h * a.p / 128;
+  a.tiles_per_img = (h * a.p + 127) / 128;  // whole tiles per image
   const int64_t nt = (int64_t)n * a.tiles_per_img;
   if (nt > INT32_MAX) return LS_ERR_UNSUPPORTED;
   a.n_tiles = (int32_t)nt;

@@ -70,6 +70,8 @@ SHAPES = [
     (2, 64, 64, 64, 32),    # halo form, 64-channel blocks (128-byte swizzle), two pipelines
     (2, 64, 64, 32, 64),    # halo form, four pipelines of 64 accumulator columns
     (1, 128, 128, 8, 16),   # halo form, 8-channel input on 130-slot rows
+    (3, 20, 32, 32, 32),    # halo form, 34-slot rows, images padded to whole tiles
+    (1, 37, 64, 16, 32),    # halo form, odd height: junk rows in the last tile
 ]
 
 
