@@ -288,7 +288,8 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 //               per K=16 MMA, the second tap's rows LBO bytes after the first's);
 //  warps 6g+2.. epilogue of pipeline g (one slot per thread; junk slots not stored).
 constexpr int kHaloMaxPipes = 4;
-constexpr int kHaloRing = 2;
+constexpr int kHaloRingMax = 8;  // ring slots declared per pipeline
+constexpr int kHaloRingUse = 4;  // boxes per pipeline a launch uses at most (as many as fit)
 constexpr int kHaloThreadsPerPipe = 192;
 constexpr size_t kHaloSmemBudget = 224 * 1024;
 
@@ -300,14 +301,14 @@ struct HaloArgs {
   int32_t cin, cout, cpt, cw, cblocks, relu, ygroup;
   int64_t ygstride;
   int32_t w, h, p, bh;          // image width, height, slots per row (w + 2), box rows
-  int32_t tiles_per_img, n_tiles, npipes;
+  int32_t tiles_per_img, n_tiles, npipes, ring;
   uint32_t wbytes, box_bytes, box_stride, acc_cols, tmem_cols, idesc, swz, rowb;
 };
 
 __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
     k_conv3x3_halo(const __grid_constant__ CUtensorMap xmap, const HaloArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t full[kHaloMaxPipes][kHaloRing], empty[kHaloMaxPipes][kHaloRing];
+  __shared__ __align__(8) uint64_t full[kHaloMaxPipes][kHaloRingMax], empty[kHaloMaxPipes][kHaloRingMax];
   __shared__ __align__(8) uint64_t tfull[kHaloMaxPipes][2], tempty[kHaloMaxPipes][2], wbar;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
   uint8_t* boxes = smem + ((a.wbytes + 1023u) & ~1023u);  // 1024-aligned: the swizzle atoms
   if (threadIdx.x == 0) {
     for (int q = 0; q < a.npipes; ++q) {
-      for (int i = 0; i < kHaloRing; ++i) {
+      for (int i = 0; i < a.ring; ++i) {
         tc::mbar_init(&full[q][i], 1);
         tc::mbar_init(&empty[q][i], 1);
       }
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
   }
   const int stride = gridDim.x * a.npipes;  // tiles are dealt out pipeline by pipeline
   const int first = blockIdx.x * a.npipes + g;
-  uint8_t* ring = boxes + (size_t)g * kHaloRing * a.box_stride;
+  uint8_t* ring = boxes + (size_t)g * a.ring * a.box_stride;
 
   if (role == 0 && lane == 0) {
     // ---------------- TMA producer of pipeline g
@@ -356,7 +357,7 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
         tc::mbar_arrive_expect_tx(&full[g][slot], a.box_bytes);
         // padded rows y0 .. y0 + bh - 1 = image rows y0 - 1 .. y0 + bh - 2, columns -1 .. w
         tc::tma_load_4d(ring + (size_t)slot * a.box_stride, &xmap, b * a.cw, -1, y0 - 1, n, &full[g][slot]);
-        if (++slot == kHaloRing) { slot = 0; ph ^= 1u; }
+        if (++slot == a.ring) { slot = 0; ph ^= 1u; }
       }
     }
   } else if (role == 1 && lane == 0) {
@@ -406,7 +407,7 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
           }
         }
         tc::mma_commit(&empty[g][slot]);
-        if (++slot == kHaloRing) { slot = 0; ph ^= 1u; }
+        if (++slot == a.ring) { slot = 0; ph ^= 1u; }
       }
       tc::mma_commit(&tfull[g][acc]);
     }
@@ -490,9 +491,7 @@ ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const floa
                               int64_t ygstride, cudaStream_t stream) {
   if (!(w == 32 || w == 64 || w == 128)) return LS_ERR_UNSUPPORTED;
   HaloArgs a = {};
-  a.cw = cin % 64 == 0 ? 64 : cin % 32 == 0 ? 32 : cin % 16 == 0 ? 16 : 8;
-  if (a.cw == 8 && cin != 8) return LS_ERR_UNSUPPORTED;
-  a.cin = cin; a.cout = cout; a.cpt = cin / 8; a.cblocks = cin / a.cw;
+  a.cin = cin; a.cout = cout; a.cpt = cin / 8;
   a.relu = relu; a.ygroup = ygroup; a.ygstride = ygstride;
   a.wpk = wpk; a.bias = bias; a.mask = mask; a.y = y;
   a.w = w; a.h = h; a.p = w + 2;
@@ -503,22 +502,39 @@ ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const floa
   const int64_t nt = (int64_t)n * a.tiles_per_img;
   if (nt > INT32_MAX) return LS_ERR_UNSUPPORTED;
   a.n_tiles = (int32_t)nt;
-  a.rowb = (uint32_t)(2 * a.cw);
-  a.swz = a.cw == 64 ? 2u : a.cw == 32 ? 4u : a.cw == 16 ? 6u : 0u;
-  a.box_bytes = (uint32_t)a.bh * (uint32_t)a.p * a.rowb;
-  a.box_stride = (a.box_bytes + 1023u) & ~1023u;
   a.wbytes = (uint32_t)chunk_count(cin) * (uint32_t)cout * 16u;
+  const size_t wsz = ((size_t)a.wbytes + 1023) & ~(size_t)1023;
   a.acc_cols = 32;
   while ((int)a.acc_cols < cout) a.acc_cols <<= 1;
+  // pipelines: as many as the TMEM holds (two accumulators each), up to four (more
+  // issuers gain nothing: at C_out <= 64 four already saturate the shared-memory operand
+  // reads of the MMAs); boxes of 32 channels (64-byte rows) where C_in allows, 16 or 8
+  // otherwise (measured: 64-channel boxes and narrower ones were both slower); a ring
+  // of up to four boxes per pipeline (deeper measured no faster)
   int np = kHaloMaxPipes;
   while (np > 1 && (uint32_t)np * 2u * a.acc_cols > 512u) np >>= 1;
-  const size_t wsz = ((size_t)a.wbytes + 1023) & ~(size_t)1023;
-  while (np > 1 && wsz + (size_t)np * kHaloRing * a.box_stride > kHaloSmemBudget) np >>= 1;
-  if (np < 2 || wsz + (size_t)np * kHaloRing * a.box_stride > kHaloSmemBudget) return LS_ERR_UNSUPPORTED;
+  const int cw = cin % 32 == 0 ? 32 : cin % 16 == 0 ? 16 : 8;
+  if (cw == 8 && cin != 8) return LS_ERR_UNSUPPORTED;
+  auto box_stride_of = [&](int c) {
+    return ((uint32_t)a.bh * (uint32_t)a.p * (uint32_t)(2 * c) + 1023u) & ~1023u;
+  };
+  auto ring_of = [&](int c, int pipes) {
+    const size_t per = (size_t)pipes * box_stride_of(c);
+    return wsz >= kHaloSmemBudget ? 0 : (int)std::min<size_t>(kHaloRingUse, (kHaloSmemBudget - wsz) / per);
+  };
+  while (np > 2 && ring_of(cw, np) < 2) np >>= 1;
+  if (ring_of(cw, np) < 2) return LS_ERR_UNSUPPORTED;
+  a.cw = cw;
+  a.cblocks = cin / cw;
   a.npipes = np;
+  a.ring = ring_of(cw, np);
+  a.rowb = (uint32_t)(2 * cw);
+  a.swz = cw == 64 ? 2u : cw == 32 ? 4u : cw == 16 ? 6u : 0u;
+  a.box_bytes = (uint32_t)a.bh * (uint32_t)a.p * a.rowb;
+  a.box_stride = box_stride_of(cw);
   a.tmem_cols = (uint32_t)np * 2u * a.acc_cols;
   a.idesc = tc::idesc_bf16(128, cout);
-  const size_t smem = wsz + (size_t)np * kHaloRing * a.box_stride;
+  const size_t smem = wsz + (size_t)np * a.ring * a.box_stride;
   CUtensorMap map;
   const uint64_t dims[4] = {(uint64_t)cin, (uint64_t)w, (uint64_t)h, (uint64_t)n};
   const uint64_t strides[3] = {(uint64_t)cin * 2, (uint64_t)w * cin * 2, (uint64_t)h * w * cin * 2};
