@@ -104,21 +104,31 @@ __global__ void k_maxpool_bwd(const uint16_t* __restrict__ x, const uint16_t* __
 }
 
 // ---- 2x nearest upsampling of `up` concatenated with `skip` along channels --------
+// One output row per CTA iteration; its 16-byte groups (8 channels) are spread over the
+// threads in order, so loads and stores are coalesced.  The group index e of a row
+// splits into pixel e / g and group e % g with a float reciprocal: e < w * g <= 2^15
+// and (e + 0.5) / g lies at least 0.5 / g from an integer, far beyond the float error.
 __global__ void k_upcat(const uint16_t* __restrict__ up, int cu, const uint16_t* __restrict__ skip, int cs, int n,
                         int h, int w, uint16_t* __restrict__ y) {  // h, w: output (full) size
   const int c = cu + cs, g = c / 8;
-  const int64_t total = (int64_t)n * h * w * g;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int gi = (int)(e % g);
-    const int64_t p = e / g;
-    const int xx = (int)(p % w), yy = (int)((p / w) % h);
-    const int64_t nn = p / ((int64_t)w * h);
-    uint4 v;
-    if (gi * 8 < cu)
-      v = *reinterpret_cast<const uint4*>(up + ((nn * (h / 2) + yy / 2) * (w / 2) + xx / 2) * cu + gi * 8);
-    else
-      v = *reinterpret_cast<const uint4*>(skip + p * cs + gi * 8 - cu);
-    *reinterpret_cast<uint4*>(y + p * c + gi * 8) = v;
+  const int row_groups = w * g;
+  const int rows = n * h;
+  const float inv_g = 1.f / (float)g;
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int nn = r / h, yy = r - nn * h;
+    const uint16_t* uprow = up + ((int64_t)nn * (h / 2) + yy / 2) * (w / 2) * cu;
+    const uint16_t* skrow = skip ? skip + (int64_t)r * w * cs : nullptr;
+    uint4* yrow = reinterpret_cast<uint4*>(y + (int64_t)r * w * c);
+    for (int e = threadIdx.x; e < row_groups; e += blockDim.x) {
+      const int xx = (int)(((float)e + 0.5f) * inv_g);
+      const int gi = e - xx * g;
+      uint4 v;
+      if (gi * 8 < cu)
+        v = *reinterpret_cast<const uint4*>(uprow + (xx / 2) * cu + gi * 8);
+      else
+        v = *reinterpret_cast<const uint4*>(skrow + xx * cs + gi * 8 - cu);
+      yrow[e] = v;
+    }
   }
 }
 
@@ -597,8 +607,8 @@ extern "C" ls_status ls_filler_forward(ls_model* m, const float* params, const u
     const int h = R >> (l - 1);
     const int cu = (l + 1 == L) ? m->widths[L - 1] : m->widths[l];
     const int cs = m->widths[l - 1];
-    const int64_t work = (int64_t)n * h * h * ((cu + cs) / 8);
-    k_upcat<<<grid_for(work, 256), 256, 0, s>>>(h_in, cu, m->act[slot_eb(l)], cs, n, h, h, m->act[slot_c(l)]);
+    k_upcat<<<grid_cap((int64_t)n * h, kSmCount * 16), 256, 0, s>>>(h_in, cu, m->act[slot_eb(l)], cs, n, h, h,
+                                                                     m->act[slot_c(l)]);
     if ((st = conv(li++, m->act[slot_c(l)], h, m->act[slot_da(l)])) != LS_OK) return st;
     if ((st = conv(li++, m->act[slot_da(l)], h, m->act[slot_db(l)])) != LS_OK) return st;
     h_in = m->act[slot_db(l)];
