@@ -93,6 +93,19 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
+// The values a BF16 store of v keeps (v rounded to bf16 and back), packed as stored
+__device__ __forceinline__ void round_bf16_16(float (&v)[16], uint4& o0, uint4& o1) {
+  uint32_t w[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    w[i] = pack_bf16x2(v[2 * i], v[2 * i + 1]);
+    v[2 * i] = __uint_as_float(w[i] << 16);
+    v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+  }
+  o0 = make_uint4(w[0], w[1], w[2], w[3]);
+  o1 = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
 // 16 accumulator columns of one output pixel: + bias, ReLU or the ReLU-derivative mask
 // (a bf16 mask value > 0 keeps the gradient), BF16 store of 32 bytes
 __device__ __forceinline__ void epilogue16(float (&v)[16], const float* bias, int relu, const uint16_t* mp,
@@ -302,6 +315,12 @@ struct HaloArgs {
   int64_t ygstride;
   int32_t w, h, p, bh;          // image width, height, slots per row (w + 2), box rows
   int32_t tiles_per_img, n_tiles, npipes, ring;
+  // optional 1x1 head fused into the epilogue: head_y[pixel][o] = head[head_out * cout + o]
+  // + sum_c head[o * cout + c] * out[c] over the bf16-rounded outputs (store_y: also
+  // store the BF16 output itself)
+  const float* __restrict__ head;
+  float* __restrict__ head_y;
+  int32_t head_out, store_y;
   uint32_t wbytes, box_bytes, box_stride, acc_cols, tmem_cols, idesc, swz, rowb;
 };
 
@@ -427,14 +446,46 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
       const bool real = xx < a.w && yy < a.h;  // slots w, w + 1 of a row and rows >= h: junk
       const size_t pix = ((size_t)n * a.h + (real ? yy : 0)) * a.w + (real ? xx : 0);
       const uint16_t* mp = a.mask ? a.mask + pix * a.cout : nullptr;
+      float hacc[8];
+      if (a.head) {
+#pragma unroll
+        for (int o = 0; o < 8; ++o) hacc[o] = o < a.head_out ? __ldg(a.head + a.head_out * a.cout + o) : 0.f;
+      }
       for (int c0 = 0; c0 < a.cout; c0 += 16) {
         float v[16];
         tc::tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * 2 + acc) * a.acc_cols + (uint32_t)c0, v);
         if (real) {
           const int gi = c0 / a.ygroup;
-          uint16_t* yp = a.y + ((int64_t)gi * a.ygstride + (int64_t)pix * a.ygroup + (c0 - gi * a.ygroup));
-          epilogue16(v, a.bias ? a.bias + c0 : nullptr, a.relu, mp ? mp + c0 : nullptr, yp);
+          uint16_t* yp = a.y ? a.y + ((int64_t)gi * a.ygstride + (int64_t)pix * a.ygroup + (c0 - gi * a.ygroup))
+                             : nullptr;
+          if (!a.head) {
+            epilogue16(v, a.bias ? a.bias + c0 : nullptr, a.relu, mp ? mp + c0 : nullptr, yp);
+          } else {
+            // bias and ReLU, then the head over the values the BF16 output holds, channel
+            // by channel in order (the arithmetic of the separate 1x1 head)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + (a.bias ? __ldg(a.bias + c0 + i) : 0.f), 0.f);
+            uint4 o0, o1;
+            round_bf16_16(v, o0, o1);
+            if (a.store_y) {
+              *reinterpret_cast<uint4*>(yp) = o0;
+              *reinterpret_cast<uint4*>(yp + 8) = o1;
+            }
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+              if (o >= a.head_out) break;
+              const float* hw = a.head + o * a.cout + c0;
+#pragma unroll
+              for (int i = 0; i < 16; ++i) hacc[o] = fmaf(v[i], __ldg(hw + i), hacc[o]);
+            }
+          }
         }
+      }
+      if (a.head && real) {
+        float* hy = a.head_y + pix * a.head_out;
+#pragma unroll
+        for (int o = 0; o < 8; ++o)
+          if (o < a.head_out) hy[o] = hacc[o];
       }
       tc::fence_before();
       tc::mbar_arrive(&tempty[g][acc]);
@@ -488,9 +539,11 @@ int chunk_count(int cin) {
 // LS_ERR_UNSUPPORTED: use the per-tap form.
 ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const float* bias, const uint16_t* mask,
                               int relu, int n, int h, int w, int cin, int cout, uint16_t* y, int ygroup,
-                              int64_t ygstride, cudaStream_t stream) {
+                              int64_t ygstride, cudaStream_t stream, const float* head = nullptr,
+                              float* head_y = nullptr, int head_out = 0, int store_y = 1) {
   if (!(w == 32 || w == 64 || w == 128)) return LS_ERR_UNSUPPORTED;
   HaloArgs a = {};
+  a.head = head; a.head_y = head_y; a.head_out = head_out; a.store_y = head ? store_y : 1;
   a.cin = cin; a.cout = cout; a.cpt = cin / 8;
   a.relu = relu; a.ygroup = ygroup; a.ygstride = ygstride;
   a.wpk = wpk; a.bias = bias; a.mask = mask; a.y = y;
@@ -551,6 +604,22 @@ ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const floa
   const int grid = grid_cap(((int64_t)a.n_tiles + np - 1) / np, kSmCount);
   k_conv3x3_halo<<<grid, np * kHaloThreadsPerPipe, smem, stream>>>(map, a);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
+}
+
+// Convolution + bias + ReLU with a 1x1 head (head_out <= 8 outputs, FP32) fused into
+// its epilogue, computed over the BF16-rounded outputs in channel order (the same
+// arithmetic as a separate head over the stored output); the BF16 output is stored
+// only when store_y.  LS_ERR_UNSUPPORTED when the shape has no halo form: the caller
+// runs the convolution and the head separately.
+ls_status conv3x3_head_launch(const uint16_t* x, const uint16_t* wpk, const float* bias, int n, int h, int w, int cin,
+                              int cout, uint16_t* y, const float* head, float* head_y, int head_out, int store_y,
+                              cudaStream_t stream) {
+  if (!x || !wpk || !head || !head_y || (store_y && !y) || n <= 0 || h <= 0 || w <= 0) return LS_ERR_INVALID_ARG;
+  if (head_out < 1 || head_out > 8) return LS_ERR_UNSUPPORTED;
+  if (cin < 8 || cin % 8 || cin > 256 || cout < 16 || cout > 256 || cout % 16) return LS_ERR_UNSUPPORTED;
+  if (((uintptr_t)x | (uintptr_t)wpk | (uintptr_t)y) % 16) return LS_ERR_INVALID_ARG;
+  return conv3x3_halo_launch(x, wpk, bias, nullptr, 1, n, h, w, cin, cout, store_y ? y : nullptr, cout, 0, stream,
+                             head, head_y, head_out, store_y);
 }
 
 // Shared with the model code: validated launch of one convolution whose output

@@ -220,6 +220,11 @@ extern "C" ls_status ls_learned_finish(const float* y, const float* base, const 
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 
+// the filler's forward pass (ls_unet.cu); keep_top = false fuses the head into the last
+// convolution and leaves no state for a backward pass
+ls_status filler_forward(ls_model* m, const float* params, const uint16_t* x, int32_t n, float* y, cudaStream_t s,
+                         bool keep_top);
+
 extern "C" ls_status ls_fill_learned(ls_model* model, const float* params, const ls_points* samples,
                                      const ls_region* region, const ls_fill_params* fp, const int32_t* tile_ids,
                                      int64_t n, float max_err_m, float* height, uint8_t* rgb, float* err_bound,
@@ -248,7 +253,7 @@ extern "C" ls_status ls_fill_learned(ls_model* model, const float* params, const
     ls_status st = ls_learned_inputs(samples, region, fp, tid, nb, x, base, cz, height + off, rgb + off * 3, aux,
                                      stream);
     if (st != LS_OK) return st;
-    st = ls_filler_forward(model, params, x, (int32_t)nb, y, stream);
+    st = filler_forward(model, params, x, (int32_t)nb, y, reinterpret_cast<cudaStream_t>(stream), false);
     if (st != LS_OK) return st;
     st = ls_learned_finish(y, base, cz, nb, fp->res, region, max_err_m, height + off, rgb + off * 3, height + off,
                            rgb + off * 3, err_bound ? err_bound + o0 : nullptr,

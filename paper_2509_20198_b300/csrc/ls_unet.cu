@@ -23,6 +23,9 @@ ls_status conv3x3_launch(const uint16_t* x, const uint16_t* wpk, const float* bi
                          int n, int h, int w, int cin, int cout, uint16_t* y, cudaStream_t stream);
 ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int w, int cin, int cout, float* dwt,
                        float* db, cudaStream_t stream);
+ls_status conv3x3_head_launch(const uint16_t* x, const uint16_t* wpk, const float* bias, int n, int h, int w, int cin,
+                              int cout, uint16_t* y, const float* head, float* head_y, int head_out, int store_y,
+                              cudaStream_t stream);
 
 namespace {
 
@@ -579,10 +582,12 @@ extern "C" ls_status ls_model_load(ls_model* m, const float* params, ls_stream_t
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 
-extern "C" ls_status ls_filler_forward(ls_model* m, const float* params, const uint16_t* x, int32_t n, float* y,
-                                       ls_stream_t stream) {
+// Forward pass.  keep_top = false (inference): the 1x1 head is fused into the last
+// convolution where the shape has a halo form and that convolution's output is not
+// stored (no backward can follow: last_n is cleared).
+ls_status filler_forward(ls_model* m, const float* params, const uint16_t* x, int32_t n, float* y, cudaStream_t s,
+                         bool keep_top) {
   if (!m || !params || !x || !y || n <= 0 || n > m->max_batch) return LS_ERR_INVALID_ARG;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int L = m->levels, R = m->res;
   auto conv = [&](int li, const uint16_t* in, int h, uint16_t* out) {
     const LayerDesc& d = m->layers[li];
@@ -610,6 +615,19 @@ extern "C" ls_status ls_filler_forward(ls_model* m, const float* params, const u
     k_upcat<<<grid_cap((int64_t)n * h, kSmCount * 16), 256, 0, s>>>(h_in, cu, m->act[slot_eb(l)], cs, n, h, h,
                                                                      m->act[slot_c(l)]);
     if ((st = conv(li++, m->act[slot_c(l)], h, m->act[slot_da(l)])) != LS_OK) return st;
+    if (l == 1 && L > 1) {
+      // the last convolution with the head in its epilogue
+      const LayerDesc& d = m->layers[li];
+      const LayerDesc& hd = m->layers[li + 1];
+      st = conv3x3_head_launch(m->act[slot_da(l)], d.wpk, params + d.b_off, n, h, h, d.cin_pad, d.cout,
+                               m->act[slot_db(l)], params + hd.w_off, y, kOut, keep_top ? 1 : 0, s);
+      if (st == LS_OK) {
+        m->x = keep_top ? x : nullptr;
+        m->last_n = keep_top ? n : 0;
+        return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
+      }
+      if (st != LS_ERR_UNSUPPORTED) return st;
+    }
     if ((st = conv(li++, m->act[slot_da(l)], h, m->act[slot_db(l)])) != LS_OK) return st;
     h_in = m->act[slot_db(l)];
   }
@@ -619,6 +637,11 @@ extern "C" ls_status ls_filler_forward(ls_model* m, const float* params, const u
   m->x = x;
   m->last_n = n;
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
+}
+
+extern "C" ls_status ls_filler_forward(ls_model* m, const float* params, const uint16_t* x, int32_t n, float* y,
+                                       ls_stream_t stream) {
+  return filler_forward(m, params, x, n, y, reinterpret_cast<cudaStream_t>(stream), true);
 }
 
 extern "C" ls_status ls_filler_backward(ls_model* m, const float* params, const float* dy, int32_t n, float* grads,
