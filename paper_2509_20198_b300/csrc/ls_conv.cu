@@ -86,6 +86,9 @@ struct ConvArgs {
   // 128 / 64 / 32 bytes, 128B / 64B / 32B swizzle; cw = 8: 8 unswizzled chunks per stage)
   int32_t cw, cblocks, blocks_per_stage, n_blocks;
   uint32_t blk_bytes, sbo_a, swz;
+  // input channels [0, c_split) come from the first tensor map, the rest from the second
+  // (an upsampled tensor and its skip connection read without a concatenated copy)
+  int32_t c_split;
 };
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
@@ -140,7 +143,8 @@ __device__ __forceinline__ void epilogue16(float (&v)[16], const float* bias, in
 }
 
 __global__ void __launch_bounds__(kConvThreads, 1)
-    k_conv3x3(const __grid_constant__ CUtensorMap xmap, const ConvArgs a) {
+    k_conv3x3(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap xmap2,
+              const ConvArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t full[kConvStages], empty[kConvStages], tfull[2], tempty[2];
   __shared__ uint32_t tmem_base;
@@ -175,6 +179,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     abort_flag = 0;
     tc::mbar_fence_init();
     tc::prefetch_tmap(&xmap);
+    if (a.c_split < a.cin) tc::prefetch_tmap(&xmap2);
   }
   if (warp == 1) tc::tmem_alloc(&tmem_base, a.tmem_cols);
   tc::fence_before();
@@ -208,7 +213,10 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         tc::mbar_arrive_expect_tx(&full[slot], (uint32_t)nl * load_bytes + (uint32_t)(nc * a.cout * 16));
         for (int k = 0; k < nl; ++k, ++li) {
           const uint32_t e = ktab[li];
-          tc::tma_load_4d(A + k * load_bytes, &xmap, (int)(e & 0xffffu), (int)((e >> 16) & 15u) - 1,
+          const int ci = (int)(e & 0xffffu);
+          const bool second = ci >= a.c_split;
+          tc::tma_load_4d(A + k * load_bytes, second ? &xmap2 : &xmap, second ? ci - a.c_split : ci,
+                          (int)((e >> 16) & 15u) - 1,
                           y0 + (int)(e >> 20) - 1, n0, &full[slot]);
         }
         tc::bulk_load(B, a.wpk + (size_t)c0 * a.cout * 8, (uint32_t)(nc * a.cout * 16), &full[slot]);
@@ -322,10 +330,12 @@ struct HaloArgs {
   float* __restrict__ head_y;
   int32_t head_out, store_y;
   uint32_t wbytes, box_bytes, box_stride, acc_cols, tmem_cols, idesc, swz, rowb;
+  int32_t c_split;  // input channels [0, c_split) from the first map, the rest from the second
 };
 
 __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
-    k_conv3x3_halo(const __grid_constant__ CUtensorMap xmap, const HaloArgs a) {
+    k_conv3x3_halo(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap xmap2,
+                   const HaloArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t full[kHaloMaxPipes][kHaloRingMax], empty[kHaloMaxPipes][kHaloRingMax];
   __shared__ __align__(8) uint64_t tfull[kHaloMaxPipes][2], tempty[kHaloMaxPipes][2], wbar;
@@ -350,6 +360,7 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
     abort_flag = 0;
     tc::mbar_fence_init();
     tc::prefetch_tmap(&xmap);
+    if (a.c_split < a.cin) tc::prefetch_tmap(&xmap2);
   }
   if (warp == 1) tc::tmem_alloc(&tmem_base, a.tmem_cols);
   tc::fence_before();
@@ -375,7 +386,10 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
         if (!tc::mbar_wait(&empty[g][slot], ph ^ 1u)) { abort_flag = 1; break; }
         tc::mbar_arrive_expect_tx(&full[g][slot], a.box_bytes);
         // padded rows y0 .. y0 + bh - 1 = image rows y0 - 1 .. y0 + bh - 2, columns -1 .. w
-        tc::tma_load_4d(ring + (size_t)slot * a.box_stride, &xmap, b * a.cw, -1, y0 - 1, n, &full[g][slot]);
+        const int c0 = b * a.cw;
+        const bool second = c0 >= a.c_split;
+        tc::tma_load_4d(ring + (size_t)slot * a.box_stride, second ? &xmap2 : &xmap, second ? c0 - a.c_split : c0,
+                        -1, y0 - 1, n, &full[g][slot]);
         if (++slot == a.ring) { slot = 0; ph ^= 1u; }
       }
     }
@@ -533,6 +547,27 @@ int chunk_count(int cin) {
 
 }  // namespace
 
+// The tensor maps of the input: channels [0, cs) of x (cs channels per pixel) and, when
+// x2 is given, channels [cs, cin) from x2 (cin - cs per pixel); without x2 the second
+// map repeats the first.  Boxes of cw channels x bx x by x 1.
+bool encode_input_maps(CUtensorMap* m1, CUtensorMap* m2, const uint16_t* x, const uint16_t* x2, int cs, int cin,
+                       int n, int h, int w, int cw, uint32_t bx, uint32_t by, uint32_t bn) {
+  const uint32_t box[4] = {(uint32_t)cw, bx, by, bn};
+  const int sw = cw == 8 ? 0 : cw * 2;
+  const int c1 = x2 ? cs : cin;
+  const uint64_t d1[4] = {(uint64_t)c1, (uint64_t)w, (uint64_t)h, (uint64_t)n};
+  const uint64_t s1[3] = {(uint64_t)c1 * 2, (uint64_t)w * c1 * 2, (uint64_t)h * w * c1 * 2};
+  if (!encode_tmap_bf16_4d(m1, x, d1, s1, box, sw)) return false;
+  if (!x2) {
+    *m2 = *m1;
+    return true;
+  }
+  const int c2 = cin - cs;
+  const uint64_t d2[4] = {(uint64_t)c2, (uint64_t)w, (uint64_t)h, (uint64_t)n};
+  const uint64_t s2[3] = {(uint64_t)c2 * 2, (uint64_t)w * c2 * 2, (uint64_t)h * w * c2 * 2};
+  return encode_tmap_bf16_4d(m2, x2, d2, s2, box, sw);
+}
+
 // The halo form (k_conv3x3_halo) when the shape allows it: W = 32, 64 or 128 (narrower
 // rows would waste too many junk slots), 8-channel inputs only as a single block, and
 // the layer's packed weights plus two pipelines' box rings within the shared memory.
@@ -540,9 +575,11 @@ int chunk_count(int cin) {
 ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const float* bias, const uint16_t* mask,
                               int relu, int n, int h, int w, int cin, int cout, uint16_t* y, int ygroup,
                               int64_t ygstride, cudaStream_t stream, const float* head = nullptr,
-                              float* head_y = nullptr, int head_out = 0, int store_y = 1) {
+                              float* head_y = nullptr, int head_out = 0, int store_y = 1,
+                              const uint16_t* x2 = nullptr, int c_split = 0) {
   if (!(w == 32 || w == 64 || w == 128)) return LS_ERR_UNSUPPORTED;
   HaloArgs a = {};
+  a.c_split = x2 ? c_split : cin;
   a.head = head; a.head_y = head_y; a.head_out = head_out; a.store_y = head ? store_y : 1;
   a.cin = cin; a.cout = cout; a.cpt = cin / 8;
   a.relu = relu; a.ygroup = ygroup; a.ygstride = ygstride;
@@ -566,8 +603,8 @@ ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const floa
   // of up to four boxes per pipeline (deeper measured no faster)
   int np = kHaloMaxPipes;
   while (np > 1 && (uint32_t)np * 2u * a.acc_cols > 512u) np >>= 1;
-  const int cw = cin % 32 == 0 ? 32 : cin % 16 == 0 ? 16 : 8;
-  if (cw == 8 && cin != 8) return LS_ERR_UNSUPPORTED;
+  const int cw = (cin % 32 == 0 && a.c_split % 32 == 0) ? 32 : (cin % 16 == 0 && a.c_split % 16 == 0) ? 16 : 8;
+  if (cw == 8 && (cin != 8 || x2)) return LS_ERR_UNSUPPORTED;
   auto box_stride_of = [&](int c) {
     return ((uint32_t)a.bh * (uint32_t)a.p * (uint32_t)(2 * c) + 1023u) & ~1023u;
   };
@@ -588,11 +625,9 @@ ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const floa
   a.tmem_cols = (uint32_t)np * 2u * a.acc_cols;
   a.idesc = tc::idesc_bf16(128, cout);
   const size_t smem = wsz + (size_t)np * a.ring * a.box_stride;
-  CUtensorMap map;
-  const uint64_t dims[4] = {(uint64_t)cin, (uint64_t)w, (uint64_t)h, (uint64_t)n};
-  const uint64_t strides[3] = {(uint64_t)cin * 2, (uint64_t)w * cin * 2, (uint64_t)h * w * cin * 2};
-  const uint32_t box[4] = {(uint32_t)a.cw, (uint32_t)a.p, (uint32_t)a.bh, 1};
-  if (!encode_tmap_bf16_4d(&map, x, dims, strides, box, a.cw == 8 ? 0 : a.cw * 2)) return LS_ERR_CUDA;
+  CUtensorMap map, map2;
+  if (!encode_input_maps(&map, &map2, x, x2, a.c_split, cin, n, h, w, a.cw, (uint32_t)a.p, (uint32_t)a.bh, 1))
+    return LS_ERR_CUDA;
   static DeviceOnce once;
   int dev = 0;
   LS_CUDA_TRY(cudaGetDevice(&dev));
@@ -602,7 +637,7 @@ ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const floa
       }))
     return LS_ERR_CUDA;
   const int grid = grid_cap(((int64_t)a.n_tiles + np - 1) / np, kSmCount);
-  k_conv3x3_halo<<<grid, np * kHaloThreadsPerPipe, smem, stream>>>(map, a);
+  k_conv3x3_halo<<<grid, np * kHaloThreadsPerPipe, smem, stream>>>(map, map2, a);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 
@@ -625,10 +660,14 @@ ls_status conv3x3_head_launch(const uint16_t* x, const uint16_t* wpk, const floa
 // Shared with the model code: validated launch of one convolution whose output
 // channels go to cout / ygroup tensors of ygroup channels each, ygstride elements apart
 // (ygroup = cout: one NHWC tensor).  Without a mask only (a mask is one NHWC tensor).
+// x2 (optional): input channels [c_split, cin) come from x2 (cin - c_split per pixel)
+// and [0, c_split) from x (c_split per pixel), as if the two were concatenated.
 ls_status conv3x3_launch_groups(const uint16_t* x, const uint16_t* wpk, const float* bias, const uint16_t* mask,
                                 int relu, int n, int h, int w, int cin, int cout, uint16_t* y, int ygroup,
-                                int64_t ygstride, cudaStream_t stream) {
+                                int64_t ygstride, cudaStream_t stream, const uint16_t* x2 = nullptr,
+                                int c_split = 0) {
   if (!x || !wpk || !y || n <= 0 || h <= 0 || w <= 0) return LS_ERR_INVALID_ARG;
+  if (x2 && (c_split <= 0 || c_split >= cin || c_split % 8 || (uintptr_t)x2 % 16)) return LS_ERR_INVALID_ARG;
   if (cin < 8 || cin % 8 || cin > 256 || cout < 16 || cout > 256 || cout % 16) return LS_ERR_UNSUPPORTED;
   if (ygroup < 16 || ygroup % 16 || cout % ygroup ||
       (ygroup != cout && (mask || ygstride % 8 || ygstride < (int64_t)n * h * w * ygroup)))
@@ -637,10 +676,12 @@ ls_status conv3x3_launch_groups(const uint16_t* x, const uint16_t* wpk, const fl
   if (((uintptr_t)x | (uintptr_t)wpk | (uintptr_t)y | (uintptr_t)mask) % 16) return LS_ERR_INVALID_ARG;
   {
     const ls_status hs = conv3x3_halo_launch(x, wpk, bias, mask, relu, n, h, w, cin, cout, y, ygroup,
-                                             ygroup == cout ? 0 : ygstride, stream);
+                                             ygroup == cout ? 0 : ygstride, stream, nullptr, nullptr, 0, 1, x2,
+                                             c_split);
     if (hs != LS_ERR_UNSUPPORTED) return hs;  // else the shape is not one for the halo form
   }
   ConvArgs a = {};
+  a.c_split = x2 ? c_split : cin;
   uint32_t box[4] = {8, (uint32_t)w, 1, 1};
   if (w * h >= 128) {
     const int rpt = 128 / w;
@@ -669,7 +710,9 @@ ls_status conv3x3_launch_groups(const uint16_t* x, const uint16_t* wpk, const fl
   a.kc = chunk_count(cin);
   a.n_stages = (a.kc + kChunksPerStage - 1) / kChunksPerStage;
   // widest channel block per TMA load: fewer, longer rows for the TMA unit
-  a.cw = cin % 64 == 0 ? 64 : cin % 32 == 0 ? 32 : cin % 16 == 0 ? 16 : 8;
+  // (a channel block never straddles the two inputs)
+  a.cw = 64;
+  while (a.cw > 8 && (cin % a.cw || a.c_split % a.cw)) a.cw >>= 1;
   a.cblocks = cin / a.cw;
   a.blocks_per_stage = 64 / a.cw;
   a.n_blocks = 9 * a.cblocks;
@@ -682,10 +725,9 @@ ls_status conv3x3_launch_groups(const uint16_t* x, const uint16_t* wpk, const fl
   a.tmem_cols = 2 * a.acc_cols;
   a.stage_bytes = (uint32_t)(kAStageBytes + cout * 8 * 16);
   a.idesc = tc::idesc_bf16(128, cout);
-  CUtensorMap map;
-  const uint64_t dims[4] = {(uint64_t)cin, (uint64_t)w, (uint64_t)h, (uint64_t)n};
-  const uint64_t strides[3] = {(uint64_t)cin * 2, (uint64_t)w * cin * 2, (uint64_t)h * w * cin * 2};
-  if (!encode_tmap_bf16_4d(&map, x, dims, strides, box, a.cw == 8 ? 0 : a.cw * 2)) return LS_ERR_CUDA;
+  CUtensorMap map, map2;
+  if (!encode_input_maps(&map, &map2, x, x2, a.c_split, cin, n, h, w, a.cw, box[1], box[2], box[3]))
+    return LS_ERR_CUDA;
   // two CTAs per SM where their accumulators fit the TMEM together (tmem_cols <= 256):
   // each gets half the shared-memory budget
   const size_t budget = a.tmem_cols <= 128 ? kConvSmemBudget3 : a.tmem_cols <= 256 ? kConvSmemBudget2 : kConvSmemBudget;
@@ -701,7 +743,7 @@ ls_status conv3x3_launch_groups(const uint16_t* x, const uint16_t* wpk, const fl
       }))
     return LS_ERR_CUDA;
   const int per_sm = a.tmem_cols <= 128 ? 3 : a.tmem_cols <= 256 ? 2 : 1;
-  k_conv3x3<<<grid_cap(a.n_mtiles, (int64_t)kSmCount * per_sm), kConvThreads, smem, stream>>>(map, a);
+  k_conv3x3<<<grid_cap(a.n_mtiles, (int64_t)kSmCount * per_sm), kConvThreads, smem, stream>>>(map, map2, a);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 

@@ -612,9 +612,20 @@ ls_status filler_forward(ls_model* m, const float* params, const uint16_t* x, in
     const int h = R >> (l - 1);
     const int cu = (l + 1 == L) ? m->widths[L - 1] : m->widths[l];
     const int cs = m->widths[l - 1];
-    k_upcat<<<grid_cap((int64_t)n * h, kSmCount * 16), 256, 0, s>>>(h_in, cu, m->act[slot_eb(l)], cs, n, h, h,
-                                                                     m->act[slot_c(l)]);
-    if ((st = conv(li++, m->act[slot_c(l)], h, m->act[slot_da(l)])) != LS_OK) return st;
+    if (keep_top) {
+      k_upcat<<<grid_cap((int64_t)n * h, kSmCount * 16), 256, 0, s>>>(h_in, cu, m->act[slot_eb(l)], cs, n, h, h,
+                                                                       m->act[slot_c(l)]);
+      if ((st = conv(li++, m->act[slot_c(l)], h, m->act[slot_da(l)])) != LS_OK) return st;
+    } else {
+      // inference: only the upsampled channels are written; the convolution reads the
+      // skip connection's channels from the encoder output directly
+      k_upcat<<<grid_cap((int64_t)n * h, kSmCount * 16), 256, 0, s>>>(h_in, cu, nullptr, 0, n, h, h,
+                                                                       m->act[slot_c(l)]);
+      const LayerDesc& d = m->layers[li++];
+      if ((st = conv3x3_launch_groups(m->act[slot_c(l)], d.wpk, params + d.b_off, nullptr, 1, n, h, h, d.cin_pad,
+                                      d.cout, m->act[slot_da(l)], d.cout, 0, s, m->act[slot_eb(l)], cu)) != LS_OK)
+        return st;
+    }
     if (l == 1 && L > 1) {
       // the last convolution with the head in its epilogue
       const LayerDesc& d = m->layers[li];
