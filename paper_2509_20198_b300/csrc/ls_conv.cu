@@ -612,8 +612,9 @@ ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const floa
     const size_t per = (size_t)pipes * box_stride_of(c);
     return wsz >= kHaloSmemBudget ? 0 : (int)std::min<size_t>(kHaloRingUse, (kHaloSmemBudget - wsz) / per);
   };
-  while (np > 2 && ring_of(cw, np) < 2) np >>= 1;
-  if (ring_of(cw, np) < 2) return LS_ERR_UNSUPPORTED;
+  // fewer than four pipelines (C_out > 64, or boxes that do not fit four rings) measured
+  // slower than the per-tap form, which runs several CTAs per SM
+  if (np < kHaloMaxPipes || ring_of(cw, np) < 2) return LS_ERR_UNSUPPORTED;
   a.cw = cw;
   a.cblocks = cin / cw;
   a.npipes = np;
