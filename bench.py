@@ -1100,6 +1100,75 @@ def run_learned_case(args):
     return 0 if st == 0 else 1
 
 
+def run_conv_case(args):
+    """Profiling case: layer d1a of the learned filler (64x64, 96 -> 32 channels, bias,
+    ReLU) on --case-tiles tiles of seeded N(0,1) inputs, three warm-up launches and a
+    fourth (the one to profile) through the C-ABI convolution."""
+    import ctypes
+    import torch
+    from paper_2509_20198_b300 import _native as N
+    from paper_2509_20198_b300 import build
+    build.build_library()
+    L = N.lib()
+    n, s, cin, cout = args.case_tiles, 64, 96, 32
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(n * s * s * cin, device="cuda", generator=g).to(torch.bfloat16)
+    w = torch.randn(cout, 3, 3, cin, device="cuda", generator=g) * 0.05
+    pk = torch.empty(L.ls_conv3x3_packed_elems(cin, cout), dtype=torch.int16, device="cuda")
+    N.check("pack", L.ls_conv3x3_pack(ctypes.c_void_p(w.data_ptr()), cin, cout, 0, ctypes.c_void_p(pk.data_ptr()),
+                                      None))
+    y = torch.empty(n * s * s * cout, dtype=torch.bfloat16, device="cuda")
+    b = torch.zeros(cout, device="cuda")
+    shp = N.LsConvShape(n, s, s, cin, cout)
+    st = 0
+    for _ in range(4):
+        st = L.ls_conv3x3_forward(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(pk.data_ptr()),
+                                  ctypes.c_void_p(b.data_ptr()), None, 1, ctypes.byref(shp),
+                                  ctypes.c_void_p(y.data_ptr()), None)
+        if st:
+            break
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "conv", "layer": "d1a", "tiles": n, "status": int(st)}))
+    return 0 if st == 0 else 1
+
+
+def run_learned_fill_case(args):
+    """Profiling case: the learned fill of --case-tiles tiles (at most one batch of 4,096)
+    of the 200 x 200-tile overview with He-initialised weights: one warm-up fill, then one
+    fill between cudaProfilerStart and cudaProfilerStop."""
+    import torch
+    import paper_2509_20198_b300 as lsb
+    from paper_2509_20198_b300 import build
+    from paper_2509_20198_b300 import train as T
+    import synth
+    import synth.gpu as sg
+    build.build_library()
+    build.build_synth()
+    dev = torch.device("cuda")
+    stream = torch.cuda.Stream()
+    region, counts = synth.overview_workload()
+    with torch.cuda.stream(stream):
+        s = sg.region_samples(3, region, counts, device=dev, stream=stream)
+    stream.synchronize()
+    nb = min(args.case_tiles, 4096)
+    filler = lsb.Filler(max_batch=4096, device=dev)
+    T.init_params(filler, seed=0)
+    ids = torch.arange(nb, dtype=torch.int32, device=dev)
+    h = torch.empty((nb, 64, 64), dtype=torch.float32, device=dev)
+    c = torch.empty((nb, 64, 64, 3), dtype=torch.uint8, device=dev)
+    scratch = torch.empty(lsb._native.lib().ls_fill_learned_scratch_bytes(filler._h), dtype=torch.uint8, device=dev)
+    for k in range(2):
+        if k == 1:
+            torch.cuda.profiler.start()
+        with torch.cuda.stream(stream):
+            lsb.fill_learned(filler, s, region, ids, height=h, rgb=c, scratch=scratch, stream=stream)
+        stream.synchronize()
+    torch.cuda.profiler.stop()
+    st = lsb.last_error()
+    print(json.dumps({"case": "learned-fill", "tiles": nb, "status": st}))
+    return 0 if st == 0 else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1109,7 +1178,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--overview", type=int, default=1, help="also time the 40,000-tile overview fills")
     ap.add_argument("--case", default="", choices=["", "bin-small", "learned", "fill", "fill-overview", "interp", "render",
-                                                   "paper-cnn"],
+                                                   "paper-cnn", "conv", "learned-fill"],
                     help="profiling case instead of the bench")
     ap.add_argument("--case-tiles", type=int, default=3, help="tiles per side of the profiling case")
     ap.add_argument("--train-tiles", type=int, default=20000, help="training pairs of the learned filler")
@@ -1129,6 +1198,10 @@ def main():
         sys.exit(run_render_case(args))
     if args.case == "paper-cnn":
         sys.exit(run_paper_cnn_case(args))
+    if args.case == "conv":
+        sys.exit(run_conv_case(args))
+    if args.case == "learned-fill":
+        sys.exit(run_learned_fill_case(args))
     if args.case:
         sys.exit(run_profile_case(args))
     if args.impl == "reference":
