@@ -1132,6 +1132,42 @@ def run_conv_case(args):
     return 0 if st == 0 else 1
 
 
+# U-Net layers of the learned filler: image side, input and output channels
+UNET_LAYERS = {"e1b": (64, 32, 32), "e2a": (32, 32, 64), "e2b": (32, 64, 64), "e3a": (16, 64, 128),
+               "e3b": (16, 128, 128), "d2a": (32, 192, 64), "d2b": (32, 64, 64), "d1a": (64, 96, 32),
+               "d1b": (64, 32, 32)}
+
+
+def run_wgrad_case(args):
+    """Profiling case: weight and bias gradients of one learned-filler layer (--case-layer,
+    default d1a: 64x64, 96 -> 32 channels) on --case-tiles tiles of seeded N(0,1) inputs
+    and output gradients, three warm-up calls and a fourth (the one to profile) through
+    the C-ABI."""
+    import ctypes
+    import torch
+    from paper_2509_20198_b300 import _native as N
+    from paper_2509_20198_b300 import build
+    build.build_library()
+    L = N.lib()
+    s, cin, cout = UNET_LAYERS[args.case_layer]
+    n = args.case_tiles
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(n * s * s * cin, device="cuda", generator=g).to(torch.bfloat16)
+    dz = torch.randn(n * s * s * cout, device="cuda", generator=g).to(torch.bfloat16)
+    dw = torch.zeros(9 * cin * cout, device="cuda")
+    db = torch.zeros(cout, device="cuda")
+    shp = N.LsConvShape(n, s, s, cin, cout)
+    st = 0
+    for _ in range(4):
+        st = L.ls_conv3x3_wgrad(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(dz.data_ptr()), ctypes.byref(shp),
+                                ctypes.c_void_p(dw.data_ptr()), ctypes.c_void_p(db.data_ptr()), None)
+        if st:
+            break
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "wgrad", "layer": args.case_layer, "tiles": n, "status": int(st)}))
+    return 0 if st == 0 else 1
+
+
 def run_learned_fill_case(args):
     """Profiling case: the learned fill of --case-tiles tiles (at most one batch of 4,096)
     of the 200 x 200-tile overview with He-initialised weights: one warm-up fill, then one
@@ -1178,9 +1214,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--overview", type=int, default=1, help="also time the 40,000-tile overview fills")
     ap.add_argument("--case", default="", choices=["", "bin-small", "learned", "fill", "fill-overview", "interp", "render",
-                                                   "paper-cnn", "conv", "learned-fill"],
+                                                   "paper-cnn", "conv", "learned-fill", "wgrad"],
                     help="profiling case instead of the bench")
     ap.add_argument("--case-tiles", type=int, default=3, help="tiles per side of the profiling case")
+    ap.add_argument("--case-layer", default="d1a", choices=sorted(UNET_LAYERS), help="layer of the wgrad case")
     ap.add_argument("--train-tiles", type=int, default=20000, help="training pairs of the learned filler")
     ap.add_argument("--train-epochs", type=int, default=24)
     ap.add_argument("--cnn-tiles", type=int, default=4096, help="training pairs of the paper's network variant")
@@ -1202,6 +1239,8 @@ def main():
         sys.exit(run_conv_case(args))
     if args.case == "learned-fill":
         sys.exit(run_learned_fill_case(args))
+    if args.case == "wgrad":
+        sys.exit(run_wgrad_case(args))
     if args.case:
         sys.exit(run_profile_case(args))
     if args.impl == "reference":

@@ -223,6 +223,228 @@ __global__ void __launch_bounds__(kWgThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Halo form for input channels in blocks of 32 on images 16 to 128 wide (a power of
+// two).  With q = p + (ky - 1, 0) the sum becomes
+//   dW^T[(ky, kx, c)][o] = sum_q X(q + (0, kx - 1))[c] dZ(q - (ky - 1, 0))[o],
+// so the horizontal tap kx shifts the input along its row and the vertical tap ky
+// shifts dZ by whole rows.  A stage is one chunk of R image rows (R * W = 128 pixels q)
+// of one image: per block of 32 input channels a TMA box of rows y0 .. y0+R-1 and
+// columns -1 .. W (P = W + 2 pixels per row, zero outside the image; 64-byte pixel rows,
+// 64-byte swizzle), and per block of cwb = 32 or 64 output channels the dZ box of rows
+// y0-1 .. y0+R (zero outside the image).  The K index is q, 16 per MMA within a row.
+//  A (M = 128): blocks kx = 0..3 of 32 channels, the same input box seen one pixel row
+//    apart (LBO = one 64-byte row), starting at box pixel row r * P + x0; block kx = 3
+//    is not a tap (its rows are computed and dropped: 3/4 of the M rows are used; it
+//    reads at most one pixel row past the box, inside the box's slack).
+//  B (N = 3 * cwb): blocks j = 0..2 of cwb channels, dZ rows r + j of the box
+//    (LBO = one dZ image row), j = 2 - ky.
+// One MMA thus serves all nine taps of a channel block and cwb outputs: the A operand
+// (4 KB per MMA, the bulk of the shared-memory reads) is read once for three taps.
+// An issuing warp owns the accumulator of one (channel block, dZ block) unit and takes
+// every nk-th of the chunk's eight 16-pixel steps: with nk > 1 (TMEM permitting) the
+// unit has nk accumulator copies that the epilogue adds in order (one thread waits
+// about 150 cycles per MMA, so the issue rate grows with the number of issuers).
+// TMEM: copy-major, per channel block 3 * C_out columns, [ob][j][cwb].
+// With the bias gradient, the four epilogue warps of the group-0 CTAs sum dZ over the
+// chunk pixels of every stage meanwhile (they release the stage too).  At the end the
+// epilogue warp of TMEM lane quadrant q stores the rows of tap column kx = q.
+// Partials land in k_wsum's layout: [slice][9 * C_in rounded up to 128][C_out]; bias
+// partials in [slice][C_out] for k_dbsum.
+constexpr int kWhMaxIssuers = 9;
+constexpr int kWhMaxStages = 8;
+constexpr int kWhSteps = 8;  // 16-pixel steps per 128-pixel chunk
+constexpr int kWhThreads = 32 * (1 + kWhMaxIssuers + 4);
+constexpr size_t kWhSmemBudget = 224 * 1024;
+
+struct WhArgs {
+  float* __restrict__ part;
+  float* __restrict__ dbpart;  // [slices][cout] bias partials, or null
+  int32_t w, p, r, cin, cout, cwb, n_dzb, gblocks, groups, nissue, nk;
+  int32_t chunks_per_img, n_chunks, chunks_per_cta, stages;
+  uint32_t box_stride, xbox_bytes, dz_blk_bytes, dz_rowb, dz_mode, stage_bytes, idesc, tmem_cols;
+  int32_t part_rows;
+};
+
+__global__ void __launch_bounds__(kWhThreads, 1)
+    k_wgrad_halo(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap dzmap, const WhArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t full[kWhMaxStages], empty[kWhMaxStages], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = blockIdx.x % a.groups, slice = blockIdx.x / a.groups;
+  const int c_begin = slice * a.chunks_per_cta;
+  const int c_end = min(c_begin + a.chunks_per_cta, a.n_chunks);
+  const int nissue = a.nissue;
+  const bool bias = a.dbpart != nullptr && g == 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < a.stages; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], nissue + (bias ? 4 : 0));
+    }
+    tc::mbar_init(&done, nissue);
+    abort_flag = 0;
+    tc::mbar_fence_init();
+    tc::prefetch_tmap(&xmap);
+    tc::prefetch_tmap(&dzmap);
+  }
+  if (warp == 1) tc::tmem_alloc(&tmem_base, a.tmem_cols);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t taddr = tmem_base;
+  const int first_epi = 1 + nissue;
+  const uint32_t dz_off = (uint32_t)a.gblocks * a.box_stride;  // dZ blocks after the input boxes
+  const int blk_cols = 3 * a.cout;                             // TMEM columns per channel block
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer: per chunk the input boxes of the group's channel
+      // blocks and the dZ boxes (one row of halo above and below)
+      const uint32_t bytes = (uint32_t)a.gblocks * a.xbox_bytes + (uint32_t)a.n_dzb * a.dz_blk_bytes;
+      int slot = 0;
+      uint32_t ph = 0;
+      for (int c = c_begin; c < c_end && !abort_flag; ++c) {
+        const int n = c / a.chunks_per_img, y0 = (c - n * a.chunks_per_img) * a.r;
+        if (!tc::mbar_wait(&empty[slot], ph ^ 1u)) { abort_flag = 1; break; }
+        uint8_t* st = smem + (size_t)slot * a.stage_bytes;
+        tc::mbar_arrive_expect_tx(&full[slot], bytes);
+        for (int lb = 0; lb < a.gblocks; ++lb)
+          tc::tma_load_4d(st + (size_t)lb * a.box_stride, &xmap, (g * a.gblocks + lb) * 32, -1, y0, n, &full[slot]);
+        for (int ob = 0; ob < a.n_dzb; ++ob)
+          tc::tma_load_4d(st + dz_off + (size_t)ob * a.dz_blk_bytes, &dzmap, ob * a.cwb, 0, y0 - 1, n, &full[slot]);
+        if (++slot == a.stages) { slot = 0; ph ^= 1u; }
+      }
+    }
+  } else if (warp <= nissue) {
+    if (lane == 0) {
+      // ---------------- MMA issuer of unit (channel block lb, dZ block ob), steps kp,
+      // kp + nk, ... of each chunk into accumulator copy kp
+      const int u = (warp - 1) / a.nk, kp = (warp - 1) - u * a.nk;
+      const int lb = u / a.n_dzb, ob = u - lb * a.n_dzb;
+      const uint32_t s0 = tc::saddr(smem);
+      const uint32_t d = taddr + (uint32_t)(kp * a.gblocks * blk_cols + lb * blk_cols + ob * 3 * a.cwb);
+      const int ksteps = a.w / 16;
+      // descriptors of the chunk's eight 16-pixel steps in stage 0, built once; a stage
+      // adds its offset to the start-address field (shared addresses stay below 256 KB)
+      uint64_t adsc[kWhSteps], bdsc[kWhSteps];
+#pragma unroll
+      for (int i = 0; i < kWhSteps; ++i) {
+        const int rr = i / ksteps, x0 = (i - rr * ksteps) * 16;
+        adsc[i] = tc::sdesc_mn(s0 + (uint32_t)lb * a.box_stride + (uint32_t)(rr * a.p + x0) * 64u, 64u, 512u, 4u);
+        bdsc[i] = tc::sdesc_mn(s0 + dz_off + (uint32_t)ob * a.dz_blk_bytes + (uint32_t)(rr * a.w + x0) * a.dz_rowb,
+                               (uint32_t)a.w * a.dz_rowb, 8u * a.dz_rowb, a.dz_mode);
+      }
+      const uint32_t idesc = a.idesc;
+      const int kmask = a.nk - 1;
+      int slot = 0;
+      uint32_t ph = 0;
+      uint32_t acc = 0u;
+      for (int c = c_begin; c < c_end && !abort_flag; ++c) {
+        if (!tc::mbar_wait(&full[slot], ph)) { abort_flag = 1; break; }
+        tc::fence_after();
+        const uint64_t so = (uint64_t)(((uint32_t)slot * a.stage_bytes) >> 4);
+#pragma unroll
+        for (int i = 0; i < kWhSteps; ++i) {
+          if ((i & kmask) == kp) {
+            tc::mma_bf16(d, adsc[i] + so, bdsc[i] + so, idesc, acc);
+            acc = 1u;
+          }
+        }
+        tc::mma_commit(&empty[slot]);
+        if (++slot == a.stages) { slot = 0; ph ^= 1u; }
+      }
+      tc::mma_commit(&done);
+    }
+  } else if (warp < first_epi + 4) {
+    const int q = warp & 3;
+    const int et = (warp - first_epi) * 32 + lane;  // 0..127
+    float bsum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int nch = a.cout / 8;                  // 16-byte channel chunks per pixel
+    const int lanes = 128 / nch, bj = et % nch;  // pixel lanes; this thread's chunk
+    const int bl = et / nch < lanes ? et / nch : 128;  // threads past the last lane idle
+    if (bias) {
+      // ---------------- bias gradient: dZ over the chunk's pixels (box rows 1 .. R),
+      // channels of chunk bj, pixels bl, bl + lanes, ...
+      const int ob = bj / (a.cwb / 8), cj = bj - ob * (a.cwb / 8);
+      int slot = 0;
+      uint32_t ph = 0;
+      for (int c = c_begin; c < c_end && !abort_flag; ++c) {
+        if (!tc::mbar_wait(&full[slot], ph)) { abort_flag = 1; break; }
+        const uint8_t* zb = smem + (size_t)slot * a.stage_bytes + dz_off + (size_t)ob * a.dz_blk_bytes;
+        for (int px = bl; px < 128; px += lanes) {
+          const int row = a.w + px;  // box row 0 is the halo row above the chunk
+          const int sc = a.cwb == 64 ? (cj ^ (row & 7)) : (cj ^ ((row >> 1) & 3));
+          const uint4 v = *reinterpret_cast<const uint4*>(zb + (size_t)row * a.dz_rowb + sc * 16);
+          const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            bsum[2 * i] += __uint_as_float(wv[i] << 16);
+            bsum[2 * i + 1] += __uint_as_float(wv[i] & 0xffff0000u);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&empty[slot]);
+        if (++slot == a.stages) { slot = 0; ph ^= 1u; }
+      }
+    }
+    // ---------------- epilogue: TMEM lane quadrant q of every channel block = tap
+    // column kx = q; column (ob, j, o') = tap row ky = 2 - j, output ob * cwb + o'
+    const bool ok = c_end > c_begin && tc::mbar_wait(&done, 0) && !abort_flag;
+    if (ok) {
+      tc::fence_after();
+      float* out = a.part + (size_t)slice * a.part_rows * a.cout;
+      for (int lb = 0; lb < a.gblocks; ++lb) {
+        const int cbase = (g * a.gblocks + lb) * 32 + lane;
+        for (int col = 0; col < blk_cols; col += 16) {
+          const int ob = col / (3 * a.cwb), rem = col - ob * 3 * a.cwb;
+          const int j = rem / a.cwb, o0 = ob * a.cwb + (rem - j * a.cwb);
+          const uint32_t ta = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(lb * blk_cols + col);
+          float v[16];
+          tc::tmem_ld16(ta, v);
+          for (int kp = 1; kp < a.nk; ++kp) {  // accumulator copies in order
+            float v2[16];
+            tc::tmem_ld16(ta + (uint32_t)(kp * a.gblocks * blk_cols), v2);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] += v2[i];
+          }
+          if (q < 3) {
+            const int k = ((2 - j) * 3 + q) * a.cin + cbase;
+            float* o = out + (size_t)k * a.cout + o0;
+#pragma unroll
+            for (int i = 0; i < 16; i += 4)
+              *reinterpret_cast<float4*>(o + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+          }
+        }
+      }
+    }
+    if (bias) {
+      // fixed-order combination of the pixel lanes through shared memory (the ring is
+      // idle: every load was consumed by the finished MMAs)
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      float* red = reinterpret_cast<float*>(smem);
+      if (ok) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) red[et * 8 + i] = bsum[i];
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (ok && et < a.cout) {
+        const int cc = et / 8, i = et - cc * 8;
+        float s = 0.f;
+        for (int l = 0; l < lanes; ++l) s += red[(l * nch + cc) * 8 + i];
+        a.dbpart[(size_t)slice * a.cout + et] = s;
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after();
+    tc::tmem_dealloc(taddr, a.tmem_cols);
+  }
+}
+
 // dW^T[k][o] += sum over slices of the CTA partials, slices in increasing order (loads
 // issued eight ahead of the in-order additions).
 // With db, row `rows` of the partials (the ones row) is the bias gradient: into db.
@@ -297,18 +519,101 @@ __global__ void __launch_bounds__(256) k_dbsum(const float* __restrict__ part, i
 
 }  // namespace
 
+// The halo form (k_wgrad_halo) when the shapes allow it; LS_ERR_UNSUPPORTED otherwise
+// (the caller falls back to the per-tap form).
+static ls_status wgrad_halo_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int w, int cin, int cout,
+                                   float* dwt, float* db, cudaStream_t stream) {
+  if (cin % 32 || cout % 32 || cout > 128 || w < 16 || w > 128 || (w & (w - 1))) return LS_ERR_UNSUPPORTED;
+  WhArgs a = {};
+  a.w = w; a.p = w + 2; a.r = 128 / w; a.cin = cin; a.cout = cout;
+  a.cwb = cout % 64 == 0 ? 64 : 32;
+  a.n_dzb = cout / a.cwb;
+  const int cblocks = cin / 32;
+  // channel blocks per CTA: all nine taps of a block in TMEM (3 * cout columns each),
+  // at most nine issuing units, a divisor of the block count
+  int gmax = 512 / (3 * cout);
+  while (gmax > 1 && gmax * a.n_dzb > kWhMaxIssuers) --gmax;
+  a.gblocks = 1;
+  for (int gb = gmax; gb >= 1; --gb)
+    if (cblocks % gb == 0) { a.gblocks = gb; break; }
+  a.groups = cblocks / a.gblocks;
+  const int units = a.gblocks * a.n_dzb;
+  // accumulator copies: as many as TMEM and the issuing warps allow, dividing the eight
+  // 16-pixel steps of a chunk
+  a.nk = 1;
+  while (a.nk < 8 && units * a.nk * 2 <= kWhMaxIssuers && a.gblocks * 3 * cout * a.nk * 2 <= 512) a.nk *= 2;
+  a.nissue = units * a.nk;
+  a.idesc = tc::idesc_bf16_mn(128, 3 * a.cwb);
+  a.tmem_cols = 32;
+  while ((int)a.tmem_cols < a.nk * a.gblocks * 3 * cout) a.tmem_cols <<= 1;
+  a.chunks_per_img = (h + a.r - 1) / a.r;
+  const int64_t n_chunks = (int64_t)n * a.chunks_per_img;
+  if (n_chunks > INT32_MAX / 2) return LS_ERR_UNSUPPORTED;
+  a.n_chunks = (int)n_chunks;
+  // input box: R rows of P pixels of 64 bytes, plus one pixel row of slack for the
+  // dropped block kx = 3, rounded up to the 1024-byte swizzle alignment
+  a.xbox_bytes = (uint32_t)(a.r * a.p * 64);
+  a.box_stride = (a.xbox_bytes + 64u + 1023u) & ~1023u;
+  a.dz_rowb = (uint32_t)a.cwb * 2u;
+  a.dz_mode = a.cwb == 64 ? 2u : 4u;
+  a.dz_blk_bytes = (uint32_t)(a.r + 2) * (uint32_t)w * a.dz_rowb;  // a multiple of 1024 (w >= 16)
+  a.stage_bytes = (uint32_t)a.gblocks * a.box_stride + (uint32_t)a.n_dzb * a.dz_blk_bytes;
+  a.stages = (int)(kWhSmemBudget / a.stage_bytes);
+  if (a.stages > kWhMaxStages) a.stages = kWhMaxStages;
+  if (a.stages < 2) return LS_ERR_UNSUPPORTED;
+  a.part_rows = (9 * cin + 127) / 128 * 128;
+  // one CTA per SM over all groups (more than 256 TMEM columns keep a CTA alone on its
+  // SM; the shared-memory request below makes sure of it); every slice non-empty
+  int64_t slices = kSmCount / a.groups > 0 ? kSmCount / a.groups : 1;
+  if (slices > n_chunks) slices = n_chunks;
+  a.chunks_per_cta = (int)((n_chunks + slices - 1) / slices);
+  slices = (n_chunks + a.chunks_per_cta - 1) / a.chunks_per_cta;
+  size_t smem = (size_t)a.stages * a.stage_bytes;
+  if (a.tmem_cols > 256 && smem < 120 * 1024) smem = 120 * 1024;
+  CUtensorMap xmap, dzmap;
+  const uint32_t xbox[4] = {32u, (uint32_t)a.p, (uint32_t)a.r, 1u};
+  const uint32_t zbox[4] = {(uint32_t)a.cwb, (uint32_t)w, (uint32_t)(a.r + 2), 1u};
+  const uint64_t xd[4] = {(uint64_t)cin, (uint64_t)w, (uint64_t)h, (uint64_t)n};
+  const uint64_t xs[3] = {(uint64_t)cin * 2, (uint64_t)w * cin * 2, (uint64_t)h * w * cin * 2};
+  const uint64_t zd[4] = {(uint64_t)cout, (uint64_t)w, (uint64_t)h, (uint64_t)n};
+  const uint64_t zs[3] = {(uint64_t)cout * 2, (uint64_t)w * cout * 2, (uint64_t)h * w * cout * 2};
+  if (!encode_tmap_bf16_4d(&xmap, x, xd, xs, xbox, 64) || !encode_tmap_bf16_4d(&dzmap, dz, zd, zs, zbox, a.cwb * 2))
+    return LS_ERR_CUDA;
+  const size_t part_bytes = (size_t)slices * a.part_rows * cout * 4, db_bytes = (size_t)slices * cout * 4;
+  uint8_t* ws = static_cast<uint8_t*>(workspace(kWsGradPart, part_bytes + db_bytes));
+  if (!ws) return LS_ERR_NO_MEMORY;
+  a.part = reinterpret_cast<float*>(ws);
+  a.dbpart = db ? reinterpret_cast<float*>(ws + part_bytes) : nullptr;
+  static DeviceOnce once;
+  int dev = 0;
+  LS_CUDA_TRY(cudaGetDevice(&dev));
+  if (!device_once(once, dev, [] {
+        return cudaFuncSetAttribute(k_wgrad_halo, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kWhSmemBudget) == cudaSuccess;
+      }))
+    return LS_ERR_CUDA;
+  k_wgrad_halo<<<(unsigned)(slices * a.groups), kWhThreads, smem, stream>>>(xmap, dzmap, a);
+  const int rows = 9 * cin;
+  k_wsum<<<grid_cap((rows * cout + 255) / 256, kSmCount * 4), 256, 0, stream>>>(
+      a.part, (int)slices, a.part_rows / 128, rows, cout, dwt, nullptr);
+  if (db) k_dbsum<<<cout, 256, 0, stream>>>(a.dbpart, (int)slices, cout, db);
+  return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
+}
+
 // Accumulates into dwt ([9*cin][cout], fp32) and db ([cout], may be NULL).
 ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int w, int cin, int cout, float* dwt,
                        float* db, cudaStream_t stream) {
   if (!x || !dz || !dwt || n <= 0 || h <= 0 || w <= 0) return LS_ERR_INVALID_ARG;
   if (cin % 8 || cout < 16 || cout > 128 || cout % 16) return LS_ERR_UNSUPPORTED;
-  // a stage is 64 pixels: half a row (w = 128), whole image rows of one image, or
+  if (((uintptr_t)x | (uintptr_t)dz) % 16) return LS_ERR_INVALID_ARG;
+  if (ls_status st = wgrad_halo_launch(x, dz, n, h, w, cin, cout, dwt, db, stream); st != LS_ERR_UNSUPPORTED)
+    return st;
+  // per-tap form: a stage is 64 pixels: half a row (w = 128), whole image rows of one image, or
   // whole images
   const int64_t hw = (int64_t)h * w;
   if ((w > kWgPix && w != 2 * kWgPix) || (w <= kWgPix && kWgPix % w) || (hw % kWgPix && kWgPix % hw))
     return LS_ERR_UNSUPPORTED;
   if (hw < kWgPix && n % (kWgPix / hw)) return LS_ERR_UNSUPPORTED;
-  if (((uintptr_t)x | (uintptr_t)dz) % 16) return LS_ERR_INVALID_ARG;
   WgArgs a = {};
   a.h = h; a.w = w; a.cin = cin; a.cout = cout; a.rows = 9 * cin;
   a.rows_per_step = hw >= kWgPix ? (w >= kWgPix ? 1 : kWgPix / w) : h;
