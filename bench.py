@@ -1133,7 +1133,7 @@ def run_conv_case(args):
 
 
 # U-Net layers of the learned filler: image side, input and output channels
-UNET_LAYERS = {"e1b": (64, 32, 32), "e2a": (32, 32, 64), "e2b": (32, 64, 64), "e3a": (16, 64, 128),
+UNET_LAYERS = {"e1a": (64, 8, 32), "e1b": (64, 32, 32), "e2a": (32, 32, 64), "e2b": (32, 64, 64), "e3a": (16, 64, 128),
                "e3b": (16, 128, 128), "d2a": (32, 192, 64), "d2b": (32, 64, 64), "d1a": (64, 96, 32),
                "d1b": (64, 32, 32)}
 

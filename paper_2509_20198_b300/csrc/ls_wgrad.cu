@@ -249,8 +249,8 @@ __global__ void __launch_bounds__(kWgThreads, 1)
 // With the bias gradient, the four epilogue warps of the group-0 CTAs sum dZ over the
 // chunk pixels of every stage meanwhile (they release the stage too).  At the end the
 // epilogue warp of TMEM lane quadrant q stores the rows of tap column kx = q.
-// Partials land in k_wsum's layout: [slice][9 * C_in rounded up to 128][C_out]; bias
-// partials in [slice][C_out] for k_dbsum.
+// Partials land in k_wsum's layout: [slice][9 * C_in + 1][C_out], the last row the bias
+// partial.
 constexpr int kWhMaxIssuers = 9;
 constexpr int kWhMaxStages = 8;
 constexpr int kWhSteps = 8;  // 16-pixel steps per 128-pixel chunk
@@ -259,7 +259,7 @@ constexpr size_t kWhSmemBudget = 224 * 1024;
 
 struct WhArgs {
   float* __restrict__ part;
-  float* __restrict__ dbpart;  // [slices][cout] bias partials, or null
+  int32_t bias;  // the group-0 CTAs store the bias partial as row 9 * C_in
   int32_t w, p, r, cin, cout, cwb, n_dzb, gblocks, groups, nissue, nk;
   int32_t chunks_per_img, n_chunks, chunks_per_cta, stages;
   uint32_t box_stride, xbox_bytes, dz_blk_bytes, dz_rowb, dz_mode, stage_bytes, idesc, tmem_cols;
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kWhThreads, 1)
   const int c_begin = slice * a.chunks_per_cta;
   const int c_end = min(c_begin + a.chunks_per_cta, a.n_chunks);
   const int nissue = a.nissue;
-  const bool bias = a.dbpart != nullptr && g == 0;
+  const bool bias = a.bias && g == 0;
   if (threadIdx.x == 0) {
     for (int i = 0; i < a.stages; ++i) {
       tc::mbar_init(&full[i], 1);
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(kWhThreads, 1)
         const int cc = et / 8, i = et - cc * 8;
         float s = 0.f;
         for (int l = 0; l < lanes; ++l) s += red[(l * nch + cc) * 8 + i];
-        a.dbpart[(size_t)slice * a.cout + et] = s;
+        a.part[((size_t)slice * a.part_rows + 9 * a.cin) * a.cout + et] = s;
       }
     }
   }
@@ -445,29 +445,223 @@ __global__ void __launch_bounds__(kWhThreads, 1)
   }
 }
 
-// dW^T[k][o] += sum over slices of the CTA partials, slices in increasing order (loads
-// issued eight ahead of the in-order additions).
-// With db, row `rows` of the partials (the ones row) is the bias gradient: into db.
-__global__ void k_wsum(const float* __restrict__ part, int slices, int n_mtiles, int rows, int cout,
-                       float* __restrict__ dwt, float* __restrict__ db) {
-  const int total = (rows + (db ? 1 : 0)) * cout;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const int k = e / cout, o = e - k * cout;
-    const int mt = k >> 7, row = k & 127;
-    const size_t stride = (size_t)n_mtiles * 128 * cout;
-    const float* p = part + ((size_t)mt * 128 + row) * cout + o;
-    float s = 0.f;
-    int sl = 0;
-    for (; sl + 8 <= slices; sl += 8) {
-      float v[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = p[(size_t)(sl + i) * stride];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) s += v[i];
+// ---------------------------------------------------------------------------------
+// Halo form for eight input channels (one 16-byte pixel row) and C_out = 32 or 64: the
+// roles of the operands swap.  The chunk, boxes and bias sums are those of
+// k_wgrad_halo (the input box has 16-byte rows, no swizzle); per 16-pixel step:
+//  A (M = 128): dZ rows r + j of the box, blocks j of cwb = C_out channels (LBO = one
+//    dZ image row): j = 0..3 in one tile at C_out = 32 (j = 3 is not a tap: dropped),
+//    j = 0, 1 and j = 2, 3 in two tiles at C_out = 64;
+//  B (N = 32): the input box seen at four pixel offsets kx = 0..3 (8-element groups one
+//    16-byte pixel row apart: SBO = 16 B, LBO = 8 pixel rows; kx = 3 dropped).
+// D[(j, o)][(kx, c)] accumulates dW^T[((2 - j) * 3 + kx) * 8 + c][o].  Issuers as in
+// k_wgrad_halo: one per (M tile, accumulator copy).
+__global__ void __launch_bounds__(kWhThreads, 1)
+    k_wgrad_halo_c8(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap dzmap,
+                    const WhArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t full[kWhMaxStages], empty[kWhMaxStages], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int slice = blockIdx.x;
+  const int c_begin = slice * a.chunks_per_cta;
+  const int c_end = min(c_begin + a.chunks_per_cta, a.n_chunks);
+  const int nissue = a.nissue;
+  const bool bias = a.bias != 0;
+  const int mtiles = a.cout / 32;  // M tiles per step
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < a.stages; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], nissue + (bias ? 4 : 0));
     }
-    for (; sl < slices; ++sl) s += p[(size_t)sl * stride];
-    if (k < rows) dwt[e] += s;
-    else db[o] += s;
+    tc::mbar_init(&done, nissue);
+    abort_flag = 0;
+    tc::mbar_fence_init();
+    tc::prefetch_tmap(&xmap);
+    tc::prefetch_tmap(&dzmap);
+  }
+  if (warp == 1) tc::tmem_alloc(&tmem_base, a.tmem_cols);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t taddr = tmem_base;
+  const int first_epi = 1 + nissue;
+  const uint32_t dz_off = a.box_stride;  // the dZ block after the input box
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const uint32_t bytes = a.xbox_bytes + a.dz_blk_bytes;
+      int slot = 0;
+      uint32_t ph = 0;
+      for (int c = c_begin; c < c_end && !abort_flag; ++c) {
+        const int n = c / a.chunks_per_img, y0 = (c - n * a.chunks_per_img) * a.r;
+        if (!tc::mbar_wait(&empty[slot], ph ^ 1u)) { abort_flag = 1; break; }
+        uint8_t* st = smem + (size_t)slot * a.stage_bytes;
+        tc::mbar_arrive_expect_tx(&full[slot], bytes);
+        tc::tma_load_4d(st, &xmap, 0, -1, y0, n, &full[slot]);
+        tc::tma_load_4d(st + dz_off, &dzmap, 0, 0, y0 - 1, n, &full[slot]);
+        if (++slot == a.stages) { slot = 0; ph ^= 1u; }
+      }
+    }
+  } else if (warp <= nissue) {
+    if (lane == 0) {
+      // ---------------- MMA issuer of M tile t (dZ rows j = t * jt ..), steps kp, kp + nk, ...
+      const int t = (warp - 1) / a.nk, kp = (warp - 1) - t * a.nk;
+      const int jt = 128 / a.cout;  // dZ row blocks per M tile
+      const uint32_t s0 = tc::saddr(smem);
+      const uint32_t d = taddr + (uint32_t)((kp * mtiles + t) * 32);
+      const int ksteps = a.w / 16;
+      uint64_t adsc[kWhSteps], bdsc[kWhSteps];
+#pragma unroll
+      for (int i = 0; i < kWhSteps; ++i) {
+        const int rr = i / ksteps, x0 = (i - rr * ksteps) * 16;
+        adsc[i] = tc::sdesc_mn(s0 + dz_off + (uint32_t)((rr + t * jt) * a.w + x0) * a.dz_rowb,
+                               (uint32_t)a.w * a.dz_rowb, 8u * a.dz_rowb, a.dz_mode);
+        bdsc[i] = tc::sdesc_mn(s0 + (uint32_t)(rr * a.p + x0) * 16u, 128u, 16u, 0u);
+      }
+      const uint32_t idesc = a.idesc;
+      const int kmask = a.nk - 1;
+      int slot = 0;
+      uint32_t ph = 0;
+      uint32_t acc = 0u;
+      for (int c = c_begin; c < c_end && !abort_flag; ++c) {
+        if (!tc::mbar_wait(&full[slot], ph)) { abort_flag = 1; break; }
+        tc::fence_after();
+        const uint64_t so = (uint64_t)(((uint32_t)slot * a.stage_bytes) >> 4);
+#pragma unroll
+        for (int i = 0; i < kWhSteps; ++i) {
+          if ((i & kmask) == kp) {
+            tc::mma_bf16(d, adsc[i] + so, bdsc[i] + so, idesc, acc);
+            acc = 1u;
+          }
+        }
+        tc::mma_commit(&empty[slot]);
+        if (++slot == a.stages) { slot = 0; ph ^= 1u; }
+      }
+      tc::mma_commit(&done);
+    }
+  } else if (warp < first_epi + 4) {
+    const int q = warp & 3;
+    const int et = (warp - first_epi) * 32 + lane;
+    float bsum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int nch = a.cout / 8;
+    const int lanes = 128 / nch, bj = et % nch;
+    const int bl = et / nch < lanes ? et / nch : 128;
+    if (bias) {
+      // bias gradient: dZ over the chunk's pixels (box rows 1 .. R), as in k_wgrad_halo
+      int slot = 0;
+      uint32_t ph = 0;
+      for (int c = c_begin; c < c_end && !abort_flag; ++c) {
+        if (!tc::mbar_wait(&full[slot], ph)) { abort_flag = 1; break; }
+        const uint8_t* zb = smem + (size_t)slot * a.stage_bytes + dz_off;
+        for (int px = bl; px < 128; px += lanes) {
+          const int row = a.w + px;
+          const int sc = a.cwb == 64 ? (bj ^ (row & 7)) : (bj ^ ((row >> 1) & 3));
+          const uint4 v = *reinterpret_cast<const uint4*>(zb + (size_t)row * a.dz_rowb + sc * 16);
+          const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            bsum[2 * i] += __uint_as_float(wv[i] << 16);
+            bsum[2 * i + 1] += __uint_as_float(wv[i] & 0xffff0000u);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&empty[slot]);
+        if (++slot == a.stages) { slot = 0; ph ^= 1u; }
+      }
+    }
+    // ---------------- epilogue: TMEM lane 32 q + lane of tile t is (j, o) with
+    // j = t * jt + (32 q + lane) / cout; columns kx * 8 + c, kx < 3 stored
+    const bool ok = c_end > c_begin && tc::mbar_wait(&done, 0) && !abort_flag;
+    if (ok) {
+      tc::fence_after();
+      float* out = a.part + (size_t)slice * a.part_rows * a.cout;
+      const int jt = 128 / a.cout;
+      const int m = q * 32 + lane, jl = m / a.cout, o = m - jl * a.cout;
+      for (int t = 0; t < mtiles; ++t) {
+        const int j = t * jt + jl;
+        const uint32_t ta = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 32);
+        float v0[16], v1[16];  // columns 0-15 (kx 0, 1) and 16-31 (kx 2, 3)
+        tc::tmem_ld16(ta, v0);
+        tc::tmem_ld16(ta + 16u, v1);
+        for (int kp = 1; kp < a.nk; ++kp) {  // accumulator copies in order
+          float v2[16];
+          const uint32_t tk = ta + (uint32_t)(kp * mtiles * 32);
+          tc::tmem_ld16(tk, v2);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v0[i] += v2[i];
+          tc::tmem_ld16(tk + 16u, v2);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v1[i] += v2[i];
+        }
+        if (j < 3) {
+          float* rowp = out + (size_t)((2 - j) * 3) * 8 * a.cout + o;  // tap (ky, kx = 0), channel 0
+#pragma unroll
+          for (int n = 0; n < 16; ++n) rowp[(size_t)n * a.cout] = v0[n];
+#pragma unroll
+          for (int n = 0; n < 8; ++n) rowp[(size_t)(16 + n) * a.cout] = v1[n];
+        }
+      }
+    }
+    if (bias) {
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      float* red = reinterpret_cast<float*>(smem);
+      if (ok) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) red[et * 8 + i] = bsum[i];
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (ok && et < a.cout) {
+        const int cc = et / 8, i = et - cc * 8;
+        float s = 0.f;
+        for (int l = 0; l < lanes; ++l) s += red[(l * nch + cc) * 8 + i];
+        a.part[((size_t)slice * a.part_rows + 9 * a.cin) * a.cout + et] = s;
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after();
+    tc::tmem_dealloc(taddr, a.tmem_cols);
+  }
+}
+
+// dW^T[k][o] += sum over slices of the CTA partials ([slice][stride] floats, element
+// e = k * cout + o).  A block takes 32 consecutive elements; warp g adds slices g, g + 8,
+// ... in increasing order (loads four ahead), then warp 0 adds the eight warp sums in
+// order: a fixed order, so the result does not depend on scheduling.  With db, row
+// `rows` of the partials is the bias gradient: into db.
+constexpr int kWsumGroups = 8;
+__global__ void __launch_bounds__(32 * kWsumGroups) k_wsum(const float* __restrict__ part, int slices,
+                                                            int64_t stride, int rows, int cout,
+                                                            float* __restrict__ dwt, float* __restrict__ db) {
+  __shared__ float red[kWsumGroups][32];
+  const int total = (rows + (db ? 1 : 0)) * cout;
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
+  float s = 0.f;
+  if (e < total) {
+    const float* p = part + e;
+    int sl = g;
+    for (; sl + 3 * kWsumGroups < slices; sl += 4 * kWsumGroups) {
+      float v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] = p[(size_t)(sl + i * kWsumGroups) * stride];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) s += v[i];
+    }
+    for (; sl < slices; sl += kWsumGroups) s += p[(size_t)sl * stride];
+  }
+  red[g][lane] = s;
+  __syncthreads();
+  if (g == 0 && e < total) {
+    float t = red[0][lane];
+#pragma unroll
+    for (int k = 1; k < kWsumGroups; ++k) t += red[k][lane];
+    if (e < rows * cout) dwt[e] += t;
+    else db[e - rows * cout] += t;
   }
 }
 
@@ -519,11 +713,79 @@ __global__ void __launch_bounds__(256) k_dbsum(const float* __restrict__ part, i
 
 }  // namespace
 
+// Launch of k_wgrad_halo_c8 (eight input channels, C_out = 32 or 64) with its partial
+// sums; the chunking, slicing and workspace follow wgrad_halo_launch.
+static ls_status wgrad_halo_c8_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int w, int cout, float* dwt,
+                                      float* db, cudaStream_t stream) {
+  WhArgs a = {};
+  a.w = w; a.p = w + 2; a.r = 128 / w; a.cin = 8; a.cout = cout;
+  a.cwb = cout;
+  a.n_dzb = 1;
+  a.gblocks = 1;
+  a.groups = 1;
+  const int mtiles = cout / 32;
+  a.nk = 1;
+  while (a.nk < kWhSteps && mtiles * a.nk * 2 <= kWhMaxIssuers) a.nk *= 2;
+  a.nissue = mtiles * a.nk;
+  a.idesc = tc::idesc_bf16_mn(128, 32);
+  a.tmem_cols = 32;
+  while ((int)a.tmem_cols < a.nk * mtiles * 32) a.tmem_cols <<= 1;
+  a.chunks_per_img = (h + a.r - 1) / a.r;
+  const int64_t n_chunks = (int64_t)n * a.chunks_per_img;
+  if (n_chunks > INT32_MAX / 2) return LS_ERR_UNSUPPORTED;
+  a.n_chunks = (int)n_chunks;
+  // input box: R rows of P 16-byte pixels plus one pixel of slack (the dropped kx = 3);
+  // dZ box: R + 2 rows plus one image row of slack (the dropped row block j = 3)
+  a.xbox_bytes = (uint32_t)(a.r * a.p * 16);
+  a.box_stride = (a.xbox_bytes + 16u + 1023u) & ~1023u;
+  a.dz_rowb = (uint32_t)cout * 2u;
+  a.dz_mode = cout == 64 ? 2u : 4u;
+  a.dz_blk_bytes = (uint32_t)(a.r + 2) * (uint32_t)w * a.dz_rowb;
+  a.stage_bytes = a.box_stride + ((a.dz_blk_bytes + (uint32_t)w * a.dz_rowb + 1023u) & ~1023u);
+  a.stages = (int)(kWhSmemBudget / a.stage_bytes);
+  if (a.stages > kWhMaxStages) a.stages = kWhMaxStages;
+  if (a.stages < 2) return LS_ERR_UNSUPPORTED;
+  a.part_rows = 73;  // 9 * 8 rows and the bias row
+  int64_t slices = kSmCount;
+  if (slices > n_chunks) slices = n_chunks;
+  a.chunks_per_cta = (int)((n_chunks + slices - 1) / slices);
+  slices = (n_chunks + a.chunks_per_cta - 1) / a.chunks_per_cta;
+  const size_t smem = (size_t)a.stages * a.stage_bytes;
+  CUtensorMap xmap, dzmap;
+  const uint32_t xbox[4] = {8u, (uint32_t)a.p, (uint32_t)a.r, 1u};
+  const uint32_t zbox[4] = {(uint32_t)cout, (uint32_t)w, (uint32_t)(a.r + 2), 1u};
+  const uint64_t xd[4] = {8u, (uint64_t)w, (uint64_t)h, (uint64_t)n};
+  const uint64_t xs[3] = {16u, (uint64_t)w * 16, (uint64_t)h * w * 16};
+  const uint64_t zd[4] = {(uint64_t)cout, (uint64_t)w, (uint64_t)h, (uint64_t)n};
+  const uint64_t zs[3] = {(uint64_t)cout * 2, (uint64_t)w * cout * 2, (uint64_t)h * w * cout * 2};
+  if (!encode_tmap_bf16_4d(&xmap, x, xd, xs, xbox, 0) || !encode_tmap_bf16_4d(&dzmap, dz, zd, zs, zbox, cout * 2))
+    return LS_ERR_CUDA;
+  const size_t part_bytes = (size_t)slices * a.part_rows * cout * 4;
+  uint8_t* ws = static_cast<uint8_t*>(workspace(kWsGradPart, part_bytes));
+  if (!ws) return LS_ERR_NO_MEMORY;
+  a.part = reinterpret_cast<float*>(ws);
+  a.bias = db ? 1 : 0;
+  static DeviceOnce once;
+  int dev = 0;
+  LS_CUDA_TRY(cudaGetDevice(&dev));
+  if (!device_once(once, dev, [] {
+        return cudaFuncSetAttribute(k_wgrad_halo_c8, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kWhSmemBudget) == cudaSuccess;
+      }))
+    return LS_ERR_CUDA;
+  k_wgrad_halo_c8<<<(unsigned)slices, kWhThreads, smem, stream>>>(xmap, dzmap, a);
+  k_wsum<<<(73 * cout + 31) / 32, 32 * kWsumGroups, 0, stream>>>(a.part, (int)slices, (int64_t)a.part_rows * cout, 72,
+                                                                  cout, dwt, db);
+  return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
+}
+
 // The halo form (k_wgrad_halo) when the shapes allow it; LS_ERR_UNSUPPORTED otherwise
 // (the caller falls back to the per-tap form).
 static ls_status wgrad_halo_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int w, int cin, int cout,
                                    float* dwt, float* db, cudaStream_t stream) {
-  if (cin % 32 || cout % 32 || cout > 128 || w < 16 || w > 128 || (w & (w - 1))) return LS_ERR_UNSUPPORTED;
+  const bool c8 = cin == 8 && (cout == 32 || cout == 64);
+  if ((cin % 32 && !c8) || cout % 32 || cout > 128 || w < 16 || w > 128 || (w & (w - 1))) return LS_ERR_UNSUPPORTED;
+  if (c8) return wgrad_halo_c8_launch(x, dz, n, h, w, cout, dwt, db, stream);
   WhArgs a = {};
   a.w = w; a.p = w + 2; a.r = 128 / w; a.cin = cin; a.cout = cout;
   a.cwb = cout % 64 == 0 ? 64 : 32;
@@ -561,7 +823,7 @@ static ls_status wgrad_halo_launch(const uint16_t* x, const uint16_t* dz, int n,
   a.stages = (int)(kWhSmemBudget / a.stage_bytes);
   if (a.stages > kWhMaxStages) a.stages = kWhMaxStages;
   if (a.stages < 2) return LS_ERR_UNSUPPORTED;
-  a.part_rows = (9 * cin + 127) / 128 * 128;
+  a.part_rows = 9 * cin + 1;  // the dW^T rows and the bias row
   // one CTA per SM over all groups (more than 256 TMEM columns keep a CTA alone on its
   // SM; the shared-memory request below makes sure of it); every slice non-empty
   int64_t slices = kSmCount / a.groups > 0 ? kSmCount / a.groups : 1;
@@ -579,11 +841,11 @@ static ls_status wgrad_halo_launch(const uint16_t* x, const uint16_t* dz, int n,
   const uint64_t zs[3] = {(uint64_t)cout * 2, (uint64_t)w * cout * 2, (uint64_t)h * w * cout * 2};
   if (!encode_tmap_bf16_4d(&xmap, x, xd, xs, xbox, 64) || !encode_tmap_bf16_4d(&dzmap, dz, zd, zs, zbox, a.cwb * 2))
     return LS_ERR_CUDA;
-  const size_t part_bytes = (size_t)slices * a.part_rows * cout * 4, db_bytes = (size_t)slices * cout * 4;
-  uint8_t* ws = static_cast<uint8_t*>(workspace(kWsGradPart, part_bytes + db_bytes));
+  const size_t part_bytes = (size_t)slices * a.part_rows * cout * 4;
+  uint8_t* ws = static_cast<uint8_t*>(workspace(kWsGradPart, part_bytes));
   if (!ws) return LS_ERR_NO_MEMORY;
   a.part = reinterpret_cast<float*>(ws);
-  a.dbpart = db ? reinterpret_cast<float*>(ws + part_bytes) : nullptr;
+  a.bias = db ? 1 : 0;
   static DeviceOnce once;
   int dev = 0;
   LS_CUDA_TRY(cudaGetDevice(&dev));
@@ -594,9 +856,8 @@ static ls_status wgrad_halo_launch(const uint16_t* x, const uint16_t* dz, int n,
     return LS_ERR_CUDA;
   k_wgrad_halo<<<(unsigned)(slices * a.groups), kWhThreads, smem, stream>>>(xmap, dzmap, a);
   const int rows = 9 * cin;
-  k_wsum<<<grid_cap((rows * cout + 255) / 256, kSmCount * 4), 256, 0, stream>>>(
-      a.part, (int)slices, a.part_rows / 128, rows, cout, dwt, nullptr);
-  if (db) k_dbsum<<<cout, 256, 0, stream>>>(a.dbpart, (int)slices, cout, db);
+  k_wsum<<<((rows + 1) * cout + 31) / 32, 32 * kWsumGroups, 0, stream>>>(
+      a.part, (int)slices, (int64_t)a.part_rows * cout, rows, cout, dwt, db);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 
@@ -666,8 +927,8 @@ ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int 
     return LS_ERR_CUDA;
   k_wgrad<<<(unsigned)ctas, kWgThreads, smem, stream>>>(xmap, dzmap, a);
   const bool ones = a.ones_row >= 0;
-  k_wsum<<<grid_cap(((a.rows + 1) * cout + 255) / 256, kSmCount * 4), 256, 0, stream>>>(
-      a.part, (int)slices, a.n_mtiles, a.rows, cout, dwt, ones ? db : nullptr);
+  k_wsum<<<((a.rows + 1) * cout + 31) / 32, 32 * kWsumGroups, 0, stream>>>(
+      a.part, (int)slices, (int64_t)a.n_mtiles * 128 * cout, a.rows, cout, dwt, ones ? db : nullptr);
   if (db && !ones) {
     float* dbp = reinterpret_cast<float*>(ws + part_bytes);
     const int threads = 256 - 256 % (cout / 8);  // whole pixel lanes of cout/8 threads

@@ -116,8 +116,12 @@ def test_input_gradient_via_flipped_weights(lib, shape):
 
 
 WGRAD_SHAPES = [
-    (2, 64, 64, 8, 32), (16, 4, 4, 16, 16), (2, 128, 128, 8, 16), (1, 128, 128, 48, 32),
+    (16, 4, 4, 16, 16), (2, 128, 128, 8, 16), (1, 128, 128, 48, 32),
     (2, 64, 64, 16, 48),      # per-tap form (input channels not in blocks of 32, or narrow images)
+    (2, 64, 64, 8, 32),       # eight-channel halo form: dZ rows as A, input views as B
+    (1, 9, 16, 8, 32),        # eight-channel halo form, 16-wide rows, ragged height
+    (2, 7, 32, 8, 64),        # eight-channel halo form, two M tiles (C_out = 64)
+    (1, 4, 128, 8, 64),       # eight-channel halo form, 128-wide rows
     (2, 32, 32, 32, 64),      # halo form: one block, 64 accumulator columns per tile
     (1, 16, 16, 64, 128),     # halo form, 16-wide rows, two CTA groups of one block
     (2, 32, 32, 192, 64),     # halo form, three CTA groups of two blocks (decoder concat)
