@@ -253,15 +253,17 @@ __global__ void __launch_bounds__(kWgThreads, 1)
 // partial.
 constexpr int kWhMaxIssuers = 9;
 constexpr int kWhMaxStages = 8;
-constexpr int kWhSteps = 8;  // 16-pixel steps per 128-pixel chunk
+constexpr int kWhSteps = 8;  // 16-pixel steps per 128-pixel block of a chunk
 constexpr int kWhThreads = 32 * (1 + kWhMaxIssuers + 4);
-constexpr size_t kWhSmemBudget = 224 * 1024;
+constexpr size_t kWhSmemBudget = 226 * 1024;  // with the 1 KB of static shared memory: the 227 KB limit
 
 struct WhArgs {
   float* __restrict__ part;
   int32_t bias;  // the group-0 CTAs store the bias partial as row 9 * C_in
   int32_t w, p, r, cin, cout, cwb, n_dzb, gblocks, groups, nissue, nk;
   int32_t chunks_per_img, n_chunks, chunks_per_cta, stages;
+  int32_t cp;             // chunk pixels: R * W = 128, 256 or 512
+  uint32_t a_h, b_h;      // descriptor start-address steps (16-byte units) per 128-pixel block
   uint32_t box_stride, xbox_bytes, dz_blk_bytes, dz_rowb, dz_mode, stage_bytes, idesc, tmem_cols;
   int32_t part_rows;
 };
@@ -345,11 +347,15 @@ __global__ void __launch_bounds__(kWhThreads, 1)
         if (!tc::mbar_wait(&full[slot], ph)) { abort_flag = 1; break; }
         tc::fence_after();
         const uint64_t so = (uint64_t)(((uint32_t)slot * a.stage_bytes) >> 4);
+        for (int h = 0; h < a.cp; h += 128) {  // 128-pixel blocks: R * 128 / cp rows each
+          const uint64_t sa = so + (uint64_t)((uint32_t)(h >> 7) * a.a_h);
+          const uint64_t sb = so + (uint64_t)((uint32_t)(h >> 7) * a.b_h);
 #pragma unroll
-        for (int i = 0; i < kWhSteps; ++i) {
-          if ((i & kmask) == kp) {
-            tc::mma_bf16(d, adsc[i] + so, bdsc[i] + so, idesc, acc);
-            acc = 1u;
+          for (int i = 0; i < kWhSteps; ++i) {
+            if ((i & kmask) == kp) {
+              tc::mma_bf16(d, adsc[i] + sa, bdsc[i] + sb, idesc, acc);
+              acc = 1u;
+            }
           }
         }
         tc::mma_commit(&empty[slot]);
@@ -363,7 +369,7 @@ __global__ void __launch_bounds__(kWhThreads, 1)
     float bsum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const int nch = a.cout / 8;                  // 16-byte channel chunks per pixel
     const int lanes = 128 / nch, bj = et % nch;  // pixel lanes; this thread's chunk
-    const int bl = et / nch < lanes ? et / nch : 128;  // threads past the last lane idle
+    const int bl = et / nch < lanes ? et / nch : (1 << 20);  // threads past the last lane idle
     if (bias) {
       // ---------------- bias gradient: dZ over the chunk's pixels (box rows 1 .. R),
       // channels of chunk bj, pixels bl, bl + lanes, ...
@@ -373,7 +379,7 @@ __global__ void __launch_bounds__(kWhThreads, 1)
       for (int c = c_begin; c < c_end && !abort_flag; ++c) {
         if (!tc::mbar_wait(&full[slot], ph)) { abort_flag = 1; break; }
         const uint8_t* zb = smem + (size_t)slot * a.stage_bytes + dz_off + (size_t)ob * a.dz_blk_bytes;
-        for (int px = bl; px < 128; px += lanes) {
+        for (int px = bl; px < a.cp; px += lanes) {
           const int row = a.w + px;  // box row 0 is the halo row above the chunk
           const int sc = a.cwb == 64 ? (cj ^ (row & 7)) : (cj ^ ((row >> 1) & 3));
           const uint4 v = *reinterpret_cast<const uint4*>(zb + (size_t)row * a.dz_rowb + sc * 16);
@@ -529,11 +535,15 @@ __global__ void __launch_bounds__(kWhThreads, 1)
         if (!tc::mbar_wait(&full[slot], ph)) { abort_flag = 1; break; }
         tc::fence_after();
         const uint64_t so = (uint64_t)(((uint32_t)slot * a.stage_bytes) >> 4);
+        for (int h = 0; h < a.cp; h += 128) {  // 128-pixel blocks: R * 128 / cp rows each
+          const uint64_t sa = so + (uint64_t)((uint32_t)(h >> 7) * a.a_h);
+          const uint64_t sb = so + (uint64_t)((uint32_t)(h >> 7) * a.b_h);
 #pragma unroll
-        for (int i = 0; i < kWhSteps; ++i) {
-          if ((i & kmask) == kp) {
-            tc::mma_bf16(d, adsc[i] + so, bdsc[i] + so, idesc, acc);
-            acc = 1u;
+          for (int i = 0; i < kWhSteps; ++i) {
+            if ((i & kmask) == kp) {
+              tc::mma_bf16(d, adsc[i] + sa, bdsc[i] + sb, idesc, acc);
+              acc = 1u;
+            }
           }
         }
         tc::mma_commit(&empty[slot]);
@@ -547,7 +557,7 @@ __global__ void __launch_bounds__(kWhThreads, 1)
     float bsum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const int nch = a.cout / 8;
     const int lanes = 128 / nch, bj = et % nch;
-    const int bl = et / nch < lanes ? et / nch : 128;
+    const int bl = et / nch < lanes ? et / nch : (1 << 20);
     if (bias) {
       // bias gradient: dZ over the chunk's pixels (box rows 1 .. R), as in k_wgrad_halo
       int slot = 0;
@@ -555,7 +565,7 @@ __global__ void __launch_bounds__(kWhThreads, 1)
       for (int c = c_begin; c < c_end && !abort_flag; ++c) {
         if (!tc::mbar_wait(&full[slot], ph)) { abort_flag = 1; break; }
         const uint8_t* zb = smem + (size_t)slot * a.stage_bytes + dz_off;
-        for (int px = bl; px < 128; px += lanes) {
+        for (int px = bl; px < a.cp; px += lanes) {
           const int row = a.w + px;
           const int sc = a.cwb == 64 ? (bj ^ (row & 7)) : (bj ^ ((row >> 1) & 3));
           const uint4 v = *reinterpret_cast<const uint4*>(zb + (size_t)row * a.dz_rowb + sc * 16);
@@ -718,7 +728,7 @@ __global__ void __launch_bounds__(256) k_dbsum(const float* __restrict__ part, i
 static ls_status wgrad_halo_c8_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int w, int cout, float* dwt,
                                       float* db, cudaStream_t stream) {
   WhArgs a = {};
-  a.w = w; a.p = w + 2; a.r = 128 / w; a.cin = 8; a.cout = cout;
+  a.w = w; a.p = w + 2; a.cin = 8; a.cout = cout;
   a.cwb = cout;
   a.n_dzb = 1;
   a.gblocks = 1;
@@ -730,18 +740,26 @@ static ls_status wgrad_halo_c8_launch(const uint16_t* x, const uint16_t* dz, int
   a.idesc = tc::idesc_bf16_mn(128, 32);
   a.tmem_cols = 32;
   while ((int)a.tmem_cols < a.nk * mtiles * 32) a.tmem_cols <<= 1;
+  // input box: R rows of P 16-byte pixels plus one pixel of slack (the dropped kx = 3);
+  // dZ box: R + 2 rows plus one image row of slack (the dropped row block j = 3); the
+  // chunk size as in wgrad_halo_launch
+  a.dz_rowb = (uint32_t)cout * 2u;
+  a.dz_mode = cout == 64 ? 2u : 4u;
+  for (int cp = 512; cp >= 128; cp >>= 1) {
+    a.cp = cp;
+    a.r = cp / w;
+    a.xbox_bytes = (uint32_t)(a.r * a.p * 16);
+    a.box_stride = (a.xbox_bytes + 16u + 1023u) & ~1023u;
+    a.dz_blk_bytes = (uint32_t)(a.r + 2) * (uint32_t)w * a.dz_rowb;
+    a.stage_bytes = a.box_stride + ((a.dz_blk_bytes + (uint32_t)w * a.dz_rowb + 1023u) & ~1023u);
+    if (cp == 128 || (a.r <= h && 3 * (size_t)a.stage_bytes <= kWhSmemBudget)) break;
+  }
+  a.a_h = (uint32_t)((128 / w) * w) * (a.dz_rowb >> 4);  // A: 128 / w dZ rows
+  a.b_h = (uint32_t)((128 / w) * a.p);                    // B: 128 / w input rows of P 16-byte pixels
   a.chunks_per_img = (h + a.r - 1) / a.r;
   const int64_t n_chunks = (int64_t)n * a.chunks_per_img;
   if (n_chunks > INT32_MAX / 2) return LS_ERR_UNSUPPORTED;
   a.n_chunks = (int)n_chunks;
-  // input box: R rows of P 16-byte pixels plus one pixel of slack (the dropped kx = 3);
-  // dZ box: R + 2 rows plus one image row of slack (the dropped row block j = 3)
-  a.xbox_bytes = (uint32_t)(a.r * a.p * 16);
-  a.box_stride = (a.xbox_bytes + 16u + 1023u) & ~1023u;
-  a.dz_rowb = (uint32_t)cout * 2u;
-  a.dz_mode = cout == 64 ? 2u : 4u;
-  a.dz_blk_bytes = (uint32_t)(a.r + 2) * (uint32_t)w * a.dz_rowb;
-  a.stage_bytes = a.box_stride + ((a.dz_blk_bytes + (uint32_t)w * a.dz_rowb + 1023u) & ~1023u);
   a.stages = (int)(kWhSmemBudget / a.stage_bytes);
   if (a.stages > kWhMaxStages) a.stages = kWhMaxStages;
   if (a.stages < 2) return LS_ERR_UNSUPPORTED;
@@ -787,7 +805,7 @@ static ls_status wgrad_halo_launch(const uint16_t* x, const uint16_t* dz, int n,
   if ((cin % 32 && !c8) || cout % 32 || cout > 128 || w < 16 || w > 128 || (w & (w - 1))) return LS_ERR_UNSUPPORTED;
   if (c8) return wgrad_halo_c8_launch(x, dz, n, h, w, cout, dwt, db, stream);
   WhArgs a = {};
-  a.w = w; a.p = w + 2; a.r = 128 / w; a.cin = cin; a.cout = cout;
+  a.w = w; a.p = w + 2; a.cin = cin; a.cout = cout;
   a.cwb = cout % 64 == 0 ? 64 : 32;
   a.n_dzb = cout / a.cwb;
   const int cblocks = cin / 32;
@@ -808,18 +826,29 @@ static ls_status wgrad_halo_launch(const uint16_t* x, const uint16_t* dz, int n,
   a.idesc = tc::idesc_bf16_mn(128, 3 * a.cwb);
   a.tmem_cols = 32;
   while ((int)a.tmem_cols < a.nk * a.gblocks * 3 * cout) a.tmem_cols <<= 1;
+  // input box: R rows of P pixels of 64 bytes, plus one pixel row of slack for the
+  // dropped block kx = 3, rounded up to the 1024-byte swizzle alignment; dZ boxes of
+  // R + 2 rows (a multiple of 1024 bytes: w >= 16).  The chunk is the largest of 512,
+  // 256 and 128 pixels (rows within the image) with three stages in shared memory: a
+  // TMA unit keeps a bounded number of boxes in flight, so larger boxes stream faster,
+  // and the dZ halo rows are a smaller share.
+  a.dz_rowb = (uint32_t)a.cwb * 2u;
+  a.dz_mode = a.cwb == 64 ? 2u : 4u;
+  for (int cp = 512; cp >= 128; cp >>= 1) {
+    a.cp = cp;
+    a.r = cp / w;
+    a.xbox_bytes = (uint32_t)(a.r * a.p * 64);
+    a.box_stride = (a.xbox_bytes + 64u + 1023u) & ~1023u;
+    a.dz_blk_bytes = (uint32_t)(a.r + 2) * (uint32_t)w * a.dz_rowb;
+    a.stage_bytes = (uint32_t)a.gblocks * a.box_stride + (uint32_t)a.n_dzb * a.dz_blk_bytes;
+    if (cp == 128 || (a.r <= h && 3 * (size_t)a.stage_bytes <= kWhSmemBudget)) break;
+  }
+  a.a_h = (uint32_t)((128 / w) * a.p * 4);                    // 128 / w input rows of P 64-byte pixels
+  a.b_h = (uint32_t)((128 / w) * w) * (a.dz_rowb >> 4);       // 128 / w dZ rows
   a.chunks_per_img = (h + a.r - 1) / a.r;
   const int64_t n_chunks = (int64_t)n * a.chunks_per_img;
   if (n_chunks > INT32_MAX / 2) return LS_ERR_UNSUPPORTED;
   a.n_chunks = (int)n_chunks;
-  // input box: R rows of P pixels of 64 bytes, plus one pixel row of slack for the
-  // dropped block kx = 3, rounded up to the 1024-byte swizzle alignment
-  a.xbox_bytes = (uint32_t)(a.r * a.p * 64);
-  a.box_stride = (a.xbox_bytes + 64u + 1023u) & ~1023u;
-  a.dz_rowb = (uint32_t)a.cwb * 2u;
-  a.dz_mode = a.cwb == 64 ? 2u : 4u;
-  a.dz_blk_bytes = (uint32_t)(a.r + 2) * (uint32_t)w * a.dz_rowb;  // a multiple of 1024 (w >= 16)
-  a.stage_bytes = (uint32_t)a.gblocks * a.box_stride + (uint32_t)a.n_dzb * a.dz_blk_bytes;
   a.stages = (int)(kWhSmemBudget / a.stage_bytes);
   if (a.stages > kWhMaxStages) a.stages = kWhMaxStages;
   if (a.stages < 2) return LS_ERR_UNSUPPORTED;
