@@ -1,10 +1,17 @@
 // Weight and bias gradients of a 3x3 convolution on the tensor cores (training of the
 // learned filler, Sec. 3.4).  dW^T[k][o] = sum_p X_shift(k)[p] dZ[p][o] with
-// k = tap * C_in + c_in: a GEMM with M = 9*C_in (tiles of 128 rows), N = C_out and
-// K = pixels (64 per stage).  Each CTA owns one 128-row tile and one slice of pixels
-// and stores its partial sums; k_wsum adds them to the FP32 gradient in a fixed order,
-// so the result does not depend on CTA scheduling (training is reproducible).
+// k = tap * C_in + c_in: a GEMM with M = 9*C_in, N = C_out and K = pixels.  Three forms:
+//  k_wgrad_halo     input channels in blocks of 32, images 16..128 wide: one input box
+//                   per chunk of rows serves all nine taps (ky as dZ row shifts in N,
+//                   kx as input pixel shifts in M);
+//  k_wgrad_halo_c8  eight input channels: the same with the operands swapped;
+//  k_wgrad          the per-tap form below for every other shape.
+// Each CTA stores the partial sums of its slice of pixels; k_wsum adds them to the FP32
+// gradient in a fixed order, so the result does not depend on CTA scheduling (training
+// is reproducible).
 //
+// Per-tap form: M tiles of 128 rows, K = 64 pixels per stage; each CTA owns one tile
+// and one slice of pixels.
 // Both operands are stored pixel-minor (NHWC): for a pixel (the GEMM's K index) the
 // channels (its M or N index) are contiguous.  That is the MN-major operand layout, so
 // the MMA reads the TMA boxes as they land, with no transposition:
