@@ -1101,16 +1101,18 @@ def run_learned_case(args):
 
 
 def run_conv_case(args):
-    """Profiling case: layer d1a of the learned filler (64x64, 96 -> 32 channels, bias,
-    ReLU) on --case-tiles tiles of seeded N(0,1) inputs, three warm-up launches and a
-    fourth (the one to profile) through the C-ABI convolution."""
+    """Profiling case: the forward convolution of one learned-filler layer (--case-layer,
+    default d1a: 64x64, 96 -> 32 channels; bias, ReLU) on --case-tiles tiles of seeded
+    N(0,1) inputs, three warm-up launches and a fourth (the one to profile) through the
+    C-ABI convolution."""
     import ctypes
     import torch
     from paper_2509_20198_b300 import _native as N
     from paper_2509_20198_b300 import build
     build.build_library()
     L = N.lib()
-    n, s, cin, cout = args.case_tiles, 64, 96, 32
+    s, cin, cout = UNET_LAYERS[args.case_layer]
+    n = args.case_tiles
     g = torch.Generator(device="cuda").manual_seed(0)
     x = torch.randn(n * s * s * cin, device="cuda", generator=g).to(torch.bfloat16)
     w = torch.randn(cout, 3, 3, cin, device="cuda", generator=g) * 0.05
@@ -1128,7 +1130,7 @@ def run_conv_case(args):
         if st:
             break
     torch.cuda.synchronize()
-    print(json.dumps({"case": "conv", "layer": "d1a", "tiles": n, "status": int(st)}))
+    print(json.dumps({"case": "conv", "layer": args.case_layer, "tiles": n, "status": int(st)}))
     return 0 if st == 0 else 1
 
 
@@ -1217,7 +1219,7 @@ def main():
                                                    "paper-cnn", "conv", "learned-fill", "wgrad"],
                     help="profiling case instead of the bench")
     ap.add_argument("--case-tiles", type=int, default=3, help="tiles per side of the profiling case")
-    ap.add_argument("--case-layer", default="d1a", choices=sorted(UNET_LAYERS), help="layer of the wgrad case")
+    ap.add_argument("--case-layer", default="d1a", choices=sorted(UNET_LAYERS), help="layer of the conv and wgrad cases")
     ap.add_argument("--train-tiles", type=int, default=20000, help="training pairs of the learned filler")
     ap.add_argument("--train-epochs", type=int, default=24)
     ap.add_argument("--cnn-tiles", type=int, default=4096, help="training pairs of the paper's network variant")

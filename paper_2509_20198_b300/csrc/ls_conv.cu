@@ -312,7 +312,8 @@ constexpr int kHaloMaxPipes = 4;
 constexpr int kHaloRingMax = 8;  // ring slots declared per pipeline
 constexpr int kHaloRingUse = 4;  // boxes per pipeline a launch uses at most (as many as fit)
 constexpr int kHaloThreadsPerPipe = 192;
-constexpr size_t kHaloSmemBudget = 224 * 1024;
+constexpr size_t kHaloSmemBudget = 223 * 1024;  // + the static bias and head copies: the 227 KB limit
+constexpr int kHaloMaxCout = 64;                 // four pipelines of two accumulators
 
 struct HaloArgs {
   const uint16_t* __restrict__ wpk;
@@ -341,8 +342,14 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
   __shared__ __align__(8) uint64_t tfull[kHaloMaxPipes][2], tempty[kHaloMaxPipes][2], wbar;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
+  // the epilogue's bias and head weights, read from shared memory instead of one global
+  // load per element and pixel
+  __shared__ float s_bias[kHaloMaxCout], s_head[8 * kHaloMaxCout + 8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = warp / 6, role = warp - g * 6;  // pipeline and role within it
+  for (int i = threadIdx.x; i < a.cout; i += blockDim.x) s_bias[i] = a.bias ? a.bias[i] : 0.f;
+  if (a.head)
+    for (int i = threadIdx.x; i < a.head_out * (a.cout + 1); i += blockDim.x) s_head[i] = a.head[i];
   uint8_t* wsm = smem;                          // packed weights (a.wbytes)
   uint8_t* boxes = smem + ((a.wbytes + 1023u) & ~1023u);  // 1024-aligned: the swizzle atoms
   if (threadIdx.x == 0) {
@@ -463,22 +470,35 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
       float hacc[8];
       if (a.head) {
 #pragma unroll
-        for (int o = 0; o < 8; ++o) hacc[o] = o < a.head_out ? __ldg(a.head + a.head_out * a.cout + o) : 0.f;
+        for (int o = 0; o < 8; ++o) hacc[o] = o < a.head_out ? s_head[a.head_out * a.cout + o] : 0.f;
       }
-      for (int c0 = 0; c0 < a.cout; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * 2 + acc) * a.acc_cols + (uint32_t)c0, v);
-        if (real) {
+      for (int c32 = 0; c32 < a.cout; c32 += 32) {
+        // 32 accumulator columns with one wait (columns past cout are inside acc_cols)
+        float v32[32];
+        tc::tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * 2 + acc) * a.acc_cols + (uint32_t)c32,
+                      v32);
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int c0 = c32 + hh * 16;
+          if (c0 >= a.cout || !real) continue;
+          float v[16];
+          if (a.bias) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = v32[hh * 16 + i] + s_bias[c0 + i];
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = v32[hh * 16 + i];
+          }
           const int gi = c0 / a.ygroup;
           uint16_t* yp = a.y ? a.y + ((int64_t)gi * a.ygstride + (int64_t)pix * a.ygroup + (c0 - gi * a.ygroup))
                              : nullptr;
           if (!a.head) {
-            epilogue16(v, a.bias ? a.bias + c0 : nullptr, a.relu, mp ? mp + c0 : nullptr, yp);
+            epilogue16(v, nullptr, a.relu, mp ? mp + c0 : nullptr, yp);
           } else {
-            // bias and ReLU, then the head over the values the BF16 output holds, channel
-            // by channel in order (the arithmetic of the separate 1x1 head)
+            // ReLU, then the head over the values the BF16 output holds, channel by
+            // channel in order (the arithmetic of the separate 1x1 head)
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + (a.bias ? __ldg(a.bias + c0 + i) : 0.f), 0.f);
+            for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
             uint4 o0, o1;
             round_bf16_16(v, o0, o1);
             if (a.store_y) {
@@ -488,9 +508,9 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
 #pragma unroll
             for (int o = 0; o < 8; ++o) {
               if (o >= a.head_out) break;
-              const float* hw = a.head + o * a.cout + c0;
+              const float* hw = s_head + o * a.cout + c0;
 #pragma unroll
-              for (int i = 0; i < 16; ++i) hacc[o] = fmaf(v[i], __ldg(hw + i), hacc[o]);
+              for (int i = 0; i < 16; ++i) hacc[o] = fmaf(v[i], hw[i], hacc[o]);
             }
           }
         }
