@@ -151,7 +151,9 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   __shared__ volatile int abort_flag;
   // per TMA load of a tile: channel offset | (kx << 16) | (ky << 20), in load order
   __shared__ uint32_t ktab[kMaxLoads];
+  __shared__ float s_bias[256];  // the epilogue's bias (C_out <= 256)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < a.cout; i += blockDim.x) s_bias[i] = a.bias ? a.bias[i] : 0.f;
   const int n_loads = a.cw == 8 ? a.kc : a.n_blocks;
   for (int i = threadIdx.x; i < n_loads; i += blockDim.x) {
     int ci, tap;
@@ -272,12 +274,27 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       tc::fence_after();
       const size_t pix = (size_t)m * 128 + row;
       const uint16_t* mp = a.mask ? a.mask + pix * a.cout : nullptr;
-      for (int c0 = 0; c0 < a.cout; c0 += 16) {
-        const int g = c0 / a.ygroup;
-        uint16_t* yp = a.y + ((int64_t)g * a.ygstride + (int64_t)pix * a.ygroup + (c0 - g * a.ygroup));
-        float v[16];
-        tc::tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * a.acc_cols + (uint32_t)c0, v);
-        epilogue16(v, a.bias ? a.bias + c0 : nullptr, a.relu, mp ? mp + c0 : nullptr, yp);
+      for (int c32 = 0; c32 < a.cout; c32 += 32) {
+        // 32 accumulator columns with one wait (columns past cout are inside acc_cols, a
+        // power of two >= 32)
+        float v32[32];
+        tc::tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * a.acc_cols + (uint32_t)c32, v32);
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int c0 = c32 + hh * 16;
+          if (c0 >= a.cout) break;
+          const int g = c0 / a.ygroup;
+          uint16_t* yp = a.y + ((int64_t)g * a.ygstride + (int64_t)pix * a.ygroup + (c0 - g * a.ygroup));
+          float v[16];
+          if (a.bias) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = v32[hh * 16 + i] + s_bias[c0 + i];
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = v32[hh * 16 + i];
+          }
+          epilogue16(v, nullptr, a.relu, mp ? mp + c0 : nullptr, yp);
+        }
       }
       tc::fence_before();
       tc::mbar_arrive(&tempty[acc]);
