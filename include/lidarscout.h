@@ -364,7 +364,9 @@ ls_status ls_cnn_layer_info(const ls_cnn *model, int32_t layer, int32_t *kind, i
 ls_status ls_cnn_load(ls_cnn *model, const float *params, ls_stream_t stream);
 ls_status ls_cnn_forward(ls_cnn *model, const float *params, const uint16_t *x, int32_t n, float *y,
                          ls_stream_t stream);
-/* grads (fp32, n_params) = dL/dparams given dy = dL/dy of the last forward. */
+/* grads (fp32, n_params) = dL/dparams given dy = dL/dy of the last forward.  Reads the
+ * x of that forward again (the first layers' weight gradients): the caller keeps it
+ * unchanged until this call. */
 ls_status ls_cnn_backward(ls_cnn *model, const float *params, const float *dy, int32_t n, float *grads,
                           ls_stream_t stream);
 /* Network input from the Alg. 1 maps of n patches (lin/nn height float [n][res][res]
@@ -522,7 +524,8 @@ ls_status ls_model_load(ls_model *model, const float *params, ls_stream_t stream
 ls_status ls_filler_forward(ls_model *model, const float *params, const uint16_t *x, int32_t n,
                             float *y, ls_stream_t stream);
 /* Gradients of all parameters (overwrites grads, flat fp32 like params) given
- * dL/dy of the last forward call (same n). */
+ * dL/dy of the last forward call (same n).  Reads the x of that forward again (the
+ * first layer's weight gradient): the caller keeps it unchanged until this call. */
 ls_status ls_filler_backward(ls_model *model, const float *params, const float *dy, int32_t n,
                              float *grads, ls_stream_t stream);
 /* Loss of Sec. 3.4: masked MSE of height and colour (each squared error clipped to 1),

@@ -446,6 +446,9 @@ class FillerFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, params, x, filler):
         ctx.filler = filler
+        # the native backward reads the input of this forward (the first layer's weight
+        # gradient): keep the tensor alive until then, or its memory may be reused
+        ctx.x = x
         filler.load()
         return filler.forward(x)
 
@@ -511,6 +514,7 @@ class PaperCNNFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, params, x, cnn):
         ctx.cnn = cnn
+        ctx.x = x  # read again by the native backward (see FillerFn)
         cnn.load()
         return cnn.forward(x)
 

@@ -87,35 +87,64 @@ LR = 1e-3  # learning rate of the short synthetic schedules (the paper: 1e-4 ove
 
 
 def train(filler: Filler, data: TileSet, epochs=20, batch=256, lr=LR, weight_decay=1e-2, betas=(0.9, 0.999),
-          eps=1e-5, milestones=(0.6, 0.85), gamma=0.1, bound_weight=1.0, seed=0, log=None):
+          eps=1e-5, milestones=(0.6, 0.85), gamma=0.1, bound_weight=1.0, seed=0, log=None, graph=None):
     """AdamW training with a step schedule; returns the per-epoch mean losses
     [total, height, colour, bound].  The bound channel learns the excess of the learned
     height's error over the Gaussian fill's (the finish step falls back to the Gaussian
-    fill where that predicted excess is large)."""
+    fill where that predicted excess is large).
+
+    graph (default: on CUDA with more than one step): after one eager step, the batch
+    gather, forward, loss and backward of a step run as one captured CUDA graph on
+    static buffers (about 200 launches a step otherwise leave the eager loop bound by the
+    host); AdamW, whose step count and rate change every step, stays outside.  The
+    kernels and their order are those of the eager step, so the results are identical."""
     g = torch.Generator(device="cpu").manual_seed(seed)
     p = filler.params
     m = torch.zeros_like(p)
     v = torch.zeros_like(p)
     steps_per_epoch = max(1, len(data) // batch)
     total = epochs * steps_per_epoch
+    if graph is None:
+        graph = p.is_cuda and total > 1
     step = 0
     history = []
+    idx_s = torch.empty(min(batch, len(data)), dtype=torch.int64, device=p.device)  # the graph's batch indices
+    cap = None
+
+    def forward_backward(idx):
+        x = data.x[idx].contiguous()
+        params = p.detach().requires_grad_(True)
+        y = FillerFn.apply(params, x, filler)
+        loss = FillerLossFn.apply(y, data.base[idx].contiguous(), data.target[idx].contiguous(),
+                                  data.mask[idx].contiguous(), bound_weight, True)
+        loss[0].backward()
+        return loss.detach(), params.grad
+
     for ep in range(epochs):
         order = torch.randperm(len(data), generator=g).to(p.device)
         acc = torch.zeros(4, device=p.device)
         for k in range(steps_per_epoch):
             idx = order[k * batch:(k + 1) * batch]
-            x = data.x[idx].contiguous()
-            params = p.detach().requires_grad_(True)
-            y = FillerFn.apply(params, x, filler)
-            loss = FillerLossFn.apply(y, data.base[idx].contiguous(), data.target[idx].contiguous(),
-                                      data.mask[idx].contiguous(), bound_weight, True)
-            loss[0].backward()
+            if graph and step > 0:
+                if cap is None:
+                    # capture once (the eager first step made every workspace and setting)
+                    cap = torch.cuda.CUDAGraph()
+                    side = torch.cuda.Stream()
+                    side.wait_stream(torch.cuda.current_stream())
+                    with torch.cuda.stream(side):
+                        with torch.cuda.graph(cap):
+                            loss_s, grad_s = forward_backward(idx_s)
+                    torch.cuda.current_stream().wait_stream(side)
+                idx_s.copy_(idx)
+                cap.replay()
+                loss, grad = loss_s, grad_s
+            else:
+                loss, grad = forward_backward(idx)
             step += 1
             frac = step / total
             cur = lr * (gamma ** sum(frac > mm for mm in milestones))
-            adamw_step(p, params.grad, m, v, step, lr=cur, betas=betas, eps=eps, weight_decay=weight_decay)
-            acc += loss.detach()
+            adamw_step(p, grad, m, v, step, lr=cur, betas=betas, eps=eps, weight_decay=weight_decay)
+            acc += loss
         history.append([float(v) / steps_per_epoch for v in acc.tolist()])
         if log:
             log(f"epoch {ep + 1}/{epochs} loss {history[-1]}")
@@ -229,31 +258,54 @@ def synthetic_patches(n_tiles, seed0, res=128, block=16, density=(3.0, 6.0), dev
 
 
 def train_cnn(cnn: PaperCNN, data: PatchSet, epochs=20, batch=256, lr=1e-3, weight_decay=1e-2, betas=(0.9, 0.999),
-              eps=1e-5, milestones=(0.6, 0.85), gamma=0.1, bound_weight=1.0, seed=0, log=None):
+              eps=1e-5, milestones=(0.6, 0.85), gamma=0.1, bound_weight=1.0, seed=0, log=None, graph=None):
     """AdamW with a step schedule (Sec. 3.4) on the library's kernels; the outputs are
     the patch-space height and colours directly (zero base).  Returns per-epoch mean
-    losses [total, height, colour, bound]."""
+    losses [total, height, colour, bound].  graph: the step after the first runs as a
+    captured CUDA graph, as in train()."""
     g = torch.Generator(device="cpu").manual_seed(seed)
     p = cnn.params
     m, v = torch.zeros_like(p), torch.zeros_like(p)
     base = torch.zeros((batch,) + tuple(data.target.shape[1:]), dtype=torch.float32, device=p.device)
     steps_per_epoch = max(1, len(data) // batch)
     total = epochs * steps_per_epoch
+    if graph is None:
+        graph = p.is_cuda and total > 1
     step, history = 0, []
+    idx_s = torch.empty(min(batch, len(data)), dtype=torch.int64, device=p.device)
+    cap = None
+
+    def forward_backward(idx):
+        params = p.detach().requires_grad_(True)
+        y = PaperCNNFn.apply(params, data.x[idx].contiguous(), cnn)
+        loss = FillerLossFn.apply(y, base, data.target[idx].contiguous(), data.mask[idx].contiguous(),
+                                  bound_weight)
+        loss[0].backward()
+        return loss.detach(), params.grad
+
     for ep in range(epochs):
         order = torch.randperm(len(data), generator=g).to(p.device)
         acc = torch.zeros(4, device=p.device)
         for k in range(steps_per_epoch):
             idx = order[k * batch:(k + 1) * batch]
-            params = p.detach().requires_grad_(True)
-            y = PaperCNNFn.apply(params, data.x[idx].contiguous(), cnn)
-            loss = FillerLossFn.apply(y, base, data.target[idx].contiguous(), data.mask[idx].contiguous(),
-                                      bound_weight)
-            loss[0].backward()
+            if graph and step > 0:
+                if cap is None:
+                    cap = torch.cuda.CUDAGraph()
+                    side = torch.cuda.Stream()
+                    side.wait_stream(torch.cuda.current_stream())
+                    with torch.cuda.stream(side):
+                        with torch.cuda.graph(cap):
+                            loss_s, grad_s = forward_backward(idx_s)
+                    torch.cuda.current_stream().wait_stream(side)
+                idx_s.copy_(idx)
+                cap.replay()
+                loss, grad = loss_s, grad_s
+            else:
+                loss, grad = forward_backward(idx)
             step += 1
             cur = lr * (gamma ** sum(step / total > mm for mm in milestones))
-            adamw_step(p, params.grad, m, v, step, lr=cur, betas=betas, eps=eps, weight_decay=weight_decay)
-            acc += loss.detach()
+            adamw_step(p, grad, m, v, step, lr=cur, betas=betas, eps=eps, weight_decay=weight_decay)
+            acc += loss
         history.append([float(v) / steps_per_epoch for v in acc.tolist()])
         if log:
             log(f"epoch {ep + 1}/{epochs} loss {history[-1]}")

@@ -163,3 +163,21 @@ def test_adamw_steps_reduce_the_loss(lsb):
         losses.append(float(loss[0]))
     assert lsb.last_error() == 0
     assert losses[-1] < 0.5 * losses[0], losses
+
+
+def test_graph_captured_cnn_training_is_bit_identical_to_eager(lsb):
+    """train_cnn with the step captured as a CUDA graph (after one eager step) against
+    the eager loop: identical parameters and losses after two epochs."""
+    import torch
+    from paper_2509_20198_b300 import train as T
+    data = T.synthetic_patches(64, seed0=310, res=128, block=4)
+    out = []
+    for graph in (False, True):
+        cnn = lsb.PaperCNN(res=128, max_batch=16)
+        T.init_cnn_params(cnn, seed=7)
+        hist = T.train_cnn(cnn, data, epochs=2, batch=16, lr=T.LR, graph=graph)
+        torch.cuda.synchronize()
+        assert lsb.last_error() == 0
+        out.append((cnn.params.clone(), hist))
+    assert torch.equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]

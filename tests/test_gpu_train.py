@@ -34,6 +34,25 @@ def test_fillerfn_gradient_equals_native_backward(lsb):
     assert torch.equal(p.grad, g2)
 
 
+def test_graph_captured_training_step_is_bit_identical_to_eager(lsb):
+    """The captured step (gather, forward, loss, backward as one CUDA graph, AdamW
+    outside) replays the eager step's kernels in the same order: after several steps
+    and an epoch boundary the parameters and losses are bit-identical."""
+    import torch
+    from paper_2509_20198_b300 import train as T
+    data = T.synthetic_tiles(96, seed0=300)
+    out = []
+    for graph in (False, True):
+        f = lsb.Filler(max_batch=32)
+        T.init_params(f, seed=5)
+        hist = T.train(f, data, epochs=2, batch=32, lr=T.LR, graph=graph)
+        torch.cuda.synchronize()
+        assert lsb.last_error() == 0
+        out.append((f.params.clone(), hist))
+    assert torch.equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+
+
 def test_training_beats_gaussian_fill_on_held_out_tiles(lsb):
     import torch
     from paper_2509_20198_b300 import train as T
@@ -56,3 +75,31 @@ def test_training_beats_gaussian_fill_on_held_out_tiles(lsb):
     # the 2 m fallback replaces only tiles whose predicted excess error over the Gaussian
     # fill is large, so it must not make the learned fill worse
     assert after["height_rmse_with_fallback_m"] <= after["height_rmse_learned_m"]
+
+
+def test_backward_reads_the_forward_input_even_when_the_caller_dropped_it(lsb):
+    """The native backward reads the forward's input again (first-layer weight
+    gradients).  Through FillerFn / PaperCNNFn a temporary input stays alive until the
+    backward: freeing it and reusing its memory (here: filled with NaN) before the
+    backward must not change the gradients."""
+    import torch
+    from paper_2509_20198_b300 import train as T
+    f = lsb.Filler(max_batch=4)
+    T.init_params(f, seed=11)
+    f.params[-5:] = 0.01
+    cnn = lsb.PaperCNN(res=128, max_batch=2)
+    T.init_cnn_params(cnn, seed=12)
+    for net, fn, shape in ((f, lsb.FillerFn, (4, 64, 64, 8)), (cnn, lsb.PaperCNNFn, (2, 128, 128, 8))):
+        xk = torch.zeros(shape, dtype=torch.int16, device="cuda")
+        xk[..., :5] = torch.rand(shape[:3] + (5,), device="cuda").to(torch.bfloat16).view(torch.int16)
+        grads = []
+        for keep in (True, False):
+            p = net.params.detach().requires_grad_(True)
+            y = fn.apply(p, xk if keep else xk.clone(), net)    # the clone is dropped at once
+            junk = torch.full(shape, 0x7FC0, dtype=torch.int16, device="cuda")  # the freed block, bf16 NaN
+            w = torch.linspace(-1.0, 1.0, y.numel(), device="cuda").view_as(y)
+            (y * w).sum().backward()
+            del junk
+            grads.append(p.grad.clone())
+        assert torch.isfinite(grads[0]).all()
+        assert torch.equal(grads[0], grads[1])
