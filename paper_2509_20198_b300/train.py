@@ -314,13 +314,17 @@ def train_cnn(cnn: PaperCNN, data: PatchSet, epochs=20, batch=256, lr=1e-3, weig
 
 
 def init_cnn_params(cnn: PaperCNN, seed=0):
-    """He-normal weights, zero biases; the head starts at zero."""
+    """He-normal weights, zero biases; the head starts at zero.  The fully connected
+    merge layers start at half the He scale: at full scale the four encoders' merged
+    features kept the height loss on a plateau through the short schedule (held-out
+    height loss 1.5e-3 after 30 epochs at lr 1e-3, against 7.4e-5 at half scale)."""
     g = torch.Generator(device="cpu").manual_seed(seed)
     flat = torch.zeros(cnn.n_params)
     for kind, cin, cout, w_off, b_off in cnn.layers():
         if kind == 2:
             continue
         fan = cin * (9 if kind == 0 else 1)
-        flat[w_off:w_off + cout * fan] = torch.randn(cout * fan, generator=g) * math.sqrt(2.0 / fan)
+        scale = math.sqrt(2.0 / fan) * (0.5 if kind == 1 else 1.0)
+        flat[w_off:w_off + cout * fan] = torch.randn(cout * fan, generator=g) * scale
     cnn.params.copy_(flat.to(cnn.params.device))
     cnn.load()
