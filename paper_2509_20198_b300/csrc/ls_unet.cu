@@ -240,6 +240,80 @@ __global__ void __launch_bounds__(kHeadThreads) k_head_bwd(const uint16_t* __res
   }
 }
 
+// The same in one pass over the pixels when the c / 8 channel groups are a power of two
+// up to 32: G = c / 8 neighbouring threads take the groups of one pixel (a warp reads
+// 32 / G whole pixels: contiguous 16-byte loads and stores), dy is read once, and each
+// thread keeps the kOut x 8 weight-gradient terms of its group.  The lanes of a group
+// are combined with xor shuffles, the warps in order in shared memory: a fixed order.
+__global__ void __launch_bounds__(kHeadThreads) k_head_bwd_g(const uint16_t* __restrict__ top, int c,
+                                                             const float* __restrict__ wb,
+                                                             const float* __restrict__ dy, int64_t P,
+                                                             uint16_t* __restrict__ dtop,
+                                                             float* __restrict__ part /* [blocks][kOut*c + kOut] */) {
+  extern __shared__ float sh[];  // weights [kOut*c], per-warp partial grads [warps][kOut*c + kOut]
+  const int ng = kOut * c + kOut, nw = blockDim.x / 32, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int G = c / 8, g = threadIdx.x & (G - 1);
+  float* sw = sh;
+  float* sg = sh + kOut * c + warp * ng;
+  for (int i = threadIdx.x; i < kOut * c; i += blockDim.x) sw[i] = wb[i];
+  __syncthreads();
+  float gacc[kOut * 8], gb[kOut];
+#pragma unroll
+  for (int i = 0; i < kOut * 8; ++i) gacc[i] = 0.f;
+#pragma unroll
+  for (int k = 0; k < kOut; ++k) gb[k] = 0.f;
+  const int64_t per_iter = (int64_t)gridDim.x * (blockDim.x / G);
+  for (int64_t p = blockIdx.x * (int64_t)(blockDim.x / G) + threadIdx.x / G; p < P; p += per_iter) {
+    float d[kOut], v[8], o[8];
+#pragma unroll
+    for (int k = 0; k < kOut; ++k) d[k] = dy[p * kOut + k];
+    unpack8(*reinterpret_cast<const uint4*>(top + p * c + g * 8), v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < kOut; ++k) {
+        s = fmaf(d[k], sw[k * c + g * 8 + i], s);
+        gacc[k * 8 + i] = fmaf(d[k], v[i], gacc[k * 8 + i]);
+      }
+      o[i] = v[i] > 0.f ? s : 0.f;
+    }
+    *reinterpret_cast<uint4*>(dtop + p * c + g * 8) = pack8(o);
+    if (g == 0) {
+#pragma unroll
+      for (int k = 0; k < kOut; ++k) gb[k] += d[k];
+    }
+  }
+  // lanes with the same group: lane = g + G * j; xor over G, 2G, ..., 16
+#pragma unroll
+  for (int i = 0; i < kOut * 8; ++i) {
+    float s = gacc[i];
+    for (int off = 16; off >= G; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    gacc[i] = s;
+  }
+#pragma unroll
+  for (int k = 0; k < kOut; ++k) {
+    float s = gb[k];  // only the g == 0 lanes hold nonzero terms
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    gb[k] = s;
+  }
+  if (lane < G) {
+#pragma unroll
+    for (int k = 0; k < kOut; ++k)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) sg[k * c + g * 8 + i] = gacc[k * 8 + i];
+  }
+  if (lane == 0)
+    for (int k = 0; k < kOut; ++k) sg[kOut * c + k] = gb[k];
+  __syncthreads();
+  const float* all = sh + kOut * c;
+  for (int i = threadIdx.x; i < ng; i += blockDim.x) {
+    float s = 0.f;
+    for (int w = 0; w < nw; ++w) s += all[w * ng + i];
+    part[(size_t)blockIdx.x * ng + i] = s;
+  }
+}
+
 // grads of the head += its per-block partials: one block per element, thread t sums
 // blocks t, t + 256, ... in order, then a fixed-shape tree over the threads
 __global__ void __launch_bounds__(256) k_head_sum(const float* __restrict__ part, int blocks, int ng,
@@ -723,7 +797,11 @@ extern "C" ls_status ls_filler_backward(ls_model* m, const float* params, const 
     float* part = static_cast<float*>(workspace(kWsHeadPart, (size_t)blocks * ng * 4));
     if (!part) return LS_ERR_NO_MEMORY;
     const size_t smem = (size_t)(kOut * hd.cin + (kHeadThreads / 32) * ng) * 4;
-    k_head_bwd<<<blocks, kHeadThreads, smem, s>>>(out_of(nl - 2), hd.cin, params + hd.w_off, dy, P, gz, part);
+    const int G = hd.cin / 8;
+    if (hd.cin % 8 == 0 && G <= 32 && (G & (G - 1)) == 0)
+      k_head_bwd_g<<<blocks, kHeadThreads, smem, s>>>(out_of(nl - 2), hd.cin, params + hd.w_off, dy, P, gz, part);
+    else
+      k_head_bwd<<<blocks, kHeadThreads, smem, s>>>(out_of(nl - 2), hd.cin, params + hd.w_off, dy, P, gz, part);
     k_head_sum<<<ng, 256, 0, s>>>(part, blocks, ng, grads + hd.w_off);
   }
   int li = nl - 2;  // d1b
