@@ -418,17 +418,43 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
       }
     }
   } else if (role == 1 && lane == 0) {
-    // ---------------- MMA issuer of pipeline g
+    // ---------------- MMA issuer of pipeline g.  A descriptor is linear in its start
+    // address (16-byte units in the low bits), so the taps' descriptors are a base plus
+    // offsets computed once: one thread's dependent integer work per MMA is what limits
+    // the issue rate, not the tensor core.
     if (!tc::mbar_wait(&wbar, 0)) abort_flag = 1;
     tc::fence_after();
     const uint32_t wb = tc::saddr(wsm), rb = tc::saddr(ring);
     const uint32_t chunkb = (uint32_t)a.cout * 16u;  // one packed chunk: C_out rows x 8 K
+    uint64_t a0[9], b0[9];
+    if (a.cw == 8) {
+      // one 8-channel block (C_in = 8): chunk c is tap c, so a K=16 MMA takes taps 2i
+      // and 2i + 1 (the second 8 K-elements LBO bytes after the first); tap 9 is the zero
+      // chunk of the pack, read against tap 8's rows
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        const int t0 = 2 * i, t1 = t0 + 1 < 9 ? t0 + 1 : t0;
+        const int r0 = (t0 / 3) * a.p + (t0 % 3), r1 = (t1 / 3) * a.p + (t1 % 3);
+        a0[i] = tc::sdesc(rb + (uint32_t)r0 * 16u, (uint32_t)(r1 - r0) * 16u, 128);
+        b0[i] = tc::sdesc(wb + (uint32_t)t0 * chunkb, chunkb, 128);
+      }
+    } else {
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        a0[tap] = tc::sdesc_sw(rb + (uint32_t)((tap / 3) * a.p + (tap % 3)) * a.rowb, 8u * a.rowb, a.swz);
+        b0[tap] = tc::sdesc(wb + (uint32_t)(tap * a.cpt) * chunkb, chunkb, 128);
+      }
+    }
+    const uint32_t bstep = (2u * chunkb) >> 4;                        // next 16 K in B
+    const uint32_t bblk = ((uint32_t)(a.cw / 8) * chunkb) >> 4;       // next channel block
+    const uint32_t slot_u = a.box_stride >> 4;
     int slot = 0, ai = 0;
     uint32_t ph = 0;
     for (int t = first; t < a.n_tiles && !abort_flag; t += stride, ++ai) {
       const int n = t / a.tiles_per_img;
       const int s0 = (t - n * a.tiles_per_img) * 128;
       const int o = s0 - (s0 / a.p) * a.p;  // the tile's first slot within the box's first row
+      const uint32_t ao = ((uint32_t)o * (a.cw == 8 ? 16u : a.rowb)) >> 4;
       const int acc = ai & 1;
       const uint32_t aph = (uint32_t)(ai >> 1) & 1u;
       if (!tc::mbar_wait(&tempty[g][acc], aph ^ 1u)) { abort_flag = 1; break; }
@@ -438,27 +464,25 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
       for (int b = 0; b < a.cblocks; ++b) {
         if (!tc::mbar_wait(&full[g][slot], ph)) { abort_flag = 1; break; }
         tc::fence_after();
-        const uint32_t box = rb + (uint32_t)slot * a.box_stride;
+        const uint32_t sa = (uint32_t)slot * slot_u + ao, sb = (uint32_t)b * bblk;
         if (a.cw == 8) {
-          // one 8-channel block (C_in = 8): chunk c is tap c, so a K=16 MMA takes taps
-          // 2i and 2i + 1 (the second 8 K-elements LBO bytes after the first); tap 9 is
-          // the zero chunk of the pack, read against tap 8's rows
+#pragma unroll
           for (int i = 0; i < 5; ++i) {
-            const int t0 = 2 * i, t1 = t0 + 1 < 9 ? t0 + 1 : t0;
-            const int r0 = o + (t0 / 3) * a.p + (t0 % 3), r1 = o + (t1 / 3) * a.p + (t1 % 3);
-            const uint64_t ad = tc::sdesc(box + (uint32_t)r0 * 16u, (uint32_t)(r1 - r0) * 16u, 128);
-            const uint64_t bd = tc::sdesc(wb + (uint32_t)t0 * chunkb, chunkb, 128);
-            tc::mma_bf16(d, ad, bd, a.idesc, accf);
+            tc::mma_bf16(d, a0[i] + sa, b0[i], a.idesc, accf);
+            accf = 1u;
+          }
+        } else if (a.cw == 32) {
+#pragma unroll
+          for (int tap = 0; tap < 9; ++tap) {
+            tc::mma_bf16(d, a0[tap] + sa, b0[tap] + sb, a.idesc, accf);
+            tc::mma_bf16(d, a0[tap] + sa + 2u, b0[tap] + sb + bstep, a.idesc, 1u);
             accf = 1u;
           }
         } else {
+#pragma unroll
           for (int tap = 0; tap < 9; ++tap) {
-            const uint32_t arow = box + (uint32_t)(o + (tap / 3) * a.p + (tap % 3)) * a.rowb;
-            const uint32_t wrow = wb + (uint32_t)(tap * a.cpt + b * (a.cw / 8)) * chunkb;
             for (int j = 0; j < a.cw / 16; ++j) {
-              const uint64_t ad = tc::sdesc_sw(arow + (uint32_t)j * 32u, 8u * a.rowb, a.swz);
-              const uint64_t bd = tc::sdesc(wrow + (uint32_t)(2 * j) * chunkb, chunkb, 128);
-              tc::mma_bf16(d, ad, bd, a.idesc, accf);
+              tc::mma_bf16(d, a0[tap] + sa + 2u * j, b0[tap] + sb + bstep * j, a.idesc, accf);
               accf = 1u;
             }
           }
