@@ -89,6 +89,7 @@ struct ConvArgs {
   // input channels [0, c_split) come from the first tensor map, the rest from the second
   // (an upsampled tensor and its skip connection read without a concatenated copy)
   int32_t c_split;
+  int32_t wide;  // outputs 32-byte aligned: 256-bit stores
 };
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
@@ -109,10 +110,23 @@ __device__ __forceinline__ void round_bf16_16(float (&v)[16], uint4& o0, uint4& 
   o1 = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
+// 32 bytes of BF16 at yp: one 256-bit store (a whole L2 sector per thread, half the
+// store instructions and L1 wavefronts of two 16-byte stores) when yp is 32-byte aligned
+__device__ __forceinline__ void store32(uint16_t* yp, const uint4& o0, const uint4& o1, bool wide) {
+  if (wide) {
+    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(yp), "r"(o0.x), "r"(o0.y), "r"(o0.z),
+                 "r"(o0.w), "r"(o1.x), "r"(o1.y), "r"(o1.z), "r"(o1.w)
+                 : "memory");
+  } else {
+    *reinterpret_cast<uint4*>(yp) = o0;
+    *reinterpret_cast<uint4*>(yp + 8) = o1;
+  }
+}
+
 // 16 accumulator columns of one output pixel: + bias, ReLU or the ReLU-derivative mask
 // (a bf16 mask value > 0 keeps the gradient), BF16 store of 32 bytes
 __device__ __forceinline__ void epilogue16(float (&v)[16], const float* bias, int relu, const uint16_t* mp,
-                                           uint16_t* yp) {
+                                           uint16_t* yp, bool wide) {
   if (bias) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] += __ldg(bias + i);
@@ -138,8 +152,7 @@ __device__ __forceinline__ void epilogue16(float (&v)[16], const float* bias, in
   o0.z = pack_bf16x2(v[4], v[5]); o0.w = pack_bf16x2(v[6], v[7]);
   o1.x = pack_bf16x2(v[8], v[9]); o1.y = pack_bf16x2(v[10], v[11]);
   o1.z = pack_bf16x2(v[12], v[13]); o1.w = pack_bf16x2(v[14], v[15]);
-  *reinterpret_cast<uint4*>(yp) = o0;
-  *reinterpret_cast<uint4*>(yp + 8) = o1;
+  store32(yp, o0, o1, wide);
 }
 
 __global__ void __launch_bounds__(kConvThreads, 1)
@@ -293,7 +306,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = v32[hh * 16 + i];
           }
-          epilogue16(v, nullptr, a.relu, mp ? mp + c0 : nullptr, yp);
+          epilogue16(v, nullptr, a.relu, mp ? mp + c0 : nullptr, yp, a.wide != 0);
         }
       }
       tc::fence_before();
@@ -349,6 +362,7 @@ struct HaloArgs {
   int32_t head_out, store_y;
   uint32_t wbytes, box_bytes, box_stride, acc_cols, tmem_cols, idesc, swz, rowb;
   int32_t c_split;  // input channels [0, c_split) from the first map, the rest from the second
+  int32_t wide;     // outputs 32-byte aligned: 256-bit stores
 };
 
 __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
@@ -534,7 +548,7 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
           uint16_t* yp = a.y ? a.y + ((int64_t)gi * a.ygstride + (int64_t)pix * a.ygroup + (c0 - gi * a.ygroup))
                              : nullptr;
           if (!a.head) {
-            epilogue16(v, nullptr, a.relu, mp ? mp + c0 : nullptr, yp);
+            epilogue16(v, nullptr, a.relu, mp ? mp + c0 : nullptr, yp, a.wide != 0);
           } else {
             // ReLU, then the head over the values the BF16 output holds, channel by
             // channel in order (the arithmetic of the separate 1x1 head)
@@ -542,10 +556,7 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
             for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
             uint4 o0, o1;
             round_bf16_16(v, o0, o1);
-            if (a.store_y) {
-              *reinterpret_cast<uint4*>(yp) = o0;
-              *reinterpret_cast<uint4*>(yp + 8) = o1;
-            }
+            if (a.store_y) store32(yp, o0, o1, a.wide != 0);
 #pragma unroll
             for (int o = 0; o < 8; ++o) {
               if (o >= a.head_out) break;
@@ -645,6 +656,7 @@ ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const floa
   a.cin = cin; a.cout = cout; a.cpt = cin / 8;
   a.relu = relu; a.ygroup = ygroup; a.ygstride = ygstride;
   a.wpk = wpk; a.bias = bias; a.mask = mask; a.y = y;
+  a.wide = (uintptr_t)y % 32 == 0 && (ygroup == cout || (ygstride * 2) % 32 == 0);
   a.w = w; a.h = h; a.p = w + 2;
   // rows of the box: the tile starts at most p - 1 slots into its first row and needs
   // 128 + 2p + 2 slots from there
@@ -766,6 +778,7 @@ ls_status conv3x3_launch_groups(const uint16_t* x, const uint16_t* wpk, const fl
   if (P % 128 || P / 128 > (int64_t)INT32_MAX) return LS_ERR_UNSUPPORTED;
   a.n_mtiles = (int32_t)(P / 128);
   a.wpk = wpk; a.bias = bias; a.mask = mask; a.y = y; a.relu = relu;
+  a.wide = (uintptr_t)y % 32 == 0 && (ygroup == cout || (ygstride * 2) % 32 == 0);
   a.ygroup = ygroup; a.ygstride = ygroup == cout ? 0 : ygstride;
   a.cin = cin; a.cout = cout; a.cpt = cin / 8;
   a.kc_real = 9 * a.cpt;
