@@ -377,7 +377,14 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
   // load per element and pixel
   __shared__ float s_bias[kHaloMaxCout], s_head[8 * kHaloMaxCout + 8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = warp / 6, role = warp - g * 6;  // pipeline and role within it
+  // pipeline g and role (0 producer, 1 issuer, 2-5 epilogue): warps [0, np) issue the
+  // MMAs, [np, 2np) produce, the rest are the epilogues, four consecutive warps per
+  // pipeline (their warp index mod 4 selects the TMEM lane quadrant).  With np = 4 each
+  // SM sub-partition (warp index mod 4) runs one issuer, one producer and four epilogue
+  // warps; pipelines of consecutive warps put two issuers on each of two sub-partitions.
+  const int np_ = a.npipes;
+  const int g = warp < np_ ? warp : warp < 2 * np_ ? warp - np_ : (warp - 2 * np_) >> 2;
+  const int role = warp < np_ ? 1 : warp < 2 * np_ ? 0 : 2 + ((warp - 2 * np_) & 3);
   for (int i = threadIdx.x; i < a.cout; i += blockDim.x) s_bias[i] = a.bias ? a.bias[i] : 0.f;
   if (a.head)
     for (int i = threadIdx.x; i < a.head_out * (a.cout + 1); i += blockDim.x) s_head[i] = a.head[i];
