@@ -353,7 +353,10 @@ struct HaloArgs {
   int32_t cin, cout, cpt, cw, cblocks, relu, ygroup;
   int64_t ygstride;
   int32_t w, h, p, bh;          // image width, height, slots per row (w + 2), box rows
-  int32_t tiles_per_img, n_tiles, npipes, ring;
+  // a box serves tpb consecutive 128-slot tiles of an image, one per pipeline of a team
+  // of tpb pipelines (npipes / tpb teams, each with one producer and one ring)
+  int32_t tpb, teams, spi, n_super, slots_img;  // boxes per image, in all, slots per image
+  int32_t npipes, ring;
   // optional 1x1 head fused into the epilogue: head_y[pixel][o] = head[head_out * cout + o]
   // + sum_c head[o * cout + c] * out[c] over the bf16-rounded outputs (store_y: also
   // store the BF16 output itself)
@@ -363,6 +366,9 @@ struct HaloArgs {
   uint32_t wbytes, box_bytes, box_stride, acc_cols, tmem_cols, idesc, swz, rowb;
   int32_t c_split;  // input channels [0, c_split) from the first map, the rest from the second
   int32_t wide;     // outputs 32-byte aligned: 256-bit stores
+  // streamed weights (wstage > 0, wbytes = 0): each stage holds, wofs bytes after its
+  // box, the nine taps' weights of its channel block (wtap bytes per tap)
+  uint32_t wstage, wtap, wofs;
 };
 
 __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
@@ -391,11 +397,13 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
   uint8_t* wsm = smem;                          // packed weights (a.wbytes)
   uint8_t* boxes = smem + ((a.wbytes + 1023u) & ~1023u);  // 1024-aligned: the swizzle atoms
   if (threadIdx.x == 0) {
-    for (int q = 0; q < a.npipes; ++q) {
+    for (int q = 0; q < a.teams; ++q) {
       for (int i = 0; i < a.ring; ++i) {
         tc::mbar_init(&full[q][i], 1);
-        tc::mbar_init(&empty[q][i], 1);
+        tc::mbar_init(&empty[q][i], (uint32_t)a.tpb);  // released by each issuer of the team
       }
+    }
+    for (int q = 0; q < a.npipes; ++q) {
       for (int i = 0; i < 2; ++i) {
         tc::mbar_init(&tfull[q][i], 1);
         tc::mbar_init(&tempty[q][i], 128);
@@ -412,29 +420,39 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
   __syncthreads();
   tc::fence_after();
   const uint32_t taddr = tmem_base;
-  if (threadIdx.x == 0) {  // the layer's weights, once
+  if (threadIdx.x == 0 && a.wbytes) {  // the layer's weights, once (unless streamed)
     tc::mbar_arrive_expect_tx(&wbar, a.wbytes);
     tc::bulk_load(wsm, a.wpk, a.wbytes, &wbar);
   }
-  const int stride = gridDim.x * a.npipes;  // tiles are dealt out pipeline by pipeline
-  const int first = blockIdx.x * a.npipes + g;
-  uint8_t* ring = boxes + (size_t)g * a.ring * a.box_stride;
+  // boxes are dealt out team by team; pipeline g takes tile r of each box of its team
+  const int team = g / a.tpb, r = g - team * a.tpb;
+  const int stride = gridDim.x * a.teams;
+  const int first = blockIdx.x * a.teams + team;
+  uint8_t* ring = boxes + (size_t)team * a.ring * a.box_stride;
 
-  if (role == 0 && lane == 0) {
-    // ---------------- TMA producer of pipeline g
+  if (role == 0 && lane == 0 && r == 0) {
+    // ---------------- TMA producer of the team
     int slot = 0;
     uint32_t ph = 0;
-    for (int t = first; t < a.n_tiles && !abort_flag; t += stride) {
-      const int n = t / a.tiles_per_img;
-      const int y0 = (t - n * a.tiles_per_img) * 128 / a.p;  // first slot row of the tile
+    for (int st = first; st < a.n_super && !abort_flag; st += stride) {
+      const int n = st / a.spi;
+      const int y0 = (st - n * a.spi) * a.tpb * 128 / a.p;  // first slot row of the box's tiles
       for (int b = 0; b < a.cblocks; ++b) {
-        if (!tc::mbar_wait(&empty[g][slot], ph ^ 1u)) { abort_flag = 1; break; }
-        tc::mbar_arrive_expect_tx(&full[g][slot], a.box_bytes);
+        if (!tc::mbar_wait(&empty[team][slot], ph ^ 1u)) { abort_flag = 1; break; }
+        tc::mbar_arrive_expect_tx(&full[team][slot], a.box_bytes + a.wstage);
         // padded rows y0 .. y0 + bh - 1 = image rows y0 - 1 .. y0 + bh - 2, columns -1 .. w
         const int c0 = b * a.cw;
         const bool second = c0 >= a.c_split;
-        tc::tma_load_4d(ring + (size_t)slot * a.box_stride, second ? &xmap2 : &xmap, second ? c0 - a.c_split : c0,
-                        -1, y0 - 1, n, &full[g][slot]);
+        uint8_t* stage = ring + (size_t)slot * a.box_stride;
+        tc::tma_load_4d(stage, second ? &xmap2 : &xmap, second ? c0 - a.c_split : c0, -1, y0 - 1, n,
+                        &full[team][slot]);
+        if (a.wstage) {
+          // the block's packed chunks of each tap: cw / 8 consecutive chunks per tap
+          const int cpb = a.cw / 8;
+          for (int tap = 0; tap < 9; ++tap)
+            tc::bulk_load(stage + a.wofs + (size_t)tap * a.wtap,
+                          a.wpk + (size_t)(tap * a.cpt + b * cpb) * a.cout * 8, a.wtap, &full[team][slot]);
+        }
         if (++slot == a.ring) { slot = 0; ph ^= 1u; }
       }
     }
@@ -443,7 +461,7 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
     // address (16-byte units in the low bits), so the taps' descriptors are a base plus
     // offsets computed once: one thread's dependent integer work per MMA is what limits
     // the issue rate, not the tensor core.
-    if (!tc::mbar_wait(&wbar, 0)) abort_flag = 1;
+    if (a.wbytes && !tc::mbar_wait(&wbar, 0)) abort_flag = 1;
     tc::fence_after();
     const uint32_t wb = tc::saddr(wsm), rb = tc::saddr(ring);
     const uint32_t chunkb = (uint32_t)a.cout * 16u;  // one packed chunk: C_out rows x 8 K
@@ -463,7 +481,9 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
 #pragma unroll
       for (int tap = 0; tap < 9; ++tap) {
         a0[tap] = tc::sdesc_sw(rb + (uint32_t)((tap / 3) * a.p + (tap % 3)) * a.rowb, 8u * a.rowb, a.swz);
-        b0[tap] = tc::sdesc(wb + (uint32_t)(tap * a.cpt) * chunkb, chunkb, 128);
+        // resident: tap's chunks in the layer pack; streamed: in stage 0 (slot added below)
+        b0[tap] = a.wstage ? tc::sdesc(rb + a.wofs + (uint32_t)tap * a.wtap, chunkb, 128)
+                           : tc::sdesc(wb + (uint32_t)(tap * a.cpt) * chunkb, chunkb, 128);
       }
     }
     const uint32_t bstep = (2u * chunkb) >> 4;                        // next 16 K in B
@@ -471,21 +491,33 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
     const uint32_t slot_u = a.box_stride >> 4;
     int slot = 0, ai = 0;
     uint32_t ph = 0;
-    for (int t = first; t < a.n_tiles && !abort_flag; t += stride, ++ai) {
-      const int n = t / a.tiles_per_img;
-      const int s0 = (t - n * a.tiles_per_img) * 128;
-      const int o = s0 - (s0 / a.p) * a.p;  // the tile's first slot within the box's first row
+    for (int st = first; st < a.n_super && !abort_flag; st += stride) {
+      const int n = st / a.spi;
+      const int sbox = (st - n * a.spi) * a.tpb * 128;  // first slot of the box's tiles
+      const int s0 = sbox + r * 128;
+      if (s0 >= a.slots_img) {
+        // a tile past the image (the last box of an image): release its boxes unread
+        for (int b = 0; b < a.cblocks; ++b) {
+          if (!tc::mbar_wait(&full[team][slot], ph)) { abort_flag = 1; break; }
+          tc::mbar_arrive(&empty[team][slot]);
+          if (++slot == a.ring) { slot = 0; ph ^= 1u; }
+        }
+        continue;
+      }
+      const int o = s0 - (sbox / a.p) * a.p;  // the tile's first slot from the box's first row
       const uint32_t ao = ((uint32_t)o * (a.cw == 8 ? 16u : a.rowb)) >> 4;
       const int acc = ai & 1;
       const uint32_t aph = (uint32_t)(ai >> 1) & 1u;
+      ++ai;
       if (!tc::mbar_wait(&tempty[g][acc], aph ^ 1u)) { abort_flag = 1; break; }
       tc::fence_after();
       const uint32_t d = taddr + (uint32_t)(g * 2 + acc) * a.acc_cols;
       uint32_t accf = 0u;
       for (int b = 0; b < a.cblocks; ++b) {
-        if (!tc::mbar_wait(&full[g][slot], ph)) { abort_flag = 1; break; }
+        if (!tc::mbar_wait(&full[team][slot], ph)) { abort_flag = 1; break; }
         tc::fence_after();
-        const uint32_t sa = (uint32_t)slot * slot_u + ao, sb = (uint32_t)b * bblk;
+        const uint32_t sa = (uint32_t)slot * slot_u + ao;
+        const uint32_t sb = a.wstage ? (uint32_t)slot * slot_u : (uint32_t)b * bblk;
         if (a.cw == 8) {
 #pragma unroll
           for (int i = 0; i < 5; ++i) {
@@ -508,7 +540,7 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
             }
           }
         }
-        tc::mma_commit(&empty[g][slot]);
+        tc::mma_commit(&empty[team][slot]);
         if (++slot == a.ring) { slot = 0; ph ^= 1u; }
       }
       tc::mma_commit(&tfull[g][acc]);
@@ -518,13 +550,16 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
     const int q = warp & 3;
     const int m = q * 32 + lane;
     int ai = 0;
-    for (int t = first; t < a.n_tiles && !abort_flag; t += stride, ++ai) {
+    for (int st = first; st < a.n_super && !abort_flag; st += stride) {
+      const int n = st / a.spi;
+      const int s0 = ((st - n * a.spi) * a.tpb + r) * 128;
+      if (s0 >= a.slots_img) continue;  // a tile past the image: no accumulator
       const int acc = ai & 1;
       const uint32_t aph = (uint32_t)(ai >> 1) & 1u;
+      ++ai;
       if (!tc::mbar_wait(&tfull[g][acc], aph)) { abort_flag = 1; break; }
       tc::fence_after();
-      const int n = t / a.tiles_per_img;
-      const int s = (t - n * a.tiles_per_img) * 128 + m;
+      const int s = s0 + m;
       const int yy = s / a.p, xx = s - yy * a.p;
       const bool real = xx < a.w && yy < a.h;  // slots w, w + 1 of a row and rows >= h: junk
       const size_t pix = ((size_t)n * a.h + (real ? yy : 0)) * a.w + (real ? xx : 0);
@@ -665,13 +700,7 @@ ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const floa
   a.wpk = wpk; a.bias = bias; a.mask = mask; a.y = y;
   a.wide = (uintptr_t)y % 32 == 0 && (ygroup == cout || (ygstride * 2) % 32 == 0);
   a.w = w; a.h = h; a.p = w + 2;
-  // rows of the box: the tile starts at most p - 1 slots into its first row and needs
-  // 128 + 2p + 2 slots from there
-  a.bh = ((a.p - 1) + 129 + 2 * a.p) / a.p + 1;
-  a.tiles_per_img = (h * a.p + 127) / 128;  // whole tiles per image
-  const int64_t nt = (int64_t)n * a.tiles_per_img;
-  if (nt > INT32_MAX) return LS_ERR_UNSUPPORTED;
-  a.n_tiles = (int32_t)nt;
+  a.slots_img = h * a.p;
   a.wbytes = (uint32_t)chunk_count(cin) * (uint32_t)cout * 16u;
   const size_t wsz = ((size_t)a.wbytes + 1023) & ~(size_t)1023;
   a.acc_cols = 32;
@@ -680,32 +709,75 @@ ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const floa
   // issuers gain nothing: at C_out <= 64 four already saturate the shared-memory operand
   // reads of the MMAs); boxes of 32 channels (64-byte rows) where C_in allows, 16 or 8
   // otherwise (measured: 64-channel boxes and narrower ones were both slower); a ring
-  // of up to four boxes per pipeline (deeper measured no faster)
+  // of up to four boxes per team (deeper measured no faster)
   int np = kHaloMaxPipes;
   while (np > 1 && (uint32_t)np * 2u * a.acc_cols > 512u) np >>= 1;
   const int cw = (cin % 32 == 0 && a.c_split % 32 == 0) ? 32 : (cin % 16 == 0 && a.c_split % 16 == 0) ? 16 : 8;
   if (cw == 8 && (cin != 8 || x2)) return LS_ERR_UNSUPPORTED;
-  auto box_stride_of = [&](int c) {
-    return ((uint32_t)a.bh * (uint32_t)a.p * (uint32_t)(2 * c) + 1023u) & ~1023u;
+  // tiles per box T: a box holds the padded rows around T consecutive tiles (the first
+  // starts at most p - 1 slots into the box's first row and the last needs 128 + 2p + 2
+  // slots from its start), shared by a team of T pipelines
+  auto bh_of = [&](int T) { return ((a.p - 1) + 128 * T + 1 + 2 * a.p) / a.p + 1; };
+  auto stride_of = [&](int T) {
+    return ((uint32_t)bh_of(T) * (uint32_t)a.p * (uint32_t)(2 * cw) + 1023u) & ~1023u;
   };
-  auto ring_of = [&](int c, int pipes) {
-    const size_t per = (size_t)pipes * box_stride_of(c);
+  auto ring_of = [&](int T) {
+    const size_t per = (size_t)(np / T) * stride_of(T);
     return wsz >= kHaloSmemBudget ? 0 : (int)std::min<size_t>(kHaloRingUse, (kHaloSmemBudget - wsz) / per);
   };
-  // fewer than four pipelines (C_out > 64, or boxes that do not fit four rings) measured
-  // slower than the per-tap form, which runs several CTAs per SM
-  if (np < kHaloMaxPipes || ring_of(cw, np) < 2) return LS_ERR_UNSUPPORTED;
+  int tpb = 0;
+  // resident weights: one tile per box (measured: sharing boxes between pipelines
+  // saved L2 traffic but no time when the weights are resident)
+  if (ring_of(1) >= 2) tpb = 1;
+  int ring = tpb ? ring_of(tpb) : 0;
+  uint32_t stride = tpb ? stride_of(tpb) : 0;
+  // fewer than four pipelines (C_out > 64) measured slower than the per-tap form, which
+  // runs several CTAs per SM
+  if (np < kHaloMaxPipes) return LS_ERR_UNSUPPORTED;
+  if (!tpb && cw == 32) {
+    // weights too large to stay resident: each stage carries its channel block's nine
+    // tap slices beside the box, shared by the T pipelines of a team.  Candidates (pipes,
+    // tiles per box) by the fewest stage bytes per image among those with two stages;
+    // three pipelines of three tiles cover a 32 x 32 image's 1,088 slots exactly
+    a.wtap = (uint32_t)(cw / 8) * (uint32_t)cout * 16u;
+    a.wstage = 9u * a.wtap;
+    const int cand[4][2] = {{4, 4}, {3, 3}, {4, 2}, {2, 2}};
+    int64_t best = 0;
+    for (const auto& c : cand) {
+      const int P = c[0], T = c[1];
+      if ((uint32_t)P * 2u * a.acc_cols > 512u) continue;
+      const uint32_t wofs = ((uint32_t)bh_of(T) * (uint32_t)a.p * (uint32_t)(2 * cw) + 1023u) & ~1023u;
+      const uint32_t st = (wofs + a.wstage + 1023u) & ~1023u;
+      const int rg = (int)std::min<size_t>(kHaloRingUse, kHaloSmemBudget / ((size_t)(P / T) * st));
+      if (rg < 2) continue;
+      const int64_t bytes = (int64_t)((a.slots_img + 128 * T - 1) / (128 * T)) * st;
+      if (!best || bytes < best) {
+        best = bytes; np = P; tpb = T; ring = rg; stride = st; a.wofs = wofs;
+      }
+    }
+    if (!tpb) return LS_ERR_UNSUPPORTED;
+    a.wbytes = 0;
+  }
+  if (!tpb) return LS_ERR_UNSUPPORTED;
+  a.tpb = tpb;
+  a.teams = np / tpb;
+  a.spi = (a.slots_img + 128 * tpb - 1) / (128 * tpb);
+  const int64_t ns = (int64_t)n * a.spi;
+  if (ns > INT32_MAX) return LS_ERR_UNSUPPORTED;
+  a.n_super = (int32_t)ns;
+  a.bh = bh_of(tpb);
   a.cw = cw;
   a.cblocks = cin / cw;
   a.npipes = np;
-  a.ring = ring_of(cw, np);
+  a.ring = ring;
   a.rowb = (uint32_t)(2 * cw);
   a.swz = cw == 64 ? 2u : cw == 32 ? 4u : cw == 16 ? 6u : 0u;
   a.box_bytes = (uint32_t)a.bh * (uint32_t)a.p * a.rowb;
-  a.box_stride = box_stride_of(cw);
-  a.tmem_cols = (uint32_t)np * 2u * a.acc_cols;
+  a.box_stride = stride;
+  a.tmem_cols = 32;  // an allocation is a power of two (three pipelines: 384 -> 512)
+  while (a.tmem_cols < (uint32_t)np * 2u * a.acc_cols) a.tmem_cols <<= 1;
   a.idesc = tc::idesc_bf16(128, cout);
-  const size_t smem = wsz + (size_t)np * a.ring * a.box_stride;
+  const size_t smem = (a.wbytes ? wsz : 0) + (size_t)a.teams * a.ring * a.box_stride;
   CUtensorMap map, map2;
   if (!encode_input_maps(&map, &map2, x, x2, a.c_split, cin, n, h, w, a.cw, (uint32_t)a.p, (uint32_t)a.bh, 1))
     return LS_ERR_CUDA;
@@ -717,7 +789,7 @@ ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const floa
                                     (int)kHaloSmemBudget) == cudaSuccess;
       }))
     return LS_ERR_CUDA;
-  const int grid = grid_cap(((int64_t)a.n_tiles + np - 1) / np, kSmCount);
+  const int grid = grid_cap(((int64_t)a.n_super + a.teams - 1) / a.teams, kSmCount);
   k_conv3x3_halo<<<grid, np * kHaloThreadsPerPipe, smem, stream>>>(map, map2, a);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }

@@ -72,6 +72,9 @@ SHAPES = [
     (1, 128, 128, 8, 16),   # halo form, 8-channel input on 130-slot rows
     (3, 20, 32, 32, 32),    # halo form, 34-slot rows, images padded to whole tiles
     (1, 37, 64, 16, 32),    # halo form, odd height: junk rows in the last tile
+    (3, 20, 32, 160, 48),   # streamed weights: three pipelines share each 3-tile box
+    (2, 64, 64, 256, 64),   # streamed weights, four pipelines, tiles past the image skipped
+    (1, 37, 64, 192, 32),   # streamed weights, odd height
 ]
 
 
