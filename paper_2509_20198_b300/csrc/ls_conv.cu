@@ -369,7 +369,14 @@ struct HaloArgs {
   // streamed weights (wstage > 0, wbytes = 0): each stage holds, wofs bytes after its
   // box, the nine taps' weights of its channel block (wtap bytes per tap)
   uint32_t wstage, wtap, wofs;
+  // multiply-shift divisions by p and by spi (spi > 1) instead of a division routine in
+  // the per-tile index arithmetic of the three roles
+  FastDiv31 f_p, f_spi;
 };
+
+__device__ __forceinline__ int halo_img(const HaloArgs& a, int st) {
+  return a.spi > 1 ? (int)fdiv31((uint32_t)st, a.f_spi) : st;
+}
 
 __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
     k_conv3x3_halo(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap xmap2,
@@ -435,8 +442,8 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
     int slot = 0;
     uint32_t ph = 0;
     for (int st = first; st < a.n_super && !abort_flag; st += stride) {
-      const int n = st / a.spi;
-      const int y0 = (st - n * a.spi) * a.tpb * 128 / a.p;  // first slot row of the box's tiles
+      const int n = halo_img(a, st);
+      const int y0 = (int)fdiv31((uint32_t)((st - n * a.spi) * a.tpb * 128), a.f_p);  // first slot row
       for (int b = 0; b < a.cblocks; ++b) {
         if (!tc::mbar_wait(&empty[team][slot], ph ^ 1u)) { abort_flag = 1; break; }
         tc::mbar_arrive_expect_tx(&full[team][slot], a.box_bytes + a.wstage);
@@ -492,7 +499,7 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
     int slot = 0, ai = 0;
     uint32_t ph = 0;
     for (int st = first; st < a.n_super && !abort_flag; st += stride) {
-      const int n = st / a.spi;
+      const int n = halo_img(a, st);
       const int sbox = (st - n * a.spi) * a.tpb * 128;  // first slot of the box's tiles
       const int s0 = sbox + r * 128;
       if (s0 >= a.slots_img) {
@@ -504,7 +511,7 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
         }
         continue;
       }
-      const int o = s0 - (sbox / a.p) * a.p;  // the tile's first slot from the box's first row
+      const int o = s0 - (int)fdiv31((uint32_t)sbox, a.f_p) * a.p;  // first slot from the box's first row
       const uint32_t ao = ((uint32_t)o * (a.cw == 8 ? 16u : a.rowb)) >> 4;
       const int acc = ai & 1;
       const uint32_t aph = (uint32_t)(ai >> 1) & 1u;
@@ -551,7 +558,7 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
     const int m = q * 32 + lane;
     int ai = 0;
     for (int st = first; st < a.n_super && !abort_flag; st += stride) {
-      const int n = st / a.spi;
+      const int n = halo_img(a, st);
       const int s0 = ((st - n * a.spi) * a.tpb + r) * 128;
       if (s0 >= a.slots_img) continue;  // a tile past the image: no accumulator
       const int acc = ai & 1;
@@ -560,7 +567,7 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
       if (!tc::mbar_wait(&tfull[g][acc], aph)) { abort_flag = 1; break; }
       tc::fence_after();
       const int s = s0 + m;
-      const int yy = s / a.p, xx = s - yy * a.p;
+      const int yy = (int)fdiv31((uint32_t)s, a.f_p), xx = s - yy * a.p;
       const bool real = xx < a.w && yy < a.h;  // slots w, w + 1 of a row and rows >= h: junk
       const size_t pix = ((size_t)n * a.h + (real ? yy : 0)) * a.w + (real ? xx : 0);
       const uint16_t* mp = a.mask ? a.mask + pix * a.cout : nullptr;
@@ -586,7 +593,7 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = v32[hh * 16 + i];
           }
-          const int gi = c0 / a.ygroup;
+          const int gi = a.ygroup == a.cout ? 0 : c0 / a.ygroup;
           uint16_t* yp = a.y ? a.y + ((int64_t)gi * a.ygstride + (int64_t)pix * a.ygroup + (c0 - gi * a.ygroup))
                              : nullptr;
           if (!a.head) {
@@ -762,6 +769,8 @@ ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const floa
   a.tpb = tpb;
   a.teams = np / tpb;
   a.spi = (a.slots_img + 128 * tpb - 1) / (128 * tpb);
+  a.f_p = make_fastdiv31((uint32_t)a.p);
+  if (a.spi > 1) a.f_spi = make_fastdiv31((uint32_t)a.spi);
   const int64_t ns = (int64_t)n * a.spi;
   if (ns > INT32_MAX) return LS_ERR_UNSUPPORTED;
   a.n_super = (int32_t)ns;
