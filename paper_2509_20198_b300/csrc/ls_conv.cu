@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         for (int hh = 0; hh < 2; ++hh) {
           const int c0 = c32 + hh * 16;
           if (c0 >= a.cout) break;
-          const int g = c0 / a.ygroup;
+          const int g = a.ygroup == a.cout ? 0 : c0 / a.ygroup;  // no division for one group
           uint16_t* yp = a.y + ((int64_t)g * a.ygstride + (int64_t)pix * a.ygroup + (c0 - g * a.ygroup));
           float v[16];
           if (a.bias) {
@@ -738,9 +738,10 @@ ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const floa
   if (ring_of(1) >= 2) tpb = 1;
   int ring = tpb ? ring_of(tpb) : 0;
   uint32_t stride = tpb ? stride_of(tpb) : 0;
-  // fewer than four pipelines (C_out > 64) measured slower than the per-tap form, which
-  // runs several CTAs per SM
-  if (np < kHaloMaxPipes) return LS_ERR_UNSUPPORTED;
+  // two pipelines where C_out is 65-128 (measured: d1a's input gradient, 32 -> 96
+  // channels, 174 -> 143 us at 512 tiles against the per-tap form); one pipeline (C_out >
+  // 128) is left to the per-tap form, which runs several CTAs per SM
+  if (np < 2) return LS_ERR_UNSUPPORTED;
   if (!tpb && cw == 32) {
     // weights too large to stay resident: each stage carries its channel block's nine
     // tap slices beside the box, shared by the T pipelines of a team.  Candidates (pipes,

@@ -75,6 +75,8 @@ SHAPES = [
     (3, 20, 32, 160, 48),   # streamed weights: three pipelines share each 3-tile box
     (2, 64, 64, 256, 64),   # streamed weights, four pipelines, tiles past the image skipped
     (1, 37, 64, 192, 32),   # streamed weights, odd height
+    (1, 64, 64, 32, 128),   # halo form, two pipelines of 128 accumulator columns
+    (2, 32, 32, 256, 128),  # streamed weights, two pipelines sharing 2-tile boxes
 ]
 
 
