@@ -372,12 +372,18 @@ struct HaloArgs {
   // multiply-shift divisions by p and by spi (spi > 1) instead of a division routine in
   // the per-tile index arithmetic of the three roles
   FastDiv31 f_p, f_spi;
+  // up2: y is the 2x nearest-neighbour upsampling of the output ([n][2h][2w][cout]):
+  // each output pixel's values are stored at its four positions there
+  int32_t up2;
 };
 
 __device__ __forceinline__ int halo_img(const HaloArgs& a, int st) {
   return a.spi > 1 ? (int)fdiv31((uint32_t)st, a.f_spi) : st;
 }
 
+// kUp2: the epilogue stores the output as its 2x upsampling (HaloArgs::up2); a separate
+// instance, so that the plain one keeps its registers
+template <bool kUp2>
 __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
     k_conv3x3_halo(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap xmap2,
                    const HaloArgs a) {
@@ -596,7 +602,18 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
           const int gi = a.ygroup == a.cout ? 0 : c0 / a.ygroup;
           uint16_t* yp = a.y ? a.y + ((int64_t)gi * a.ygstride + (int64_t)pix * a.ygroup + (c0 - gi * a.ygroup))
                              : nullptr;
-          if (!a.head) {
+          if (kUp2) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
+            uint4 o0, o1;
+            round_bf16_16(v, o0, o1);
+            const size_t up = (((size_t)n * 2 * a.h + 2 * yy) * (2 * a.w) + 2 * xx) * a.cout + c0;
+            const size_t row = (size_t)2 * a.w * a.cout;
+            store32(a.y + up, o0, o1, a.wide != 0);
+            store32(a.y + up + a.cout, o0, o1, a.wide != 0);
+            store32(a.y + up + row, o0, o1, a.wide != 0);
+            store32(a.y + up + row + a.cout, o0, o1, a.wide != 0);
+          } else if (!a.head) {
             epilogue16(v, nullptr, a.relu, mp ? mp + c0 : nullptr, yp, a.wide != 0);
           } else {
             // ReLU, then the head over the values the BF16 output holds, channel by
@@ -697,9 +714,10 @@ ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const floa
                               int relu, int n, int h, int w, int cin, int cout, uint16_t* y, int ygroup,
                               int64_t ygstride, cudaStream_t stream, const float* head = nullptr,
                               float* head_y = nullptr, int head_out = 0, int store_y = 1,
-                              const uint16_t* x2 = nullptr, int c_split = 0) {
+                              const uint16_t* x2 = nullptr, int c_split = 0, int up2 = 0) {
   if (!(w == 32 || w == 64 || w == 128)) return LS_ERR_UNSUPPORTED;
   HaloArgs a = {};
+  a.up2 = up2;
   a.c_split = x2 ? c_split : cin;
   a.head = head; a.head_y = head_y; a.head_out = head_out; a.store_y = head ? store_y : 1;
   a.cin = cin; a.cout = cout; a.cpt = cin / 8;
@@ -795,12 +813,17 @@ ls_status conv3x3_halo_launch(const uint16_t* x, const uint16_t* wpk, const floa
   int dev = 0;
   LS_CUDA_TRY(cudaGetDevice(&dev));
   if (!device_once(once, dev, [] {
-        return cudaFuncSetAttribute(k_conv3x3_halo, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        return cudaFuncSetAttribute(k_conv3x3_halo<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kHaloSmemBudget) == cudaSuccess &&
+               cudaFuncSetAttribute(k_conv3x3_halo<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)kHaloSmemBudget) == cudaSuccess;
       }))
     return LS_ERR_CUDA;
   const int grid = grid_cap(((int64_t)a.n_super + a.teams - 1) / a.teams, kSmCount);
-  k_conv3x3_halo<<<grid, np * kHaloThreadsPerPipe, smem, stream>>>(map, map2, a);
+  if (a.up2)
+    k_conv3x3_halo<true><<<grid, np * kHaloThreadsPerPipe, smem, stream>>>(map, map2, a);
+  else
+    k_conv3x3_halo<false><<<grid, np * kHaloThreadsPerPipe, smem, stream>>>(map, map2, a);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 
@@ -818,6 +841,19 @@ ls_status conv3x3_head_launch(const uint16_t* x, const uint16_t* wpk, const floa
   if (((uintptr_t)x | (uintptr_t)wpk | (uintptr_t)y) % 16) return LS_ERR_INVALID_ARG;
   return conv3x3_halo_launch(x, wpk, bias, nullptr, 1, n, h, w, cin, cout, store_y ? y : nullptr, cout, 0, stream,
                              head, head_y, head_out, store_y);
+}
+
+// Convolution + bias + ReLU whose output is stored only as its 2x nearest-neighbour
+// upsampling y_up ([n][2h][2w][cout]), for a decoder convolution whose output feeds
+// the next level's upsampling alone.  LS_ERR_UNSUPPORTED when the shape has no halo
+// form (the caller stores the output and upsamples it).
+ls_status conv3x3_up2_launch(const uint16_t* x, const uint16_t* wpk, const float* bias, int n, int h, int w, int cin,
+                             int cout, uint16_t* y_up, cudaStream_t stream) {
+  if (!x || !wpk || !y_up || n <= 0 || h <= 0 || w <= 0) return LS_ERR_INVALID_ARG;
+  if (cin < 8 || cin % 8 || cin > 256 || cout < 16 || cout > 256 || cout % 16) return LS_ERR_UNSUPPORTED;
+  if (((uintptr_t)x | (uintptr_t)wpk | (uintptr_t)y_up) % 16) return LS_ERR_INVALID_ARG;
+  return conv3x3_halo_launch(x, wpk, bias, nullptr, 1, n, h, w, cin, cout, y_up, cout, 0, stream, nullptr, nullptr,
+                             0, 1, nullptr, 0, 1);
 }
 
 // Shared with the model code: validated launch of one convolution whose output

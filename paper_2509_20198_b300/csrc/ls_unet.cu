@@ -23,6 +23,8 @@ ls_status conv3x3_launch(const uint16_t* x, const uint16_t* wpk, const float* bi
                          int n, int h, int w, int cin, int cout, uint16_t* y, cudaStream_t stream);
 ls_status wgrad_launch(const uint16_t* x, const uint16_t* dz, int n, int h, int w, int cin, int cout, float* dwt,
                        float* db, cudaStream_t stream);
+ls_status conv3x3_up2_launch(const uint16_t* x, const uint16_t* wpk, const float* bias, int n, int h, int w, int cin,
+                             int cout, uint16_t* y_up, cudaStream_t stream);
 ls_status conv3x3_head_launch(const uint16_t* x, const uint16_t* wpk, const float* bias, int n, int h, int w, int cin,
                               int cout, uint16_t* y, const float* head, float* head_y, int head_out, int store_y,
                               cudaStream_t stream);
@@ -670,6 +672,7 @@ ls_status filler_forward(ls_model* m, const float* params, const uint16_t* x, in
   int li = 0;
   const uint16_t* h_in = x;
   ls_status st;
+  bool up_ready = false;  // the next decoder level's upsampled input is already stored
   for (int l = 1; l <= L; ++l) {
     const int h = R >> (l - 1);
     if (l > 1) {
@@ -691,10 +694,13 @@ ls_status filler_forward(ls_model* m, const float* params, const uint16_t* x, in
                                                                        m->act[slot_c(l)]);
       if ((st = conv(li++, m->act[slot_c(l)], h, m->act[slot_da(l)])) != LS_OK) return st;
     } else {
-      // inference: only the upsampled channels are written; the convolution reads the
-      // skip connection's channels from the encoder output directly
-      k_upcat<<<grid_cap((int64_t)n * h, kSmCount * 16), 256, 0, s>>>(h_in, cu, nullptr, 0, n, h, h,
-                                                                       m->act[slot_c(l)]);
+      // inference: only the upsampled channels are written (unless the level below
+      // already stored its output upsampled); the convolution reads the skip
+      // connection's channels from the encoder output directly
+      if (!up_ready)
+        k_upcat<<<grid_cap((int64_t)n * h, kSmCount * 16), 256, 0, s>>>(h_in, cu, nullptr, 0, n, h, h,
+                                                                         m->act[slot_c(l)]);
+      up_ready = false;
       const LayerDesc& d = m->layers[li++];
       if ((st = conv3x3_launch_groups(m->act[slot_c(l)], d.wpk, params + d.b_off, nullptr, 1, n, h, h, d.cin_pad,
                                       d.cout, m->act[slot_da(l)], d.cout, 0, s, m->act[slot_eb(l)], cu)) != LS_OK)
@@ -710,6 +716,21 @@ ls_status filler_forward(ls_model* m, const float* params, const uint16_t* x, in
         m->x = keep_top ? x : nullptr;
         m->last_n = keep_top ? n : 0;
         return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
+      }
+      if (st != LS_ERR_UNSUPPORTED) return st;
+    }
+    if (!keep_top && l >= 2) {
+      // inference: this output feeds only the next level's upsampling, so the
+      // convolution stores it upsampled, where that level reads it
+      const LayerDesc& d = m->layers[li];
+      const int cu_next = m->widths[l - 1];
+      st = d.cout == cu_next ? conv3x3_up2_launch(m->act[slot_da(l)], d.wpk, params + d.b_off, n, h, h, d.cin_pad,
+                                                  d.cout, m->act[slot_c(l - 1)], s)
+                             : LS_ERR_UNSUPPORTED;
+      if (st == LS_OK) {
+        ++li;
+        up_ready = true;
+        continue;
       }
       if (st != LS_ERR_UNSUPPORTED) return st;
     }
