@@ -90,6 +90,8 @@ struct ConvArgs {
   // (an upsampled tensor and its skip connection read without a concatenated copy)
   int32_t c_split;
   int32_t wide;  // outputs 32-byte aligned: 256-bit stores
+  // up2: y is the 2x nearest-neighbour upsampling of the output ([n][2h][2w][cout])
+  int32_t up2, img_h, img_w;
 };
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
@@ -155,6 +157,9 @@ __device__ __forceinline__ void epilogue16(float (&v)[16], const float* bias, in
   store32(yp, o0, o1, wide);
 }
 
+// kUp2: the epilogue stores the output as its 2x upsampling (ConvArgs::up2), a
+// separate instance
+template <bool kUp2>
 __global__ void __launch_bounds__(kConvThreads, 1)
     k_conv3x3(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap xmap2,
               const ConvArgs a) {
@@ -306,7 +311,24 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = v32[hh * 16 + i];
           }
-          epilogue16(v, nullptr, a.relu, mp ? mp + c0 : nullptr, yp, a.wide != 0);
+          if (kUp2) {
+            // output pixel (nn, yy, xx) at its four positions of the 2x upsampling
+            const size_t hw = (size_t)a.img_h * a.img_w;
+            const size_t nn = pix / hw, r = pix - nn * hw;
+            const int yy = (int)(r / (size_t)a.img_w), xx = (int)(r - (size_t)yy * a.img_w);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
+            uint4 o0, o1;
+            round_bf16_16(v, o0, o1);
+            uint16_t* up = a.y + (((nn * 2 * a.img_h + 2 * yy) * (2 * a.img_w) + 2 * xx) * a.cout + c0);
+            const size_t row = (size_t)2 * a.img_w * a.cout;
+            store32(up, o0, o1, a.wide != 0);
+            store32(up + a.cout, o0, o1, a.wide != 0);
+            store32(up + row, o0, o1, a.wide != 0);
+            store32(up + row + a.cout, o0, o1, a.wide != 0);
+          } else {
+            epilogue16(v, nullptr, a.relu, mp ? mp + c0 : nullptr, yp, a.wide != 0);
+          }
         }
       }
       tc::fence_before();
@@ -843,19 +865,6 @@ ls_status conv3x3_head_launch(const uint16_t* x, const uint16_t* wpk, const floa
                              head, head_y, head_out, store_y);
 }
 
-// Convolution + bias + ReLU whose output is stored only as its 2x nearest-neighbour
-// upsampling y_up ([n][2h][2w][cout]), for a decoder convolution whose output feeds
-// the next level's upsampling alone.  LS_ERR_UNSUPPORTED when the shape has no halo
-// form (the caller stores the output and upsamples it).
-ls_status conv3x3_up2_launch(const uint16_t* x, const uint16_t* wpk, const float* bias, int n, int h, int w, int cin,
-                             int cout, uint16_t* y_up, cudaStream_t stream) {
-  if (!x || !wpk || !y_up || n <= 0 || h <= 0 || w <= 0) return LS_ERR_INVALID_ARG;
-  if (cin < 8 || cin % 8 || cin > 256 || cout < 16 || cout > 256 || cout % 16) return LS_ERR_UNSUPPORTED;
-  if (((uintptr_t)x | (uintptr_t)wpk | (uintptr_t)y_up) % 16) return LS_ERR_INVALID_ARG;
-  return conv3x3_halo_launch(x, wpk, bias, nullptr, 1, n, h, w, cin, cout, y_up, cout, 0, stream, nullptr, nullptr,
-                             0, 1, nullptr, 0, 1);
-}
-
 // Shared with the model code: validated launch of one convolution whose output
 // channels go to cout / ygroup tensors of ygroup channels each, ygstride elements apart
 // (ygroup = cout: one NHWC tensor).  Without a mask only (a mask is one NHWC tensor).
@@ -864,7 +873,7 @@ ls_status conv3x3_up2_launch(const uint16_t* x, const uint16_t* wpk, const float
 ls_status conv3x3_launch_groups(const uint16_t* x, const uint16_t* wpk, const float* bias, const uint16_t* mask,
                                 int relu, int n, int h, int w, int cin, int cout, uint16_t* y, int ygroup,
                                 int64_t ygstride, cudaStream_t stream, const uint16_t* x2 = nullptr,
-                                int c_split = 0) {
+                                int c_split = 0, int up2 = 0) {
   if (!x || !wpk || !y || n <= 0 || h <= 0 || w <= 0) return LS_ERR_INVALID_ARG;
   if (x2 && (c_split <= 0 || c_split >= cin || c_split % 8 || (uintptr_t)x2 % 16)) return LS_ERR_INVALID_ARG;
   if (cin < 8 || cin % 8 || cin > 256 || cout < 16 || cout > 256 || cout % 16) return LS_ERR_UNSUPPORTED;
@@ -876,7 +885,7 @@ ls_status conv3x3_launch_groups(const uint16_t* x, const uint16_t* wpk, const fl
   {
     const ls_status hs = conv3x3_halo_launch(x, wpk, bias, mask, relu, n, h, w, cin, cout, y, ygroup,
                                              ygroup == cout ? 0 : ygstride, stream, nullptr, nullptr, 0, 1, x2,
-                                             c_split);
+                                             c_split, up2);
     if (hs != LS_ERR_UNSUPPORTED) return hs;  // else the shape is not one for the halo form
   }
   ConvArgs a = {};
@@ -903,6 +912,7 @@ ls_status conv3x3_launch_groups(const uint16_t* x, const uint16_t* wpk, const fl
   if (P % 128 || P / 128 > (int64_t)INT32_MAX) return LS_ERR_UNSUPPORTED;
   a.n_mtiles = (int32_t)(P / 128);
   a.wpk = wpk; a.bias = bias; a.mask = mask; a.y = y; a.relu = relu;
+  a.up2 = up2; a.img_h = h; a.img_w = w;
   a.wide = (uintptr_t)y % 32 == 0 && (ygroup == cout || (ygstride * 2) % 32 == 0);
   a.ygroup = ygroup; a.ygstride = ygroup == cout ? 0 : ygstride;
   a.cin = cin; a.cout = cout; a.cpt = cin / 8;
@@ -938,13 +948,30 @@ ls_status conv3x3_launch_groups(const uint16_t* x, const uint16_t* wpk, const fl
   int dev = 0;
   LS_CUDA_TRY(cudaGetDevice(&dev));
   if (!device_once(once, dev, [] {
-        return cudaFuncSetAttribute(k_conv3x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        return cudaFuncSetAttribute(k_conv3x3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kConvSmemBudget) == cudaSuccess &&
+               cudaFuncSetAttribute(k_conv3x3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)kConvSmemBudget) == cudaSuccess;
       }))
     return LS_ERR_CUDA;
   const int per_sm = a.tmem_cols <= 128 ? 3 : a.tmem_cols <= 256 ? 2 : 1;
-  k_conv3x3<<<grid_cap(a.n_mtiles, (int64_t)kSmCount * per_sm), kConvThreads, smem, stream>>>(map, map2, a);
+  if (a.up2)
+    k_conv3x3<true><<<grid_cap(a.n_mtiles, (int64_t)kSmCount * per_sm), kConvThreads, smem, stream>>>(map, map2, a);
+  else
+    k_conv3x3<false><<<grid_cap(a.n_mtiles, (int64_t)kSmCount * per_sm), kConvThreads, smem, stream>>>(map, map2, a);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
+}
+
+// Convolution + bias + ReLU whose output is stored only as its 2x nearest-neighbour
+// upsampling y_up ([n][2h][2w][cout]), for a convolution whose output feeds the next
+// decoder level's upsampling alone.  LS_ERR_UNSUPPORTED when the shape has neither form
+// (the caller stores the output and upsamples it).
+ls_status conv3x3_up2_launch(const uint16_t* x, const uint16_t* wpk, const float* bias, int n, int h, int w, int cin,
+                             int cout, uint16_t* y_up, cudaStream_t stream) {
+  if (!x || !wpk || !y_up || n <= 0 || h <= 0 || w <= 0) return LS_ERR_INVALID_ARG;
+  if (cin < 8 || cin % 8 || cin > 256 || cout < 16 || cout > 256 || cout % 16) return LS_ERR_UNSUPPORTED;
+  if (((uintptr_t)x | (uintptr_t)wpk | (uintptr_t)y_up) % 16) return LS_ERR_INVALID_ARG;
+  return conv3x3_launch_groups(x, wpk, bias, nullptr, 1, n, h, w, cin, cout, y_up, cout, 0, stream, nullptr, 0, 1);
 }
 
 ls_status conv3x3_launch(const uint16_t* x, const uint16_t* wpk, const float* bias, const uint16_t* mask, int relu,

@@ -682,6 +682,21 @@ ls_status filler_forward(ls_model* m, const float* params, const uint16_t* x, in
       h_in = m->act[slot_p(l - 1)];
     }
     if ((st = conv(li++, h_in, h, m->act[slot_ea(l)])) != LS_OK) return st;
+    if (!keep_top && l == L && L > 1) {
+      // inference: the bottleneck's output feeds only the first decoder level's
+      // upsampling, so it is stored upsampled there
+      const LayerDesc& d = m->layers[li];
+      st = d.cout == m->widths[L - 1]
+               ? conv3x3_up2_launch(m->act[slot_ea(l)], d.wpk, params + d.b_off, n, h, h, d.cin_pad, d.cout,
+                                    m->act[slot_c(L - 1)], s)
+               : LS_ERR_UNSUPPORTED;
+      if (st == LS_OK) {
+        ++li;
+        up_ready = true;
+        continue;
+      }
+      if (st != LS_ERR_UNSUPPORTED) return st;
+    }
     if ((st = conv(li++, m->act[slot_ea(l)], h, m->act[slot_eb(l)])) != LS_OK) return st;
     h_in = m->act[slot_eb(l)];
   }
