@@ -675,34 +675,73 @@ __global__ void __launch_bounds__(kHaloMaxPipes * kHaloThreadsPerPipe, 1)
 
 
 // elements of one tap) is a block of C_out rows x 16 bytes, 8-row groups of 128 bytes.
+__device__ __forceinline__ uint16_t pack_elem(const float* __restrict__ w, int cin, int cout, int tflip, int64_t e) {
+  const int cpt = cin / 8;
+  const int c = (int)(e / (cout * 8));
+  const int r = (int)(e - (int64_t)c * cout * 8);
+  const int o = (r >> 6) * 8 + ((r & 63) >> 3);
+  const int ee = r & 7;
+  float v = 0.f;
+  if (c < 9 * cpt) {
+    const int tap = c / cpt, ci = (c - tap * cpt) * 8 + ee;
+    const int ky = tap / 3, kx = tap - ky * 3;
+    if (!tflip) {
+      v = w[(((int64_t)o * 3 + ky) * 3 + kx) * cin + ci];
+    } else {
+      // input-gradient conv: W'[o][ky][kx][ci] = W[ci][2-ky][2-kx][o], W is [cin][3][3][cout]
+      v = w[(((int64_t)ci * 3 + (2 - ky)) * 3 + (2 - kx)) * cout + o];
+    }
+  }
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  return *reinterpret_cast<const uint16_t*>(&h);
+}
+
 __global__ void k_pack_weights(const float* __restrict__ w, int cin, int cout, int tflip, int kc,
                                uint16_t* __restrict__ out) {
   const int64_t total = (int64_t)kc * cout * 8;
-  const int cpt = cin / 8;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = pack_elem(w, cin, cout, tflip, e);
+}
+
+// Several packs in one launch (a model's layers, each step of a training): job j covers
+// elements [begin[j], begin[j + 1]) of the concatenated outputs
+struct PackBatch {
+  PackJob job[kMaxPackJobs];
+  int64_t begin[kMaxPackJobs + 1];
+  int32_t n;
+};
+__global__ void k_pack_batch(const __grid_constant__ PackBatch b) {
+  const int64_t total = b.begin[b.n];
+  int j = 0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / (cout * 8));
-    const int r = (int)(e - (int64_t)c * cout * 8);
-    const int o = (r >> 6) * 8 + ((r & 63) >> 3);
-    const int ee = r & 7;
-    float v = 0.f;
-    if (c < 9 * cpt) {
-      const int tap = c / cpt, ci = (c - tap * cpt) * 8 + ee;
-      const int ky = tap / 3, kx = tap - ky * 3;
-      if (!tflip) {
-        v = w[(((int64_t)o * 3 + ky) * 3 + kx) * cin + ci];
-      } else {
-        // input-gradient conv: W'[o][ky][kx][ci] = W[ci][2-ky][2-kx][o], W is [cin][3][3][cout]
-        v = w[(((int64_t)ci * 3 + (2 - ky)) * 3 + (2 - kx)) * cout + o];
-      }
-    }
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    out[e] = *reinterpret_cast<const uint16_t*>(&h);
+    while (e >= b.begin[j + 1]) ++j;  // e only grows in a thread's loop
+    const PackJob& J = b.job[j];
+    const int64_t le = e - b.begin[j];
+    J.out[le] = pack_elem(J.w, J.cin, J.cout, J.tflip, le);
   }
 }
 
 int chunk_count(int cin) {
   const int kc = 9 * (cin / 8);
   return kc + (kc & 1);
+}
+
+// All packs of `jobs` with as few launches as the job table allows (kMaxPackJobs each)
+ls_status conv3x3_pack_batch(const PackJob* jobs, int n, cudaStream_t stream) {
+  for (int j0 = 0; j0 < n; j0 += kMaxPackJobs) {
+    PackBatch b = {};
+    b.n = std::min(kMaxPackJobs, n - j0);
+    b.begin[0] = 0;
+    for (int j = 0; j < b.n; ++j) {
+      const PackJob& J = jobs[j0 + j];
+      if (!J.w || !J.out || J.cin < 8 || J.cin % 8 || J.cout < 16 || J.cout % 16) return LS_ERR_INVALID_ARG;
+      b.job[j] = J;
+      b.begin[j + 1] = b.begin[j] + (int64_t)chunk_count(J.cin) * J.cout * 8;
+    }
+    k_pack_batch<<<grid_cap((b.begin[b.n] + 255) / 256, kSmCount * 8), 256, 0, stream>>>(b);
+    LS_CUDA_TRY(cudaGetLastError());
+  }
+  return LS_OK;
 }
 
 }  // namespace

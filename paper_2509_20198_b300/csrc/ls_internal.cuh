@@ -89,6 +89,15 @@ enum WorkspaceSlot {
   kWsGemmPart = 7,
   kWsSlots = 8
 };
+// One conv weight pack (ls_conv3x3_pack's arguments): w [cout][3][3][cin] FP32 (or the
+// transposed, flipped form when tflip), out the packed BF16 operand chunks
+struct PackJob {
+  const float* w;
+  uint16_t* out;
+  int32_t cin, cout, tflip;
+};
+constexpr int kMaxPackJobs = 32;  // packs per launch of the batched pack
+
 // Returns a device pointer of at least `bytes` for the given slot (nullptr on failure).
 void* workspace(WorkspaceSlot slot, size_t bytes);
 // Forgets the cached device address of the fixed binning scratch of a device, so that

@@ -636,6 +636,9 @@ extern "C" ls_status ls_model_layer_info(const ls_model* m, int32_t i, int32_t* 
 extern "C" ls_status ls_model_load(ls_model* m, const float* params, ls_stream_t stream) {
   if (!m || !params) return LS_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // every layer's packs (and the transposed packs of the input gradients) in one launch,
+  // after the first layer's input channels are padded
+  std::vector<PackJob> jobs;
   for (auto& d : m->layers) {
     if (d.k == 1) {
       LS_CUDA_TRY(cudaMemcpyAsync(m->head, params + d.w_off, (size_t)(d.cout * d.cin + d.cout) * 4,
@@ -648,13 +651,11 @@ extern "C" ls_status ls_model_load(ls_model* m, const float* params, ls_stream_t
       k_pad_in<<<grid_for(total, 256), 256, 0, s>>>(w, d.cout, d.cin, d.cin_pad, m->w0pad);
       w = m->w0pad;
     }
-    ls_status st = ls_conv3x3_pack(w, d.cin_pad, d.cout, 0, d.wpk, stream);
-    if (st != LS_OK) return st;
-    if (d.wpk_t) {
-      st = ls_conv3x3_pack(params + d.w_off, d.cout, d.cin, 1, d.wpk_t, stream);
-      if (st != LS_OK) return st;
-    }
+    jobs.push_back({w, d.wpk, d.cin_pad, d.cout, 0});
+    if (d.wpk_t) jobs.push_back({params + d.w_off, d.wpk_t, d.cout, d.cin, 1});
   }
+  const ls_status st = conv3x3_pack_batch(jobs.data(), (int)jobs.size(), s);
+  if (st != LS_OK) return st;
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
 
