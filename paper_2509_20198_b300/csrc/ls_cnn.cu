@@ -500,6 +500,7 @@ extern "C" ls_status ls_cnn_layer_info(const ls_cnn* m, int32_t i, int32_t* kind
 extern "C" ls_status ls_cnn_load(ls_cnn* m, const float* params, ls_stream_t stream) {
   if (!m || !params) return LS_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<PackJob> jobs;
   for (size_t li = 0; li < m->layers.size(); ++li) {
     const CnnLayer& d = m->layers[li];
     if (d.kind != kCnnConv) continue;
@@ -513,20 +514,25 @@ extern "C" ls_status ls_cnn_load(ls_cnn* m, const float* params, ls_stream_t str
                                   cudaMemcpyDeviceToDevice, s));
       continue;
     }
-    if (d.cin != d.cin_pad) {
+    // a padded layer packs at once (the padding scratch is reused by the next one); the
+    // others join one batched pack launch at the end
+    const bool padded = d.cin != d.cin_pad;
+    if (padded) {
       k_cnn_pad_w<<<cnn_grid((int64_t)d.cout * 9 * d.cin_pad), 256, 0, s>>>(w, d.cout, d.cin, d.cin_pad, d.c0,
                                                                           m->wpad);
       w = m->wpad;
     }
-    ls_status st = ls_conv3x3_pack(w, d.cin_pad, d.cout, 0, d.wpk, stream);
-    if (st != LS_OK) return st;
-    if (d.wpk_t) {
-      // input-gradient operand: cin_pad x cout weights, flipped and transposed
-      st = ls_conv3x3_pack(w, d.cout, d.cin_pad, 1, d.wpk_t, stream);
+    PackJob pj[2] = {{w, d.wpk, d.cin_pad, d.cout, 0}, {w, d.wpk_t, d.cout, d.cin_pad, 1}};
+    const int np = d.wpk_t ? 2 : 1;  // the input-gradient operand: flipped and transposed
+    if (padded) {
+      const ls_status st = conv3x3_pack_batch(pj, np, s);
       if (st != LS_OK) return st;
+    } else {
+      for (int j = 0; j < np; ++j) jobs.push_back(pj[j]);
     }
   }
-  const ls_status st = ls_conv3x3_pack(m->wpad_e0, kCnnIn, kCnnE0Fused, 0, m->wpk_e0, stream);
+  jobs.push_back({m->wpad_e0, m->wpk_e0, kCnnIn, kCnnE0Fused, 0});
+  const ls_status st = conv3x3_pack_batch(jobs.data(), (int)jobs.size(), s);
   if (st != LS_OK) return st;
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }
