@@ -87,7 +87,8 @@ enum WorkspaceSlot {
   kWsInterpRecs = 5,
   kWsInterpQueue = 6,
   kWsGemmPart = 7,
-  kWsSlots = 8
+  kWsLossPart = 8,  // per-block partial loss sums
+  kWsSlots = 9
 };
 // One conv weight pack (ls_conv3x3_pack's arguments): w [cout][3][3][cin] FP32 (or the
 // transposed, flipped form when tflip), out the packed BF16 operand chunks

@@ -366,7 +366,8 @@ __device__ __forceinline__ float bound_target(float eh, float base_h, float t_h,
 
 __global__ void k_loss_sums(const float* __restrict__ y, const float* __restrict__ base,
                             const float* __restrict__ target, const uint8_t* __restrict__ mask, int64_t P,
-                            int excess, double* __restrict__ sums /* [4]: count, sh, sc, sb */) {
+                            int excess, double* __restrict__ part /* [gridDim.x][4]: count, sh, sc, sb */) {
+  __shared__ double ws[8][4];  // per warp (256 threads)
   double s[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
     if (!mask[p]) continue;
@@ -380,10 +381,29 @@ __global__ void k_loss_sums(const float* __restrict__ y, const float* __restrict
     const float db = y[p * kOut + 4] - bound_target(eh, base[p * 4], target[p * 4], excess);
     s[3] += db * db;
   }
+  // fixed-order sums: warp tree, then the block's warps in order; the blocks' partials are
+  // added in order by k_loss_reduce (no contended atomics, the same sums every run)
+  const int warp = threadIdx.x >> 5;
   for (int k = 0; k < 4; ++k) {
     double v = s[k];
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&sums[k], v);
+    if ((threadIdx.x & 31) == 0) ws[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += ws[w][threadIdx.x];
+    part[(size_t)blockIdx.x * 4 + threadIdx.x] = v;
+  }
+}
+
+// One warp: sums[k] = the blocks' partials k in a fixed order (lane-strided, then a tree)
+__global__ void k_loss_reduce(const double* __restrict__ part, int nb, double* __restrict__ sums) {
+  for (int k = 0; k < 4; ++k) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 32) v += part[(size_t)b * 4 + k];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (threadIdx.x == 0) sums[k] = v;
   }
 }
 
@@ -896,9 +916,11 @@ extern "C" ls_status ls_filler_loss(const float* y, const float* base, const flo
   if (!y || !base || !target || !mask || !sums || !dy || n_px <= 0) return LS_ERR_INVALID_ARG;
   if (bound_excess != 0 && bound_excess != 1) return LS_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  LS_CUDA_TRY(cudaMemsetAsync(sums, 0, 4 * sizeof(double), s));
-  k_loss_sums<<<grid_cap((n_px + 255) / 256, kSmCount * 8), 256, 0, s>>>(y, base, target, mask, n_px, bound_excess,
-                                                                         sums);
+  const int nb = grid_cap((n_px + 255) / 256, kSmCount * 8);
+  double* part = static_cast<double*>(workspace(kWsLossPart, (size_t)nb * 4 * sizeof(double)));
+  if (!part) return LS_ERR_NO_MEMORY;
+  k_loss_sums<<<nb, 256, 0, s>>>(y, base, target, mask, n_px, bound_excess, part);
+  k_loss_reduce<<<1, 32, 0, s>>>(part, nb, sums);
   k_loss_grad<<<grid_cap((n_px + 255) / 256, kSmCount * 8), 256, 0, s>>>(y, base, target, mask, n_px, sums,
                                                                          bound_weight, bound_excess, dy, loss);
   return cudaGetLastError() == cudaSuccess ? LS_OK : LS_ERR_CUDA;
